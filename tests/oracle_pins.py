@@ -1,0 +1,543 @@
+"""Pins of the EM-PP oracle to facts that do not come from the oracle itself.
+
+Every pin is a function ``pin_*(lib)`` taking a loaded oracle library, so that the same checks run
+against the real oracle (test_oracle_pins.py) and against deliberately broken copies of it
+(test_oracle_mutants.py), which must each fail at least one pin.
+
+Sources of truth: textbook closed forms (Coulomb, Heaviside's field of a uniformly moving charge,
+the uniform-motion retarded delay, centred-dipole values, cyclotron rotation, relativistic E x B
+drift), the Lienard-Wiechert potentials differentiated numerically in high precision, brute-force
+scans of the bracket, exact symmetries, and conservation laws.
+"""
+from __future__ import annotations
+
+import math
+
+import mpmath as mp
+import numpy as np
+
+import oracle
+
+C = 299792458.0
+QE = 1.602176634e-19
+ME = 9.1093837015e-31
+EPS0 = 8.8541878128e-12
+MU0 = 1.25663706212e-6
+K_C = 1.0 / (4.0 * math.pi * EPS0)
+
+
+def _two_body_history(r_target, w_of_t, v_of_t, n, dt):
+    """Slots 0..n for particle 0 resting at r_target and source 1 on the trajectory w_of_t."""
+    T = np.array([k * dt for k in range(n + 1)])
+    W = np.zeros((n + 1, 2, 3))
+    V = np.zeros((n + 1, 2, 3))
+    W[:, 0, :] = r_target
+    for k in range(n + 1):
+        W[k, 1] = w_of_t(T[k])
+        V[k, 1] = v_of_t(T[k])
+    return T, W, V
+
+
+def _field_on_target(lib, T, W, V, n, D):
+    E, B, st = oracle.self_fields(T, W, V, n, D, targets=[0], lib=lib)
+    return E[0], B[0], st
+
+
+def _branch(lib, T, W, V, n, D, r):
+    return oracle.retarded(T, W, V, n, D, 1, r, lib=lib)["branch"]
+
+
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.1, eq:LW_E / eq:LW_B: static source -> Coulomb field, B = 0 (every branch)
+# ---------------------------------------------------------------------------------------------
+def pin_coulomb_static(lib):
+    dt, n, D = 1e-15, 10, 64
+    rng = np.random.default_rng(1)
+    w0 = np.array([1e-6, -2e-6, 0.5e-6])
+    seen = set()
+    for dist in (0.1e-6, 1.0e-6, 2.5e-6, 10e-6):
+        d = rng.normal(size=3)
+        d *= dist / np.linalg.norm(d)
+        r = w0 + d
+        T, W, V = _two_body_history(r, lambda t: w0, lambda t: np.zeros(3), n, dt)
+        E, B, _ = _field_on_target(lib, T, W, V, n, D)
+        seen.add(_branch(lib, T, W, V, n, D, r))
+        Eref = -QE * K_C * d / dist ** 3
+        assert np.max(np.abs(E - Eref)) <= 1e-13 * np.linalg.norm(Eref), (E, Eref)
+        assert np.max(np.abs(B)) <= 1e-13 * np.linalg.norm(Eref) / C
+    assert seen == {0, 1, 2}, seen
+
+
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.1-2.2: uniformly moving source with exactly sampled history -> Heaviside field about the
+# present position, B = v x E / c^2 (every branch; the reconstruction is exact for this motion)
+# ---------------------------------------------------------------------------------------------
+def _heaviside(q, beta_vec, R):
+    b2 = float(beta_vec @ beta_vec)
+    Rn = np.linalg.norm(R)
+    cospsi = float(R @ beta_vec) / (Rn * math.sqrt(b2)) if b2 > 0 else 0.0
+    sin2 = 1.0 - cospsi * cospsi
+    E = q * K_C * (1.0 - b2) / (1.0 - b2 * sin2) ** 1.5 * R / Rn ** 3
+    B = np.cross(beta_vec * C, E) / C ** 2
+    return E, B
+
+
+def pin_heaviside_uniform_motion(lib):
+    dt, n, D = 1e-15, 24, 64
+    rng = np.random.default_rng(2)
+    seen = set()
+    for beta in (0.3, 0.9, 0.99):
+        for trial in range(8):
+            bdir = rng.normal(size=3)
+            bdir /= np.linalg.norm(bdir)
+            v = beta * C * bdir
+            w_now = rng.normal(size=3) * 1e-6
+            tn = n * dt
+            d = rng.normal(size=3)
+            d *= rng.uniform(0.05e-6, 8e-6) / np.linalg.norm(d)
+            r = w_now + d
+            T, W, V = _two_body_history(r, lambda t: w_now + v * (t - tn), lambda t: v, n, dt)
+            T[n] = tn
+            E, B, _ = _field_on_target(lib, T, W, V, n, D)
+            seen.add(_branch(lib, T, W, V, n, D, r))
+            Eref, Bref = _heaviside(-QE, v / C, r - W[n, 1])
+            scale = np.linalg.norm(Eref)
+            assert np.max(np.abs(E - Eref)) <= 1e-12 * scale, (beta, E, Eref)
+            assert np.max(np.abs(B - Bref)) <= 1e-12 * scale / C, (beta, B, Bref)
+    assert seen == {0, 1, 2}, seen
+
+
+# ---------------------------------------------------------------------------------------------
+# eq:linear2 at n = 0: the retarded delay of uniform motion from the only stored slot,
+# t - t_r = [d.v + sqrt((d.v)^2 + (c^2 - v^2) d^2)] / (c^2 - v^2)
+# ---------------------------------------------------------------------------------------------
+def pin_out_of_history_delay(lib):
+    mp.mp.dps = 40
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        beta = rng.uniform(0.0, 0.995)
+        v = rng.normal(size=3)
+        v *= beta * C / np.linalg.norm(v)
+        w0 = rng.normal(size=3) * 1e-5
+        d = rng.normal(size=3) * 1e-5
+        r = w0 + d
+        T = np.array([3e-15])
+        W = np.stack([r, w0])[None]
+        V = np.stack([np.zeros(3), v])[None]
+        res = oracle.retarded(T, W, V, 0, 16, 1, r, lib=lib)
+        assert res["branch"] == 0
+        dv = mp.fsum(mp.mpf(float(a)) * mp.mpf(float(b)) for a, b in zip(d, v))
+        dd = mp.fsum(mp.mpf(float(a)) ** 2 for a in d)
+        vv = mp.fsum(mp.mpf(float(a)) ** 2 for a in v)
+        c = mp.mpf(C)
+        tau = (dv + mp.sqrt(dv * dv + (c * c - vv) * dd)) / (c * c - vv)
+        got = T[0] - res["tr"]
+        assert abs(got - float(tau)) <= 1e-13 * float(tau), (got, tau)
+        # the reconstructed retarded position sits on the past light cone of (r, t)
+        assert abs(np.linalg.norm(r - res["w"]) - C * got) <= 1e-13 * C * got
+
+
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.2 bracket: brute-force scan of the node test in exact (mpmath) arithmetic over all
+# usable slots: a single false->true change, and the branch and k1 the oracle returns
+# ---------------------------------------------------------------------------------------------
+def _exact_test(r, t, tk, wk):
+    mp.mp.dps = 50
+    ct = mp.mpf(C) * (mp.mpf(float(t)) - mp.mpf(float(tk)))
+    dd = mp.fsum((mp.mpf(float(a)) - mp.mpf(float(b))) ** 2 for a, b in zip(r, wk))
+    return ct * ct <= dd
+
+
+def pin_bracket_bruteforce(lib):
+    from paper_2605_05543_gb300 import inputs
+
+    seen = set()
+    cases = [(5, 40, 64, 5e-6), (6, 60, 17, 5e-6), (4, 33, 33, 2e-6), (5, 80, 9, 5e-6), (3, 1, 4, 1e-6),
+             (8, 20, 32, 0.2e-6)]
+    for seed, (N, n, D, sigma) in enumerate(cases):
+        b = inputs.gaussian_bunch(N, sigma, 3.0, seed=seed)
+        h = inputs.synthetic_history(b.x, b.u, n, 1e-15, wiggle=3e-3, period_steps=40.0, seed=seed)
+        k0 = max(0, n - D + 1)
+        for i in range(N):
+            r = h.W[n, i]
+            for j in range(N):
+                if j == i:
+                    continue
+                tests = [_exact_test(r, h.T[n], h.T[k], h.W[k, j]) for k in range(k0, n + 1)]
+                assert tests[-1]  # at the present slot c (t - t_n) = 0 <= |r - w_n|
+                changes = sum(1 for a, c in zip(tests[:-1], tests[1:]) if a != c)
+                assert changes <= 1 and (changes == 0 or not tests[0])
+                res = oracle.retarded(h.T, h.W, h.V, n, D, j, r, lib=lib)
+                if tests[0]:
+                    assert res["branch"] == 0 and res["k1"] == k0
+                else:
+                    last_false = k0 + max(k for k in range(len(tests)) if not tests[k])
+                    assert res["k1"] == last_false, (res, last_false)
+                    assert res["branch"] == (1 if last_false == n - 1 else 2)
+                seen.add(res["branch"])
+    assert seen == {0, 1, 2}, seen
+
+
+# ---------------------------------------------------------------------------------------------
+# eq:dt: the root lies on the past light cone of the linear model, |r - w1 - v1 dt| = c (t - t1 - dt),
+# and equals the smaller root of the quadratic computed in 50-digit arithmetic
+# ---------------------------------------------------------------------------------------------
+def pin_quadratic_root(lib):
+    mp.mp.dps = 50
+    rng = np.random.default_rng(5)
+    dt = 1e-15
+    for trial in range(30):
+        n = int(rng.integers(2, 30))
+        beta = rng.uniform(0.1, 0.99)
+        vdir = rng.normal(size=3)
+        vdir /= np.linalg.norm(vdir)
+        v1 = beta * C * vdir
+        v2 = v1 * (1.0 + rng.uniform(-1e-3, 1e-3))
+        w_now = np.zeros(3)
+        tn = n * dt
+
+        def w_of(t):
+            return w_now + v1 * (t - tn)
+
+        def v_of(t):
+            return v1 if t < tn - 0.5 * dt else v2
+
+        d = rng.normal(size=3)
+        d *= rng.uniform(0.05e-6, 3e-6) / np.linalg.norm(d)
+        r = d
+        T, W, V = _two_body_history(r, w_of, v_of, n, dt)
+        res = oracle.retarded(T, W, V, n, 128, 1, r, lib=lib)
+        k1 = res["k1"]
+        t1 = T[k1]
+        w1 = W[k1, 1]
+        vv1 = V[k1, 1]
+        dtr = res["tr"] - t1
+        # light-cone invariant in FP64
+        wr = res["w"]
+        lhs = np.linalg.norm(r - wr)
+        rhs = C * (T[n] - res["tr"])
+        assert abs(lhs - rhs) <= 1e-13 * max(rhs, 1e-300) + 1e-24, (lhs, rhs)
+        # smaller root of C2 x^2 + C1 x + C0 = 0 in 50 digits
+        c = mp.mpf(C)
+        dm = [mp.mpf(float(a)) - mp.mpf(float(b)) for a, b in zip(r, w1)]
+        vm = [mp.mpf(float(a)) for a in vv1]
+        T1 = mp.mpf(float(T[n])) - mp.mpf(float(t1))
+        C2 = c * c - mp.fsum(x * x for x in vm)
+        C1 = 2 * (mp.fsum(a * b for a, b in zip(dm, vm)) - c * c * T1)
+        C0 = c * c * T1 * T1 - mp.fsum(x * x for x in dm)
+        root = (-C1 - mp.sqrt(C1 * C1 - 4 * C2 * C0)) / (2 * C2)
+        assert abs(dtr - float(root)) <= 1e-12 * max(abs(float(root)), dt), (dtr, root)
+
+
+# ---------------------------------------------------------------------------------------------
+# eq:linear: for a source whose velocity is linear in time (constant acceleration a), the rebuilt
+# acceleration is a and the rebuilt velocity is v(t_r) of the model's t_r; eq:linear2 gives a = 0
+# ---------------------------------------------------------------------------------------------
+def pin_reconstruction_constant_acceleration(lib):
+    rng = np.random.default_rng(6)
+    dt, n, D = 1e-15, 40, 64
+    seen = set()
+    for trial in range(20):
+        v0 = rng.normal(size=3)
+        v0 *= 0.5 * C / np.linalg.norm(v0)
+        acc = rng.normal(size=3) * 1e19
+        w00 = rng.normal(size=3) * 1e-6
+
+        def w_of(t):
+            return w00 + v0 * t + 0.5 * acc * t * t
+
+        def v_of(t):
+            return v0 + acc * t
+
+        d = rng.normal(size=3)
+        d *= rng.uniform(0.05e-6, 9e-6) / np.linalg.norm(d)
+        r = w_of(n * dt) + d
+        T, W, V = _two_body_history(r, w_of, v_of, n, dt)
+        res = oracle.retarded(T, W, V, n, D, 1, r, lib=lib)
+        seen.add(res["branch"])
+        vscale = np.linalg.norm(v0)
+        if res["branch"] == 0:
+            assert np.all(res["a"] == 0.0)
+            assert np.allclose(res["v"], V[0, 1], rtol=0, atol=1e-15 * vscale)
+        else:
+            assert np.allclose(res["a"], acc, rtol=0, atol=1e-6 * np.linalg.norm(acc))
+            vexp = v0 + acc * res["tr"]
+            assert np.allclose(res["v"], vexp, rtol=0, atol=1e-12 * vscale), (res["v"], vexp)
+    assert {0, 2} <= seen, seen
+
+
+# ---------------------------------------------------------------------------------------------
+# eq:LW_E / eq:LW_B including the acceleration term: compare with E = -grad V - dA/dt and
+# B = curl A of the Lienard-Wiechert potentials (Sec. 2.1), differentiated in 40-digit arithmetic
+# along a circular orbit (beta = 0.6)
+# ---------------------------------------------------------------------------------------------
+def pin_acceleration_field_from_potentials(lib):
+    mp.mp.dps = 40
+    c = mp.mpf(C)
+    q = mp.mpf(-QE)
+    k = 1 / (4 * mp.pi * mp.mpf(EPS0))
+    Rc = mp.mpf("1e-6")
+    beta = mp.mpf("0.6")
+    om = beta * c / Rc
+
+    def w(t):
+        return [Rc * mp.cos(om * t), Rc * mp.sin(om * t), mp.mpf(0)]
+
+    def wd(t):
+        return [-Rc * om * mp.sin(om * t), Rc * om * mp.cos(om * t), mp.mpf(0)]
+
+    def wdd(t):
+        return [-Rc * om * om * mp.cos(om * t), -Rc * om * om * mp.sin(om * t), mp.mpf(0)]
+
+    def tret(x, t):
+        def f(tr):
+            wt = w(tr)
+            return c * (t - tr) - mp.sqrt(sum((x[i] - wt[i]) ** 2 for i in range(3)))
+
+        dist = mp.sqrt(sum((x[i] - w(t)[i]) ** 2 for i in range(3)))
+        return mp.findroot(f, t - dist / c)
+
+    def pots(x, t):
+        tr = tret(x, t)
+        wt, vt = w(tr), wd(tr)
+        eta = [x[i] - wt[i] for i in range(3)]
+        en = mp.sqrt(sum(e * e for e in eta))
+        V = k * q * c / (en * c - sum(eta[i] * vt[i] for i in range(3)))
+        return V, [vt[i] * V / (c * c) for i in range(3)]
+
+    HX = mp.mpf("1e-18")  # spatial step, m (orbit radius 1e-6 m)
+    HT = mp.mpf("1e-27")  # time step, s (orbit period 3.5e-14 s)
+    rng = np.random.default_rng(7)
+    for trial in range(3):
+        x0 = [mp.mpf(float(a)) for a in rng.normal(size=3) * 2e-6]
+        t0 = mp.mpf(float(rng.uniform(0, 1e-14)))
+        Eref, Bref = [], [0, 0, 0]
+        for i in range(3):
+            def Vi(s, i=i):
+                xx = list(x0)
+                xx[i] = s
+                return pots(xx, t0)[0]
+
+            def Ai(s, i=i):
+                return pots(x0, s)[1][i]
+
+            Eref.append(-mp.diff(Vi, x0[i], h=HX) - mp.diff(Ai, t0, h=HT))
+        dA = [[None] * 3 for _ in range(3)]  # dA[comp][deriv]
+        for a in range(3):
+            for dvar in range(3):
+                if a == dvar:
+                    continue
+
+                def Acomp(s, a=a, dvar=dvar):
+                    xx = list(x0)
+                    xx[dvar] = s
+                    return pots(xx, t0)[1][a]
+
+                dA[a][dvar] = mp.diff(Acomp, x0[dvar], h=HX)
+        Bref = [dA[2][1] - dA[1][2], dA[0][2] - dA[2][0], dA[1][0] - dA[0][1]]
+        tr = tret(x0, t0)
+        wt, vt, at = w(tr), wd(tr), wdd(tr)
+        eta = np.array([float(x0[i] - wt[i]) for i in range(3)])
+        E, B = oracle.lw_fields(eta, [float(a) for a in vt], [float(a) for a in at], -QE, lib=lib)
+        Er = np.array([float(a) for a in Eref])
+        Br = np.array([float(a) for a in Bref])
+        assert np.max(np.abs(E - Er)) <= 1e-10 * np.linalg.norm(Er), (E, Er)
+        assert np.max(np.abs(B - Br)) <= 1e-10 * np.linalg.norm(Br), (B, Br)
+
+
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.3 Higuera-Cary: closed forms
+# ---------------------------------------------------------------------------------------------
+def pin_hc_pure_electric(lib):
+    rng = np.random.default_rng(8)
+    for trial in range(10):
+        u = rng.normal(size=3) * 3e8
+        E = rng.normal(size=3) * 1e7
+        h = -QE * 1e-13 / (2 * ME)
+        un = oracle.hc_kick(u, E, np.zeros(3), h, lib=lib)
+        ref = u + 2 * h * E
+        assert np.max(np.abs(un - ref)) <= 1e-15 * np.linalg.norm(ref), (un, ref)
+
+
+def pin_hc_pure_magnetic(lib):
+    """|u| is conserved (magnetic force does no work) and the rotation angle per step tends to the
+    relativistic cyclotron angle |q| B dt / (gamma m) as dt -> 0."""
+    rng = np.random.default_rng(9)
+    for trial in range(5):
+        u = rng.normal(size=3) * 5e8
+        Bv = rng.normal(size=3)
+        Bv *= 0.7 / np.linalg.norm(Bv)
+        g = math.sqrt(1 + u @ u / C ** 2)
+        wc = QE * 0.7 / (g * ME)
+        dt = 1e-4 / wc
+        h = -QE * dt / (2 * ME)
+        un = oracle.hc_kick(u, np.zeros(3), Bv, h, lib=lib)
+        assert abs(np.linalg.norm(un) - np.linalg.norm(u)) <= 4e-16 * np.linalg.norm(u)
+        bh = Bv / np.linalg.norm(Bv)
+        up = u - (u @ bh) * bh
+        unp = un - (un @ bh) * bh
+        assert abs(un @ bh - u @ bh) <= 1e-15 * np.linalg.norm(u)
+        ang = math.atan2(np.cross(up, unp) @ bh, up @ unp)
+        # electrons (q < 0) rotate counter-clockwise about B
+        assert abs(ang - wc * dt) <= 1e-7 * wc * dt, (ang, wc * dt)
+
+
+def pin_hc_exb_drift(lib):
+    """Crossed fields with |E| < c|B|: the mean velocity is the relativistic drift E x B / B^2."""
+    B0 = 1.0
+    E0 = 0.5 * C * B0
+    E = np.array([0.0, E0, 0.0])
+    Bv = np.array([0.0, 0.0, B0])
+    wc = QE * B0 / ME
+    dt = 0.05 / wc
+    h = -QE * dt / (2 * ME)
+    u = np.zeros(3)
+    vsum = np.zeros(3)
+    nsteps = 40000
+    for _ in range(nsteps):
+        u = oracle.hc_kick(u, E, Bv, h, lib=lib)
+        vsum += u / math.sqrt(1 + u @ u / C ** 2)
+    vmean = vsum / nsteps
+    vd = np.cross(E, Bv) / (B0 * B0)
+    assert np.linalg.norm(vmean - vd) <= 5e-3 * np.linalg.norm(vd), (vmean, vd)
+
+
+def pin_hc_stationary_drift(lib):
+    """Higuera-Cary's defining property: a particle moving at the relativistic E x B drift (where
+    E + v x B = 0) stays there exactly, for any step size (Boris' gamma^- would not)."""
+    B0 = 1.0
+    for frac in (0.5, 0.9, 0.99):
+        E0 = frac * C * B0
+        E = np.array([0.0, E0, 0.0])
+        Bv = np.array([0.0, 0.0, B0])
+        gd = 1.0 / math.sqrt(1.0 - frac * frac)
+        u0 = np.array([gd * E0 / B0, 0.0, 0.0])
+        for wdt in (0.3, 1.0, 3.0):
+            h = -QE * (wdt * ME / (QE * B0)) / (2 * ME)
+            u = u0.copy()
+            for _ in range(50):
+                u = oracle.hc_kick(u, E, Bv, h, lib=lib)
+            assert np.max(np.abs(u - u0)) <= 1e-12 * np.linalg.norm(u0), (frac, wdt, u, u0)
+
+
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.6 centred dipole: equatorial field -B_eq e_z, polar field +2 B_eq e_z, div B = curl B = 0
+# ---------------------------------------------------------------------------------------------
+def pin_dipole(lib):
+    RE = 6.371e6
+    M0 = 8.6e22
+    par = oracle.bext_params(2, m0=M0)
+    Beq = MU0 / (4 * math.pi) * M0 / RE ** 3
+    for x, ref in (((RE, 0, 0), (0, 0, -Beq)), ((0, -2 * RE, 0), (0, 0, -Beq / 8)), ((0, 0, RE), (0, 0, 2 * Beq)),
+                   ((0, 0, -3 * RE), (0, 0, 2 * Beq / 27))):
+        Bv = oracle.background_b(2, par, x, lib=lib)
+        assert np.max(np.abs(Bv - np.array(ref))) <= 1e-14 * Beq, (x, Bv, ref)
+    rng = np.random.default_rng(10)
+    for trial in range(5):
+        x = rng.normal(size=3) * 4 * RE
+        hstep = 1e-4 * np.linalg.norm(x)
+        J = np.zeros((3, 3))
+        for d in range(3):
+            e = np.zeros(3)
+            e[d] = hstep
+            J[:, d] = (oracle.background_b(2, par, x + e, lib=lib) - oracle.background_b(2, par, x - e, lib=lib)) / (
+                2 * hstep)
+        scale = np.linalg.norm(oracle.background_b(2, par, x, lib=lib)) / np.linalg.norm(x)
+        assert abs(np.trace(J)) <= 1e-6 * scale
+        curl = np.array([J[2, 1] - J[1, 2], J[0, 2] - J[2, 0], J[1, 0] - J[0, 1]])
+        assert np.max(np.abs(curl)) <= 1e-6 * scale
+    # uniform model returns its vector everywhere
+    par = oracle.bext_params(1, b=(5e-5, -1e-6, 2e-7))
+    assert np.all(oracle.background_b(1, par, (1.0, 2.0, 3.0), lib=lib) == np.array([5e-5, -1e-6, 2e-7]))
+
+
+# ---------------------------------------------------------------------------------------------
+# Full steps: exact point-reflection symmetry of a two-electron collision (momentum balance),
+# energy bookkeeping of a slow pair, invariances
+# ---------------------------------------------------------------------------------------------
+def pin_symmetric_collision(lib):
+    """x2 = -x1, u2 = -u1 is kept exactly by every step: E is odd and B even under point reflection,
+    so p1 + p2 = 0 holds to the last bit."""
+    x1 = np.array([0.3e-6, -0.1e-6, -2e-6])
+    u1 = np.array([1e7, 3e6, 8e8])
+    run = oracle.Run(np.stack([x1, -x1]), np.stack([u1, -u1]), D=32, dt=1e-15, nmax=60, lib=lib)
+    run.step(60)
+    assert np.array_equal(run.x[1], -run.x[0])
+    assert np.array_equal(run.u[1], -run.u[0])
+    # the pair repels: the transverse separation grows faster than without interaction
+    free = oracle.Run(np.stack([x1, -x1]), np.stack([u1, -u1]), D=32, dt=1e-15, nmax=60, lib=lib)
+    free.step(60, self_on=False)
+    assert np.array_equal(free.x[1], -free.x[0])
+    sep = np.linalg.norm((run.x[1] - run.x[0])[:2])
+    sep_free = np.linalg.norm((free.x[1] - free.x[0])[:2])
+    assert sep > sep_free, (sep, sep_free)
+    assert run.stats["shortcut"] + run.stats["bisection"] + run.stats["out_of_history"] == 2
+
+
+def pin_slow_pair_energy(lib):
+    """Two electrons released at rest 10 nm apart: kinetic + Coulomb energy is conserved to the
+    first-order accuracy of a push with fields held from x^n (|dE|/E ~ dt / t_dyn)."""
+    d0 = 1e-8
+    x = np.array([[0.0, 0.0, -d0 / 2], [0.0, 0.0, d0 / 2]])
+    u = np.zeros((2, 3))
+    U0 = QE * QE * K_C / d0
+    t_dyn = d0 / math.sqrt(U0 / ME)
+    dt = 1e-3 * t_dyn
+    run = oracle.Run(x, u, D=16, dt=dt, nmax=3000, lib=lib)
+    run.step(3000)
+    g = np.sqrt(1 + np.sum(run.u ** 2, axis=1) / C ** 2)
+    ke = float(np.sum((g - 1) * ME * C * C))
+    sep = np.linalg.norm(run.x[1] - run.x[0])
+    pe = QE * QE * K_C / sep
+    assert sep > 3 * d0
+    assert abs(ke + pe - U0) <= 5e-3 * U0, (ke, pe, U0)
+
+
+def pin_invariances(lib):
+    from paper_2605_05543_gb300 import inputs
+
+    N, n, D = 24, 30, 20
+    b = inputs.gaussian_bunch(N, 5e-6, 3.0, seed=11)
+    h = inputs.synthetic_history(b.x, b.u, n, 1e-15, wiggle=1e-3, period_steps=50.0, seed=11)
+    E, B, _ = oracle.self_fields(h.T, h.W, h.V, n, D, lib=lib)
+    scaleE = np.linalg.norm(E, axis=1).max()
+    scaleB = np.linalg.norm(B, axis=1).max()
+    # translation of every stored and present position
+    shift = np.array([3e-5, -2e-5, 1e-5])
+    E2, B2, _ = oracle.self_fields(h.T, h.W + shift, h.V, n, D, lib=lib)
+    assert np.max(np.abs(E2 - E)) <= 1e-9 * scaleE
+    assert np.max(np.abs(B2 - B)) <= 1e-9 * scaleB
+    # relabelling of the particles
+    perm = np.random.default_rng(12).permutation(N)
+    E3, B3, _ = oracle.self_fields(h.T, h.W[:, perm], h.V[:, perm], n, D, lib=lib)
+    assert np.max(np.abs(E3 - E[perm])) <= 1e-13 * scaleE
+    assert np.max(np.abs(B3 - B[perm])) <= 1e-13 * scaleB
+    # fields are linear in the source weights: doubling every weight doubles them exactly
+    E4, B4, _ = oracle.self_fields(h.T, h.W, h.V, n, D, weights=np.full(N, 2.0), lib=lib)
+    assert np.array_equal(E4, 2 * E) and np.array_equal(B4, 2 * B)
+    # a single target excludes itself: the field on i does not depend on i's own history
+    W5 = h.W.copy()
+    V5 = h.V.copy()
+    W5[:n, 0] += 1e-6
+    V5[:, 0] *= 0.5
+    E5, B5, _ = oracle.self_fields(h.T, W5, V5, n, D, targets=[0], lib=lib)
+    assert np.array_equal(E5[0], E[0]) and np.array_equal(B5[0], B[0])
+
+
+PINS = [
+    pin_hc_pure_electric,
+    pin_hc_pure_magnetic,
+    pin_hc_stationary_drift,
+    pin_dipole,
+    pin_coulomb_static,
+    pin_heaviside_uniform_motion,
+    pin_out_of_history_delay,
+    pin_reconstruction_constant_acceleration,
+    pin_quadratic_root,
+    pin_symmetric_collision,
+    pin_invariances,
+    pin_bracket_bruteforce,
+    pin_acceleration_field_from_potentials,
+    pin_slow_pair_energy,
+    pin_hc_exb_drift,
+]
