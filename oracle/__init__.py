@@ -65,7 +65,7 @@ def _bind(lib):
                                  _d, _d, _d, _i64]
     lib.orc_retarded.restype = ctypes.c_int
     lib.orc_self_fields.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _i64,
-                                    ctypes.c_int64, _d, _d, _i64]
+                                    ctypes.c_int64, _d, _d, _d, _i64]
     lib.orc_self_fields.restype = ctypes.c_int
     lib.orc_push.argtypes = [ctypes.c_int64, ctypes.c_double, _d, _d, _d, _d, ctypes.c_int, _d, _d, _d]
     lib.orc_push.restype = ctypes.c_int
@@ -175,8 +175,9 @@ def retarded(T, W, V, n, D, j, r, lib=None):
                 branch=int(info[0]), k1=int(info[1]), ntest=int(info[2]))
 
 
-def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None):
-    """Self fields on targets (all if None) at step n. Returns (E, B, stats).
+def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None, mags=False):
+    """Self fields on targets (all if None) at step n. Returns (E, B, stats), or (E, B, stats, M) with
+    mags=True where M[:, 0] = sum_j |E_ij| and M[:, 1] = sum_j |B_ij| per target.
 
     stats = dict(out_of_history, shortcut, bisection, node_tests) over all evaluated pairs.
     """
@@ -193,10 +194,12 @@ def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None):
     E = np.zeros((nt, 3))
     B = np.zeros((nt, 3))
     stats = np.zeros(4, dtype=np.int64)
+    M = np.zeros((nt, 2))
     st = lib.orc_self_fields(N, _p(T), _p(W), _p(V), int(n), int(D), None if wts is None else _p(wts),
-                             None if tg is None else _pi(tg), nt, _p(E), _p(B), _pi(stats))
+                             None if tg is None else _pi(tg), nt, _p(E), _p(B), _p(M), _pi(stats))
     _check(st, "self_fields")
-    return E, B, dict(zip(("out_of_history", "shortcut", "bisection", "node_tests"), stats.tolist()))
+    sd = dict(zip(("out_of_history", "shortcut", "bisection", "node_tests"), stats.tolist()))
+    return (E, B, sd, M) if mags else (E, B, sd)
 
 
 def velocity(u):

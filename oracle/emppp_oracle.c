@@ -27,8 +27,8 @@
  *   - order of the three cases: P(k0) -> out-of-history case (eq:linear2, t_r < t_0);
  *     else not P(n-1) -> near-field shortcut [t-dt, t]; else bisection on slot indices
  *     starting from [t_0, t].
- *   - the root of the quadratic eq:dt is taken in the algebraically identical form
- *     2 C0 / (-C1 + sqrt(C1^2 - 4 C2 C0)), which avoids cancellation.
+ *   - the root of the quadratic eq:dt is the smaller (minus-sign) root, formed without cancellation
+ *     as q / C2 or C0 / q with q = -(C1 + sgn(C1) sqrt(C1^2 - 4 C2 C0)) / 2.
  *   - the retarded position is w1 + v1 dt (first form of eq:linear); the velocity is
  *     v1 (1 - df) + v2 df and the acceleration (v2 - v1) / (t2 - t1).
  *   - self fields are evaluated at the present positions x^n and time t_n; the background field
@@ -140,17 +140,22 @@ static int bracket(const history* h, int64_t j, const double r[3], double t, int
   return BR_BISECTION;
 }
 
-/* Quadratic of eq:dt: delta t = t_r - t1 for the line w1 + v1 delta t, with T1 = t - t1 and
-   d = r - w1. The smaller root (past light cone) in cancellation-free form. */
+/* Quadratic of eq:dt for delta t = t_r - t1 on the line w1 + v1 delta t, with T1 = t - t1 and
+   d = r - w1: C2 x^2 + C1 x + C0 = 0. The physically relevant root is the one with the minus sign,
+   i.e. the smaller root (the other lies on the future light cone, delta t > t - t1). Both roots are
+   formed in the textbook cancellation-free way, q = -(C1 + sgn(C1) sqrt(disc)) / 2 with roots
+   q / C2 and C0 / q, and the smaller one is returned. */
 static int solve_dt(const double d[3], double T1, const double v1[3], double* dt_out) {
   double C2 = C_LIGHT * C_LIGHT - dot3(v1, v1);
   double C1 = 2.0 * (dot3(d, v1) - C_LIGHT * C_LIGHT * T1);
   double C0 = C_LIGHT * C_LIGHT * T1 * T1 - dot3(d, d);
   double disc = C1 * C1 - 4.0 * C2 * C0;
   if (!(C2 > 0.0) || !(disc >= 0.0)) return ORC_ERR_NUMERIC;
-  double den = -C1 + sqrt(disc);
-  if (!(den > 0.0)) return ORC_ERR_NUMERIC;
-  *dt_out = 2.0 * C0 / den;
+  double sq = sqrt(disc);
+  double q = -0.5 * (C1 + (C1 >= 0.0 ? sq : -sq));
+  if (!(q != 0.0)) return ORC_ERR_NUMERIC;
+  double ra = q / C2, rb = C0 / q;
+  *dt_out = ra < rb ? ra : rb;
   return ORC_OK;
 }
 
@@ -321,9 +326,12 @@ int orc_retarded(int64_t N, const double* T, const double* W, const double* V, i
 /* Self fields (Sec. 2.1 superposition over j != i) at the present positions W[n][i] and time
    T[n] for the targets listed in tgt (or all N if tgt is NULL, ntgt ignored), using history
    slots k0..n, k0 = max(0, n - D + 1). q[j] = -e w[j] (wts NULL: w = 1).
-   E, B: [ntgt][3]. stats (may be NULL): {out-of-history, shortcut, bisection, node tests}. */
+   E, B: [ntgt][3]. mags (may be NULL): [ntgt][2] = {sum_j |E_ij|, sum_j |B_ij|}, the scale against
+   which a per-component error of the sum is measured. stats (may be NULL): {out-of-history,
+   shortcut, bisection, node tests}. */
 int orc_self_fields(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D,
-                    const double* wts, const int64_t* tgt, int64_t ntgt, double* E, double* B, int64_t* stats) {
+                    const double* wts, const int64_t* tgt, int64_t ntgt, double* E, double* B, double* mags,
+                    int64_t* stats) {
   if (N < 1 || n < 0 || D < 1) return ORC_ERR_ARG;
   history h = {N, T, W, V};
   int64_t k0 = n - D + 1 > 0 ? n - D + 1 : 0;
@@ -336,6 +344,7 @@ int orc_self_fields(int64_t N, const double* T, const double* W, const double* V
     int64_t i = tgt ? tgt[ii] : ii;
     const double* r = hist_w(&h, n, i);
     csum Es[3] = {{0, 0}, {0, 0}, {0, 0}}, Bs[3] = {{0, 0}, {0, 0}, {0, 0}};
+    csum Em = {0, 0}, Bm = {0, 0};
     for (int64_t j = 0; j < N; j++) {
       if (j == i) continue;
       double w[3], v[3], a[3], tr, Ej[3], Bj[3];
@@ -359,10 +368,16 @@ int orc_self_fields(int64_t N, const double* T, const double* W, const double* V
         csum_add(&Es[c], Ej[c]);
         csum_add(&Bs[c], Bj[c]);
       }
+      csum_add(&Em, sqrt(dot3(Ej, Ej)));
+      csum_add(&Bm, sqrt(dot3(Bj, Bj)));
     }
     for (int c = 0; c < 3; c++) {
       E[ii * 3 + c] = csum_get(&Es[c]);
       B[ii * 3 + c] = csum_get(&Bs[c]);
+    }
+    if (mags) {
+      mags[ii * 2] = csum_get(&Em);
+      mags[ii * 2 + 1] = csum_get(&Bm);
     }
   }
   if (stats) {
@@ -421,7 +436,7 @@ int orc_step(int64_t N, double* T, double* W, double* V, double* u, int64_t n, i
     return ORC_ERR_ARG;
   }
   int st = ORC_OK;
-  if (self_on) st = orc_self_fields(N, T, W, V, n, D, wts, NULL, 0, Es, Bs, stats);
+  if (self_on) st = orc_self_fields(N, T, W, V, n, D, wts, NULL, 0, Es, Bs, NULL, stats);
   memcpy(x, W + n * N * 3, (size_t)N * 3 * sizeof(double));
   if (st == ORC_OK) {
     double* vnew = V + (n + 1) * N * 3;

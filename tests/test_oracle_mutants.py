@@ -25,7 +25,7 @@ MUTANTS = [
     # eq:dt
     ("dt_c1_sign", "double C1 = 2.0 * (dot3(d, v1) - C_LIGHT * C_LIGHT * T1);",
      "double C1 = 2.0 * (-dot3(d, v1) - C_LIGHT * C_LIGHT * T1);"),
-    ("dt_other_root", "double den = -C1 + sqrt(disc);", "double den = -C1 - sqrt(disc);"),
+    ("dt_other_root", "*dt_out = ra < rb ? ra : rb;", "*dt_out = ra < rb ? rb : ra;"),
     ("dt_c0_sign", "double C0 = C_LIGHT * C_LIGHT * T1 * T1 - dot3(d, d);",
      "double C0 = dot3(d, d) - C_LIGHT * C_LIGHT * T1 * T1;"),
     # eq:linear
