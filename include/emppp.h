@@ -1,0 +1,166 @@
+/*
+ * emppp.h -- C ABI of the GB300 EM-PP library (electromagnetic particle-particle bunch solver).
+ *
+ * One EM-PP step (arXiv 2605.05543, Sec. 2.1-2.3) advances N interacting electrons: every target i
+ * sees every source j != i through the Lienard-Wiechert fields eq:LW_E / eq:LW_B evaluated at the
+ * retarded time, which is bracketed in j's stored trajectory history and rebuilt by the linear
+ * reconstruction eq:dt / eq:linear (eq:linear2 when it is older than the history); the summed self
+ * fields plus a prescribed background B field (Sec. 2.6) drive a Higuera-Cary push (Sec. 2.3).
+ *
+ * Conventions for every call:
+ *   - SI units: positions m, proper velocities u = gamma v in m/s, times s, fields V/m and T.
+ *   - Vectors are interleaved per particle: x[3*i + c], c = 0,1,2 (x, y, z).
+ *   - Pointers marked "host or device" are read as device pointers when is_device_ptr != 0, else as
+ *     host pointers. Host arrays stay owned by the caller and are copied before the call returns;
+ *     device arrays must stay valid until the call returns and are read on the handle's stream.
+ *   - Every call returns an emppp_status. Calls never abort and never print. emppp_last_error()
+ *     gives a text for the last failing call of this thread. A numeric fault found on the device
+ *     (negative discriminant, |v| >= c, coincident particles, non-finite field) is reported as
+ *     EMPPP_ERR_NUMERIC by the next call that synchronises (get_*, emppp_synchronize).
+ *   - The library owns all device memory it allocates (cudaMalloc at create time; nothing is
+ *     allocated by emppp_step).
+ *   - A handle is not thread-safe: one thread at a time may use it.
+ */
+#ifndef EMPPP_H
+#define EMPPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define EMPPP_API __attribute__((visibility("default")))
+#else
+#define EMPPP_API
+#endif
+
+typedef struct emppp_ctx* emppp_handle;
+
+typedef enum {
+  EMPPP_OK = 0,
+  EMPPP_ERR_ARG = -1,     /* bad handle, size, pointer or option */
+  EMPPP_ERR_CUDA = -2,    /* a CUDA runtime call failed (text in emppp_last_error) */
+  EMPPP_ERR_NUMERIC = -3, /* device-side numeric fault in a previous step */
+  EMPPP_ERR_TIMEOUT = -4, /* a bounded device wait gave up */
+  EMPPP_ERR_STATE = -5,   /* call out of order (e.g. step before set_particles) */
+  EMPPP_ERR_OOM = -6      /* device allocation failed */
+} emppp_status;
+
+/* Background magnetic field models (Sec. 2.6). NONE: B_ext = 0. UNIFORM: B_ext = b.
+ * DIPOLE: centred dipole, B = mu0/(4 pi) [3 (M.rhat) rhat - M] / r^3 with M = m0 e_z and r measured
+ * from `center`. B_ext is evaluated at the half-step position x^{n+1/2}. */
+typedef enum { EMPPP_BEXT_NONE = 0, EMPPP_BEXT_UNIFORM = 1, EMPPP_BEXT_DIPOLE = 2 } emppp_bext_kind;
+
+typedef struct {
+  int32_t kind;     /* emppp_bext_kind */
+  int32_t pad_;
+  double b[3];      /* UNIFORM: field vector, T */
+  double m0;        /* DIPOLE: moment along +z, A m^2 */
+  double center[3]; /* DIPOLE: dipole position, m */
+} emppp_bext;
+
+/* Precision of the pair-field path.
+ *   FP64:  every step of the pair path in FP64; agrees with the FP64 oracle to ~1e-14.
+ *   MIXED: pair geometry and fields in FP32 on hi/lo-split coordinates with compensated FP32
+ *          sums; time stamps, the bracket decision and the push stay FP64. */
+typedef enum { EMPPP_FP64 = 0, EMPPP_MIXED = 1 } emppp_precision;
+
+/* First guess of the retarded-time search (Sec. 2.2). Every proposal ends in the same bracket
+ * [t_k1, t_k1+1] as the plain search, because the bracket is the unique change of sign of the
+ * node test and each guess is checked by it.
+ *   BISECT:      the paper's search: out-of-history test, near-field shortcut, bisection.
+ *   CLOSED_FORM: uniform-motion delay from the source's present state, then a guarded walk.
+ *   MLP:         delay predicted by the 10-64-64-1 network set by emppp_set_proposal. */
+typedef enum { EMPPP_PROPOSAL_BISECT = 0, EMPPP_PROPOSAL_CLOSED_FORM = 1, EMPPP_PROPOSAL_MLP = 2 } emppp_proposal;
+
+typedef struct {
+  int32_t precision;   /* emppp_precision, default FP64 */
+  int32_t proposal;    /* emppp_proposal, default BISECT */
+  int32_t pair_fields; /* 1 (default): self fields on; 0: E = 0, B = B_ext (stage-2 transport, Sec. 2.7) */
+  int32_t source_split;/* 0 (default): automatic; >0: number of source slices per target block */
+  int32_t reserved[4]; /* must be 0 */
+} emppp_options;
+
+/* Counters of the last completed step's pair evaluation (Sec. 2.2 branches). */
+typedef struct {
+  int64_t pairs;          /* N (N - 1) */
+  int64_t out_of_history; /* pairs with t_r older than the history (eq:linear2) */
+  int64_t shortcut;       /* pairs bracketed by the near-field shortcut */
+  int64_t bisection;      /* pairs bracketed by the search */
+  int64_t node_tests;     /* evaluations of c (t - t_k) <= |r - w_k| over all pairs */
+  int64_t guard_fallbacks;/* node tests decided in FP64 after an inconclusive FP32 test */
+} emppp_stats;
+
+/* Fills *out with the defaults listed above. */
+EMPPP_API void emppp_default_options(emppp_options* out);
+
+/* Creates a solver for n particles with a history of `history_depth` slots (the present slot
+ * included; depth >= 2) and fixed step dt > 0. opt may be NULL (defaults). cuda_stream is a
+ * cudaStream_t (NULL: the legacy default stream). Allocates all device memory of the solver on the
+ * current device. *out is NULL on failure. Sec. 2.2 (history), Sec. 2.3 (time step). */
+EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt, const emppp_options* opt,
+                                    void* cuda_stream, emppp_handle* out);
+
+/* Frees every device resource of the handle (NULL is ignored). */
+EMPPP_API void emppp_destroy(emppp_handle h);
+
+/* Sets the initial state at t = 0, step 0: positions x [3n], proper velocities u [3n] (host or
+ * device) and optional macro-particle weights w [n] (charge -e w, mass m_e w; NULL: all 1). Resets
+ * the history to the single slot 0 holding (x, v = u / gamma). Sec. 2.2, Sec. 2.5. */
+EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, const double* u, const double* w,
+                                           int32_t is_device_ptr);
+
+/* Restores a state with history (checkpoint resume, or a prepared history): the present step
+ * index n >= 0, nslots = min(n + 1, depth) most recent slots k = n - nslots + 1 .. n with time
+ * stamps T [nslots] (increasing), positions W [nslots][n_particles][3] and velocities
+ * V [nslots][n_particles][3] (|V| < c), the present proper velocities u [3n] and optional weights
+ * w [n] (NULL: all 1). Host or device. The present position is W[nslots - 1]. */
+EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslots, const double* T,
+                                         const double* W, const double* V, const double* u, const double* w,
+                                         int32_t is_device_ptr);
+
+/* Copies the stored history out in the layout emppp_set_history takes. T [nslots], W, V
+ * [nslots][n][3], u [3n] (host or device); *n_now and *nslots receive the present step and the
+ * number of slots written (= min(n + 1, depth)); the arrays must hold `depth` slots. */
+EMPPP_API emppp_status emppp_get_history(emppp_handle h, int64_t* n_now, int32_t* nslots, double* T, double* W,
+                                         double* V, double* u, int32_t is_device_ptr);
+
+/* Advances nsteps >= 0 steps (Sec. 2.1-2.3): self fields at (x^n, t_n), B_ext at x^{n+1/2},
+ * Higuera-Cary push, append of slot n+1. bext may be NULL (NONE). Asynchronous on the handle's
+ * stream: returns once the work is enqueued. */
+EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_bext* bext);
+
+/* Present positions x [3n], proper velocities u [3n] (host or device, either may be NULL), time
+ * and step index (either may be NULL). Synchronises the stream. */
+EMPPP_API emppp_status emppp_get_state(emppp_handle h, double* x, double* u, double* t_now, int64_t* n_now,
+                                       int32_t is_device_ptr);
+
+/* Fields used by the last completed step: self E [3n] and B [3n] = self + B_ext(x^{n+1/2})
+ * (host or device, either may be NULL). Synchronises the stream. */
+EMPPP_API emppp_status emppp_get_fields(emppp_handle h, double* E, double* B, int32_t is_device_ptr);
+
+/* Branch and node-test counters of the last completed step. Synchronises the stream. */
+EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out);
+
+/* Replaces the options (precision, proposal, pair_fields, source_split) for later steps. */
+EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt);
+
+/* Replaces the stream later calls enqueue on (cudaStream_t, NULL: legacy default stream). */
+EMPPP_API emppp_status emppp_set_stream(emppp_handle h, void* cuda_stream);
+
+/* Waits for the handle's stream and reports a pending device-side numeric fault. */
+EMPPP_API emppp_status emppp_synchronize(emppp_handle h);
+
+/* Text of the last failing call on this thread ("" if none). Valid until the next call. */
+EMPPP_API const char* emppp_last_error(void);
+
+/* Library version string. */
+EMPPP_API const char* emppp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMPPP_H */

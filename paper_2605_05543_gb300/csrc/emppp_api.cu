@@ -1,0 +1,492 @@
+// C ABI of the EM-PP library: handle lifetime, state transfer and the step driver.
+// Every entry point validates its arguments, enqueues work on the handle's stream and returns a
+// status; nothing here aborts or prints.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/emppp.h"
+#include "emppp_internal.cuh"
+
+using namespace emppp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+emppp_status fail(emppp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CU(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess) return fail(EMPPP_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+struct emppp_ctx {
+  DeviceState ds{};
+  int64_t N = 0;
+  int32_t D = 0;
+  double dt = 0.0;
+  emppp_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  bool has_state = false;
+  int64_t n = 0;    // host mirror of the present step
+  double t = 0.0;   // host mirror of t_n
+  double* staging = nullptr;  // [7N] doubles for host transfers
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+emppp_status check_handle(emppp_handle h) {
+  if (!h) return fail(EMPPP_ERR_ARG, "null handle");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return fail(EMPPP_ERR_CUDA, "cudaSetDevice: %s", cudaGetErrorString(e));
+  return EMPPP_OK;
+}
+
+template <typename T>
+emppp_status dalloc(emppp_ctx* c, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EMPPP_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  c->allocs.push_back(q);
+  *p = static_cast<T*>(q);
+  return EMPPP_OK;
+}
+
+emppp_status validate_options(const emppp_options* o) {
+  if (o->precision != EMPPP_FP64 && o->precision != EMPPP_MIXED)
+    return fail(EMPPP_ERR_ARG, "unknown precision %d", o->precision);
+  if (o->precision == EMPPP_MIXED) return fail(EMPPP_ERR_ARG, "MIXED precision path is not available in this build");
+  if (o->proposal != EMPPP_PROPOSAL_BISECT && o->proposal != EMPPP_PROPOSAL_CLOSED_FORM)
+    return fail(EMPPP_ERR_ARG, "proposal %d is not available in this build", o->proposal);
+  if (o->pair_fields != 0 && o->pair_fields != 1) return fail(EMPPP_ERR_ARG, "pair_fields must be 0 or 1");
+  if (o->source_split < 0) return fail(EMPPP_ERR_ARG, "source_split must be >= 0");
+  for (int k = 0; k < 4; k++)
+    if (o->reserved[k] != 0) return fail(EMPPP_ERR_ARG, "reserved option fields must be 0");
+  return EMPPP_OK;
+}
+
+// Number of source slices per target block: all blocks of the pair kernel are resident at once,
+// so the step takes as long as the busiest SM; pick the smallest split whose blocks spread over the
+// SMs within 5% of evenly (or the most even one).
+int choose_split(const emppp_ctx* c) {
+  if (c->opt.source_split > 0) return c->opt.source_split < c->ds.max_split ? c->opt.source_split : c->ds.max_split;
+  const long long ntb = (c->N + 127) / 128;
+  int best = 1;
+  double best_eff = 0.0;
+  for (int s = 1; s <= c->ds.max_split; s++) {
+    if (s > 1 && c->N / s < 16) break;
+    const double per_sm = (double)(ntb * s) / c->num_sms;
+    const double eff = per_sm / (double)((ntb * s + c->num_sms - 1) / c->num_sms);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = s;
+    }
+    if (eff >= 0.95) break;
+  }
+  return best;
+}
+
+emppp_status read_err(emppp_handle h) {
+  int herr = 0;
+  CU(cudaMemcpyAsync(&herr, h->ds.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  if (herr) {
+    return fail(EMPPP_ERR_NUMERIC,
+                "device numeric fault (bits 0x%x: 1 = negative discriminant or |v| >= c, 2 = coincident pair, "
+                "4 = non-finite state, 8 = wait limit)",
+                herr);
+  }
+  return EMPPP_OK;
+}
+
+// copy n doubles from caller memory (host or device) into device memory
+emppp_status to_device(emppp_handle h, double* dst, const double* src, size_t n, int is_dev) {
+  CU(cudaMemcpyAsync(dst, src, n * sizeof(double), is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     h->stream));
+  return EMPPP_OK;
+}
+
+emppp_status from_device(emppp_handle h, double* dst, const double* src, size_t n, int is_dev) {
+  CU(cudaMemcpyAsync(dst, src, n * sizeof(double), is_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->stream));
+  return EMPPP_OK;
+}
+
+void set_origin(emppp_handle h, const double* x0) {
+  for (int c = 0; c < 3; c++) h->ds.origin[c] = x0[c];
+}
+
+}  // namespace
+
+extern "C" {
+
+EMPPP_API const char* emppp_version(void) { return "emppp 0.1 (sm_103a)"; }
+
+EMPPP_API const char* emppp_last_error(void) { return g_last_error.c_str(); }
+
+EMPPP_API void emppp_default_options(emppp_options* out) {
+  if (!out) return;
+  memset(out, 0, sizeof(*out));
+  out->precision = EMPPP_FP64;
+  out->proposal = EMPPP_PROPOSAL_BISECT;
+  out->pair_fields = 1;
+  out->source_split = 0;
+}
+
+EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt, const emppp_options* opt,
+                                    void* cuda_stream, emppp_handle* out) {
+  if (!out) return fail(EMPPP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 1) return fail(EMPPP_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
+  if (history_depth < 2) return fail(EMPPP_ERR_ARG, "history_depth must be >= 2 (got %d)", history_depth);
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(EMPPP_ERR_ARG, "dt must be positive and finite");
+  if ((double)n * (double)history_depth > 4e10) return fail(EMPPP_ERR_ARG, "n * history_depth too large");
+  emppp_options o;
+  emppp_default_options(&o);
+  if (opt) o = *opt;
+  emppp_status st = validate_options(&o);
+  if (st != EMPPP_OK) return st;
+
+  emppp_ctx* c = new (std::nothrow) emppp_ctx();
+  if (!c) return fail(EMPPP_ERR_OOM, "host allocation failed");
+  c->N = n;
+  c->D = history_depth;
+  c->dt = dt;
+  c->opt = o;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(EMPPP_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
+  }
+  DeviceState& s = c->ds;
+  s.N = n;
+  s.D = history_depth;
+  const size_t N = (size_t)n, D = (size_t)history_depth;
+  const long long ntb = (n + 127) / 128;
+  long long ms = (8LL * c->num_sms + ntb - 1) / ntb;
+  s.max_split = (int)(ms < 1 ? 1 : (ms > 64 ? 64 : ms));
+#define ALLOC(p, cnt)                   \
+  do {                                  \
+    st = dalloc(c, &(p), (cnt));        \
+    if (st != EMPPP_OK) {               \
+      emppp_destroy(c);                 \
+      return st;                        \
+    }                                   \
+  } while (0)
+  ALLOC(s.rec64, N * D * 6);
+  ALLOC(s.rec32, N * D * 12);
+  ALLOC(s.slot_t, D);
+  ALLOC(s.tab.lhs64, D);
+  ALLOC(s.tab.lhs32, D);
+  ALLOC(s.tab.ct32, D);
+  ALLOC(s.tab.inv_dtk, D);
+  ALLOC(s.u, N * 3);
+  ALLOC(s.wts, N);
+  ALLOC(s.Eself, N * 3);
+  ALLOC(s.Bself, N * 3);
+  ALLOC(s.Bout, N * 3);
+  ALLOC(s.partial, (size_t)s.max_split * N * 6);
+  ALLOC(s.state, 1);
+  ALLOC(s.stats, kStatCount);
+  ALLOC(s.err, 1);
+  ALLOC(c->staging, N * 7);
+#undef ALLOC
+  e = cudaMemsetAsync(s.err, 0, sizeof(int), c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.stats, 0, sizeof(unsigned long long) * kStatCount, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.Eself, 0, sizeof(double) * N * 3, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.Bout, 0, sizeof(double) * N * 3, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    emppp_destroy(c);
+    return fail(EMPPP_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return EMPPP_OK;
+}
+
+EMPPP_API void emppp_destroy(emppp_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  delete h;
+}
+
+EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, const double* u, const double* w,
+                                           int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!x || !u) return fail(EMPPP_ERR_ARG, "x and u must not be NULL");
+  const size_t N = (size_t)h->N;
+  const double* dx = x;
+  const double* du = u;
+  const double* dw = w;
+  if (!is_device_ptr) {
+    double* sx = h->staging;
+    double* su = h->staging + 3 * N;
+    double* sw = h->staging + 6 * N;
+    if ((st = to_device(h, sx, x, 3 * N, 0)) != EMPPP_OK) return st;
+    if ((st = to_device(h, su, u, 3 * N, 0)) != EMPPP_OK) return st;
+    if (w && (st = to_device(h, sw, w, N, 0)) != EMPPP_OK) return st;
+    dx = sx;
+    du = su;
+    dw = w ? sw : nullptr;
+  }
+  double x0[3];
+  if (is_device_ptr) {
+    CU(cudaMemcpyAsync(x0, x, sizeof(x0), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  } else {
+    memcpy(x0, x, sizeof(x0));
+  }
+  set_origin(h, x0);
+  CU(launch_set_state(h->ds, 0, 0.0, h->dt, du, dw, h->stream));
+  CU(launch_init_slot0(h->ds, dx, du, dw, h->stream));
+  CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
+  CU(cudaMemsetAsync(h->ds.Bout, 0, sizeof(double) * N * 3, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->n = 0;
+  h->t = 0.0;
+  h->has_state = true;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslots, const double* T,
+                                         const double* W, const double* V, const double* u, const double* w,
+                                         int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!T || !W || !V || !u) return fail(EMPPP_ERR_ARG, "T, W, V and u must not be NULL");
+  if (n < 0) return fail(EMPPP_ERR_ARG, "n must be >= 0");
+  const int64_t want = n + 1 < h->D ? n + 1 : h->D;
+  if (nslots != want)
+    return fail(EMPPP_ERR_ARG, "nslots must be min(n + 1, depth) = %lld (got %d)", (long long)want, nslots);
+  const size_t N = (size_t)h->N;
+  std::vector<double> hT(nslots);
+  if (is_device_ptr) {
+    CU(cudaMemcpyAsync(hT.data(), T, sizeof(double) * nslots, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  } else {
+    memcpy(hT.data(), T, sizeof(double) * nslots);
+  }
+  for (int s = 0; s < nslots; s++) {
+    if (!(hT[s] == hT[s]) || (s > 0 && !(hT[s] > hT[s - 1])))
+      return fail(EMPPP_ERR_ARG, "time stamps must be finite and strictly increasing (slot %d)", s);
+  }
+  // origin of the FP32 split: the present position of particle 0
+  double x0[3];
+  const double* Wlast = W + (size_t)(nslots - 1) * N * 3;
+  if (is_device_ptr) {
+    CU(cudaMemcpyAsync(x0, Wlast, sizeof(x0), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  } else {
+    memcpy(x0, Wlast, sizeof(x0));
+  }
+  set_origin(h, x0);
+  std::vector<double> ht((size_t)h->D, 0.0);
+  for (int s = 0; s < nslots; s++) {
+    const int64_t k = n - nslots + 1 + s;
+    const int p = (int)(k % h->D);
+    ht[p] = hT[s];
+    const double* Ws = W + (size_t)s * N * 3;
+    const double* Vs = V + (size_t)s * N * 3;
+    if (!is_device_ptr) {
+      if ((st = to_device(h, h->staging, Ws, 3 * N, 0)) != EMPPP_OK) return st;
+      if ((st = to_device(h, h->staging + 3 * N, Vs, 3 * N, 0)) != EMPPP_OK) return st;
+      Ws = h->staging;
+      Vs = h->staging + 3 * N;
+    }
+    CU(launch_scatter_slot(h->ds, p, Ws, Vs, h->stream));
+    if (!is_device_ptr) CU(cudaStreamSynchronize(h->stream));  // staging is reused by the next slot
+  }
+  CU(cudaMemcpyAsync(h->ds.slot_t, ht.data(), sizeof(double) * h->D, cudaMemcpyHostToDevice, h->stream));
+  const double* du = u;
+  const double* dw = w;
+  if (!is_device_ptr) {
+    if ((st = to_device(h, h->staging, u, 3 * N, 0)) != EMPPP_OK) return st;
+    if (w && (st = to_device(h, h->staging + 6 * N, w, N, 0)) != EMPPP_OK) return st;
+    du = h->staging;
+    dw = w ? h->staging + 6 * N : nullptr;
+  }
+  CU(launch_set_state(h->ds, n, hT[nslots - 1], h->dt, du, dw, h->stream));
+  CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
+  CU(cudaMemsetAsync(h->ds.Bout, 0, sizeof(double) * N * 3, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->n = n;
+  h->t = hT[nslots - 1];
+  h->has_state = true;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_get_history(emppp_handle h, int64_t* n_now, int32_t* nslots, double* T, double* W,
+                                         double* V, double* u, int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  const size_t N = (size_t)h->N;
+  const int32_t ns = (int32_t)(h->n + 1 < h->D ? h->n + 1 : h->D);
+  std::vector<double> ht((size_t)h->D);
+  CU(cudaMemcpyAsync(ht.data(), h->ds.slot_t, sizeof(double) * h->D, cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  std::vector<double> hTs(ns);
+  for (int s = 0; s < ns; s++) {
+    const int64_t k = h->n - ns + 1 + s;
+    const int p = (int)(k % h->D);
+    hTs[s] = ht[p];
+    double* Ws = W ? W + (size_t)s * N * 3 : nullptr;
+    double* Vs = V ? V + (size_t)s * N * 3 : nullptr;
+    if (is_device_ptr) {
+      CU(launch_gather_slot(h->ds, p, Ws, Vs, h->stream));
+    } else {
+      CU(launch_gather_slot(h->ds, p, h->staging, h->staging + 3 * N, h->stream));
+      if (Ws && (st = from_device(h, Ws, h->staging, 3 * N, 0)) != EMPPP_OK) return st;
+      if (Vs && (st = from_device(h, Vs, h->staging + 3 * N, 3 * N, 0)) != EMPPP_OK) return st;
+      CU(cudaStreamSynchronize(h->stream));
+    }
+  }
+  if (T) {
+    if (is_device_ptr)
+      CU(cudaMemcpyAsync(T, hTs.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, h->stream));
+    else
+      memcpy(T, hTs.data(), sizeof(double) * ns);
+  }
+  if (u && (st = from_device(h, u, h->ds.u, 3 * N, is_device_ptr)) != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  if (n_now) *n_now = h->n;
+  if (nslots) *nslots = ns;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_bext* bext) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if (nsteps < 0) return fail(EMPPP_ERR_ARG, "nsteps must be >= 0");
+  BextParams bp{};
+  if (bext) {
+    if (bext->kind < EMPPP_BEXT_NONE || bext->kind > EMPPP_BEXT_DIPOLE)
+      return fail(EMPPP_ERR_ARG, "unknown background field kind %d", bext->kind);
+    bp.kind = bext->kind;
+    for (int c = 0; c < 3; c++) {
+      bp.b[c] = bext->b[c];
+      bp.center[c] = bext->center[c];
+    }
+    bp.m0 = bext->m0;
+  }
+  const int split = choose_split(h);
+  for (int64_t k = 0; k < nsteps; k++) {
+    CU(launch_prep(h->ds, h->stream));
+    if (h->opt.pair_fields) {
+      CU(launch_pair_fp64(h->ds, h->opt.proposal, split, h->stream));
+      if (split > 1) CU(launch_reduce_partials(h->ds, split, h->stream));
+    } else {
+      CU(launch_zero_self(h->ds, h->stream));
+    }
+    CU(launch_push(h->ds, bp, h->stream));
+    CU(launch_advance(h->ds, h->stream));
+    h->n += 1;
+    h->t = h->t + h->dt;
+  }
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_get_state(emppp_handle h, double* x, double* u, double* t_now, int64_t* n_now,
+                                       int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  const size_t N = (size_t)h->N;
+  if (x) {
+    if (is_device_ptr) {
+      CU(launch_gather_positions(h->ds, x, h->stream));
+    } else {
+      CU(launch_gather_positions(h->ds, h->staging, h->stream));
+      if ((st = from_device(h, x, h->staging, 3 * N, 0)) != EMPPP_OK) return st;
+    }
+  }
+  if (u && (st = from_device(h, u, h->ds.u, 3 * N, is_device_ptr)) != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  if (t_now) *t_now = h->t;
+  if (n_now) *n_now = h->n;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_get_fields(emppp_handle h, double* E, double* B, int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  const size_t N = (size_t)h->N;
+  if (E && (st = from_device(h, E, h->ds.Eself, 3 * N, is_device_ptr)) != EMPPP_OK) return st;
+  if (B && (st = from_device(h, B, h->ds.Bout, 3 * N, is_device_ptr)) != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!out) return fail(EMPPP_ERR_ARG, "out is NULL");
+  unsigned long long hs[kStatCount];
+  CU(cudaMemcpyAsync(hs, h->ds.stats, sizeof(hs), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  out->pairs = h->N * (h->N - 1);
+  out->out_of_history = (int64_t)hs[kStatOOH];
+  out->shortcut = (int64_t)hs[kStatShortcut];
+  out->bisection = (int64_t)hs[kStatBisect];
+  out->node_tests = (int64_t)hs[kStatNodeTests];
+  out->guard_fallbacks = (int64_t)hs[kStatGuard];
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!opt) return fail(EMPPP_ERR_ARG, "opt is NULL");
+  if ((st = validate_options(opt)) != EMPPP_OK) return st;
+  h->opt = *opt;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_set_stream(emppp_handle h, void* cuda_stream) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_synchronize(emppp_handle h) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  CU(cudaGetLastError());
+  return read_err(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal declarations of the EM-PP CUDA library (not part of the C ABI).
+//
+// Device data layout (one GPU, all resident in HBM):
+//   rec64  [N][D][6] double   history ring, source-major: slot p of particle j holds the position
+//                             w (3) and velocity v (3) at the time slot_t[p]; slots are used
+//                             modulo D, so one particle's whole history is one contiguous 48*D-byte
+//                             run (pair gathers of one source stay within a few cache lines).
+//   rec32  [N][D][12] float   FP32 shadow of rec64 for the mixed path: hi(3) lo(3) of w - origin,
+//                             v(3), pad(3); 48-byte records, three 16-byte loads each.
+//   slot_t [D]                time stamp of each physical slot.
+//   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
+//                             1 / (t_{k+1} - t_k).
+//   u      [N][3]             present proper velocities (FP64).
+//   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
+//   StepState (device)        present step n, t_n, dt and the derived window k0..n; kernels read it
+//                             so that one captured step can be replayed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace emppp {
+
+// CODATA 2018 (SI)
+constexpr double kC = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kPi = 3.14159265358979323846;
+
+// device error word bits
+enum : int {
+  kErrDisc = 1,      // negative discriminant or C2 <= 0 in eq:dt (|v| >= c)
+  kErrCoincide = 2,  // eta = 0 or eta . v' <= 0
+  kErrNonFinite = 4, // non-finite field or state
+  kErrTimeout = 8,   // a bounded wait gave up
+};
+
+struct StepState {
+  long long n;   // present (absolute) step index
+  double t;      // t_n
+  double dt;     // step of the next push
+  long long k0;  // earliest usable slot max(0, n - D + 1)
+  int p0;        // physical slot of k0
+  int pn;        // physical slot of n
+};
+
+// retarded-time search proposals (values of emppp_proposal)
+enum { kPropBisect = 0, kPropClosedForm = 1, kPropMlp = 2 };
+
+// counters, reset by the prep kernel of every step
+enum { kStatOOH = 0, kStatShortcut = 1, kStatBisect = 2, kStatNodeTests = 3, kStatGuard = 4, kStatCount = 8 };
+
+struct SlotTables {
+  double* lhs64;    // [D] (c (t_n - t_k))^2, formed as c*(t_n - t_k) then squared (no FMA)
+  float* lhs32;     // [D] same, FP32
+  float* ct32;      // [D] c (t_n - t_k), FP32
+  double* inv_dtk;  // [D] 1 / (t_{k+1} - t_k) for k < n
+};
+
+struct DeviceState {
+  long long N;
+  int D;
+  double* rec64;
+  float* rec32;
+  double* slot_t;
+  SlotTables tab;
+  double* u;
+  double* wts;  // [N] weights (always present; 1 by default)
+  double* Eself;
+  double* Bself;
+  double* Bout;
+  double* partial;  // [S][N][6] per-source-slice partial sums
+  int max_split;
+  StepState* state;
+  unsigned long long* stats;  // [kStatCount]
+  int* err;
+  double origin[3];  // origin of the FP32 hi/lo split
+};
+
+struct BextParams {
+  int kind;
+  double b[3];
+  double m0;
+  double center[3];
+};
+
+// ---- launchers (each in its own translation unit) ------------------------------------------
+// ring.cu
+cudaError_t launch_init_slot0(const DeviceState& s, const double* x, const double* u, const double* w,
+                              cudaStream_t st);
+cudaError_t launch_scatter_slot(const DeviceState& s, int p, const double* W, const double* V, cudaStream_t st);
+cudaError_t launch_gather_slot(const DeviceState& s, int p, double* W, double* V, cudaStream_t st);
+cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, const double* u,
+                             const double* w, cudaStream_t st);
+cudaError_t launch_prep(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_advance(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st);
+// pair_fp64.cu
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int split, cudaStream_t st);
+cudaError_t launch_reduce_partials(const DeviceState& s, int split, cudaStream_t st);
+cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
+// push.cu
+cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st);
+
+}  // namespace emppp

@@ -1,0 +1,393 @@
+// FP64 all-pairs Lienard-Wiechert field evaluation with the retarded-time solve (Sec. 2.1-2.2).
+//
+// One thread owns one target i (present position r = x_i^n at t = t_n) and walks the sources j of
+// its slice. Per pair:
+//   1. bracket the retarded time in j's history with the node test
+//        P(k):  (c (t - t_k))^2 <= |r - w_{j,k}|^2       (true: t_r at or before t_k)
+//      evaluated in FP64 in the same operation order as the reference (so decisions agree bit for
+//      bit): out-of-history if P(k0), near-field shortcut if not P(n-1), else bisection (Sec. 2.2);
+//      or, with the closed-form proposal, a guarded galloping search started at the slot predicted
+//      by uniform motion from j's present state. Both return the unique sign change of P.
+//   2. linear reconstruction (eq:dt, eq:linear; eq:linear2 out of history): delta t from the
+//      quadratic, w = w1 + v1 dt, v = v1 + (dt / (t2 - t1)) (v2 - v1), a = (v2 - v1) / (t2 - t1).
+//   3. Lienard-Wiechert E (eq:LW_E) and B = eta_hat x E / c (eq:LW_B), summed over j != i in
+//      blocks of kSumBlock sources (blocked summation keeps the FP64 rounding error of a 65536-term
+//      sum near 1e-14 of the sum of magnitudes).
+// The arithmetic is FP64-pipe bound (GB300: 2 DFMA/clk/SM); everything that is not an FP64 result
+// (the guess, indices, loads) runs on the FP32/INT pipes beside it.
+#include "emppp_internal.cuh"
+
+namespace emppp {
+
+namespace {
+
+constexpr int kBlock = 128;
+constexpr int kSumBlock = 64;
+constexpr double kCoulomb = 1.0 / (4.0 * kPi * kEps0);
+
+struct PairArgs {
+  const double* __restrict__ rec64;
+  const float* __restrict__ rec32;
+  const double* __restrict__ slot_t;
+  const double* __restrict__ lhs64;
+  const double* __restrict__ inv_dtk;
+  const double* __restrict__ wts;
+  const StepState* __restrict__ state;
+  double* __restrict__ out;  // [S][N][6] (S = 1: [N][6] temporary) -- see launch
+  double* __restrict__ E;
+  double* __restrict__ B;
+  unsigned long long* stats;
+  int* err;
+  long long N;
+  int D;
+  long long chunk;  // sources per slice
+};
+
+// node test P(k) with the reference operation order (no contraction)
+__device__ __forceinline__ bool node_test(double r0, double r1, double r2, const double* __restrict__ w,
+                                          double lhs) {
+  const double d0 = __dsub_rn(r0, __ldg(w + 0));
+  const double d1 = __dsub_rn(r1, __ldg(w + 1));
+  const double d2 = __dsub_rn(r2, __ldg(w + 2));
+  const double rhs = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+  return lhs <= rhs;
+}
+
+struct Window {
+  long long k0, n;
+  int p0, D;
+  __device__ __forceinline__ int phys(long long k) const {
+    int p = p0 + (int)(k - k0);
+    return p >= D ? p - D : p;
+  }
+};
+
+// Guess of the older bracket node from uniform motion of the source from its present state:
+// t - t_r = [d.v + sqrt((d.v)^2 + (c^2 - v^2) d^2)] / (c^2 - v^2), d = r - w_n (FP32 inputs).
+__device__ __forceinline__ long long closed_form_guess(float r0, float r1, float r2, const float* __restrict__ q,
+                                                       float inv_dt, const Window& win) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(q));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(q) + 1);
+  const float4 c4 = __ldg(reinterpret_cast<const float4*>(q) + 2);
+  const float d0 = r0 - a.x, d1 = r1 - a.y, d2 = r2 - a.z;
+  const float v0 = b.z, v1 = b.w, v2 = c4.x;
+  const float cc = (float)kC;
+  const float dv = d0 * v0 + d1 * v1 + d2 * v2;
+  const float dd = d0 * d0 + d1 * d1 + d2 * d2;
+  const float c2v2 = cc * cc - (v0 * v0 + v1 * v1 + v2 * v2);
+  const float tau = (dv + sqrtf(fmaxf(dv * dv + c2v2 * dd, 0.f))) / fmaxf(c2v2, 1e-30f);
+  const float steps = floorf(tau * inv_dt);
+  long long k = win.n - 1 - (long long)fminf(steps, 1e9f);
+  if (k < win.k0) k = win.k0;
+  if (k > win.n - 1) k = win.n - 1;
+  return k;
+}
+
+}  // namespace
+
+template <int PROP>
+__global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
+  const long long N = a.N;
+  const int D = a.D;
+  const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
+  const bool active = i < N;
+  const long long ic = active ? i : 0;
+
+  Window win;
+  win.n = a.state->n;
+  win.k0 = a.state->k0;
+  win.p0 = a.state->p0;
+  win.D = D;
+  const int pn = a.state->pn;
+  const double t = a.state->t;
+
+  const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
+  const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
+  float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f, inv_dt = 0.f;
+  if (PROP == kPropClosedForm) {
+    const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
+    rh0 = q[0];
+    rh1 = q[1];
+    rh2 = q[2];
+    inv_dt = (float)(1.0 / a.state->dt);
+  }
+
+  const long long j_begin = (long long)blockIdx.y * a.chunk;
+  const long long j_end = min(N, j_begin + a.chunk);
+
+  double Et[3] = {0, 0, 0}, Bt[3] = {0, 0, 0};
+  double Ep[3] = {0, 0, 0}, Bp[3] = {0, 0, 0};
+  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
+  int errbits = 0;
+  int in_block = 0;
+
+  const double c2 = kC * kC;
+  for (long long j = j_begin; active && j < j_end; ++j) {
+    if (j == i) continue;
+    const double* src = a.rec64 + (size_t)j * D * 6;
+    // ---- 1. bracket ------------------------------------------------------------------------
+    long long k1;
+    int br;
+    if (PROP == kPropBisect) {
+      n_tests += 1;
+      if (node_test(r0, r1, r2, src + win.p0 * 6, __ldg(a.lhs64 + win.p0))) {
+        k1 = win.k0;
+        br = 0;
+      } else {
+        n_tests += 1;
+        const int pm1 = win.phys(win.n - 1);
+        if (!node_test(r0, r1, r2, src + pm1 * 6, __ldg(a.lhs64 + pm1))) {
+          k1 = win.n - 1;
+          br = 1;
+        } else {
+          long long lo = win.k0, hi = win.n;
+          while (hi - lo > 1) {
+            const long long m = (lo + hi) >> 1;
+            const int pm = win.phys(m);
+            n_tests += 1;
+            if (node_test(r0, r1, r2, src + pm * 6, __ldg(a.lhs64 + pm)))
+              hi = m;
+            else
+              lo = m;
+          }
+          k1 = lo;
+          br = 2;
+        }
+      }
+    } else {
+      // guarded galloping search from the closed-form guess
+      if (win.n == win.k0) {
+        k1 = win.k0;
+        br = 0;
+        n_tests += 1;
+      } else {
+        const long long kg =
+            closed_form_guess(rh0, rh1, rh2, a.rec32 + ((size_t)j * D + pn) * 12, inv_dt, win);
+        long long lo, hi;
+        bool ooh = false;
+        n_tests += 1;
+        int pg = win.phys(kg);
+        if (node_test(r0, r1, r2, src + pg * 6, __ldg(a.lhs64 + pg))) {
+          hi = kg;
+          long long s = 1;
+          for (;;) {
+            if (hi == win.k0) {
+              ooh = true;
+              break;
+            }
+            lo = hi - s;
+            if (lo < win.k0) lo = win.k0;
+            const int pl = win.phys(lo);
+            n_tests += 1;
+            if (!node_test(r0, r1, r2, src + pl * 6, __ldg(a.lhs64 + pl))) break;
+            hi = lo;
+            s <<= 1;
+          }
+        } else {
+          lo = kg;
+          long long s = 1;
+          for (;;) {
+            hi = lo + s;
+            if (hi >= win.n) {
+              hi = win.n;
+              break;
+            }
+            const int ph = win.phys(hi);
+            n_tests += 1;
+            if (node_test(r0, r1, r2, src + ph * 6, __ldg(a.lhs64 + ph))) break;
+            lo = hi;
+            s <<= 1;
+          }
+        }
+        if (ooh) {
+          k1 = win.k0;
+          br = 0;
+        } else {
+          while (hi - lo > 1) {
+            const long long m = (lo + hi) >> 1;
+            const int pm = win.phys(m);
+            n_tests += 1;
+            if (node_test(r0, r1, r2, src + pm * 6, __ldg(a.lhs64 + pm)))
+              hi = m;
+            else
+              lo = m;
+          }
+          k1 = lo;
+          br = (k1 == win.n - 1) ? 1 : 2;
+        }
+      }
+    }
+    if (br == 0)
+      n_ooh++;
+    else if (br == 1)
+      n_sc++;
+    else
+      n_bi++;
+
+    // ---- 2. reconstruction (eq:dt, eq:linear, eq:linear2) -------------------------------------
+    const int p1 = win.phys(k1);
+    const double2* R1 = reinterpret_cast<const double2*>(src + p1 * 6);
+    const double2 x01 = __ldg(R1), x23 = __ldg(R1 + 1), x45 = __ldg(R1 + 2);
+    const double w10 = x01.x, w11 = x01.y, w12 = x23.x;
+    const double v10 = x23.y, v11 = x45.x, v12 = x45.y;
+    const double T1 = t - __ldg(a.slot_t + p1);
+    const double d0 = r0 - w10, d1 = r1 - w11, d2 = r2 - w12;
+    const double C2 = c2 - (v10 * v10 + v11 * v11 + v12 * v12);
+    const double hb = (d0 * v10 + d1 * v11 + d2 * v12) - c2 * T1;  // C1 / 2
+    const double C0 = c2 * T1 * T1 - (d0 * d0 + d1 * d1 + d2 * d2);
+    const double qd = hb * hb - C2 * C0;  // disc / 4
+    if (!(C2 > 0.0) || !(qd >= 0.0)) {
+      errbits |= kErrDisc;
+      continue;
+    }
+    const double sq = sqrt(qd);
+    // smaller root of C2 x^2 + 2 hb x + C0 without cancellation
+    const double dt = (hb <= 0.0) ? C0 / (sq - hb) : -(hb + sq) / C2;
+    const double w0 = w10 + v10 * dt, w1 = w11 + v11 * dt, w2 = w12 + v12 * dt;
+    double v0 = v10, v1 = v11, v2 = v12, a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    if (br != 0) {
+      const int p2 = p1 + 1 == D ? 0 : p1 + 1;
+      const double2* R2 = reinterpret_cast<const double2*>(src + p2 * 6);
+      const double2 y23 = __ldg(R2 + 1), y45 = __ldg(R2 + 2);
+      const double idt = __ldg(a.inv_dtk + p1);
+      a0 = (y23.y - v10) * idt;
+      a1 = (y45.x - v11) * idt;
+      a2 = (y45.y - v12) * idt;
+      v0 = v10 + dt * a0;
+      v1 = v11 + dt * a1;
+      v2 = v12 + dt * a2;
+    }
+    // ---- 3. Lienard-Wiechert fields ----------------------------------------------------------
+    const double e0 = r0 - w0, e1 = r1 - w1, e2 = r2 - w2;
+    const double R2s = e0 * e0 + e1 * e1 + e2 * e2;
+    const double invR = rsqrt(R2s);
+    const double R = R2s * invR;
+    const double cinvR = kC * invR;
+    const double vp0 = e0 * cinvR - v0, vp1 = e1 * cinvR - v1, vp2 = e2 * cinvR - v2;
+    const double evp = e0 * vp0 + e1 * vp1 + e2 * vp2;
+    if (!(R2s > 0.0) || !(evp > 0.0)) {
+      errbits |= kErrCoincide;
+      continue;
+    }
+    const double c2mv2 = c2 - (v0 * v0 + v1 * v1 + v2 * v2);
+    // eta x (v' x a)
+    const double xa0 = vp1 * a2 - vp2 * a1, xa1 = vp2 * a0 - vp0 * a2, xa2 = vp0 * a1 - vp1 * a0;
+    const double ac0 = e1 * xa2 - e2 * xa1, ac1 = e2 * xa0 - e0 * xa2, ac2 = e0 * xa1 - e1 * xa0;
+    const double ievp = 1.0 / evp;
+    const double q = -kQe * __ldg(a.wts + j);
+    const double pref = kCoulomb * q * R * (ievp * ievp * ievp);
+    const double E0 = pref * (c2mv2 * vp0 + ac0), E1 = pref * (c2mv2 * vp1 + ac1), E2 = pref * (c2mv2 * vp2 + ac2);
+    const double bs = invR * (1.0 / kC);
+    Ep[0] += E0;
+    Ep[1] += E1;
+    Ep[2] += E2;
+    Bp[0] += (e1 * E2 - e2 * E1) * bs;
+    Bp[1] += (e2 * E0 - e0 * E2) * bs;
+    Bp[2] += (e0 * E1 - e1 * E0) * bs;
+    if (++in_block == kSumBlock) {
+      in_block = 0;
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        Et[c] += Ep[c];
+        Bt[c] += Bp[c];
+        Ep[c] = 0.0;
+        Bp[c] = 0.0;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    Et[c] += Ep[c];
+    Bt[c] += Bp[c];
+  }
+  if (active) {
+    if (gridDim.y == 1) {
+      for (int c = 0; c < 3; c++) {
+        a.E[3 * i + c] = Et[c];
+        a.B[3 * i + c] = Bt[c];
+      }
+    } else {
+      double* o = a.out + ((size_t)blockIdx.y * N + i) * 6;
+      for (int c = 0; c < 3; c++) {
+        o[c] = Et[c];
+        o[3 + c] = Bt[c];
+      }
+    }
+  }
+  // counters: one atomic per warp and counter
+  n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
+  n_sc = __reduce_add_sync(0xffffffffu, n_sc);
+  n_bi = __reduce_add_sync(0xffffffffu, n_bi);
+  n_tests = __reduce_add_sync(0xffffffffu, n_tests);
+  errbits = __reduce_or_sync(0xffffffffu, errbits);
+  if ((threadIdx.x & 31) == 0) {
+    if (n_ooh) atomicAdd(a.stats + kStatOOH, (unsigned long long)n_ooh);
+    if (n_sc) atomicAdd(a.stats + kStatShortcut, (unsigned long long)n_sc);
+    if (n_bi) atomicAdd(a.stats + kStatBisect, (unsigned long long)n_bi);
+    if (n_tests) atomicAdd(a.stats + kStatNodeTests, (unsigned long long)n_tests);
+    if (errbits) atomicOr(a.err, errbits);
+  }
+}
+
+// E_i = sum over slices s of partial[s][i] (fixed order).
+__global__ void reduce_partials_kernel(const double* __restrict__ part, int S, long long N, double* __restrict__ E,
+                                       double* __restrict__ B) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = 0; s < S; s++) {
+    const double* o = part + ((size_t)s * N + i) * 6;
+#pragma unroll
+    for (int c = 0; c < 6; c++) acc[c] += o[c];
+  }
+  for (int c = 0; c < 3; c++) {
+    E[3 * i + c] = acc[c];
+    B[3 * i + c] = acc[3 + c];
+  }
+}
+
+__global__ void zero_kernel(double* __restrict__ a, double* __restrict__ b, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    a[i] = 0.0;
+    b[i] = 0.0;
+  }
+}
+
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int split, cudaStream_t st) {
+  PairArgs a;
+  a.rec64 = s.rec64;
+  a.rec32 = s.rec32;
+  a.slot_t = s.slot_t;
+  a.lhs64 = s.tab.lhs64;
+  a.inv_dtk = s.tab.inv_dtk;
+  a.wts = s.wts;
+  a.state = s.state;
+  a.out = s.partial;
+  a.E = s.Eself;
+  a.B = s.Bself;
+  a.stats = s.stats;
+  a.err = s.err;
+  a.N = s.N;
+  a.D = s.D;
+  if (split < 1) split = 1;
+  a.chunk = (s.N + split - 1) / split;
+  dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock), (unsigned)split);
+  if (proposal == kPropClosedForm)
+    pair_fp64_kernel<kPropClosedForm><<<grid, kBlock, 0, st>>>(a);
+  else
+    pair_fp64_kernel<kPropBisect><<<grid, kBlock, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const DeviceState& s, int split, cudaStream_t st) {
+  reduce_partials_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s.partial, split, s.N, s.Eself, s.Bself);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st) {
+  zero_kernel<<<(unsigned)((3 * s.N + 255) / 256), 256, 0, st>>>(s.Eself, s.Bself, 3 * s.N);
+  return cudaGetLastError();
+}
+
+}  // namespace emppp

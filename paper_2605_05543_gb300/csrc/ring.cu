@@ -1,0 +1,172 @@
+// History ring (Sec. 2.2: positions and velocities stored at discrete steps; the acceleration is not
+// stored) and per-step slot tables.
+#include "emppp_internal.cuh"
+
+namespace emppp {
+
+// Writes record (j, p) of both rings from an FP64 position and velocity.
+__device__ __forceinline__ void write_record(const DeviceState& s, long long j, int p, double w0, double w1,
+                                             double w2, double v0, double v1, double v2) {
+  double* r = s.rec64 + ((size_t)j * s.D + p) * 6;
+  reinterpret_cast<double2*>(r)[0] = make_double2(w0, w1);
+  reinterpret_cast<double2*>(r)[1] = make_double2(w2, v0);
+  reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
+  const double d0 = w0 - s.origin[0], d1 = w1 - s.origin[1], d2 = w2 - s.origin[2];
+  const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
+  const float l0 = (float)(d0 - (double)h0), l1 = (float)(d1 - (double)h1), l2 = (float)(d2 - (double)h2);
+  float4* q = reinterpret_cast<float4*>(s.rec32 + ((size_t)j * s.D + p) * 12);
+  q[0] = make_float4(h0, h1, h2, l0);
+  q[1] = make_float4(l1, l2, (float)v0, (float)v1);
+  q[2] = make_float4((float)v2, 0.f, 0.f, 0.f);
+}
+
+// v = u / gamma with gamma = sqrt(1 + u.u / c^2), in the operation order of a plain FP64 evaluation
+__device__ __forceinline__ void velocity_of(double u0, double u1, double u2, double& v0, double& v1, double& v2) {
+  const double uu = __dadd_rn(__dadd_rn(__dmul_rn(u0, u0), __dmul_rn(u1, u1)), __dmul_rn(u2, u2));
+  const double g = __dsqrt_rn(__dadd_rn(1.0, __ddiv_rn(uu, __dmul_rn(kC, kC))));
+  v0 = __ddiv_rn(u0, g);
+  v1 = __ddiv_rn(u1, g);
+  v2 = __ddiv_rn(u2, g);
+}
+
+__global__ void init_slot0_kernel(DeviceState s, const double* __restrict__ x, const double* __restrict__ u,
+                                  const double* __restrict__ w) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    s.slot_t[0] = 0.0;
+    *s.err = 0;
+  }
+  if (i >= s.N) return;
+  const double u0 = u[3 * i], u1 = u[3 * i + 1], u2 = u[3 * i + 2];
+  double v0, v1, v2;
+  velocity_of(u0, u1, u2, v0, v1, v2);
+  write_record(s, i, 0, x[3 * i], x[3 * i + 1], x[3 * i + 2], v0, v1, v2);
+  s.u[3 * i] = u0;
+  s.u[3 * i + 1] = u1;
+  s.u[3 * i + 2] = u2;
+  s.wts[i] = w ? w[i] : 1.0;
+}
+
+__global__ void scatter_slot_kernel(DeviceState s, int p, const double* __restrict__ W, const double* __restrict__ V) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s.N) return;
+  write_record(s, j, p, W[3 * j], W[3 * j + 1], W[3 * j + 2], V[3 * j], V[3 * j + 1], V[3 * j + 2]);
+}
+
+__global__ void gather_slot_kernel(DeviceState s, int p, double* __restrict__ W, double* __restrict__ V) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s.N) return;
+  const double* r = s.rec64 + ((size_t)j * s.D + p) * 6;
+  for (int c = 0; c < 3; c++) {
+    if (W) W[3 * j + c] = r[c];
+    if (V) V[3 * j + c] = r[3 + c];
+  }
+}
+
+__global__ void set_state_kernel(DeviceState s, long long n, double t, double dt, const double* __restrict__ u,
+                                 const double* __restrict__ w) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) {
+    s.state->n = n;
+    s.state->t = t;
+    s.state->dt = dt;
+    *s.err = 0;
+  }
+  if (i >= s.N) return;
+  if (u) {
+    s.u[3 * i] = u[3 * i];
+    s.u[3 * i + 1] = u[3 * i + 1];
+    s.u[3 * i + 2] = u[3 * i + 2];
+  }
+  s.wts[i] = w ? w[i] : 1.0;
+}
+
+// Per-step slot tables over the usable window k0..n (Sec. 2.2): the squared light-travel distance
+// (c (t_n - t_k))^2 in exactly the operation order of the reference evaluation (so that the FP64
+// node test decides identically), its FP32 rounding, c (t_n - t_k) in FP32, and 1 / (t_{k+1} - t_k).
+__global__ void prep_kernel(DeviceState s) {
+  const long long n = s.state->n;
+  const double t_n = s.state->t;
+  const long long k0 = n - s.D + 1 > 0 ? n - s.D + 1 : 0;
+  const int p0 = (int)(k0 % s.D);
+  const int pn = (int)(n % s.D);
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    s.state->k0 = k0;
+    s.state->p0 = p0;
+    s.state->pn = pn;
+    for (int c = 0; c < kStatCount; c++) s.stats[c] = 0ull;
+  }
+  const int nwin = (int)(n - k0 + 1);
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nwin; l += gridDim.x * blockDim.x) {
+    int p = p0 + l;
+    if (p >= s.D) p -= s.D;
+    const double tk = s.slot_t[p];
+    const double ct = __dmul_rn(kC, __dsub_rn(t_n, tk));
+    const double lhs = __dmul_rn(ct, ct);
+    s.tab.lhs64[p] = lhs;
+    s.tab.lhs32[p] = (float)lhs;
+    s.tab.ct32[p] = (float)ct;
+    if (l + 1 < nwin) {
+      int q = p + 1 == s.D ? 0 : p + 1;
+      s.tab.inv_dtk[p] = 1.0 / (s.slot_t[q] - tk);
+    } else {
+      s.tab.inv_dtk[p] = 0.0;
+    }
+  }
+}
+
+__global__ void advance_kernel(StepState* state) {
+  state->n = state->n + 1;
+  state->t = state->t + state->dt;
+}
+
+__global__ void gather_positions_kernel(DeviceState s, double* __restrict__ x) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s.N) return;
+  const int pn = (int)(s.state->n % s.D);
+  const double* r = s.rec64 + ((size_t)j * s.D + pn) * 6;
+  x[3 * j] = r[0];
+  x[3 * j + 1] = r[1];
+  x[3 * j + 2] = r[2];
+}
+
+static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+cudaError_t launch_init_slot0(const DeviceState& s, const double* x, const double* u, const double* w,
+                              cudaStream_t st) {
+  init_slot0_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, x, u, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_slot(const DeviceState& s, int p, const double* W, const double* V, cudaStream_t st) {
+  scatter_slot_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, p, W, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_slot(const DeviceState& s, int p, double* W, double* V, cudaStream_t st) {
+  gather_slot_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, p, W, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, const double* u,
+                             const double* w, cudaStream_t st) {
+  set_state_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, n, t, dt, u, w);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep(const DeviceState& s, cudaStream_t st) {
+  prep_kernel<<<1, 1024, 0, st>>>(s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(const DeviceState& s, cudaStream_t st) {
+  advance_kernel<<<1, 1, 0, st>>>(s.state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st) {
+  gather_positions_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, x);
+  return cudaGetLastError();
+}
+
+}  // namespace emppp

@@ -1,0 +1,286 @@
+"""Python binding of the EM-PP C ABI (``include/emppp.h``): argument marshalling only.
+
+Host arrays are numpy float64 arrays; device arrays are contiguous float64 CUDA tensors (their
+pointers are passed with ``is_device_ptr = 1``). Streams are ``torch.cuda.Stream`` objects or raw
+``cudaStream_t`` integers. Every computation runs in the library's CUDA kernels; if the library is
+missing this module raises instead of computing anything itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_lib = None
+
+OK, ERR_ARG, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_OOM = 0, -1, -2, -3, -4, -5, -6
+_STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NUMERIC", -4: "ERR_TIMEOUT", -5: "ERR_STATE",
+           -6: "ERR_OOM"}
+
+PRECISION = {"fp64": 0, "mixed": 1}
+PROPOSAL = {"bisect": 0, "closed_form": 1, "mlp": 2}
+BEXT = {"none": 0, "uniform": 1, "dipole": 2}
+
+
+class EmpppError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("pair_fields", ctypes.c_int32),
+                ("source_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class Bext(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("b", ctypes.c_double * 3),
+                ("m0", ctypes.c_double), ("center", ctypes.c_double * 3)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int64), ("out_of_history", ctypes.c_int64), ("shortcut", ctypes.c_int64),
+                ("bisection", ctypes.c_int64), ("node_tests", ctypes.c_int64), ("guard_fallbacks", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_H = ctypes.c_void_p
+
+# name -> (restype, argtypes); every symbol declared in include/emppp.h
+SIGNATURES = {
+    "emppp_default_options": (None, [ctypes.POINTER(Options)]),
+    "emppp_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(Options), _vp,
+                                    ctypes.POINTER(_H)]),
+    "emppp_destroy": (None, [_H]),
+    "emppp_set_particles": (ctypes.c_int, [_H, _vp, _vp, _vp, ctypes.c_int32]),
+    "emppp_set_history": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
+                                         ctypes.c_int32]),
+    "emppp_get_history": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), _vp, _vp,
+                                         _vp, _vp, ctypes.c_int32]),
+    "emppp_step": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.POINTER(Bext)]),
+    "emppp_get_state": (ctypes.c_int, [_H, _vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.c_int32]),
+    "emppp_get_fields": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int32]),
+    "emppp_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(Stats)]),
+    "emppp_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
+    "emppp_set_stream": (ctypes.c_int, [_H, _vp]),
+    "emppp_synchronize": (ctypes.c_int, [_H]),
+    "emppp_last_error": (ctypes.c_char_p, []),
+    "emppp_version": (ctypes.c_char_p, []),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library (raises if it is not built, unless build_if_missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"EM-PP CUDA library not built ({path}); run __graft_entry__.build()")
+        _build.build_library()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != OK:
+        raise EmpppError(st, load().emppp_last_error().decode())
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr(a, n_expected, name):
+    """(pointer, is_device) of a float64 host array or CUDA tensor with n_expected elements."""
+    if a is None:
+        return None, None
+    if _is_torch(a):
+        import torch
+
+        if a.dtype != torch.float64 or not a.is_contiguous() or not a.is_cuda:
+            raise ValueError(f"{name}: need a contiguous float64 CUDA tensor")
+        if a.numel() != n_expected:
+            raise ValueError(f"{name}: expected {n_expected} elements, got {a.numel()}")
+        return a.data_ptr(), 1
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]):
+        raise ValueError(f"{name}: need a C-contiguous float64 numpy array")
+    if a.size != n_expected:
+        raise ValueError(f"{name}: expected {n_expected} elements, got {a.size}")
+    return a.ctypes.data, 0
+
+
+def _same_kind(*pairs):
+    kinds = {k for _, k in pairs if k is not None}
+    if len(kinds) > 1:
+        raise ValueError("mix of host and device arrays in one call")
+    return kinds.pop() if kinds else 0
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def bext_none() -> Bext:
+    return Bext(kind=0)
+
+
+def bext_uniform(b) -> Bext:
+    e = Bext(kind=1)
+    for c in range(3):
+        e.b[c] = float(b[c])
+    return e
+
+
+def bext_dipole(m0: float, center=(0.0, 0.0, 0.0)) -> Bext:
+    e = Bext(kind=2, m0=float(m0))
+    for c in range(3):
+        e.center[c] = float(center[c])
+    return e
+
+
+def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_split=0) -> Options:
+    o = Options()
+    load().emppp_default_options(ctypes.byref(o))
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.proposal = PROPOSAL[proposal] if isinstance(proposal, str) else int(proposal)
+    o.pair_fields = 1 if pair_fields else 0
+    o.source_split = int(source_split)
+    return o
+
+
+class Solver:
+    """One EM-PP system of n particles with history depth `depth` and step dt (all on one GPU)."""
+
+    def __init__(self, n: int, depth: int, dt: float, precision="fp64", proposal="bisect", pair_fields=True,
+                 source_split=0, stream=None):
+        self.lib = load()
+        self.n = int(n)
+        self.depth = int(depth)
+        self.dt = float(dt)
+        self._h = _H()
+        self._opt = make_options(precision, proposal, pair_fields, source_split)
+        _check(self.lib.emppp_create(self.n, self.depth, self.dt, ctypes.byref(self._opt),
+                                     _stream_handle(stream), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            self.lib.emppp_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_options(self, precision=None, proposal=None, pair_fields=None, source_split=None):
+        o = self._opt
+        if precision is not None:
+            o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        if proposal is not None:
+            o.proposal = PROPOSAL[proposal] if isinstance(proposal, str) else int(proposal)
+        if pair_fields is not None:
+            o.pair_fields = 1 if pair_fields else 0
+        if source_split is not None:
+            o.source_split = int(source_split)
+        _check(self.lib.emppp_set_options(self._h, ctypes.byref(o)))
+
+    def set_stream(self, stream):
+        _check(self.lib.emppp_set_stream(self._h, _stream_handle(stream)))
+
+    def set_particles(self, x, u, w=None):
+        px, kx = _ptr(x, 3 * self.n, "x")
+        pu, ku = _ptr(u, 3 * self.n, "u")
+        pw, kw = _ptr(w, self.n, "w")
+        dev = _same_kind((px, kx), (pu, ku), (pw, kw))
+        _check(self.lib.emppp_set_particles(self._h, px, pu, pw, dev))
+
+    def set_history(self, n, T, W, V, u, w=None):
+        nslots = min(int(n) + 1, self.depth)
+        pT, kT = _ptr(T, nslots, "T")
+        pW, kW = _ptr(W, nslots * 3 * self.n, "W")
+        pV, kV = _ptr(V, nslots * 3 * self.n, "V")
+        pu, ku = _ptr(u, 3 * self.n, "u")
+        pw, kw = _ptr(w, self.n, "w")
+        dev = _same_kind((pT, kT), (pW, kW), (pV, kV), (pu, ku), (pw, kw))
+        _check(self.lib.emppp_set_history(self._h, int(n), nslots, pT, pW, pV, pu, pw, dev))
+
+    def get_history(self):
+        """(n, T, W, V, u) as numpy arrays (the most recent min(n+1, depth) slots)."""
+        T = np.zeros(self.depth)
+        W = np.zeros((self.depth, self.n, 3))
+        V = np.zeros((self.depth, self.n, 3))
+        u = np.zeros((self.n, 3))
+        n_now = ctypes.c_int64()
+        ns = ctypes.c_int32()
+        _check(self.lib.emppp_get_history(self._h, ctypes.byref(n_now), ctypes.byref(ns), T.ctypes.data,
+                                          W.ctypes.data, V.ctypes.data, u.ctypes.data, 0))
+        k = ns.value
+        return n_now.value, T[:k].copy(), W[:k].copy(), V[:k].copy(), u
+
+    def step(self, nsteps=1, bext=None):
+        _check(self.lib.emppp_step(self._h, int(nsteps), None if bext is None else ctypes.byref(bext)))
+
+    def get_state(self, x=None, u=None):
+        """Returns (x, u, t, n). Pass preallocated host arrays or CUDA tensors to fill them in place."""
+        if x is None and u is None:
+            x = np.zeros((self.n, 3))
+            u = np.zeros((self.n, 3))
+        px, kx = _ptr(x, 3 * self.n, "x")
+        pu, ku = _ptr(u, 3 * self.n, "u")
+        dev = _same_kind((px, kx), (pu, ku))
+        t = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(self.lib.emppp_get_state(self._h, px, pu, ctypes.byref(t), ctypes.byref(n), dev))
+        return x, u, t.value, n.value
+
+    def get_fields(self, E=None, B=None):
+        if E is None and B is None:
+            E = np.zeros((self.n, 3))
+            B = np.zeros((self.n, 3))
+        pE, kE = _ptr(E, 3 * self.n, "E")
+        pB, kB = _ptr(B, 3 * self.n, "B")
+        dev = _same_kind((pE, kE), (pB, kB))
+        _check(self.lib.emppp_get_fields(self._h, pE, pB, dev))
+        return E, B
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self.lib.emppp_get_stats(self._h, ctypes.byref(s)))
+        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+
+    def synchronize(self):
+        _check(self.lib.emppp_synchronize(self._h))
+
+
+def version() -> str:
+    return load().emppp_version().decode()
