@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark: Lienard-Wiechert pair interactions per second, retarded-time solve included, at N = 65536.
+
+Workload (seeded, synthetic; shaped like the paper's Gaussian bunches): a free-expansion electron
+bunch of N = 65536, sigma = 20 um, gamma0 = 3 (energy spread 1e-3, transverse momentum spread
+1e-4 p0), dt = 1e-15 s, history depth 1024, no external field, taken at step 250 of its 500-step run
+with a 251-slot stored history. One benchmark step = one full EM-PP step through the C ABI: slot
+tables, the all-pairs field kernel (bracket + reconstruction + LW fields + sums), the Higuera-Cary
+push and the ring append. pairs/step = N (N - 1).
+
+  python bench.py [--gpus N --steps K --warmup W] [--path mixed|fp64] [--proposal ...]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample of the same workload
+
+Prints one JSON line (rank 0). With N > 1 ranks (torchrun), every rank runs an independent replica
+of the workload (no data-path collective: this path is single-GPU) and value = all pairs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LW pair interactions/s incl. retarded solve, N=65536; rel. field err vs FP64"
+UNIT = "pairs/s"
+WL = dict(N=65536, sigma=20e-6, gamma0=3.0, dt=1e-15, depth=1024, n0=250, seed=0)
+WORKLOAD_NAME = ("free-expansion Gaussian bunch N=65536 sigma=20um gamma0=3 dt=1e-15s depth=1024, "
+                 "at step 250 of 500 with a 251-slot history")
+
+# peaks of the plain ALU pipes, from the unit counts and the maximum SM clock of GB300:
+# 152 SMs x 128 FP32 lanes (FMA = 2 flop) and 152 SMs x 2 FP64 lanes per clock, at 2.07 GHz
+# (DFMA/FFMA-chain microbenchmarks on this GPU reach 1.194 and 74.6 TFLOP/s at the load clock)
+SM_COUNT = 152
+SM_MAX_GHZ = 2.07
+PEAK_FP64_TFLOPS = SM_COUNT * 2 * 2 * SM_MAX_GHZ / 1e3
+PEAK_FP32_TFLOPS = SM_COUNT * 128 * 2 * SM_MAX_GHZ / 1e3
+
+# algorithmic flops of one ordered pair (+ - * / sqrt = 1 flop each; per-slot constants excluded):
+#   every pair: quadratic + reconstruction of the retarded position 40, LW E and B 73, sums 6
+#   regular bracket (not out of history): velocity interpolation and acceleration 18
+#   every node test c^2 (t - t_k)^2 <= |r - w_k|^2: 8
+FLOP_PAIR, FLOP_REGULAR, FLOP_NODE = 119, 18, 8
+
+
+def algorithmic_flops(st):
+    return (FLOP_PAIR * st["pairs"] + FLOP_REGULAR * (st["shortcut"] + st["bisection"])
+            + FLOP_NODE * st["node_tests"])
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--proposal", choices=["bisect", "closed_form", "mlp"], default="closed_form")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--small", action="store_true", help="tiny workload for smoke tests of this script")
+    ap.add_argument("--n", type=int, default=None, help="override N (profiling captures of a smaller case)")
+    ap.add_argument("--depth", type=int, default=None, help="override the history depth")
+    ap.add_argument("--n0", type=int, default=None, help="override the stored-history step")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------------------------------------
+# ranks
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(backend):
+    rank, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        if shutil.which("nvidia-smi") is None:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.f = open(self.path, "w")
+        self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                      "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                     stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------------------
+def workload(small=False, rank=0, args=None):
+    from paper_2605_05543_gb300 import inputs
+
+    wl = dict(WL)
+    if small:
+        wl.update(N=2048, n0=60, depth=128)
+    if args is not None:
+        for k, a in (("N", args.n), ("depth", args.depth), ("n0", args.n0)):
+            if a is not None:
+                wl[k] = a
+    b = inputs.gaussian_bunch(wl["N"], wl["sigma"], wl["gamma0"], seed=wl["seed"] + rank)
+    h = inputs.synthetic_history(b.x, b.u, wl["n0"], wl["dt"], seed=wl["seed"] + rank + 100)
+    k0 = max(0, h.n - wl["depth"] + 1)
+    win = tuple(map(lambda a: a.copy(), (h.T[k0:], h.W[k0:], h.V[k0:], h.u)))
+    return wl, h, win
+
+
+def kernel_traffic_record(path_name):
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it was taken on the
+    kernel source as it is now (else None)."""
+    rec = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+    if not os.path.exists(rec):
+        return None
+    try:
+        d = json.load(open(rec))
+        ent = d.get(path_name)
+        if not ent:
+            return None
+        src = os.path.join(ROOT, "paper_2605_05543_gb300", "csrc", ent["source"])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return ent["dram_bytes_per_launch"] if digest == ent["source_sha256_16"] else None
+    except Exception:
+        return None
+
+
+def cpu_baseline(h, wl, seconds, E_gpu=None, B_gpu=None, seed=1):
+    """The oracle, as it stands, timed on this host's cores on a bounded sample of the workload: the
+    fields of a random subset of targets against all N sources at the stored history. The oracle
+    fields it produces are also compared with the GPU's fields of the same state (per component,
+    relative to sum_j |E_ij| of the target)."""
+    import numpy as np
+
+    import oracle
+
+    rng = np.random.default_rng(seed)
+    N = wl["N"]
+    t0 = time.perf_counter()
+    oracle.self_fields(h.T, h.W, h.V, h.n, wl["depth"], targets=rng.choice(N, 32, replace=False))
+    dt_cal = max(time.perf_counter() - t0, 1e-3)
+    nt = int(min(N, max(32, 32 * seconds / dt_cal)))
+    tg = np.sort(rng.choice(N, nt, replace=False))
+    t0 = time.perf_counter()
+    Er, Br, _, M = oracle.self_fields(h.T, h.W, h.V, h.n, wl["depth"], targets=tg, mags=True)
+    el = time.perf_counter() - t0
+    base = {"value": nt * (N - 1) / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"fields of {nt} random targets x all {N} sources at the step-{h.n} history ({el:.1f} s)"}
+    parity = None
+    if E_gpu is not None:
+        parity = {"E": float(np.max(np.abs(E_gpu[tg] - Er) / M[:, 0:1])),
+                  "B": float(np.max(np.abs(B_gpu[tg] - Br) / M[:, 1:2])), "targets": int(nt),
+                  "metric": "max over sampled targets and components of |F_gpu - F_oracle| / sum_j |F_ij|"}
+    return base, parity
+
+
+def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True):
+    import numpy as np
+    import torch
+
+    from paper_2605_05543_gb300 import emppp
+
+    stream = torch.cuda.current_stream()
+    T, W, V, u = win
+    N, D = wl["N"], wl["depth"]
+    out = {}
+    with emppp.Solver(N, D, wl["dt"], precision=path, proposal=proposal, stream=stream, timing=True) as s:
+        s.set_history(h.n, T, W, V, u)
+        # warm-up; the first step's fields are those of the stored state
+        s.step(1)
+        if keep_fields and rank == 0:
+            out["fields0"] = s.get_fields()
+        if warmup > 1:
+            s.step(warmup - 1)
+        s.synchronize()
+        s.reset_stats()
+        l0 = s.stats()["kernel_launches"]
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(torch.cuda.current_device())
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1) / steps
+        st = s.stats()
+        out.update(ms=ms, stats=st, launches=st["kernel_launches"] - l0, clocks=clocks)
+        if e2e:
+            # end to end through the public API with host buffers: restore the stored state from
+            # pinned host memory, then every step read the state and the fields back
+            pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+            hT, hW, hV, hu = (pin(a) for a in win)
+            xo = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            uo = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            Eo = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            Bo = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.set_history(h.n, hT, hW, hV, hu)
+            for _ in range(steps):
+                s.step(1)
+                s.get_state(xo, uo)
+                s.get_fields(Eo, Bo)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            barrier()
+            h2d = sum(a.nbytes for a in (hT, hW, hV, hu))
+            d2h = 4 * N * 3 * 8
+            out["e2e"] = dict(seconds=el, h2d_per_step=h2d // steps, d2h_per_step=d2h)
+    return out
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    from paper_2605_05543_gb300 import emppp
+
+    emppp.load(build_if_missing=True)
+    wl, h, win = workload(args.small, rank, args)
+    steps = args.steps if args.steps is not None else (5 if args.path == "fp64" else 20)
+    warmup = max(args.warmup, 1)
+    dev = torch.device("cuda", local)
+    res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e)
+    ms = max_over_ranks(res["ms"], dev)
+    pairs_per_step = wl["N"] * (wl["N"] - 1)
+    total_pairs = sum_over_ranks(pairs_per_step * steps, dev)
+    value = total_pairs / (ms * steps / 1e3)
+    st = res["stats"]
+    flops = algorithmic_flops(st)
+    pair_ms_avg = st["pair_ms"] / max(st["timed_steps"], 1)
+    achieved = flops / max(st["timed_steps"], 1) / (pair_ms_avg / 1e3) / 1e12
+    peak = PEAK_FP64_TFLOPS if args.path == "fp64" else PEAK_FP32_TFLOPS
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.path == "fp64" else "f32+f64",
+        "data": "synthetic (seeded Gaussian bunch and stored history; no dataset)",
+        "config": {"workload": WORKLOAD_NAME if wl["N"] == WL["N"] and wl["n0"] == WL["n0"] else
+                   f"reduced case N={wl['N']} depth={wl['depth']} history slots={wl['n0'] + 1}", "path": args.path, "proposal": args.proposal,
+                   "N": wl["N"], "history_depth": wl["depth"], "history_slots": wl["n0"] + 1, "dt": wl["dt"],
+                   "pairs_per_step": pairs_per_step, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: 0.79 GB of history window read per step (L2 129 MB)"},
+        "roofline": {"bound": "alu", "kernel": "pair_fp64_kernel" if args.path == "fp64" else "pair_mixed_kernel",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": kernel_traffic_record(args.path),
+                     "peak_note": ("FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz" if args.path == "fp64"
+                                   else "FP32: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+                     "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1)},
+        "clocks": res["clocks"],
+        "gpu_launches": res["launches"],
+        "branch_mix": {k: st[k] / max(st["pairs"], 1) for k in ("out_of_history", "shortcut", "bisection")},
+        "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
+    }
+    if "e2e" in res:
+        e = res["e2e"]
+        el = max_over_ranks(e["seconds"], dev)
+        line["e2e"] = {"value": total_pairs / el, "unit": UNIT, "h2d_bytes_per_step": e["h2d_per_step"],
+                       "d2h_bytes_per_step": e["d2h_per_step"],
+                       "note": "restore of the stored state from pinned host memory (amortised over the steps), "
+                               "then per step: emppp_step + emppp_get_state + emppp_get_fields to pinned host"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        E0, B0 = res.get("fields0", (None, None))
+        line["cpu_baseline"], parity = cpu_baseline(h, wl, args.cpu_seconds, E0, B0)
+        if parity:
+            line["rel_field_err_vs_fp64_oracle"] = parity
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm: each step is a bounded sample of the workload (the fields
+    of a fixed random subset of targets against all N sources)."""
+    import numpy as np
+
+    rank, world, _ = dist_env()
+    if world > 1:
+        dist_init("gloo")
+        if rank != 0:
+            barrier()
+            return
+    import oracle
+
+    wl, h, win = workload(args.small, 0, args)
+    steps = args.steps if args.steps is not None else 3
+    warmup = args.warmup
+    N = wl["N"]
+    # size one step to about cpu-seconds / (steps + warmup) of work (at least 16 targets)
+    rng = np.random.default_rng(5)
+    t0 = time.perf_counter()
+    oracle.self_fields(h.T, h.W, h.V, h.n, wl["depth"], targets=rng.choice(N, 16, replace=False))
+    per_target = max((time.perf_counter() - t0) / 16, 1e-6)
+    budget = max(args.cpu_seconds, 1.0) * 6 / max(steps + warmup, 1)
+    nt = int(min(N, max(16, budget / per_target)))
+    tg = rng.choice(N, nt, replace=False)
+    for _ in range(warmup):
+        oracle.self_fields(h.T, h.W, h.V, h.n, wl["depth"], targets=tg)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.self_fields(h.T, h.W, h.V, h.n, wl["depth"], targets=tg)
+    el = time.perf_counter() - t0
+    value = steps * nt * (N - 1) / el
+    sample = f"per step: fields of {nt} random targets x all {N} sources at the step-{h.n} history"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian bunch and stored history)",
+            "config": {"workload": WORKLOAD_NAME, "path": "cpu oracle", "N": N, "history_depth": wl["depth"],
+                       "parallelism": "host threads"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        barrier()
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    try:
+        import torch.distributed as dist
+
+        if dist.is_available() and dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

@@ -80,17 +80,23 @@ typedef struct {
   int32_t proposal;    /* emppp_proposal, default BISECT */
   int32_t pair_fields; /* 1 (default): self fields on; 0: E = 0, B = B_ext (stage-2 transport, Sec. 2.7) */
   int32_t source_split;/* 0 (default): automatic; >0: number of source slices per target block */
-  int32_t reserved[4]; /* must be 0 */
+  int32_t timing;      /* 1: record CUDA events around every pair evaluation and step (see emppp_stats) */
+  int32_t reserved[3]; /* must be 0 */
 } emppp_options;
 
-/* Counters of the last completed step's pair evaluation (Sec. 2.2 branches). */
+/* Counters accumulated over the steps since the last emppp_reset_stats (Sec. 2.2 branches). */
 typedef struct {
-  int64_t pairs;          /* N (N - 1) */
-  int64_t out_of_history; /* pairs with t_r older than the history (eq:linear2) */
-  int64_t shortcut;       /* pairs bracketed by the near-field shortcut */
-  int64_t bisection;      /* pairs bracketed by the search */
-  int64_t node_tests;     /* evaluations of c (t - t_k) <= |r - w_k| over all pairs */
-  int64_t guard_fallbacks;/* node tests decided in FP64 after an inconclusive FP32 test */
+  int64_t steps;           /* steps taken */
+  int64_t pairs;           /* ordered pairs (i, j != i) evaluated: steps * N (N - 1) with pair fields on */
+  int64_t out_of_history;  /* pairs with t_r older than the history (eq:linear2) */
+  int64_t shortcut;        /* pairs bracketed by the near-field shortcut */
+  int64_t bisection;       /* pairs bracketed by the search */
+  int64_t node_tests;      /* evaluations of c (t - t_k) <= |r - w_k| over all pairs */
+  int64_t guard_fallbacks; /* node tests decided in FP64 after an inconclusive FP32 test */
+  int64_t kernel_launches; /* kernels launched by the library (cumulative since emppp_create) */
+  double pair_ms;          /* device time of the pair evaluations (timing option on, else 0) */
+  double step_ms;          /* device time of whole steps (timing option on, else 0) */
+  int64_t timed_steps;     /* steps whose events were recorded (the event pool holds 4096 steps) */
 } emppp_stats;
 
 /* Fills *out with the defaults listed above. */
@@ -141,10 +147,14 @@ EMPPP_API emppp_status emppp_get_state(emppp_handle h, double* x, double* u, dou
  * (host or device, either may be NULL). Synchronises the stream. */
 EMPPP_API emppp_status emppp_get_fields(emppp_handle h, double* E, double* B, int32_t is_device_ptr);
 
-/* Branch and node-test counters of the last completed step. Synchronises the stream. */
+/* Counters accumulated since the last emppp_reset_stats (or create / set_particles / set_history).
+ * Synchronises the stream. */
 EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out);
 
-/* Replaces the options (precision, proposal, pair_fields, source_split) for later steps. */
+/* Zeroes the accumulated counters and recorded times (not kernel_launches). */
+EMPPP_API emppp_status emppp_reset_stats(emppp_handle h);
+
+/* Replaces the options (precision, proposal, pair_fields, source_split, timing) for later steps. */
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt);
 
 /* Replaces the stream later calls enqueue on (cudaStream_t, NULL: legacy default stream). */

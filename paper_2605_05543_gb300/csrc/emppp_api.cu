@@ -48,6 +48,14 @@ struct emppp_ctx {
   double t = 0.0;   // host mirror of t_n
   double* staging = nullptr;  // [7N] doubles for host transfers
   std::vector<void*> allocs;
+  // counters
+  int64_t launches = 0;   // kernels launched (cumulative)
+  int64_t steps_acc = 0;  // steps since the last stats reset
+  int64_t pairs_acc = 0;
+  // timing: 4 events per step (step start, pair start, pair end, step end)
+  static constexpr int kTimedSteps = 1024;
+  std::vector<cudaEvent_t> events;
+  int ev_used = 0;
 };
 
 namespace {
@@ -80,7 +88,8 @@ emppp_status validate_options(const emppp_options* o) {
     return fail(EMPPP_ERR_ARG, "proposal %d is not available in this build", o->proposal);
   if (o->pair_fields != 0 && o->pair_fields != 1) return fail(EMPPP_ERR_ARG, "pair_fields must be 0 or 1");
   if (o->source_split < 0) return fail(EMPPP_ERR_ARG, "source_split must be >= 0");
-  for (int k = 0; k < 4; k++)
+  if (o->timing != 0 && o->timing != 1) return fail(EMPPP_ERR_ARG, "timing must be 0 or 1");
+  for (int k = 0; k < 3; k++)
     if (o->reserved[k] != 0) return fail(EMPPP_ERR_ARG, "reserved option fields must be 0");
   return EMPPP_OK;
 }
@@ -134,6 +143,21 @@ emppp_status from_device(emppp_handle h, double* dst, const double* src, size_t 
 
 void set_origin(emppp_handle h, const double* x0) {
   for (int c = 0; c < 3; c++) h->ds.origin[c] = x0[c];
+}
+
+emppp_status ensure_events(emppp_handle h) {
+  if (!h->opt.timing || !h->events.empty()) return EMPPP_OK;
+  h->events.resize(4 * emppp_ctx::kTimedSteps, nullptr);
+  for (auto& e : h->events) CU(cudaEventCreate(&e));
+  return EMPPP_OK;
+}
+
+emppp_status reset_counters(emppp_handle h) {
+  CU(cudaMemsetAsync(h->ds.stats, 0, sizeof(unsigned long long) * kStatCount, h->stream));
+  h->steps_acc = 0;
+  h->pairs_acc = 0;
+  h->ev_used = 0;
+  return EMPPP_OK;
 }
 
 }  // namespace
@@ -222,6 +246,10 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
     emppp_destroy(c);
     return fail(EMPPP_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
   }
+  if ((st = ensure_events(c)) != EMPPP_OK) {
+    emppp_destroy(c);
+    return st;
+  }
   *out = c;
   return EMPPP_OK;
 }
@@ -231,6 +259,8 @@ EMPPP_API void emppp_destroy(emppp_handle h) {
   cudaSetDevice(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : h->events)
+    if (e) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }
@@ -265,6 +295,8 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
   set_origin(h, x0);
   CU(launch_set_state(h->ds, 0, 0.0, h->dt, du, dw, h->stream));
   CU(launch_init_slot0(h->ds, dx, du, dw, h->stream));
+  h->launches += 2;
+  if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
   CU(cudaMemsetAsync(h->ds.Bout, 0, sizeof(double) * N * 3, h->stream));
   CU(cudaStreamSynchronize(h->stream));
@@ -320,6 +352,7 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
       Vs = h->staging + 3 * N;
     }
     CU(launch_scatter_slot(h->ds, p, Ws, Vs, h->stream));
+    h->launches += 1;
     if (!is_device_ptr) CU(cudaStreamSynchronize(h->stream));  // staging is reused by the next slot
   }
   CU(cudaMemcpyAsync(h->ds.slot_t, ht.data(), sizeof(double) * h->D, cudaMemcpyHostToDevice, h->stream));
@@ -332,6 +365,8 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
     dw = w ? h->staging + 6 * N : nullptr;
   }
   CU(launch_set_state(h->ds, n, hT[nslots - 1], h->dt, du, dw, h->stream));
+  h->launches += 1;
+  if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
   CU(cudaMemsetAsync(h->ds.Bout, 0, sizeof(double) * N * 3, h->stream));
   CU(cudaStreamSynchronize(h->stream));
@@ -361,8 +396,10 @@ EMPPP_API emppp_status emppp_get_history(emppp_handle h, int64_t* n_now, int32_t
     double* Vs = V ? V + (size_t)s * N * 3 : nullptr;
     if (is_device_ptr) {
       CU(launch_gather_slot(h->ds, p, Ws, Vs, h->stream));
+      h->launches += 1;
     } else {
       CU(launch_gather_slot(h->ds, p, h->staging, h->staging + 3 * N, h->stream));
+      h->launches += 1;
       if (Ws && (st = from_device(h, Ws, h->staging, 3 * N, 0)) != EMPPP_OK) return st;
       if (Vs && (st = from_device(h, Vs, h->staging + 3 * N, 3 * N, 0)) != EMPPP_OK) return st;
       CU(cudaStreamSynchronize(h->stream));
@@ -399,15 +436,30 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
   }
   const int split = choose_split(h);
   for (int64_t k = 0; k < nsteps; k++) {
+    cudaEvent_t* ev = nullptr;
+    if (h->opt.timing && h->ev_used < emppp_ctx::kTimedSteps) ev = &h->events[4 * h->ev_used++];
+    if (ev) CU(cudaEventRecord(ev[0], h->stream));
     CU(launch_prep(h->ds, h->stream));
+    h->launches += 1;
+    if (ev) CU(cudaEventRecord(ev[1], h->stream));
     if (h->opt.pair_fields) {
       CU(launch_pair_fp64(h->ds, h->opt.proposal, split, h->stream));
-      if (split > 1) CU(launch_reduce_partials(h->ds, split, h->stream));
+      h->launches += 1;
+      if (split > 1) {
+        CU(launch_reduce_partials(h->ds, split, h->stream));
+        h->launches += 1;
+      }
+      h->pairs_acc += h->N * (h->N - 1);
     } else {
       CU(launch_zero_self(h->ds, h->stream));
+      h->launches += 1;
     }
+    if (ev) CU(cudaEventRecord(ev[2], h->stream));
     CU(launch_push(h->ds, bp, h->stream));
     CU(launch_advance(h->ds, h->stream));
+    h->launches += 2;
+    if (ev) CU(cudaEventRecord(ev[3], h->stream));
+    h->steps_acc += 1;
     h->n += 1;
     h->t = h->t + h->dt;
   }
@@ -422,6 +474,7 @@ EMPPP_API emppp_status emppp_get_state(emppp_handle h, double* x, double* u, dou
   if ((st = read_err(h)) != EMPPP_OK) return st;
   const size_t N = (size_t)h->N;
   if (x) {
+    h->launches += 1;
     if (is_device_ptr) {
       CU(launch_gather_positions(h->ds, x, h->stream));
     } else {
@@ -455,13 +508,33 @@ EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out) {
   unsigned long long hs[kStatCount];
   CU(cudaMemcpyAsync(hs, h->ds.stats, sizeof(hs), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
-  out->pairs = h->N * (h->N - 1);
+  memset(out, 0, sizeof(*out));
+  out->steps = h->steps_acc;
+  out->pairs = h->pairs_acc;
   out->out_of_history = (int64_t)hs[kStatOOH];
   out->shortcut = (int64_t)hs[kStatShortcut];
   out->bisection = (int64_t)hs[kStatBisect];
   out->node_tests = (int64_t)hs[kStatNodeTests];
   out->guard_fallbacks = (int64_t)hs[kStatGuard];
+  out->kernel_launches = h->launches;
+  double pair_ms = 0.0, step_ms = 0.0;
+  for (int k = 0; k < h->ev_used; k++) {
+    float a = 0.f, b = 0.f;
+    CU(cudaEventElapsedTime(&a, h->events[4 * k + 1], h->events[4 * k + 2]));
+    CU(cudaEventElapsedTime(&b, h->events[4 * k + 0], h->events[4 * k + 3]));
+    pair_ms += a;
+    step_ms += b;
+  }
+  out->pair_ms = pair_ms;
+  out->step_ms = step_ms;
+  out->timed_steps = h->ev_used;
   return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_reset_stats(emppp_handle h) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  return reset_counters(h);
 }
 
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt) {
@@ -470,7 +543,7 @@ EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* op
   if (!opt) return fail(EMPPP_ERR_ARG, "opt is NULL");
   if ((st = validate_options(opt)) != EMPPP_OK) return st;
   h->opt = *opt;
-  return EMPPP_OK;
+  return ensure_events(h);
 }
 
 EMPPP_API emppp_status emppp_set_stream(emppp_handle h, void* cuda_stream) {

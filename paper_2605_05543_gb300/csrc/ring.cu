@@ -94,7 +94,6 @@ __global__ void prep_kernel(DeviceState s) {
     s.state->k0 = k0;
     s.state->p0 = p0;
     s.state->pn = pn;
-    for (int c = 0; c < kStatCount; c++) s.stats[c] = 0ull;
   }
   const int nwin = (int)(n - k0 + 1);
   for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nwin; l += gridDim.x * blockDim.x) {

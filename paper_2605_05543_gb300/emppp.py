@@ -33,7 +33,7 @@ class EmpppError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("pair_fields", ctypes.c_int32),
-                ("source_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("source_split", ctypes.c_int32), ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class Bext(ctypes.Structure):
@@ -42,8 +42,10 @@ class Bext(ctypes.Structure):
 
 
 class Stats(ctypes.Structure):
-    _fields_ = [("pairs", ctypes.c_int64), ("out_of_history", ctypes.c_int64), ("shortcut", ctypes.c_int64),
-                ("bisection", ctypes.c_int64), ("node_tests", ctypes.c_int64), ("guard_fallbacks", ctypes.c_int64)]
+    _fields_ = [("steps", ctypes.c_int64), ("pairs", ctypes.c_int64), ("out_of_history", ctypes.c_int64),
+                ("shortcut", ctypes.c_int64), ("bisection", ctypes.c_int64), ("node_tests", ctypes.c_int64),
+                ("guard_fallbacks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("pair_ms", ctypes.c_double),
+                ("step_ms", ctypes.c_double), ("timed_steps", ctypes.c_int64)]
 
 
 _vp = ctypes.c_void_p
@@ -65,6 +67,7 @@ SIGNATURES = {
                                        ctypes.c_int32]),
     "emppp_get_fields": (ctypes.c_int, [_H, _vp, _vp, ctypes.c_int32]),
     "emppp_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(Stats)]),
+    "emppp_reset_stats": (ctypes.c_int, [_H]),
     "emppp_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
     "emppp_set_stream": (ctypes.c_int, [_H, _vp]),
     "emppp_synchronize": (ctypes.c_int, [_H]),
@@ -157,13 +160,14 @@ def bext_dipole(m0: float, center=(0.0, 0.0, 0.0)) -> Bext:
     return e
 
 
-def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_split=0) -> Options:
+def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_split=0, timing=False) -> Options:
     o = Options()
     load().emppp_default_options(ctypes.byref(o))
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.proposal = PROPOSAL[proposal] if isinstance(proposal, str) else int(proposal)
     o.pair_fields = 1 if pair_fields else 0
     o.source_split = int(source_split)
+    o.timing = 1 if timing else 0
     return o
 
 
@@ -171,13 +175,13 @@ class Solver:
     """One EM-PP system of n particles with history depth `depth` and step dt (all on one GPU)."""
 
     def __init__(self, n: int, depth: int, dt: float, precision="fp64", proposal="bisect", pair_fields=True,
-                 source_split=0, stream=None):
+                 source_split=0, stream=None, timing=False):
         self.lib = load()
         self.n = int(n)
         self.depth = int(depth)
         self.dt = float(dt)
         self._h = _H()
-        self._opt = make_options(precision, proposal, pair_fields, source_split)
+        self._opt = make_options(precision, proposal, pair_fields, source_split, timing)
         _check(self.lib.emppp_create(self.n, self.depth, self.dt, ctypes.byref(self._opt),
                                      _stream_handle(stream), ctypes.byref(self._h)))
 
@@ -202,8 +206,10 @@ class Solver:
     def handle(self):
         return self._h
 
-    def set_options(self, precision=None, proposal=None, pair_fields=None, source_split=None):
+    def set_options(self, precision=None, proposal=None, pair_fields=None, source_split=None, timing=None):
         o = self._opt
+        if timing is not None:
+            o.timing = 1 if timing else 0
         if precision is not None:
             o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
         if proposal is not None:
@@ -276,7 +282,10 @@ class Solver:
     def stats(self) -> dict:
         s = Stats()
         _check(self.lib.emppp_get_stats(self._h, ctypes.byref(s)))
-        return {k: int(getattr(s, k)) for k, _ in Stats._fields_}
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def reset_stats(self):
+        _check(self.lib.emppp_reset_stats(self._h))
 
     def synchronize(self):
         _check(self.lib.emppp_synchronize(self._h))
