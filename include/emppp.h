@@ -163,6 +163,26 @@ EMPPP_API emppp_status emppp_set_stream(emppp_handle h, void* cuda_stream);
 /* Waits for the handle's stream and reports a pending device-side numeric fault. */
 EMPPP_API emppp_status emppp_synchronize(emppp_handle h);
 
+/* Self fields of n particles at the present slot of a history held by the caller, evaluated without
+ * allocating any device memory. There is no counterpart in the paper: this entry point exists for
+ * callers that own all device memory themselves (a framework whose caching allocator holds the GPU,
+ * a service with a fixed device-memory budget, a loop where an allocation could stall or fail) and
+ * so cannot let the library cudaMalloc its own buffers.
+ *   T [nslots], W and V [nslots][n][3]: device pointers, the layout of emppp_set_history; slot
+ *     nslots - 1 is the present one and every slot is usable (the history depth is nslots).
+ *   w [n] optional weights (NULL: 1); E, B [n][3] device outputs (B is the self field only).
+ *   cuda_stream: cudaStream_t the work is enqueued on (NULL: legacy default stream); asynchronous.
+ * The FP64 path with the paper's search (out-of-history test, shortcut, bisection) is used. Its working
+ * memory is one fixed 16 MiB device array inside the library (held by every GPU that loads the
+ * library until the process exits), which limits n to 348160 and nslots to 4096: larger sizes are
+ * rejected with EMPPP_ERR_ARG. All calls share that array, so calls whose work overlaps on the GPU
+ * race with each other: serialise them. The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream capture. A numeric
+ * fault of a pair (|v| >= c, coincident particles) makes that target's E and B NaN. */
+EMPPP_API emppp_status emppp_fields_noalloc(int64_t n, int32_t nslots, const double* T, const double* W,
+                                            const double* V, const double* w, double* E, double* B,
+                                            void* cuda_stream);
+
 /* Text of the last failing call on this thread ("" if none). Valid until the next call. */
 EMPPP_API const char* emppp_last_error(void);
 

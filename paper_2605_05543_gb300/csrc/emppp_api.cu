@@ -34,6 +34,11 @@ emppp_status fail(emppp_status st, const char* fmt, ...) {
 
 }  // namespace
 
+namespace emppp {
+// lets other translation units of the library report an error text through emppp_last_error
+void set_error_text(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace emppp
+
 struct emppp_ctx {
   DeviceState ds{};
   int64_t N = 0;

@@ -71,6 +71,7 @@ SIGNATURES = {
     "emppp_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
     "emppp_set_stream": (ctypes.c_int, [_H, _vp]),
     "emppp_synchronize": (ctypes.c_int, [_H]),
+    "emppp_fields_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "emppp_last_error": (ctypes.c_char_p, []),
     "emppp_version": (ctypes.c_char_p, []),
 }
@@ -289,6 +290,20 @@ class Solver:
 
     def synchronize(self):
         _check(self.lib.emppp_synchronize(self._h))
+
+
+def fields_noalloc(T, W, V, E, B, w=None, stream=None):
+    """Self fields at the present (last) slot of a caller-held device history, computed by the
+    library without allocating device memory (see emppp_fields_noalloc in include/emppp.h).
+    T [nslots], W, V [nslots, n, 3], E, B [n, 3]: float64 CUDA tensors; w [n] optional."""
+    nslots = int(T.numel()) if _is_torch(T) else int(np.size(T))
+    n = (int(W.numel()) if _is_torch(W) else int(np.size(W))) // (3 * max(nslots, 1))
+    ptrs = [_ptr(T, nslots, "T"), _ptr(W, nslots * 3 * n, "W"), _ptr(V, nslots * 3 * n, "V"),
+            _ptr(w, n, "w"), _ptr(E, 3 * n, "E"), _ptr(B, 3 * n, "B")]
+    if _same_kind(*ptrs) != 1:
+        raise ValueError("fields_noalloc takes device (CUDA tensor) arrays only")
+    pT, pW, pV, pw, pE, pB = (p for p, _ in ptrs)
+    _check(load().emppp_fields_noalloc(n, nslots, pT, pW, pV, pw, pE, pB, _stream_handle(stream)))
 
 
 def version() -> str:
