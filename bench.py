@@ -63,7 +63,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--path", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--path", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--proposal", choices=["bisect", "closed_form", "mlp"], default="closed_form")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -52,6 +52,10 @@ struct emppp_ctx {
   int64_t n = 0;    // host mirror of the present step
   double t = 0.0;   // host mirror of t_n
   double* staging = nullptr;  // [7N] doubles for host transfers
+  // spatial target order of the mixed path
+  int* ord_scratch = nullptr;  // bbox (6) + cell histogram
+  unsigned short* ord_key = nullptr;
+  int* order = nullptr;
   std::vector<void*> allocs;
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
@@ -88,7 +92,6 @@ emppp_status dalloc(emppp_ctx* c, T** p, size_t count) {
 emppp_status validate_options(const emppp_options* o) {
   if (o->precision != EMPPP_FP64 && o->precision != EMPPP_MIXED)
     return fail(EMPPP_ERR_ARG, "unknown precision %d", o->precision);
-  if (o->precision == EMPPP_MIXED) return fail(EMPPP_ERR_ARG, "MIXED precision path is not available in this build");
   if (o->proposal != EMPPP_PROPOSAL_BISECT && o->proposal != EMPPP_PROPOSAL_CLOSED_FORM)
     return fail(EMPPP_ERR_ARG, "proposal %d is not available in this build", o->proposal);
   if (o->pair_fields != 0 && o->pair_fields != 1) return fail(EMPPP_ERR_ARG, "pair_fields must be 0 or 1");
@@ -241,6 +244,10 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   ALLOC(s.stats, kStatCount);
   ALLOC(s.err, 1);
   ALLOC(c->staging, N * 7);
+  ALLOC(s.tab.icdt32, D);
+  ALLOC(c->ord_scratch, order_scratch_ints());
+  ALLOC(c->ord_key, N);
+  ALLOC(c->order, N);
 #undef ALLOC
   e = cudaMemsetAsync(s.err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.stats, 0, sizeof(unsigned long long) * kStatCount, c->stream);
@@ -446,9 +453,16 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
     if (ev) CU(cudaEventRecord(ev[0], h->stream));
     CU(launch_prep(h->ds, h->stream));
     h->launches += 1;
+    if (h->opt.pair_fields && h->opt.precision == EMPPP_MIXED) {
+      CU(launch_target_order(h->ds, h->ord_scratch, h->ord_scratch + 6, h->ord_key, h->order, h->stream));
+      h->launches += 5;
+    }
     if (ev) CU(cudaEventRecord(ev[1], h->stream));
     if (h->opt.pair_fields) {
-      CU(launch_pair_fp64(h->ds, h->opt.proposal, split, h->stream));
+      if (h->opt.precision == EMPPP_MIXED)
+        CU(launch_pair_mixed(h->ds, h->order, h->opt.proposal, split, h->stream));
+      else
+        CU(launch_pair_fp64(h->ds, h->opt.proposal, split, h->stream));
       h->launches += 1;
       if (split > 1) {
         CU(launch_reduce_partials(h->ds, split, h->stream));

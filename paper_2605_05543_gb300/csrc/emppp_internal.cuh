@@ -5,11 +5,11 @@
 //                             w (3) and velocity v (3) at the time slot_t[p]; slots are used
 //                             modulo D, so one particle's whole history is one contiguous 48*D-byte
 //                             run (pair gathers of one source stay within a few cache lines).
-//   rec32  [N][D][12] float   FP32 shadow of rec64 for the mixed path: hi(3) lo(3) of w - origin,
-//                             v(3), pad(3); 48-byte records, three 16-byte loads each.
+//   rec32  [N][D][12] float   FP32 shadow of rec64 (shadow.cuh): hi(3) 1/gamma^2 | lo(3) 0 |
+//                             beta(3) gamma^2; 48-byte records, three 16-byte loads each.
 //   slot_t [D]                time stamp of each physical slot.
 //   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
-//                             1 / (t_{k+1} - t_k).
+//                             1 / (t_{k+1} - t_k) in FP64 and 1 / (c (t_{k+1} - t_k)) in FP32.
 //   u      [N][3]             present proper velocities (FP64).
 //   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
 //   StepState (device)        present step n, t_n, dt and the derived window k0..n; kernels read it
@@ -57,6 +57,7 @@ struct SlotTables {
   float* lhs32;     // [D] same, FP32
   float* ct32;      // [D] c (t_n - t_k), FP32
   double* inv_dtk;  // [D] 1 / (t_{k+1} - t_k) for k < n
+  float* icdt32;    // [D] 1 / (c (t_{k+1} - t_k)), FP32
 };
 
 struct DeviceState {
@@ -103,5 +104,11 @@ cudaError_t launch_reduce_partials(const DeviceState& s, int split, cudaStream_t
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
 cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st);
+// order.cu
+size_t order_scratch_ints();
+cudaError_t launch_target_order(const DeviceState& s, int* bbox, int* hist, unsigned short* key, int* order,
+                                cudaStream_t st);
+// pair_mixed.cu
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, int split, cudaStream_t st);
 
 }  // namespace emppp

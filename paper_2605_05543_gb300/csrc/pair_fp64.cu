@@ -16,6 +16,7 @@
 // The arithmetic is FP64-pipe bound (GB300: 2 DFMA/clk/SM); everything that is not an FP64 result
 // (the guess, indices, loads) runs on the FP32/INT pipes beside it.
 #include "emppp_internal.cuh"
+#include "shadow.cuh"
 
 namespace emppp {
 
@@ -62,27 +63,6 @@ struct Window {
   }
 };
 
-// Guess of the older bracket node from uniform motion of the source from its present state:
-// t - t_r = [d.v + sqrt((d.v)^2 + (c^2 - v^2) d^2)] / (c^2 - v^2), d = r - w_n (FP32 inputs).
-__device__ __forceinline__ long long closed_form_guess(float r0, float r1, float r2, const float* __restrict__ q,
-                                                       float inv_dt, const Window& win) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(q));
-  const float4 b = __ldg(reinterpret_cast<const float4*>(q) + 1);
-  const float4 c4 = __ldg(reinterpret_cast<const float4*>(q) + 2);
-  const float d0 = r0 - a.x, d1 = r1 - a.y, d2 = r2 - a.z;
-  const float v0 = b.z, v1 = b.w, v2 = c4.x;
-  const float cc = (float)kC;
-  const float dv = d0 * v0 + d1 * v1 + d2 * v2;
-  const float dd = d0 * d0 + d1 * d1 + d2 * d2;
-  const float c2v2 = cc * cc - (v0 * v0 + v1 * v1 + v2 * v2);
-  const float tau = (dv + sqrtf(fmaxf(dv * dv + c2v2 * dd, 0.f))) / fmaxf(c2v2, 1e-30f);
-  const float steps = floorf(tau * inv_dt);
-  long long k = win.n - 1 - (long long)fminf(steps, 1e9f);
-  if (k < win.k0) k = win.k0;
-  if (k > win.n - 1) k = win.n - 1;
-  return k;
-}
-
 }  // namespace
 
 template <int PROP>
@@ -103,13 +83,13 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
 
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
-  float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f, inv_dt = 0.f;
+  float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f, inv_cdt = 0.f;
   if (PROP == kPropClosedForm) {
     const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
     rh0 = q[0];
     rh1 = q[1];
     rh2 = q[2];
-    inv_dt = (float)(1.0 / a.state->dt);
+    inv_cdt = (float)(1.0 / (kC * a.state->dt));
   }
 
   const long long j_begin = (long long)blockIdx.y * a.chunk;
@@ -161,8 +141,8 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
         br = 0;
         n_tests += 1;
       } else {
-        const long long kg =
-            closed_form_guess(rh0, rh1, rh2, a.rec32 + ((size_t)j * D + pn) * 12, inv_dt, win);
+        const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
+        const long long kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), inv_cdt, win.k0, win.n);
         long long lo, hi;
         bool ooh = false;
         n_tests += 1;

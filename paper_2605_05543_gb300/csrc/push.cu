@@ -10,6 +10,7 @@
 // Then slot n+1 (modulo D) receives (x^{n+1}, v^{n+1}) and the time stamp t_n + dt.
 // O(N) work; FP64 throughout (the momentum update needs it).
 #include "emppp_internal.cuh"
+#include "shadow.cuh"
 
 namespace emppp {
 
@@ -89,12 +90,12 @@ __global__ void push_kernel(DeviceState s, BextParams bp) {
   reinterpret_cast<double2*>(r)[0] = make_double2(x0, x1);
   reinterpret_cast<double2*>(r)[1] = make_double2(x2, v0);
   reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
-  const double d0 = x0 - s.origin[0], d1 = x1 - s.origin[1], d2 = x2 - s.origin[2];
-  const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-  float4* q = reinterpret_cast<float4*>(s.rec32 + ((size_t)i * s.D + pnext) * 12);
-  q[0] = make_float4(h0, h1, h2, (float)(d0 - (double)h0));
-  q[1] = make_float4((float)(d1 - (double)h1), (float)(d2 - (double)h2), (float)v0, (float)v1);
-  q[2] = make_float4((float)v2, 0.f, 0.f, 0.f);
+  float4 q[3];
+  shadow_record(s.origin, x0, x1, x2, v0, v1, v2, gamma2_of_u(u[0], u[1], u[2]), q);
+  float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)i * s.D + pnext) * 12);
+  o[0] = q[0];
+  o[1] = q[1];
+  o[2] = q[2];
 }
 
 cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st) {

@@ -1,6 +1,7 @@
 // History ring (Sec. 2.2: positions and velocities stored at discrete steps; the acceleration is not
 // stored) and per-step slot tables.
 #include "emppp_internal.cuh"
+#include "shadow.cuh"
 
 namespace emppp {
 
@@ -11,13 +12,12 @@ __device__ __forceinline__ void write_record(const DeviceState& s, long long j, 
   reinterpret_cast<double2*>(r)[0] = make_double2(w0, w1);
   reinterpret_cast<double2*>(r)[1] = make_double2(w2, v0);
   reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
-  const double d0 = w0 - s.origin[0], d1 = w1 - s.origin[1], d2 = w2 - s.origin[2];
-  const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-  const float l0 = (float)(d0 - (double)h0), l1 = (float)(d1 - (double)h1), l2 = (float)(d2 - (double)h2);
-  float4* q = reinterpret_cast<float4*>(s.rec32 + ((size_t)j * s.D + p) * 12);
-  q[0] = make_float4(h0, h1, h2, l0);
-  q[1] = make_float4(l1, l2, (float)v0, (float)v1);
-  q[2] = make_float4((float)v2, 0.f, 0.f, 0.f);
+  float4 q[3];
+  shadow_record(s.origin, w0, w1, w2, v0, v1, v2, gamma2_of_v(v0, v1, v2), q);
+  float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)j * s.D + p) * 12);
+  o[0] = q[0];
+  o[1] = q[1];
+  o[2] = q[2];
 }
 
 // v = u / gamma with gamma = sqrt(1 + u.u / c^2), in the operation order of a plain FP64 evaluation
@@ -107,9 +107,12 @@ __global__ void prep_kernel(DeviceState s) {
     s.tab.ct32[p] = (float)ct;
     if (l + 1 < nwin) {
       int q = p + 1 == s.D ? 0 : p + 1;
-      s.tab.inv_dtk[p] = 1.0 / (s.slot_t[q] - tk);
+      const double dtk = s.slot_t[q] - tk;
+      s.tab.inv_dtk[p] = 1.0 / dtk;
+      s.tab.icdt32[p] = (float)(1.0 / (kC * dtk));
     } else {
       s.tab.inv_dtk[p] = 0.0;
+      s.tab.icdt32[p] = 0.f;
     }
   }
 }
