@@ -1,6 +1,7 @@
 // C ABI of the EM-PP library: handle lifetime, state transfer and the step driver.
 // Every entry point validates its arguments, enqueues work on the handle's stream and returns a
 // status; nothing here aborts or prints.
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -149,8 +150,13 @@ emppp_status from_device(emppp_handle h, double* dst, const double* src, size_t 
   return EMPPP_OK;
 }
 
-void set_origin(emppp_handle h, const double* x0) {
-  for (int c = 0; c < 3; c++) h->ds.origin[c] = x0[c];
+// origin of the FP32 position split and reference velocity of the FP32 velocities: those of one
+// particle of the bunch when the state is set
+void set_origin(emppp_handle h, const double* x0, const double* v0) {
+  for (int c = 0; c < 3; c++) {
+    h->ds.origin[c] = x0[c];
+    h->ds.beta_ref[c] = v0[c] / kC;
+  }
 }
 
 emppp_status ensure_events(emppp_handle h) {
@@ -193,6 +199,7 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   if (history_depth < 2) return fail(EMPPP_ERR_ARG, "history_depth must be >= 2 (got %d)", history_depth);
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(EMPPP_ERR_ARG, "dt must be positive and finite");
   if ((double)n * (double)history_depth > 4e10) return fail(EMPPP_ERR_ARG, "n * history_depth too large");
+  if (n > 2147483647LL) return fail(EMPPP_ERR_ARG, "n must be below 2^31");
   emppp_options o;
   emppp_default_options(&o);
   if (opt) o = *opt;
@@ -245,6 +252,7 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   ALLOC(s.err, 1);
   ALLOC(c->staging, N * 7);
   ALLOC(s.tab.icdt32, D);
+  ALLOC(s.kq32, N);
   ALLOC(c->ord_scratch, order_scratch_ints());
   ALLOC(c->ord_key, N);
   ALLOC(c->order, N);
@@ -297,14 +305,20 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
     du = su;
     dw = w ? sw : nullptr;
   }
-  double x0[3];
+  double x0[3], u0[3];
   if (is_device_ptr) {
     CU(cudaMemcpyAsync(x0, x, sizeof(x0), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(u0, u, sizeof(u0), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   } else {
     memcpy(x0, x, sizeof(x0));
+    memcpy(u0, u, sizeof(u0));
   }
-  set_origin(h, x0);
+  {
+    const double g = sqrt(1.0 + (u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]) / (kC * kC));
+    const double v0[3] = {u0[0] / g, u0[1] / g, u0[2] / g};
+    set_origin(h, x0, v0);
+  }
   CU(launch_set_state(h->ds, 0, 0.0, h->dt, du, dw, h->stream));
   CU(launch_init_slot0(h->ds, dx, du, dw, h->stream));
   h->launches += 2;
@@ -340,16 +354,19 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
     if (!(hT[s] == hT[s]) || (s > 0 && !(hT[s] > hT[s - 1])))
       return fail(EMPPP_ERR_ARG, "time stamps must be finite and strictly increasing (slot %d)", s);
   }
-  // origin of the FP32 split: the present position of particle 0
-  double x0[3];
+  // origin and reference velocity of the FP32 shadow: the present position and velocity of particle 0
+  double x0[3], v0[3];
   const double* Wlast = W + (size_t)(nslots - 1) * N * 3;
+  const double* Vlast = V + (size_t)(nslots - 1) * N * 3;
   if (is_device_ptr) {
     CU(cudaMemcpyAsync(x0, Wlast, sizeof(x0), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(v0, Vlast, sizeof(v0), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
   } else {
     memcpy(x0, Wlast, sizeof(x0));
+    memcpy(v0, Vlast, sizeof(v0));
   }
-  set_origin(h, x0);
+  set_origin(h, x0, v0);
   std::vector<double> ht((size_t)h->D, 0.0);
   for (int s = 0; s < nslots; s++) {
     const int64_t k = n - nslots + 1 + s;

@@ -6,7 +6,7 @@
 //                             modulo D, so one particle's whole history is one contiguous 48*D-byte
 //                             run (pair gathers of one source stay within a few cache lines).
 //   rec32  [N][D][12] float   FP32 shadow of rec64 (shadow.cuh): hi(3) 1/gamma^2 | lo(3) 0 |
-//                             beta(3) gamma^2; 48-byte records, three 16-byte loads each.
+//                             beta - beta_ref (3) gamma^2; 48-byte records, three 16-byte loads each.
 //   slot_t [D]                time stamp of each physical slot.
 //   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
 //                             1 / (t_{k+1} - t_k) in FP64 and 1 / (c (t_{k+1} - t_k)) in FP32.
@@ -69,6 +69,7 @@ struct DeviceState {
   SlotTables tab;
   double* u;
   double* wts;  // [N] weights (always present; 1 by default)
+  float* kq32;  // [N] -e w_j / (4 pi eps0) in FP32 (mixed path)
   double* Eself;
   double* Bself;
   double* Bout;
@@ -77,7 +78,8 @@ struct DeviceState {
   StepState* state;
   unsigned long long* stats;  // [kStatCount]
   int* err;
-  double origin[3];  // origin of the FP32 hi/lo split
+  double origin[3];    // origin of the FP32 hi/lo split
+  double beta_ref[3];  // reference velocity / c of the FP32 shadow's velocities
 };
 
 struct BextParams {

@@ -42,6 +42,7 @@ struct PairArgs {
   long long N;
   int D;
   long long chunk;  // sources per slice
+  double beta_ref[3];
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
   float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f, inv_cdt = 0.f;
+  const float3 bref = make_float3((float)a.beta_ref[0], (float)a.beta_ref[1], (float)a.beta_ref[2]);
   if (PROP == kPropClosedForm) {
     const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
     rh0 = q[0];
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
         n_tests += 1;
       } else {
         const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
-        const long long kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), inv_cdt, win.k0, win.n);
+        const long long kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), bref, inv_cdt, win.k0, win.n);
         long long lo, hi;
         bool ooh = false;
         n_tests += 1;
@@ -350,6 +352,7 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int split, cuda
   a.err = s.err;
   a.N = s.N;
   a.D = s.D;
+  for (int c = 0; c < 3; c++) a.beta_ref[c] = s.beta_ref[c];
   if (split < 1) split = 1;
   a.chunk = (s.N + split - 1) / split;
   dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock), (unsigned)split);

@@ -7,8 +7,9 @@
 //             (u = 2^-24: two roundings in each component of d, three in |d|^2, one in the table value
 //             L^2 and one in M), so |M| > kBand (|d|^2 + L^2) with kBand = 32u decides exactly as the
 //             FP64 test would; otherwise the FP64 test itself (reference operation order) decides. The
-//             bracket is therefore the FP64 one. Search: the paper's bisection or the guarded galloping
-//             search from the uniform-motion guess.
+//             bracket is therefore the FP64 one. Search: the paper's bisection, or the guarded galloping
+//             search from the uniform-motion guess; with the guess, the records of the one or two slots
+//             the guess points at are loaded together, so a correct guess needs a single gather round.
 //   retarded  in light units (lengths in m, velocities as beta = v/c): with L1 = c (t - t1) and d = r - w1,
 //             (1 - beta1^2) s^2 + 2 (d.beta1 - L1) s + (L1^2 - |d|^2) = 0 for s = c (t_r - t1) (eq:dt),
 //             smaller root without cancellation; eta = d - beta1 s (eq:linear, retarded position w1 + v1 dt);
@@ -16,10 +17,14 @@
 //             (eq:linear2 out of history: beta = beta1, alpha = 0); 1 - beta^2 = 1/gamma1^2 - dbeta.(2 beta1
 //             + dbeta), so 1 - beta^2 is never formed by cancellation.
 //   fields    with u' = eta_hat - beta: E = (q / 4 pi eps0) R [(1 - beta^2) u' + eta x (u' x alpha)] / (eta.u')^3
-//             (eq:LW_E with v' = c u', a = c^2 alpha), B = eta_hat x E / c (eq:LW_B).
-//   sums      Kahan-compensated FP32 per target, converted to FP64 at the end.
-// Targets are taken in the spatial order of order.cu so that a warp's retarded slots of a source are
-// close together in the source-major FP32 shadow ring.
+//             (eq:LW_E with v' = c u', a = c^2 alpha), B = eta_hat x E / c (eq:LW_B). eta.u' = R - eta.beta
+//             cancels for a source moving towards the target; there it is formed as
+//             [R^2 (1 - beta^2) + |eta x beta|^2] / (R + eta.beta), a sum of non-negative terms.
+//   sums      FP32 partial sums over 8 sources, added with Kahan compensation into FP32 running totals,
+//             converted to FP64 at the end.
+// Sources are walked in tiles of kTile whose present records and FP32 charges are staged in shared
+// memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
+// source are close together in the source-major FP32 shadow ring.
 #include "emppp_internal.cuh"
 #include "shadow.cuh"
 
@@ -27,9 +32,14 @@ namespace emppp {
 
 namespace {
 
+#ifndef EMPPP_MIXED_MIN_BLOCKS
+#define EMPPP_MIXED_MIN_BLOCKS 6  // resident blocks per SM the register budget is fitted to
+#endif
+
 constexpr int kBlock = 128;
+constexpr int kTile = 128;
+constexpr int kSub = 8;  // sources per FP32 partial sum
 constexpr float kBand = 32.0f * 5.9604645e-8f;  // 32 u, u = 2^-24
-constexpr double kCoulomb = 1.0 / (4.0 * kPi * kEps0);
 
 struct MixedArgs {
   const float4* __restrict__ rec32;
@@ -38,7 +48,7 @@ struct MixedArgs {
   const float* __restrict__ lhs32;
   const float* __restrict__ ct32;
   const float* __restrict__ icdt32;
-  const double* __restrict__ wts;
+  const float* __restrict__ kq32;  // -e w_j / (4 pi eps0), FP32
   const int* __restrict__ order;
   const StepState* __restrict__ state;
   double* __restrict__ out;
@@ -46,9 +56,10 @@ struct MixedArgs {
   double* __restrict__ B;
   unsigned long long* stats;
   int* err;
-  long long N;
+  int N;
   int D;
-  long long chunk;
+  int chunk;  // sources per slice
+  float bref[3];  // reference velocity of the shadow's dbeta
 };
 
 struct Target {
@@ -57,14 +68,26 @@ struct Target {
   bool exact_only;  // coordinates too far from the split origin for the FP32 band: FP64 tests only
 };
 
+// slots of the usable window k0..n are addressed by their offset l = k - k0 (0..nw-1)
 struct Window {
-  long long k0, n;
-  int p0, D;
-  __device__ __forceinline__ int phys(long long k) const {
-    int p = p0 + (int)(k - k0);
+  int p0, D, nw;
+  __device__ __forceinline__ int phys(int l) const {
+    const int p = p0 + l;
     return p >= D ? p - D : p;
   }
 };
+
+struct Rec {  // one FP32 shadow record
+  float4 q0, q1, q2;
+};
+
+__device__ __forceinline__ Rec load_rec(const float4* __restrict__ src32, int p) {
+  Rec r;
+  r.q0 = __ldg(src32 + 3 * p);
+  r.q1 = __ldg(src32 + 3 * p + 1);
+  r.q2 = __ldg(src32 + 3 * p + 2);
+  return r;
+}
 
 __device__ __forceinline__ bool exact_test(const Target& r, const double* __restrict__ w, double lhs) {
   const double d0 = __dsub_rn(r.r0, __ldg(w + 0));
@@ -74,12 +97,9 @@ __device__ __forceinline__ bool exact_test(const Target& r, const double* __rest
   return lhs <= rhs;
 }
 
-// P(k) at physical slot p of the source whose rings start at src32 / src64
-__device__ __forceinline__ bool node_test(const Target& r, const float4* __restrict__ src32,
-                                          const double* __restrict__ src64, int p, const MixedArgs& a,
-                                          unsigned& n_fb) {
-  const float4 q0 = __ldg(src32 + 3 * p);
-  const float4 q1 = __ldg(src32 + 3 * p + 1);
+// P(k) from the slot's position parts q0, q1 (already loaded) at physical slot p
+__device__ __forceinline__ bool node_test_q(const Target& r, float4 q0, float4 q1, const double* __restrict__ src64,
+                                            int p, const MixedArgs& a, unsigned& n_fb) {
   const float d0 = (r.h0 - q0.x) + (r.l0 - q1.x);
   const float d1 = (r.h1 - q0.y) + (r.l1 - q1.y);
   const float d2 = (r.h2 - q0.z) + (r.l2 - q1.z);
@@ -95,21 +115,47 @@ __device__ __forceinline__ bool node_test(const Target& r, const float4* __restr
   return exact_test(r, src64 + 6 * p, __ldg(a.lhs64 + p));
 }
 
+__device__ __forceinline__ bool node_test(const Target& r, const float4* __restrict__ src32,
+                                          const double* __restrict__ src64, int p, const MixedArgs& a,
+                                          unsigned& n_fb) {
+  return node_test_q(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1), src64, p, a, n_fb);
+}
+
+// bisection between offsets lo (P false) and hi (P true); returns lo
+__device__ __forceinline__ int bisect(const Target& r, const float4* __restrict__ src32, const double* __restrict__ src64,
+                                      const Window& w, int lo, int hi, const MixedArgs& a, unsigned& n_tests,
+                                      unsigned& n_fb) {
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    n_tests += 1;
+    if (node_test(r, src32, src64, w.phys(m), a, n_fb))
+      hi = m;
+    else
+      lo = m;
+  }
+  return lo;
+}
+
 }  // namespace
 
 template <int PROP>
-__global__ void __launch_bounds__(kBlock) pair_mixed_kernel(MixedArgs a) {
-  const long long N = a.N;
+__global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
+  __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
+  __shared__ float4 s_q2[kTile];  // (beta, gamma^2)
+  __shared__ float s_kq[kTile];
+
+  const int N = a.N;
   const int D = a.D;
-  const long long t = (long long)blockIdx.x * kBlock + threadIdx.x;
+  const int t = blockIdx.x * kBlock + threadIdx.x;
   const bool active = t < N;
-  const long long i = active ? (a.order ? (long long)a.order[t] : t) : 0;
+  const int i = active ? (a.order ? a.order[t] : t) : 0;
 
   Window win;
-  win.n = a.state->n;
-  win.k0 = a.state->k0;
+  const long long n_abs = a.state->n;
+  const long long k0_abs = a.state->k0;
   win.p0 = a.state->p0;
   win.D = D;
+  win.nw = (int)(n_abs - k0_abs) + 1;
   const int pn = a.state->pn;
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
 
@@ -130,179 +176,248 @@ __global__ void __launch_bounds__(kBlock) pair_mixed_kernel(MixedArgs a) {
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
 
-  const long long j_begin = (long long)blockIdx.y * a.chunk;
-  const long long j_end = min(N, j_begin + a.chunk);
+  const int j_begin = blockIdx.y * a.chunk;
+  const int j_end = min(N, j_begin + a.chunk);
 
   float Es[3] = {0.f, 0.f, 0.f}, Ec[3] = {0.f, 0.f, 0.f}, Bs[3] = {0.f, 0.f, 0.f}, Bc[3] = {0.f, 0.f, 0.f};
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   int errbits = 0;
-  const float kq_unit = (float)(-kQe * kCoulomb);
+  const float ic = (float)(1.0 / kC);
 
-  for (long long j = j_begin; active && j < j_end; ++j) {
-    if (j == i) continue;
-    const float4* src32 = a.rec32 + (size_t)j * D * 3;
-    const double* src64 = a.rec64 + (size_t)j * D * 6;
-    // ---- bracket --------------------------------------------------------------------------------
-    long long k1;
-    int br;
-    if (PROP == kPropBisect) {
-      n_tests += 1;
-      if (node_test(r, src32, src64, win.p0, a, n_fb)) {
-        k1 = win.k0;
-        br = 0;
-      } else {
-        n_tests += 1;
-        if (!node_test(r, src32, src64, win.phys(win.n - 1), a, n_fb)) {
-          k1 = win.n - 1;
-          br = 1;
-        } else {
-          long long lo = win.k0, hi = win.n;
-          while (hi - lo > 1) {
-            const long long m = (lo + hi) >> 1;
-            n_tests += 1;
-            if (node_test(r, src32, src64, win.phys(m), a, n_fb))
-              hi = m;
-            else
-              lo = m;
-          }
-          k1 = lo;
-          br = 2;
-        }
-      }
-    } else {
-      if (win.n == win.k0) {
-        k1 = win.k0;
-        br = 0;
-        n_tests += 1;
-      } else {
-        const long long kg = uniform_motion_guess(r.h0, r.h1, r.h2, __ldg(src32 + 3 * pn), __ldg(src32 + 3 * pn + 2),
-                                                  inv_cdt, win.k0, win.n);
-        long long lo = kg, hi = kg;
-        bool ooh = false;
-        n_tests += 1;
-        if (node_test(r, src32, src64, win.phys(kg), a, n_fb)) {
-          long long s = 1;
-          for (;;) {
-            if (hi == win.k0) {
-              ooh = true;
-              break;
-            }
-            lo = hi - s;
-            if (lo < win.k0) lo = win.k0;
-            n_tests += 1;
-            if (!node_test(r, src32, src64, win.phys(lo), a, n_fb)) break;
-            hi = lo;
-            s <<= 1;
-          }
-        } else {
-          long long s = 1;
-          for (;;) {
-            hi = lo + s;
-            if (hi >= win.n) {
-              hi = win.n;
-              break;
-            }
-            n_tests += 1;
-            if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
-            lo = hi;
-            s <<= 1;
-          }
-        }
-        if (ooh) {
-          k1 = win.k0;
+  for (int tile = j_begin; tile < j_end; tile += kTile) {
+    const int tn = min(kTile, j_end - tile);
+    __syncthreads();
+    if (threadIdx.x < tn) {
+      const int j = tile + threadIdx.x;
+      const float4* q = a.rec32 + ((size_t)j * D + pn) * 3;
+      s_q0[threadIdx.x] = q[0];
+      s_q2[threadIdx.x] = q[2];
+      s_kq[threadIdx.x] = a.kq32[j];
+    }
+    __syncthreads();
+    for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
+      float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      const int jend = min(jj0 + kSub, tn);
+      for (int jj = jj0; active && jj < jend; ++jj) {
+        const int j = tile + jj;
+        if (j == i) continue;
+        const float4* src32 = a.rec32 + (size_t)j * D * 3;
+        const double* src64 = a.rec64 + (size_t)j * D * 6;
+        // ---- bracket: offsets l1 (older node) and the records it needs ---------------------------
+        int l1;
+        int br;
+        Rec A;          // record of the older node
+        float4 q2b;     // (beta, gamma^2) of the newer node (regular brackets)
+        bool have_b = false;
+        if (win.nw == 1) {
+          // n = k0: only the present slot exists; every pair is out of history
+          n_tests += 1;
+          l1 = 0;
           br = 0;
-        } else {
-          while (hi - lo > 1) {
-            const long long m = (lo + hi) >> 1;
+          A = load_rec(src32, win.phys(0));
+        } else if (PROP == kPropBisect) {
+          n_tests += 1;
+          const int pa = win.phys(0);
+          A = load_rec(src32, pa);
+          if (node_test_q(r, A.q0, A.q1, src64, pa, a, n_fb)) {
+            l1 = 0;
+            br = 0;
+          } else {
             n_tests += 1;
-            if (node_test(r, src32, src64, win.phys(m), a, n_fb))
-              hi = m;
-            else
-              lo = m;
+            if (!node_test(r, src32, src64, win.phys(win.nw - 2), a, n_fb)) {
+              l1 = win.nw - 2;
+              br = 1;
+            } else {
+              l1 = bisect(r, src32, src64, win, 0, win.nw - 1, a, n_tests, n_fb);
+              br = 2;
+            }
+            if (l1 != 0) A = load_rec(src32, win.phys(l1));
           }
-          k1 = lo;
-          br = (k1 == win.n - 1) ? 1 : 2;
+        } else {
+          // uniform-motion guess from the staged present record of the source
+          const float4 g0 = s_q0[jj], g2 = s_q2[jj];
+          const float d0 = r.h0 - g0.x, d1 = r.h1 - g0.y, d2 = r.h2 - g0.z;
+          const float db = d0 * (a.bref[0] + g2.x) + d1 * (a.bref[1] + g2.y) + d2 * (a.bref[2] + g2.z);
+          const float dd = d0 * d0 + d1 * d1 + d2 * d2;
+          const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
+          const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
+          const float steps = fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
+          // offset of the guessed older node: (nw - 2) - steps, clamped to 0..nw-2
+          const int lraw = (steps > (float)(win.nw - 2)) ? -1 : (win.nw - 2) - (int)steps;
+          const int lg = max(lraw, 0);
+          const int pg = win.phys(lg);
+          A = load_rec(src32, pg);
+          bool fast = false;
+          if (lraw < 0) {
+            // predicted out of history: the only record needed is the oldest slot's
+            n_tests += 1;
+            if (node_test_q(r, A.q0, A.q1, src64, pg, a, n_fb)) {
+              l1 = 0;
+              br = 0;
+              fast = true;
+            } else {
+              // guess wrong: gallop up from lo = 0 (P false)
+              int lo = 0, hi, s = 1;
+              for (;;) {
+                hi = lo + s;
+                if (hi >= win.nw - 1) {
+                  hi = win.nw - 1;
+                  break;
+                }
+                n_tests += 1;
+                if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
+                lo = hi;
+                s <<= 1;
+              }
+              l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
+              br = (l1 == win.nw - 2) ? 1 : 2;
+            }
+          } else {
+            // predicted bracket [lg, lg + 1]: load both records at once
+            const int pg1 = win.phys(lg + 1);
+            const Rec Bn = load_rec(src32, pg1);
+            n_tests += 1;
+            const bool tA = node_test_q(r, A.q0, A.q1, src64, pg, a, n_fb);
+            if (!tA) {
+              bool tB = true;  // P(n) is always true
+              if (lg + 1 < win.nw - 1) {
+                n_tests += 1;
+                tB = node_test_q(r, Bn.q0, Bn.q1, src64, pg1, a, n_fb);
+              }
+              if (tB) {
+                l1 = lg;
+                br = (l1 == win.nw - 2) ? 1 : 2;
+                q2b = Bn.q2;
+                have_b = true;
+                fast = true;
+              } else {
+                // gallop up from lo = lg + 1 (P false)
+                int lo = lg + 1, hi, s = 1;
+                for (;;) {
+                  hi = lo + s;
+                  if (hi >= win.nw - 1) {
+                    hi = win.nw - 1;
+                    break;
+                  }
+                  n_tests += 1;
+                  if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
+                  lo = hi;
+                  s <<= 1;
+                }
+                l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
+                br = (l1 == win.nw - 2) ? 1 : 2;
+              }
+            } else if (lg == 0) {
+              l1 = 0;
+              br = 0;
+              fast = true;
+            } else {
+              // gallop down from hi = lg (P true)
+              int hi = lg, lo = lg, s = 1;
+              bool ooh = false;
+              for (;;) {
+                if (hi == 0) {
+                  ooh = true;
+                  break;
+                }
+                lo = max(hi - s, 0);
+                n_tests += 1;
+                if (!node_test(r, src32, src64, win.phys(lo), a, n_fb)) break;
+                hi = lo;
+                s <<= 1;
+              }
+              if (ooh) {
+                l1 = 0;
+                br = 0;
+              } else {
+                l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
+                br = (l1 == win.nw - 2) ? 1 : 2;
+              }
+            }
+          }
+          if (!fast) A = load_rec(src32, win.phys(l1));
         }
-      }
-    }
-    if (br == 0)
-      n_ooh++;
-    else if (br == 1)
-      n_sc++;
-    else
-      n_bi++;
+        if (br == 0)
+          n_ooh++;
+        else if (br == 1)
+          n_sc++;
+        else
+          n_bi++;
 
-    // ---- retarded state (light units) --------------------------------------------------------------
-    const int p1 = win.phys(k1);
-    const float4 q0 = __ldg(src32 + 3 * p1);
-    const float4 q1 = __ldg(src32 + 3 * p1 + 1);
-    const float4 q2 = __ldg(src32 + 3 * p1 + 2);
-    const float d0 = (r.h0 - q0.x) + (r.l0 - q1.x);
-    const float d1 = (r.h1 - q0.y) + (r.l1 - q1.y);
-    const float d2 = (r.h2 - q0.z) + (r.l2 - q1.z);
-    const float L1 = __ldg(a.ct32 + p1);
-    const float b10 = q2.x, b11 = q2.y, b12 = q2.z;
-    const float ig2 = q0.w, g2 = q2.w;
-    const float hb = (d0 * b10 + d1 * b11 + d2 * b12) - L1;
-    const float C0 = fmaf(L1, L1, -(d0 * d0 + d1 * d1 + d2 * d2));
-    const float qd = fmaf(hb, hb, -ig2 * C0);
-    if (!(qd >= 0.f) || !(ig2 > 0.f)) {
-      errbits |= kErrDisc;
-      continue;
-    }
-    const float sq = qd > 0.f ? qd * rsqrtf(qd) : 0.f;
-    const float s = (hb <= 0.f) ? __fdividef(C0, sq - hb) : -(hb + sq) * g2;
-    const float e0 = fmaf(-b10, s, d0), e1 = fmaf(-b11, s, d1), e2 = fmaf(-b12, s, d2);
-    float be0 = b10, be1 = b11, be2 = b12, al0 = 0.f, al1 = 0.f, al2 = 0.f, ug = ig2;
-    if (br != 0) {
-      const int p2 = p1 + 1 == D ? 0 : p1 + 1;
-      const float4 q2b = __ldg(src32 + 3 * p2 + 2);
-      const float icdt = __ldg(a.icdt32 + p1);
-      const float db0 = q2b.x - b10, db1 = q2b.y - b11, db2 = q2b.z - b12;
-      al0 = db0 * icdt;
-      al1 = db1 * icdt;
-      al2 = db2 * icdt;
-      const float df = s * icdt;
-      const float x0 = db0 * df, x1 = db1 * df, x2 = db2 * df;
-      be0 = b10 + x0;
-      be1 = b11 + x1;
-      be2 = b12 + x2;
-      ug = ig2 - (x0 * (2.f * b10 + x0) + x1 * (2.f * b11 + x1) + x2 * (2.f * b12 + x2));
-    }
-    // ---- Lienard-Wiechert fields -------------------------------------------------------------------
-    const float R2 = e0 * e0 + e1 * e1 + e2 * e2;
-    const float invR = rsqrtf(R2);
-    const float R = R2 * invR;
-    const float n0 = e0 * invR, n1 = e1 * invR, n2 = e2 * invR;
-    const float u0 = n0 - be0, u1 = n1 - be1, u2 = n2 - be2;
-    const float eu = R - (e0 * be0 + e1 * be1 + e2 * be2);
-    if (!(R2 > 0.f) || !(eu > 0.f)) {
-      errbits |= kErrCoincide;
-      continue;
-    }
-    const float ieu = __fdividef(1.f, eu);
-    const float kq = kq_unit * (float)__ldg(a.wts + j);
-    const float pref = kq * (R * ieu) * ieu * ieu;
-    // eta x (u' x alpha)
-    const float c0 = u1 * al2 - u2 * al1, c1 = u2 * al0 - u0 * al2, c2 = u0 * al1 - u1 * al0;
-    const float F0 = fmaf(ug, u0, e1 * c2 - e2 * c1);
-    const float F1 = fmaf(ug, u1, e2 * c0 - e0 * c2);
-    const float F2 = fmaf(ug, u2, e0 * c1 - e1 * c0);
-    const float E0 = pref * F0, E1 = pref * F1, E2 = pref * F2;
-    const float ic = (float)(1.0 / kC);
-    const float B0 = (n1 * E2 - n2 * E1) * ic, B1 = (n2 * E0 - n0 * E2) * ic, B2 = (n0 * E1 - n1 * E0) * ic;
-    // ---- Kahan-compensated sums ---------------------------------------------------------------------
-    const float xs[6] = {E0, E1, E2, B0, B1, B2};
+        // ---- retarded state (light units) --------------------------------------------------------
+        const int p1 = win.phys(l1);
+        const float d0 = (r.h0 - A.q0.x) + (r.l0 - A.q1.x);
+        const float d1 = (r.h1 - A.q0.y) + (r.l1 - A.q1.y);
+        const float d2 = (r.h2 - A.q0.z) + (r.l2 - A.q1.z);
+        const float L1 = __ldg(a.ct32 + p1);
+        const float b10 = a.bref[0] + A.q2.x, b11 = a.bref[1] + A.q2.y, b12 = a.bref[2] + A.q2.z;
+        const float ig2 = A.q0.w, g2 = A.q2.w;
+        const float hb = (d0 * b10 + d1 * b11 + d2 * b12) - L1;
+        const float C0 = fmaf(L1, L1, -(d0 * d0 + d1 * d1 + d2 * d2));
+        const float qd = fmaf(hb, hb, -ig2 * C0);
+        if (!(qd >= 0.f) || !(ig2 > 0.f)) {
+          errbits |= kErrDisc;
+          continue;
+        }
+        const float sq = qd * rsqrtf(fmaxf(qd, 1e-37f));
+        const float s = (hb <= 0.f) ? __fdividef(C0, sq - hb) : -(hb + sq) * g2;
+        const float e0 = fmaf(-b10, s, d0), e1 = fmaf(-b11, s, d1), e2 = fmaf(-b12, s, d2);
+        float be0 = b10, be1 = b11, be2 = b12, al0 = 0.f, al1 = 0.f, al2 = 0.f, ug = ig2;
+        if (br != 0) {
+          if (!have_b) q2b = __ldg(src32 + 3 * win.phys(l1 + 1) + 2);
+          const float icdt = __ldg(a.icdt32 + p1);
+          const float db0 = q2b.x - A.q2.x, db1 = q2b.y - A.q2.y, db2 = q2b.z - A.q2.z;
+          al0 = db0 * icdt;
+          al1 = db1 * icdt;
+          al2 = db2 * icdt;
+          const float df = s * icdt;
+          const float x0 = db0 * df, x1 = db1 * df, x2 = db2 * df;
+          be0 = b10 + x0;
+          be1 = b11 + x1;
+          be2 = b12 + x2;
+          ug = ig2 - (x0 * (2.f * b10 + x0) + x1 * (2.f * b11 + x1) + x2 * (2.f * b12 + x2));
+        }
+        // ---- Lienard-Wiechert fields ---------------------------------------------------------------
+        const float R2 = e0 * e0 + e1 * e1 + e2 * e2;
+        const float invR = rsqrtf(R2);
+        const float R = R2 * invR;
+        const float n0 = e0 * invR, n1 = e1 * invR, n2 = e2 * invR;
+        const float u0 = n0 - be0, u1 = n1 - be1, u2 = n2 - be2;
+        const float eb = e0 * be0 + e1 * be1 + e2 * be2;
+        // 1 / (eta . u'): R - eta.beta directly when eta.beta <= 0, else the rationalised form
+        const float xb0 = e1 * be2 - e2 * be1, xb1 = e2 * be0 - e0 * be2, xb2 = e0 * be1 - e1 * be0;
+        const float rat = fmaf(R2, ug, xb0 * xb0 + xb1 * xb1 + xb2 * xb2);
+        const bool fw = eb > 0.f;
+        const float ieu = __fdividef(fw ? (R + eb) : 1.f, fw ? rat : (R - eb));
+        if (!(R2 > 0.f) || !(ieu > 0.f) || !(ieu < 3.0e38f)) {
+          errbits |= kErrCoincide;
+          continue;
+        }
+        const float pref = s_kq[jj] * (R * ieu) * ieu * ieu;
+        // eta x (u' x alpha)
+        const float c0 = u1 * al2 - u2 * al1, c1 = u2 * al0 - u0 * al2, c2 = u0 * al1 - u1 * al0;
+        const float E0 = pref * fmaf(ug, u0, e1 * c2 - e2 * c1);
+        const float E1 = pref * fmaf(ug, u1, e2 * c0 - e0 * c2);
+        const float E2 = pref * fmaf(ug, u2, e0 * c1 - e1 * c0);
+        P[0] += E0;
+        P[1] += E1;
+        P[2] += E2;
+        P[3] += (n1 * E2 - n2 * E1) * ic;
+        P[4] += (n2 * E0 - n0 * E2) * ic;
+        P[5] += (n0 * E1 - n1 * E0) * ic;
+      }
+      // Kahan-add the partial sums of these kSub sources
 #pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const float y = xs[c] - Ec[c];
-      const float tt = Es[c] + y;
-      Ec[c] = (tt - Es[c]) - y;
-      Es[c] = tt;
-      const float yb = xs[3 + c] - Bc[c];
-      const float tb = Bs[c] + yb;
-      Bc[c] = (tb - Bs[c]) - yb;
-      Bs[c] = tb;
+      for (int c = 0; c < 3; c++) {
+        const float y = P[c] - Ec[c];
+        const float tt = Es[c] + y;
+        Ec[c] = (tt - Es[c]) - y;
+        Es[c] = tt;
+        const float yb = P[3 + c] - Bc[c];
+        const float tb = Bs[c] + yb;
+        Bc[c] = (tb - Bs[c]) - yb;
+        Bs[c] = tb;
+      }
     }
   }
   if (active) {
@@ -348,7 +463,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.lhs32 = s.tab.lhs32;
   a.ct32 = s.tab.ct32;
   a.icdt32 = s.tab.icdt32;
-  a.wts = s.wts;
+  a.kq32 = s.kq32;
   a.order = order;
   a.state = s.state;
   a.out = s.partial;
@@ -356,10 +471,11 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.B = s.Bself;
   a.stats = s.stats;
   a.err = s.err;
-  a.N = s.N;
+  a.N = (int)s.N;
   a.D = s.D;
+  for (int c = 0; c < 3; c++) a.bref[c] = (float)s.beta_ref[c];
   if (split < 1) split = 1;
-  a.chunk = (s.N + split - 1) / split;
+  a.chunk = (int)((s.N + split - 1) / split);
   dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock), (unsigned)split);
   if (proposal == kPropClosedForm)
     pair_mixed_kernel<kPropClosedForm><<<grid, kBlock, 0, st>>>(a);

@@ -91,7 +91,7 @@ __global__ void push_kernel(DeviceState s, BextParams bp) {
   reinterpret_cast<double2*>(r)[1] = make_double2(x2, v0);
   reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
   float4 q[3];
-  shadow_record(s.origin, x0, x1, x2, v0, v1, v2, gamma2_of_u(u[0], u[1], u[2]), q);
+  shadow_record(s.origin, s.beta_ref, x0, x1, x2, v0, v1, v2, gamma2_of_u(u[0], u[1], u[2]), q);
   float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)i * s.D + pnext) * 12);
   o[0] = q[0];
   o[1] = q[1];

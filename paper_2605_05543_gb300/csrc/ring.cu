@@ -13,7 +13,7 @@ __device__ __forceinline__ void write_record(const DeviceState& s, long long j, 
   reinterpret_cast<double2*>(r)[1] = make_double2(w2, v0);
   reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
   float4 q[3];
-  shadow_record(s.origin, w0, w1, w2, v0, v1, v2, gamma2_of_v(v0, v1, v2), q);
+  shadow_record(s.origin, s.beta_ref, w0, w1, w2, v0, v1, v2, gamma2_of_v(v0, v1, v2), q);
   float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)j * s.D + p) * 12);
   o[0] = q[0];
   o[1] = q[1];
@@ -45,6 +45,7 @@ __global__ void init_slot0_kernel(DeviceState s, const double* __restrict__ x, c
   s.u[3 * i + 1] = u1;
   s.u[3 * i + 2] = u2;
   s.wts[i] = w ? w[i] : 1.0;
+  s.kq32[i] = (float)(-kQe * s.wts[i] / (4.0 * kPi * kEps0));
 }
 
 __global__ void scatter_slot_kernel(DeviceState s, int p, const double* __restrict__ W, const double* __restrict__ V) {
@@ -79,6 +80,7 @@ __global__ void set_state_kernel(DeviceState s, long long n, double t, double dt
     s.u[3 * i + 2] = u[3 * i + 2];
   }
   s.wts[i] = w ? w[i] : 1.0;
+  s.kq32[i] = (float)(-kQe * s.wts[i] / (4.0 * kPi * kEps0));
 }
 
 // Per-step slot tables over the usable window k0..n (Sec. 2.2): the squared light-travel distance
