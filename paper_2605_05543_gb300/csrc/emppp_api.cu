@@ -57,6 +57,9 @@ struct emppp_ctx {
   int* ord_scratch = nullptr;  // bbox (6) + cell histogram
   unsigned short* ord_key = nullptr;
   int* order = nullptr;
+  // resident blocks per SM of the pair kernels (queried on first use), per proposal
+  int blocks_fp64[2] = {0, 0};
+  int blocks_mixed[2] = {0, 0};
   std::vector<void*> allocs;
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
@@ -103,25 +106,33 @@ emppp_status validate_options(const emppp_options* o) {
   return EMPPP_OK;
 }
 
-// Number of source slices per target block: all blocks of the pair kernel are resident at once,
-// so the step takes as long as the busiest SM; pick the smallest split whose blocks spread over the
-// SMs within 5% of evenly (or the most even one).
-int choose_split(const emppp_ctx* c) {
-  if (c->opt.source_split > 0) return c->opt.source_split < c->ds.max_split ? c->opt.source_split : c->ds.max_split;
-  const long long ntb = (c->N + 127) / 128;
-  int best = 1;
-  double best_eff = 0.0;
-  for (int s = 1; s <= c->ds.max_split; s++) {
-    if (s > 1 && c->N / s < 16) break;
-    const double per_sm = (double)(ntb * s) / c->num_sms;
-    const double eff = per_sm / (double)((ntb * s + c->num_sms - 1) / c->num_sms);
-    if (eff > best_eff + 1e-9) {
-      best_eff = eff;
-      best = s;
-    }
-    if (eff >= 0.95) break;
+// Work split of the persistent pair kernel: one block per resident slot (from the occupancy of the
+// kernel actually launched) and about 16 work items per block, so that the uneven cost of the items
+// (the branch mix differs across the bunch) evens out; chunks hold at least 256 sources.
+PairSchedule make_schedule(emppp_ctx* c) {
+  const bool mixed = c->opt.precision == EMPPP_MIXED;
+  int& nb = mixed ? c->blocks_mixed[c->opt.proposal & 1] : c->blocks_fp64[c->opt.proposal & 1];
+  if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal) : max_blocks_pair_fp64(c->opt.proposal);
+  const long long R = (long long)nb * c->num_sms;
+  PairSchedule sc;
+  sc.ntb = (int)((c->N + 127) / 128);
+  long long nchunk;
+  if (c->opt.source_split > 0) {
+    nchunk = c->opt.source_split;
+  } else {
+    nchunk = (16 * R + sc.ntb - 1) / sc.ntb;
+    const long long by_size = (c->N + 255) / 256;
+    if (nchunk > by_size) nchunk = by_size;
   }
-  return best;
+  if (nchunk > c->ds.max_split) nchunk = c->ds.max_split;
+  if (nchunk < 1) nchunk = 1;
+  long long chunk = (c->N + nchunk - 1) / nchunk;
+  chunk = (chunk + 127) / 128 * 128;
+  sc.chunk = (int)chunk;
+  sc.nchunk = (int)((c->N + chunk - 1) / chunk);
+  sc.nitems = sc.ntb * sc.nchunk;
+  sc.grid = (int)(R < sc.nitems ? R : sc.nitems);
+  return sc;
 }
 
 emppp_status read_err(emppp_handle h) {
@@ -223,9 +234,11 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   s.N = n;
   s.D = history_depth;
   const size_t N = (size_t)n, D = (size_t)history_depth;
-  const long long ntb = (n + 127) / 128;
-  long long ms = (8LL * c->num_sms + ntb - 1) / ntb;
-  s.max_split = (int)(ms < 1 ? 1 : (ms > 64 ? 64 : ms));
+  {
+    // partial sums of up to 64 source chunks, within 1 GiB
+    const long long by_mem = (1LL << 30) / ((long long)n * 48);
+    s.max_split = (int)(by_mem < 1 ? 1 : (by_mem > 64 ? 64 : by_mem));
+  }
 #define ALLOC(p, cnt)                   \
   do {                                  \
     st = dalloc(c, &(p), (cnt));        \
@@ -248,6 +261,7 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   ALLOC(s.Bout, N * 3);
   ALLOC(s.partial, (size_t)s.max_split * N * 6);
   ALLOC(s.state, 1);
+  ALLOC(s.work, 1);
   ALLOC(s.stats, kStatCount);
   ALLOC(s.err, 1);
   ALLOC(c->staging, N * 7);
@@ -463,7 +477,7 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
     }
     bp.m0 = bext->m0;
   }
-  const int split = choose_split(h);
+  const PairSchedule sc = make_schedule(h);
   for (int64_t k = 0; k < nsteps; k++) {
     cudaEvent_t* ev = nullptr;
     if (h->opt.timing && h->ev_used < emppp_ctx::kTimedSteps) ev = &h->events[4 * h->ev_used++];
@@ -477,12 +491,12 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
     if (ev) CU(cudaEventRecord(ev[1], h->stream));
     if (h->opt.pair_fields) {
       if (h->opt.precision == EMPPP_MIXED)
-        CU(launch_pair_mixed(h->ds, h->order, h->opt.proposal, split, h->stream));
+        CU(launch_pair_mixed(h->ds, h->order, h->opt.proposal, sc, h->stream));
       else
-        CU(launch_pair_fp64(h->ds, h->opt.proposal, split, h->stream));
+        CU(launch_pair_fp64(h->ds, h->opt.proposal, sc, h->stream));
       h->launches += 1;
-      if (split > 1) {
-        CU(launch_reduce_partials(h->ds, split, h->stream));
+      if (sc.nchunk > 1) {
+        CU(launch_reduce_partials(h->ds, sc.nchunk, h->stream));
         h->launches += 1;
       }
       h->pairs_acc += h->N * (h->N - 1);

@@ -73,8 +73,9 @@ struct DeviceState {
   double* Eself;
   double* Bself;
   double* Bout;
-  double* partial;  // [S][N][6] per-source-slice partial sums
-  int max_split;
+  double* partial;  // [C][N][6] per-source-chunk partial sums
+  int max_split;    // chunks the partial buffer holds
+  int* work;        // work-item counter of the persistent pair kernels
   StepState* state;
   unsigned long long* stats;  // [kStatCount]
   int* err;
@@ -89,6 +90,17 @@ struct BextParams {
   double center[3];
 };
 
+// Work split of a persistent pair kernel: items are (source chunk, target tile of 128) pairs taken
+// chunk-major from an atomic counter by `grid` resident blocks; per-chunk partial sums are reduced in a
+// fixed order afterwards (nchunk > 1).
+struct PairSchedule {
+  int ntb;     // target tiles
+  int nchunk;  // source chunks
+  int chunk;   // sources per chunk
+  int nitems;  // ntb * nchunk
+  int grid;    // blocks launched
+};
+
 // ---- launchers (each in its own translation unit) ------------------------------------------
 // ring.cu
 cudaError_t launch_init_slot0(const DeviceState& s, const double* x, const double* u, const double* w,
@@ -101,8 +113,9 @@ cudaError_t launch_prep(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_advance(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st);
 // pair_fp64.cu
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int split, cudaStream_t st);
-cudaError_t launch_reduce_partials(const DeviceState& s, int split, cudaStream_t st);
+int max_blocks_pair_fp64(int proposal);
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairSchedule& sc, cudaStream_t st);
+cudaError_t launch_reduce_partials(const DeviceState& s, int nchunk, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
 cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st);
@@ -111,6 +124,8 @@ size_t order_scratch_ints();
 cudaError_t launch_target_order(const DeviceState& s, int* bbox, int* hist, unsigned short* key, int* order,
                                 cudaStream_t st);
 // pair_mixed.cu
-cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, int split, cudaStream_t st);
+int max_blocks_pair_mixed(int proposal);
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairSchedule& sc,
+                              cudaStream_t st);
 
 }  // namespace emppp

@@ -41,7 +41,10 @@ struct PairArgs {
   int* err;
   long long N;
   int D;
-  long long chunk;  // sources per slice
+  long long chunk;  // sources per work item
+  int ntb;          // target tiles
+  int nitems;       // work items = source chunks x target tiles, chunk-major
+  int* work;        // work-item counter (zero at launch)
   double beta_ref[3];
 };
 
@@ -68,11 +71,9 @@ struct Window {
 
 template <int PROP>
 __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
+  __shared__ int s_item;
   const long long N = a.N;
   const int D = a.D;
-  const long long i = (long long)blockIdx.x * kBlock + threadIdx.x;
-  const bool active = i < N;
-  const long long ic = active ? i : 0;
 
   Window win;
   win.n = a.state->n;
@@ -81,26 +82,40 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   win.D = D;
   const int pn = a.state->pn;
   const double t = a.state->t;
+  const float3 bref = make_float3((float)a.beta_ref[0], (float)a.beta_ref[1], (float)a.beta_ref[2]);
+  const float inv_cdt = PROP == kPropClosedForm ? (float)(1.0 / (kC * a.state->dt)) : 0.f;
+
+  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
+  int errbits = 0;
+
+  // persistent blocks pull (source chunk, target tile) items, chunk-major, until none is left
+  for (;;) {
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
+  __syncthreads();
+  const int item = s_item;
+  if (item >= a.nitems) break;
+  const int chunk_id = item / a.ntb;
+  const int tb = item - chunk_id * a.ntb;
+  const long long i = (long long)tb * kBlock + threadIdx.x;
+  const bool active = i < N;
+  const long long ic = active ? i : 0;
 
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
-  float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f, inv_cdt = 0.f;
-  const float3 bref = make_float3((float)a.beta_ref[0], (float)a.beta_ref[1], (float)a.beta_ref[2]);
+  float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f;
   if (PROP == kPropClosedForm) {
     const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
     rh0 = q[0];
     rh1 = q[1];
     rh2 = q[2];
-    inv_cdt = (float)(1.0 / (kC * a.state->dt));
   }
 
-  const long long j_begin = (long long)blockIdx.y * a.chunk;
+  const long long j_begin = (long long)chunk_id * a.chunk;
   const long long j_end = min(N, j_begin + a.chunk);
 
   double Et[3] = {0, 0, 0}, Bt[3] = {0, 0, 0};
   double Ep[3] = {0, 0, 0}, Bp[3] = {0, 0, 0};
-  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
-  int errbits = 0;
   int in_block = 0;
 
   const double c2 = kC * kC;
@@ -283,19 +298,20 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     Bt[c] += Bp[c];
   }
   if (active) {
-    if (gridDim.y == 1) {
+    if (a.nitems == a.ntb) {
       for (int c = 0; c < 3; c++) {
         a.E[3 * i + c] = Et[c];
         a.B[3 * i + c] = Bt[c];
       }
     } else {
-      double* o = a.out + ((size_t)blockIdx.y * N + i) * 6;
+      double* o = a.out + ((size_t)chunk_id * N + i) * 6;
       for (int c = 0; c < 3; c++) {
         o[c] = Et[c];
         o[3 + c] = Bt[c];
       }
     }
   }
+  }  // work items
   // counters: one atomic per warp and counter
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
@@ -336,7 +352,16 @@ __global__ void zero_kernel(double* __restrict__ a, double* __restrict__ b, long
   }
 }
 
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int split, cudaStream_t st) {
+int max_blocks_pair_fp64(int proposal) {
+  int nb = 0;
+  if (proposal == kPropClosedForm)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm>, kBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect>, kBlock, 0);
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairSchedule& sc, cudaStream_t st) {
   PairArgs a;
   a.rec64 = s.rec64;
   a.rec32 = s.rec32;
@@ -352,19 +377,22 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int split, cuda
   a.err = s.err;
   a.N = s.N;
   a.D = s.D;
+  a.chunk = sc.chunk;
+  a.ntb = sc.ntb;
+  a.nitems = sc.nitems;
+  a.work = s.work;
   for (int c = 0; c < 3; c++) a.beta_ref[c] = s.beta_ref[c];
-  if (split < 1) split = 1;
-  a.chunk = (s.N + split - 1) / split;
-  dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock), (unsigned)split);
+  cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)
-    pair_fp64_kernel<kPropClosedForm><<<grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropClosedForm><<<sc.grid, kBlock, 0, st>>>(a);
   else
-    pair_fp64_kernel<kPropBisect><<<grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropBisect><<<sc.grid, kBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_partials(const DeviceState& s, int split, cudaStream_t st) {
-  reduce_partials_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s.partial, split, s.N, s.Eself, s.Bself);
+cudaError_t launch_reduce_partials(const DeviceState& s, int nchunk, cudaStream_t st) {
+  reduce_partials_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s.partial, nchunk, s.N, s.Eself, s.Bself);
   return cudaGetLastError();
 }
 

@@ -58,7 +58,10 @@ struct MixedArgs {
   int* err;
   int N;
   int D;
-  int chunk;  // sources per slice
+  int chunk;   // sources per work item
+  int ntb;     // target tiles (kBlock targets each)
+  int nitems;  // work items = source chunks x target tiles, chunk-major
+  int* work;   // work-item counter (zero at launch)
   float bref[3];  // reference velocity of the shadow's dbeta
 };
 
@@ -97,13 +100,15 @@ __device__ __forceinline__ bool exact_test(const Target& r, const double* __rest
   return lhs <= rhs;
 }
 
-// P(k) from the slot's position parts q0, q1 (already loaded) at physical slot p
-__device__ __forceinline__ bool node_test_q(const Target& r, float4 q0, float4 q1, const double* __restrict__ src64,
-                                            int p, const MixedArgs& a, unsigned& n_fb) {
-  const float d0 = (r.h0 - q0.x) + (r.l0 - q1.x);
-  const float d1 = (r.h1 - q0.y) + (r.l1 - q1.y);
-  const float d2 = (r.h2 - q0.z) + (r.l2 - q1.z);
-  const float D2 = d0 * d0 + d1 * d1 + d2 * d2;
+// r - w of a record, from the hi and lo parts (each component exact to two roundings)
+__device__ __forceinline__ float3 separation(const Target& r, float4 q0, float4 q1) {
+  return make_float3((r.h0 - q0.x) + (r.l0 - q1.x), (r.h1 - q0.y) + (r.l1 - q1.y), (r.h2 - q0.z) + (r.l2 - q1.z));
+}
+
+// P(k) from a separation d already formed at physical slot p
+__device__ __forceinline__ bool node_test_d(const Target& r, float3 d, const double* __restrict__ src64, int p,
+                                            const MixedArgs& a, unsigned& n_fb) {
+  const float D2 = d.x * d.x + d.y * d.y + d.z * d.z;
   const float L2 = __ldg(a.lhs32 + p);
   const float M = D2 - L2;
   const float band = kBand * (D2 + L2);
@@ -118,7 +123,7 @@ __device__ __forceinline__ bool node_test_q(const Target& r, float4 q0, float4 q
 __device__ __forceinline__ bool node_test(const Target& r, const float4* __restrict__ src32,
                                           const double* __restrict__ src64, int p, const MixedArgs& a,
                                           unsigned& n_fb) {
-  return node_test_q(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1), src64, p, a, n_fb);
+  return node_test_d(r, separation(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1)), src64, p, a, n_fb);
 }
 
 // bisection between offsets lo (P false) and hi (P true); returns lo
@@ -141,14 +146,12 @@ __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict_
 template <int PROP>
 __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
-  __shared__ float4 s_q2[kTile];  // (beta, gamma^2)
+  __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
 
+  __shared__ int s_item;
   const int N = a.N;
   const int D = a.D;
-  const int t = blockIdx.x * kBlock + threadIdx.x;
-  const bool active = t < N;
-  const int i = active ? (a.order ? a.order[t] : t) : 0;
 
   Window win;
   const long long n_abs = a.state->n;
@@ -158,6 +161,22 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
   win.nw = (int)(n_abs - k0_abs) + 1;
   const int pn = a.state->pn;
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
+
+  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
+  int errbits = 0;
+
+  // persistent blocks pull (source chunk, target tile) items, chunk-major, until none is left
+  for (;;) {
+  __syncthreads();
+  if (threadIdx.x == 0) s_item = atomicAdd(a.work, 1);
+  __syncthreads();
+  const int item = s_item;
+  if (item >= a.nitems) break;
+  const int chunk_id = item / a.ntb;
+  const int tb = item - chunk_id * a.ntb;
+  const int t = tb * kBlock + threadIdx.x;
+  const bool active = t < N;
+  const int i = active ? (a.order ? a.order[t] : t) : 0;
 
   Target r;
   {
@@ -176,12 +195,10 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
 
-  const int j_begin = blockIdx.y * a.chunk;
+  const int j_begin = chunk_id * a.chunk;
   const int j_end = min(N, j_begin + a.chunk);
 
   float Es[3] = {0.f, 0.f, 0.f}, Ec[3] = {0.f, 0.f, 0.f}, Bs[3] = {0.f, 0.f, 0.f}, Bc[3] = {0.f, 0.f, 0.f};
-  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
-  int errbits = 0;
   const float ic = (float)(1.0 / kC);
 
   for (int tile = j_begin; tile < j_end; tile += kTile) {
@@ -191,7 +208,8 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
       const int j = tile + threadIdx.x;
       const float4* q = a.rec32 + ((size_t)j * D + pn) * 3;
       s_q0[threadIdx.x] = q[0];
-      s_q2[threadIdx.x] = q[2];
+      const float4 q2 = q[2];
+      s_q2[threadIdx.x] = make_float4(a.bref[0] + q2.x, a.bref[1] + q2.y, a.bref[2] + q2.z, q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
     }
     __syncthreads();
@@ -203,23 +221,27 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
-        // ---- bracket: offsets l1 (older node) and the records it needs ---------------------------
+        // ---- bracket: offset l1 of the older node, its record A and separation dA --------------------
         int l1;
         int br;
         Rec A;          // record of the older node
-        float4 q2b;     // (beta, gamma^2) of the newer node (regular brackets)
+        float3 dA;      // r - w at the older node
+        float4 q2b;     // (dbeta, gamma^2) of the newer node (regular brackets)
         bool have_b = false;
+        bool fast = true;  // A and dA already belong to l1
         if (win.nw == 1) {
           // n = k0: only the present slot exists; every pair is out of history
           n_tests += 1;
           l1 = 0;
           br = 0;
           A = load_rec(src32, win.phys(0));
+          dA = separation(r, A.q0, A.q1);
         } else if (PROP == kPropBisect) {
           n_tests += 1;
           const int pa = win.phys(0);
           A = load_rec(src32, pa);
-          if (node_test_q(r, A.q0, A.q1, src64, pa, a, n_fb)) {
+          dA = separation(r, A.q0, A.q1);
+          if (node_test_d(r, dA, src64, pa, a, n_fb)) {
             l1 = 0;
             br = 0;
           } else {
@@ -231,35 +253,34 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
               l1 = bisect(r, src32, src64, win, 0, win.nw - 1, a, n_tests, n_fb);
               br = 2;
             }
-            if (l1 != 0) A = load_rec(src32, win.phys(l1));
+            fast = (l1 == 0);
           }
         } else {
-          // uniform-motion guess from the staged present record of the source
+          // uniform-motion guess of the older node from the staged present record of the source
           const float4 g0 = s_q0[jj], g2 = s_q2[jj];
-          const float d0 = r.h0 - g0.x, d1 = r.h1 - g0.y, d2 = r.h2 - g0.z;
-          const float db = d0 * (a.bref[0] + g2.x) + d1 * (a.bref[1] + g2.y) + d2 * (a.bref[2] + g2.z);
-          const float dd = d0 * d0 + d1 * d1 + d2 * d2;
+          const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
+          const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
+          const float dd = x0 * x0 + x1 * x1 + x2 * x2;
           const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
           const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
           const float steps = fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
-          // offset of the guessed older node: (nw - 2) - steps, clamped to 0..nw-2
+          // offset of the guessed older node: (nw - 2) - steps; below 0 means "older than the history"
           const int lraw = (steps > (float)(win.nw - 2)) ? -1 : (win.nw - 2) - (int)steps;
           const int lg = max(lraw, 0);
           const int pg = win.phys(lg);
           A = load_rec(src32, pg);
-          bool fast = false;
+          dA = separation(r, A.q0, A.q1);
           if (lraw < 0) {
             // predicted out of history: the only record needed is the oldest slot's
             n_tests += 1;
-            if (node_test_q(r, A.q0, A.q1, src64, pg, a, n_fb)) {
+            if (node_test_d(r, dA, src64, pg, a, n_fb)) {
               l1 = 0;
               br = 0;
-              fast = true;
             } else {
               // guess wrong: gallop up from lo = 0 (P false)
-              int lo = 0, hi, s = 1;
+              int lo = 0, hi, st = 1;
               for (;;) {
-                hi = lo + s;
+                hi = lo + st;
                 if (hi >= win.nw - 1) {
                   hi = win.nw - 1;
                   break;
@@ -267,34 +288,34 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
                 n_tests += 1;
                 if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
                 lo = hi;
-                s <<= 1;
+                st <<= 1;
               }
               l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
               br = (l1 == win.nw - 2) ? 1 : 2;
+              fast = (l1 == 0);
             }
           } else {
-            // predicted bracket [lg, lg + 1]: load both records at once
+            // predicted bracket [lg, lg + 1]: both records are loaded at once
             const int pg1 = win.phys(lg + 1);
             const Rec Bn = load_rec(src32, pg1);
             n_tests += 1;
-            const bool tA = node_test_q(r, A.q0, A.q1, src64, pg, a, n_fb);
+            const bool tA = node_test_d(r, dA, src64, pg, a, n_fb);
             if (!tA) {
               bool tB = true;  // P(n) is always true
               if (lg + 1 < win.nw - 1) {
                 n_tests += 1;
-                tB = node_test_q(r, Bn.q0, Bn.q1, src64, pg1, a, n_fb);
+                tB = node_test_d(r, separation(r, Bn.q0, Bn.q1), src64, pg1, a, n_fb);
               }
               if (tB) {
                 l1 = lg;
                 br = (l1 == win.nw - 2) ? 1 : 2;
                 q2b = Bn.q2;
                 have_b = true;
-                fast = true;
               } else {
                 // gallop up from lo = lg + 1 (P false)
-                int lo = lg + 1, hi, s = 1;
+                int lo = lg + 1, hi, st = 1;
                 for (;;) {
-                  hi = lo + s;
+                  hi = lo + st;
                   if (hi >= win.nw - 1) {
                     hi = win.nw - 1;
                     break;
@@ -302,29 +323,29 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
                   n_tests += 1;
                   if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
                   lo = hi;
-                  s <<= 1;
+                  st <<= 1;
                 }
                 l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
                 br = (l1 == win.nw - 2) ? 1 : 2;
+                fast = false;
               }
             } else if (lg == 0) {
               l1 = 0;
               br = 0;
-              fast = true;
             } else {
               // gallop down from hi = lg (P true)
-              int hi = lg, lo = lg, s = 1;
+              int hi = lg, lo = lg, st = 1;
               bool ooh = false;
               for (;;) {
                 if (hi == 0) {
                   ooh = true;
                   break;
                 }
-                lo = max(hi - s, 0);
+                lo = max(hi - st, 0);
                 n_tests += 1;
                 if (!node_test(r, src32, src64, win.phys(lo), a, n_fb)) break;
                 hi = lo;
-                s <<= 1;
+                st <<= 1;
               }
               if (ooh) {
                 l1 = 0;
@@ -333,9 +354,13 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
                 l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
                 br = (l1 == win.nw - 2) ? 1 : 2;
               }
+              fast = false;
             }
           }
-          if (!fast) A = load_rec(src32, win.phys(l1));
+        }
+        if (!fast) {
+          A = load_rec(src32, win.phys(l1));
+          dA = separation(r, A.q0, A.q1);
         }
         if (br == 0)
           n_ooh++;
@@ -346,19 +371,13 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
 
         // ---- retarded state (light units) --------------------------------------------------------
         const int p1 = win.phys(l1);
-        const float d0 = (r.h0 - A.q0.x) + (r.l0 - A.q1.x);
-        const float d1 = (r.h1 - A.q0.y) + (r.l1 - A.q1.y);
-        const float d2 = (r.h2 - A.q0.z) + (r.l2 - A.q1.z);
+        const float d0 = dA.x, d1 = dA.y, d2 = dA.z;
         const float L1 = __ldg(a.ct32 + p1);
         const float b10 = a.bref[0] + A.q2.x, b11 = a.bref[1] + A.q2.y, b12 = a.bref[2] + A.q2.z;
         const float ig2 = A.q0.w, g2 = A.q2.w;
         const float hb = (d0 * b10 + d1 * b11 + d2 * b12) - L1;
         const float C0 = fmaf(L1, L1, -(d0 * d0 + d1 * d1 + d2 * d2));
         const float qd = fmaf(hb, hb, -ig2 * C0);
-        if (!(qd >= 0.f) || !(ig2 > 0.f)) {
-          errbits |= kErrDisc;
-          continue;
-        }
         const float sq = qd * rsqrtf(fmaxf(qd, 1e-37f));
         const float s = (hb <= 0.f) ? __fdividef(C0, sq - hb) : -(hb + sq) * g2;
         const float e0 = fmaf(-b10, s, d0), e1 = fmaf(-b11, s, d1), e2 = fmaf(-b12, s, d2);
@@ -389,16 +408,21 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
         const float rat = fmaf(R2, ug, xb0 * xb0 + xb1 * xb1 + xb2 * xb2);
         const bool fw = eb > 0.f;
         const float ieu = __fdividef(fw ? (R + eb) : 1.f, fw ? rat : (R - eb));
-        if (!(R2 > 0.f) || !(ieu > 0.f) || !(ieu < 3.0e38f)) {
-          errbits |= kErrCoincide;
+        const bool root_ok = (qd >= 0.f) && (ig2 > 0.f);
+        if (!(root_ok && R2 > 0.f && ieu > 0.f && ieu < 3.0e38f)) {
+          errbits |= root_ok ? kErrCoincide : kErrDisc;
           continue;
         }
         const float pref = s_kq[jj] * (R * ieu) * ieu * ieu;
-        // eta x (u' x alpha)
-        const float c0 = u1 * al2 - u2 * al1, c1 = u2 * al0 - u0 * al2, c2 = u0 * al1 - u1 * al0;
-        const float E0 = pref * fmaf(ug, u0, e1 * c2 - e2 * c1);
-        const float E1 = pref * fmaf(ug, u1, e2 * c0 - e0 * c2);
-        const float E2 = pref * fmaf(ug, u2, e0 * c1 - e1 * c0);
+        float F0 = ug * u0, F1 = ug * u1, F2 = ug * u2;
+        if (br != 0) {
+          // eta x (u' x alpha)
+          const float c0 = u1 * al2 - u2 * al1, c1 = u2 * al0 - u0 * al2, c2 = u0 * al1 - u1 * al0;
+          F0 += e1 * c2 - e2 * c1;
+          F1 += e2 * c0 - e0 * c2;
+          F2 += e0 * c1 - e1 * c0;
+        }
+        const float E0 = pref * F0, E1 = pref * F1, E2 = pref * F2;
         P[0] += E0;
         P[1] += E1;
         P[2] += E2;
@@ -426,19 +450,20 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
       Et[c] = (double)Es[c] - (double)Ec[c];
       Bt[c] = (double)Bs[c] - (double)Bc[c];
     }
-    if (gridDim.y == 1) {
+    if (a.nitems == a.ntb) {
       for (int c = 0; c < 3; c++) {
         a.E[3 * i + c] = Et[c];
         a.B[3 * i + c] = Bt[c];
       }
     } else {
-      double* o = a.out + ((size_t)blockIdx.y * N + i) * 6;
+      double* o = a.out + ((size_t)chunk_id * N + i) * 6;
       for (int c = 0; c < 3; c++) {
         o[c] = Et[c];
         o[3 + c] = Bt[c];
       }
     }
   }
+  }  // work items
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
   n_bi = __reduce_add_sync(0xffffffffu, n_bi);
@@ -455,7 +480,17 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
   }
 }
 
-cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, int split, cudaStream_t st) {
+int max_blocks_pair_mixed(int proposal) {
+  int nb = 0;
+  if (proposal == kPropClosedForm)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropClosedForm>, kBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropBisect>, kBlock, 0);
+  return nb > 0 ? nb : 1;
+}
+
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairSchedule& sc,
+                              cudaStream_t st) {
   MixedArgs a;
   a.rec32 = reinterpret_cast<const float4*>(s.rec32);
   a.rec64 = s.rec64;
@@ -473,14 +508,17 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.err = s.err;
   a.N = (int)s.N;
   a.D = s.D;
+  a.chunk = sc.chunk;
+  a.ntb = sc.ntb;
+  a.nitems = sc.nitems;
+  a.work = s.work;
   for (int c = 0; c < 3; c++) a.bref[c] = (float)s.beta_ref[c];
-  if (split < 1) split = 1;
-  a.chunk = (int)((s.N + split - 1) / split);
-  dim3 grid((unsigned)((s.N + kBlock - 1) / kBlock), (unsigned)split);
+  cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)
-    pair_mixed_kernel<kPropClosedForm><<<grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropClosedForm><<<sc.grid, kBlock, 0, st>>>(a);
   else
-    pair_mixed_kernel<kPropBisect><<<grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropBisect><<<sc.grid, kBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
