@@ -68,6 +68,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 path (FP64 + bisection) on the same state")
     ap.add_argument("--small", action="store_true", help="tiny workload for smoke tests of this script")
     ap.add_argument("--n", type=int, default=None, help="override N (profiling captures of a smaller case)")
     ap.add_argument("--depth", type=int, default=None, help="override the history depth")
@@ -310,7 +312,7 @@ def run_ours(args):
 
     emppp.load(build_if_missing=True)
     wl, h, win = workload(args.small, rank, args)
-    steps = args.steps if args.steps is not None else (5 if args.path == "fp64" else 20)
+    steps = args.steps if args.steps is not None else (5 if args.path == "fp64" else 50)
     warmup = max(args.warmup, 1)
     dev = torch.device("cuda", local)
     res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e)
@@ -351,6 +353,13 @@ def run_ours(args):
                        "d2h_bytes_per_step": e["d2h_per_step"],
                        "note": "restore of the stored state from pinned host memory (amortised over the steps), "
                                "then per step: emppp_step + emppp_get_state + emppp_get_fields to pinned host"}
+    if args.path != "fp64" and not args.no_fp64_compare:
+        # the plain FP64 path (the paper's search) on the same state, for the speed-up
+        ref = run_path(args, "fp64", "bisect", 2, 1, wl, h, win, rank, e2e=False, keep_fields=False)
+        ref_ms = max_over_ranks(ref["ms"], dev)
+        line["fp64_plain_path"] = {"proposal": "bisect", "ms_per_step": ref_ms,
+                                   "value": pairs_per_step * world / (ref_ms / 1e3), "unit": UNIT, "steps": 2}
+        line["speedup_vs_fp64_plain"] = ref_ms / ms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         E0, B0 = res.get("fields0", (None, None))
         line["cpu_baseline"], parity = cpu_baseline(h, wl, args.cpu_seconds, E0, B0)

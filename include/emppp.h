@@ -81,7 +81,9 @@ typedef struct {
   int32_t pair_fields; /* 1 (default): self fields on; 0: E = 0, B = B_ext (stage-2 transport, Sec. 2.7) */
   int32_t source_split;/* 0 (default): automatic; >0: number of source slices per target block */
   int32_t timing;      /* 1: record CUDA events around every pair evaluation and step (see emppp_stats) */
-  int32_t reserved[3]; /* must be 0 */
+  int32_t graphs;      /* 1 (default): emppp_step with nsteps > 1 replays one captured CUDA graph per step
+                          (only on a non-default stream and with timing off) */
+  int32_t reserved[2]; /* must be 0 */
 } emppp_options;
 
 /* Counters accumulated over the steps since the last emppp_reset_stats (Sec. 2.2 branches). */
@@ -108,6 +110,15 @@ EMPPP_API void emppp_default_options(emppp_options* out);
  * current device. *out is NULL on failure. Sec. 2.2 (history), Sec. 2.3 (time step). */
 EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt, const emppp_options* opt,
                                     void* cuda_stream, emppp_handle* out);
+
+/* Creates a solver for nbunch independent bunches (particles interact only within their own bunch)
+ * with n_per_bunch[b] >= 1 particles each, sharing the history depth, the step dt and the time. All
+ * per-particle arrays of the other calls then hold the bunches one after the other (bunch 0 first).
+ * Every step evaluates all bunches in one persistent launch of the pair kernel whose work items are
+ * (bunch, source chunk, target tile). emppp_create(n, ...) is the case nbunch = 1. */
+EMPPP_API emppp_status emppp_create_batch(int32_t nbunch, const int64_t* n_per_bunch, int32_t history_depth,
+                                          double dt, const emppp_options* opt, void* cuda_stream,
+                                          emppp_handle* out);
 
 /* Frees every device resource of the handle (NULL is ignored). */
 EMPPP_API void emppp_destroy(emppp_handle h);
@@ -137,6 +148,20 @@ EMPPP_API emppp_status emppp_get_history(emppp_handle h, int64_t* n_now, int32_t
  * Higuera-Cary push, append of slot n+1. bext may be NULL (NONE). Asynchronous on the handle's
  * stream: returns once the work is enqueued. */
 EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_bext* bext);
+
+/* Stage-1 -> stage-2 handoff (Sec. 2.7): translates every bunch so that its weighted centroid sits at
+ * center[3] (momenta kept) and restarts the history at the present slot. Used before
+ * emppp_transport to start the field-dominated transport at a given place (e.g. 4 Earth radii on the
+ * equator). Synchronises the stream. */
+EMPPP_API emppp_status emppp_handoff(emppp_handle h, const double* center);
+
+/* Stage-2 transport (Sec. 2.7): advances every particle nsteps >= 0 steps of dt > 0 with the pair
+ * interaction off (E = 0, B = B_ext evaluated at x^{n+1/2}, the same Higuera-Cary step as
+ * emppp_step), keeping no history on the way; afterwards the history holds only the present slot,
+ * the step index has grown by nsteps and the time by nsteps * dt (accumulated step by step).
+ * Particles are independent here, so each GPU thread keeps its particle in registers for up to 4096
+ * steps per launch. Asynchronous. */
+EMPPP_API emppp_status emppp_transport(emppp_handle h, int64_t nsteps, double dt, const emppp_bext* bext);
 
 /* Present positions x [3n], proper velocities u [3n] (host or device, either may be NULL), time
  * and step index (either may be NULL). Synchronises the stream. */

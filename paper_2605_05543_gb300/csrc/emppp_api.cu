@@ -1,10 +1,11 @@
-// C ABI of the EM-PP library: handle lifetime, state transfer and the step driver.
-// Every entry point validates its arguments, enqueues work on the handle's stream and returns a
-// status; nothing here aborts or prints.
+// C ABI of the EM-PP library: handle lifetime, state transfer, the step driver, the stage-2 handoff
+// and transport. Every entry point validates its arguments, enqueues work on the handle's stream and
+// returns a status; nothing here aborts or prints.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -50,17 +51,26 @@ struct emppp_ctx {
   int device = 0;
   int num_sms = 0;
   bool has_state = false;
-  int64_t n = 0;    // host mirror of the present step
-  double t = 0.0;   // host mirror of t_n
+  int64_t n = 0;           // host mirror of the present step
+  double t = 0.0;          // host mirror of t_n
+  int64_t hist_start = 0;  // host mirror of the earliest stored slot
   double* staging = nullptr;  // [7N] doubles for host transfers
+  std::vector<void*> allocs;
+  // bunches
+  int nbunch = 1;
+  std::vector<BunchDesc> hb;
+  std::vector<BunchSched> hs;
+  BunchDesc* d_bunches = nullptr;
+  BunchSched* d_sched = nullptr;
+  int* d_bunch_of = nullptr;
+  PairLaunch launch{};
+  int sched_key = -1;  // configuration the uploaded schedule belongs to
   // spatial target order of the mixed path
-  int* ord_scratch = nullptr;  // bbox (6) + cell histogram
-  unsigned short* ord_key = nullptr;
+  unsigned* ord_key = nullptr;
   int* order = nullptr;
   // resident blocks per SM of the pair kernels (queried on first use), per proposal
   int blocks_fp64[2] = {0, 0};
   int blocks_mixed[2] = {0, 0};
-  std::vector<void*> allocs;
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
   int64_t steps_acc = 0;  // steps since the last stats reset
@@ -69,6 +79,12 @@ struct emppp_ctx {
   static constexpr int kTimedSteps = 1024;
   std::vector<cudaEvent_t> events;
   int ev_used = 0;
+  // one captured step, replayed by emppp_step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int graph_launches = 0;        // kernels per replayed step
+  unsigned char graph_key[sizeof(emppp_options) + sizeof(BextParams)];  // configuration of the graph
+  bool graph_valid = false;
 };
 
 namespace {
@@ -101,38 +117,68 @@ emppp_status validate_options(const emppp_options* o) {
   if (o->pair_fields != 0 && o->pair_fields != 1) return fail(EMPPP_ERR_ARG, "pair_fields must be 0 or 1");
   if (o->source_split < 0) return fail(EMPPP_ERR_ARG, "source_split must be >= 0");
   if (o->timing != 0 && o->timing != 1) return fail(EMPPP_ERR_ARG, "timing must be 0 or 1");
-  for (int k = 0; k < 3; k++)
+  if (o->graphs != 0 && o->graphs != 1) return fail(EMPPP_ERR_ARG, "graphs must be 0 or 1");
+  for (int k = 0; k < 2; k++)
     if (o->reserved[k] != 0) return fail(EMPPP_ERR_ARG, "reserved option fields must be 0");
   return EMPPP_OK;
 }
 
-// Work split of the persistent pair kernel: one block per resident slot (from the occupancy of the
-// kernel actually launched) and about 16 work items per block, so that the uneven cost of the items
-// (the branch mix differs across the bunch) evens out; chunks hold at least 256 sources.
-PairSchedule make_schedule(emppp_ctx* c) {
+void invalidate_graph(emppp_handle h) {
+  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  h->graph_exec = nullptr;
+  h->graph = nullptr;
+  h->graph_valid = false;
+}
+
+// Work split of the persistent pair kernel, per bunch: one block per resident slot of the kernel that
+// is launched (occupancy query) and about 16 work items per block over all bunches, so that the uneven
+// cost of the items (the branch mix differs across a bunch) evens out; chunks hold at least 256
+// sources. Uploaded when the configuration changes.
+emppp_status update_schedule(emppp_handle c) {
   const bool mixed = c->opt.precision == EMPPP_MIXED;
+  const int key = (mixed ? 1 : 0) | ((c->opt.proposal & 1) << 1) | (c->opt.source_split << 2);
+  if (key == c->sched_key) return EMPPP_OK;
   int& nb = mixed ? c->blocks_mixed[c->opt.proposal & 1] : c->blocks_fp64[c->opt.proposal & 1];
   if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal) : max_blocks_pair_fp64(c->opt.proposal);
   const long long R = (long long)nb * c->num_sms;
-  PairSchedule sc;
-  sc.ntb = (int)((c->N + 127) / 128);
-  long long nchunk;
-  if (c->opt.source_split > 0) {
-    nchunk = c->opt.source_split;
-  } else {
-    nchunk = (16 * R + sc.ntb - 1) / sc.ntb;
-    const long long by_size = (c->N + 255) / 256;
-    if (nchunk > by_size) nchunk = by_size;
+  long long total_tiles = 0;
+  for (int b = 0; b < c->nbunch; b++) total_tiles += (c->hb[b].n + 127) / 128;
+  int item = 0;
+  for (int b = 0; b < c->nbunch; b++) {
+    BunchSched& s = c->hs[b];
+    const long long n = c->hb[b].n;
+    s.ntb = (int)((n + 127) / 128);
+    long long nchunk;
+    if (c->opt.source_split > 0) {
+      nchunk = c->opt.source_split;
+    } else {
+      nchunk = (16 * R + total_tiles - 1) / total_tiles;
+      const long long by_size = (n + 255) / 256;
+      if (nchunk > by_size) nchunk = by_size;
+    }
+    if (nchunk > c->ds.max_split) nchunk = c->ds.max_split;
+    if (nchunk < 1) nchunk = 1;
+    long long chunk = (n + nchunk - 1) / nchunk;
+    chunk = (chunk + 127) / 128 * 128;
+    s.chunk = (int)chunk;
+    s.nchunk = (int)((n + chunk - 1) / chunk);
+    s.item_off = item;
+    item += s.ntb * s.nchunk;
   }
-  if (nchunk > c->ds.max_split) nchunk = c->ds.max_split;
-  if (nchunk < 1) nchunk = 1;
-  long long chunk = (c->N + nchunk - 1) / nchunk;
-  chunk = (chunk + 127) / 128 * 128;
-  sc.chunk = (int)chunk;
-  sc.nchunk = (int)((c->N + chunk - 1) / chunk);
-  sc.nitems = sc.ntb * sc.nchunk;
-  sc.grid = (int)(R < sc.nitems ? R : sc.nitems);
-  return sc;
+  c->launch.nitems = item;
+  c->launch.grid = (int)(R < item ? R : item);
+  CU(cudaMemcpyAsync(c->d_sched, c->hs.data(), sizeof(BunchSched) * c->nbunch, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->sched_key = key;
+  invalidate_graph(c);
+  return EMPPP_OK;
+}
+
+bool any_chunked(const emppp_ctx* c) {
+  for (int b = 0; b < c->nbunch; b++)
+    if (c->hs[b].nchunk > 1) return true;
+  return false;
 }
 
 emppp_status read_err(emppp_handle h) {
@@ -161,13 +207,37 @@ emppp_status from_device(emppp_handle h, double* dst, const double* src, size_t 
   return EMPPP_OK;
 }
 
-// origin of the FP32 position split and reference velocity of the FP32 velocities: those of one
-// particle of the bunch when the state is set
-void set_origin(emppp_handle h, const double* x0, const double* v0) {
-  for (int c = 0; c < 3; c++) {
-    h->ds.origin[c] = x0[c];
-    h->ds.beta_ref[c] = v0[c] / kC;
+// reads 3 doubles at element 3*i of a caller array (host or device)
+emppp_status read3(emppp_handle h, const double* a, long long i, int is_dev, double out[3]) {
+  if (is_dev) {
+    CU(cudaMemcpyAsync(out, a + 3 * i, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  } else {
+    memcpy(out, a + 3 * i, 3 * sizeof(double));
   }
+  return EMPPP_OK;
+}
+
+// Origin of each bunch's FP32 position split and reference velocity of its FP32 velocities: those of
+// the bunch's first particle when the state is set. x and v_or_u index the present positions and
+// velocities (or proper velocities).
+emppp_status set_bunch_frames(emppp_handle h, const double* x, const double* v_or_u, bool is_u, int is_dev) {
+  for (int b = 0; b < h->nbunch; b++) {
+    double x0[3], v0[3];
+    emppp_status st = read3(h, x, h->hb[b].off, is_dev, x0);
+    if (st != EMPPP_OK) return st;
+    st = read3(h, v_or_u, h->hb[b].off, is_dev, v0);
+    if (st != EMPPP_OK) return st;
+    double g = 1.0;
+    if (is_u) g = sqrt(1.0 + (v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2]) / (kC * kC));
+    for (int c = 0; c < 3; c++) {
+      h->hb[b].origin[c] = x0[c];
+      h->hb[b].beta_ref[c] = v0[c] / g / kC;
+    }
+  }
+  CU(cudaMemcpyAsync(h->d_bunches, h->hb.data(), sizeof(BunchDesc) * h->nbunch, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  return EMPPP_OK;
 }
 
 emppp_status ensure_events(emppp_handle h) {
@@ -185,32 +255,97 @@ emppp_status reset_counters(emppp_handle h) {
   return EMPPP_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-EMPPP_API const char* emppp_version(void) { return "emppp 0.1 (sm_103a)"; }
-
-EMPPP_API const char* emppp_last_error(void) { return g_last_error.c_str(); }
-
-EMPPP_API void emppp_default_options(emppp_options* out) {
-  if (!out) return;
-  memset(out, 0, sizeof(*out));
-  out->precision = EMPPP_FP64;
-  out->proposal = EMPPP_PROPOSAL_BISECT;
-  out->pair_fields = 1;
-  out->source_split = 0;
+emppp_status convert_bext(const emppp_bext* bext, BextParams* bp) {
+  memset(bp, 0, sizeof(*bp));
+  if (!bext) return EMPPP_OK;
+  if (bext->kind < EMPPP_BEXT_NONE || bext->kind > EMPPP_BEXT_DIPOLE)
+    return fail(EMPPP_ERR_ARG, "unknown background field kind %d", bext->kind);
+  bp->kind = bext->kind;
+  for (int c = 0; c < 3; c++) {
+    bp->b[c] = bext->b[c];
+    bp->center[c] = bext->center[c];
+  }
+  bp->m0 = bext->m0;
+  return EMPPP_OK;
 }
 
-EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt, const emppp_options* opt,
-                                    void* cuda_stream, emppp_handle* out) {
+// enqueues the kernels of one step and reports how many kernels it launched
+emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev, int* nkernels) {
+  int k = 0;
+  if (ev) CU(cudaEventRecord(ev[0], h->stream));
+  CU(launch_prep(h->ds, h->stream));
+  k += 1;
+  if (h->opt.pair_fields && h->opt.precision == EMPPP_MIXED) {
+    CU(launch_target_order(h->ds, h->ord_key, h->order, h->stream));
+    k += 1;
+  }
+  if (ev) CU(cudaEventRecord(ev[1], h->stream));
+  if (h->opt.pair_fields) {
+    if (h->opt.precision == EMPPP_MIXED)
+      CU(launch_pair_mixed(h->ds, h->order, h->opt.proposal, h->launch, h->stream));
+    else
+      CU(launch_pair_fp64(h->ds, h->opt.proposal, h->launch, h->stream));
+    k += 1;
+    if (any_chunked(h)) {
+      CU(launch_reduce_partials(h->ds, h->stream));
+      k += 1;
+    }
+  } else {
+    CU(launch_zero_self(h->ds, h->stream));
+    k += 1;
+  }
+  if (ev) CU(cudaEventRecord(ev[2], h->stream));
+  CU(launch_push(h->ds, bp, h->stream));
+  CU(launch_advance(h->ds, h->stream));
+  k += 2;
+  if (ev) CU(cudaEventRecord(ev[3], h->stream));
+  *nkernels = k;
+  return EMPPP_OK;
+}
+
+// captures one step into a CUDA graph for the current configuration (options and background field)
+emppp_status capture_step(emppp_handle h, const BextParams& bp) {
+  unsigned char key[sizeof(emppp_options) + sizeof(BextParams)];
+  memcpy(key, &h->opt, sizeof(emppp_options));
+  memcpy(key + sizeof(emppp_options), &bp, sizeof(BextParams));
+  if (h->graph_valid && memcmp(key, h->graph_key, sizeof(key)) == 0) return EMPPP_OK;
+  invalidate_graph(h);
+  CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  int k = 0;
+  emppp_status st = enqueue_step(h, bp, nullptr, &k);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (st != EMPPP_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(EMPPP_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(EMPPP_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
+  }
+  h->graph = g;
+  h->graph_launches = k;
+  memcpy(h->graph_key, key, sizeof(key));
+  h->graph_valid = true;
+  return EMPPP_OK;
+}
+
+emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_depth, double dt,
+                         const emppp_options* opt, void* cuda_stream, emppp_handle* out) {
   if (!out) return fail(EMPPP_ERR_ARG, "out is NULL");
   *out = nullptr;
-  if (n < 1) return fail(EMPPP_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
+  if (nbunch < 1 || !nper) return fail(EMPPP_ERR_ARG, "nbunch must be >= 1 with n_per_bunch given");
+  long long n = 0;
+  for (int b = 0; b < nbunch; b++) {
+    if (nper[b] < 1) return fail(EMPPP_ERR_ARG, "every bunch needs n >= 1 (bunch %d has %lld)", b, (long long)nper[b]);
+    n += nper[b];
+  }
   if (history_depth < 2) return fail(EMPPP_ERR_ARG, "history_depth must be >= 2 (got %d)", history_depth);
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(EMPPP_ERR_ARG, "dt must be positive and finite");
   if ((double)n * (double)history_depth > 4e10) return fail(EMPPP_ERR_ARG, "n * history_depth too large");
-  if (n > 2147483647LL) return fail(EMPPP_ERR_ARG, "n must be below 2^31");
+  if (n > 2147483647LL) return fail(EMPPP_ERR_ARG, "the total particle count must be below 2^31");
   emppp_options o;
   emppp_default_options(&o);
   if (opt) o = *opt;
@@ -224,28 +359,42 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   c->dt = dt;
   c->opt = o;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
+  c->nbunch = nbunch;
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e == cudaSuccess) e = prepare_target_order();
   if (e != cudaSuccess) {
     delete c;
     return fail(EMPPP_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
   }
+  c->hb.resize(nbunch);
+  c->hs.resize(nbunch);
+  std::vector<int> bunch_of((size_t)n);
+  long long off = 0;
+  for (int b = 0; b < nbunch; b++) {
+    memset(&c->hb[b], 0, sizeof(BunchDesc));
+    c->hb[b].off = off;
+    c->hb[b].n = (int)nper[b];
+    for (long long k = 0; k < nper[b]; k++) bunch_of[(size_t)(off + k)] = b;
+    off += nper[b];
+  }
   DeviceState& s = c->ds;
   s.N = n;
   s.D = history_depth;
+  s.nbunch = nbunch;
   const size_t N = (size_t)n, D = (size_t)history_depth;
   {
     // partial sums of up to 64 source chunks, within 1 GiB
     const long long by_mem = (1LL << 30) / ((long long)n * 48);
     s.max_split = (int)(by_mem < 1 ? 1 : (by_mem > 64 ? 64 : by_mem));
   }
-#define ALLOC(p, cnt)                   \
-  do {                                  \
-    st = dalloc(c, &(p), (cnt));        \
-    if (st != EMPPP_OK) {               \
-      emppp_destroy(c);                 \
-      return st;                        \
-    }                                   \
+#define ALLOC(p, cnt)            \
+  do {                           \
+    st = dalloc(c, &(p), (cnt)); \
+    if (st != EMPPP_OK) {        \
+      emppp_destroy(c);          \
+      return st;                 \
+    }                            \
   } while (0)
   ALLOC(s.rec64, N * D * 6);
   ALLOC(s.rec32, N * D * 12);
@@ -254,8 +403,10 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   ALLOC(s.tab.lhs32, D);
   ALLOC(s.tab.ct32, D);
   ALLOC(s.tab.inv_dtk, D);
+  ALLOC(s.tab.icdt32, D);
   ALLOC(s.u, N * 3);
   ALLOC(s.wts, N);
+  ALLOC(s.kq32, N);
   ALLOC(s.Eself, N * 3);
   ALLOC(s.Bself, N * 3);
   ALLOC(s.Bout, N * 3);
@@ -264,14 +415,21 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   ALLOC(s.work, 1);
   ALLOC(s.stats, kStatCount);
   ALLOC(s.err, 1);
+  ALLOC(s.bsum, (size_t)nbunch * 4);
   ALLOC(c->staging, N * 7);
-  ALLOC(s.tab.icdt32, D);
-  ALLOC(s.kq32, N);
-  ALLOC(c->ord_scratch, order_scratch_ints());
   ALLOC(c->ord_key, N);
   ALLOC(c->order, N);
+  ALLOC(c->d_bunches, (size_t)nbunch);
+  ALLOC(c->d_sched, (size_t)nbunch);
+  ALLOC(c->d_bunch_of, N);
 #undef ALLOC
-  e = cudaMemsetAsync(s.err, 0, sizeof(int), c->stream);
+  s.bunches = c->d_bunches;
+  s.sched = c->d_sched;
+  s.bunch_of = c->d_bunch_of;
+  e = cudaMemcpyAsync(c->d_bunch_of, bunch_of.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_bunches, c->hb.data(), sizeof(BunchDesc) * nbunch, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.err, 0, sizeof(int), c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.stats, 0, sizeof(unsigned long long) * kStatCount, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.Eself, 0, sizeof(double) * N * 3, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.Bout, 0, sizeof(double) * N * 3, c->stream);
@@ -280,7 +438,7 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
     emppp_destroy(c);
     return fail(EMPPP_ERR_CUDA, "initialisation: %s", cudaGetErrorString(e));
   }
-  if ((st = ensure_events(c)) != EMPPP_OK) {
+  if ((st = ensure_events(c)) != EMPPP_OK || (st = update_schedule(c)) != EMPPP_OK) {
     emppp_destroy(c);
     return st;
   }
@@ -288,11 +446,48 @@ EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt,
   return EMPPP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+EMPPP_API const char* emppp_version(void) { return "emppp 0.2 (sm_103a)"; }
+
+EMPPP_API const char* emppp_last_error(void) { return g_last_error.c_str(); }
+
+EMPPP_API void emppp_default_options(emppp_options* out) {
+  if (!out) return;
+  memset(out, 0, sizeof(*out));
+  out->precision = EMPPP_FP64;
+  out->proposal = EMPPP_PROPOSAL_BISECT;
+  out->pair_fields = 1;
+  out->source_split = 0;
+  out->timing = 0;
+  out->graphs = 1;
+}
+
+EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt, const emppp_options* opt,
+                                    void* cuda_stream, emppp_handle* out) {
+  if (n < 1) {
+    if (out) *out = nullptr;
+    return fail(EMPPP_ERR_ARG, "n must be >= 1 (got %lld)", (long long)n);
+  }
+  return create_impl(1, &n, history_depth, dt, opt, cuda_stream, out);
+}
+
+EMPPP_API emppp_status emppp_create_batch(int32_t nbunch, const int64_t* n_per_bunch, int32_t history_depth,
+                                          double dt, const emppp_options* opt, void* cuda_stream,
+                                          emppp_handle* out) {
+  return create_impl(nbunch, n_per_bunch, history_depth, dt, opt, cuda_stream, out);
+}
+
 EMPPP_API void emppp_destroy(emppp_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  else cudaDeviceSynchronize();
+  if (h->stream)
+    cudaStreamSynchronize(h->stream);
+  else
+    cudaDeviceSynchronize();
+  invalidate_graph(h);
   for (cudaEvent_t e : h->events)
     if (e) cudaEventDestroy(e);
   for (void* p : h->allocs) cudaFree(p);
@@ -319,21 +514,8 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
     du = su;
     dw = w ? sw : nullptr;
   }
-  double x0[3], u0[3];
-  if (is_device_ptr) {
-    CU(cudaMemcpyAsync(x0, x, sizeof(x0), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(u0, u, sizeof(u0), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-  } else {
-    memcpy(x0, x, sizeof(x0));
-    memcpy(u0, u, sizeof(u0));
-  }
-  {
-    const double g = sqrt(1.0 + (u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]) / (kC * kC));
-    const double v0[3] = {u0[0] / g, u0[1] / g, u0[2] / g};
-    set_origin(h, x0, v0);
-  }
-  CU(launch_set_state(h->ds, 0, 0.0, h->dt, du, dw, h->stream));
+  if ((st = set_bunch_frames(h, x, u, true, is_device_ptr)) != EMPPP_OK) return st;
+  CU(launch_set_state(h->ds, 0, 0.0, h->dt, 0, du, dw, h->stream));
   CU(launch_init_slot0(h->ds, dx, du, dw, h->stream));
   h->launches += 2;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
@@ -342,6 +524,7 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
   CU(cudaStreamSynchronize(h->stream));
   h->n = 0;
   h->t = 0.0;
+  h->hist_start = 0;
   h->has_state = true;
   return EMPPP_OK;
 }
@@ -368,19 +551,10 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
     if (!(hT[s] == hT[s]) || (s > 0 && !(hT[s] > hT[s - 1])))
       return fail(EMPPP_ERR_ARG, "time stamps must be finite and strictly increasing (slot %d)", s);
   }
-  // origin and reference velocity of the FP32 shadow: the present position and velocity of particle 0
-  double x0[3], v0[3];
+  // FP32 frames: the present position and velocity of each bunch's first particle
   const double* Wlast = W + (size_t)(nslots - 1) * N * 3;
   const double* Vlast = V + (size_t)(nslots - 1) * N * 3;
-  if (is_device_ptr) {
-    CU(cudaMemcpyAsync(x0, Wlast, sizeof(x0), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaMemcpyAsync(v0, Vlast, sizeof(v0), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-  } else {
-    memcpy(x0, Wlast, sizeof(x0));
-    memcpy(v0, Vlast, sizeof(v0));
-  }
-  set_origin(h, x0, v0);
+  if ((st = set_bunch_frames(h, Wlast, Vlast, false, is_device_ptr)) != EMPPP_OK) return st;
   std::vector<double> ht((size_t)h->D, 0.0);
   for (int s = 0; s < nslots; s++) {
     const int64_t k = n - nslots + 1 + s;
@@ -407,7 +581,8 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
     du = h->staging;
     dw = w ? h->staging + 6 * N : nullptr;
   }
-  CU(launch_set_state(h->ds, n, hT[nslots - 1], h->dt, du, dw, h->stream));
+  const int64_t hs = n - nslots + 1;
+  CU(launch_set_state(h->ds, n, hT[nslots - 1], h->dt, hs, du, dw, h->stream));
   h->launches += 1;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
@@ -415,6 +590,7 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
   CU(cudaStreamSynchronize(h->stream));
   h->n = n;
   h->t = hT[nslots - 1];
+  h->hist_start = hs;
   h->has_state = true;
   return EMPPP_OK;
 }
@@ -426,7 +602,8 @@ EMPPP_API emppp_status emppp_get_history(emppp_handle h, int64_t* n_now, int32_t
   if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
   if ((st = read_err(h)) != EMPPP_OK) return st;
   const size_t N = (size_t)h->N;
-  const int32_t ns = (int32_t)(h->n + 1 < h->D ? h->n + 1 : h->D);
+  const int64_t stored = h->n - h->hist_start + 1;
+  const int32_t ns = (int32_t)(stored < h->D ? stored : h->D);
   std::vector<double> ht((size_t)h->D);
   CU(cudaMemcpyAsync(ht.data(), h->ds.slot_t, sizeof(double) * h->D, cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
@@ -466,53 +643,83 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
   if (st != EMPPP_OK) return st;
   if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
   if (nsteps < 0) return fail(EMPPP_ERR_ARG, "nsteps must be >= 0");
-  BextParams bp{};
-  if (bext) {
-    if (bext->kind < EMPPP_BEXT_NONE || bext->kind > EMPPP_BEXT_DIPOLE)
-      return fail(EMPPP_ERR_ARG, "unknown background field kind %d", bext->kind);
-    bp.kind = bext->kind;
-    for (int c = 0; c < 3; c++) {
-      bp.b[c] = bext->b[c];
-      bp.center[c] = bext->center[c];
-    }
-    bp.m0 = bext->m0;
-  }
-  const PairSchedule sc = make_schedule(h);
+  BextParams bp;
+  if ((st = convert_bext(bext, &bp)) != EMPPP_OK) return st;
+  if ((st = update_schedule(h)) != EMPPP_OK) return st;
+  const bool use_graph = h->opt.graphs && !h->opt.timing && h->stream != nullptr && nsteps > 1;
+  if (use_graph && (st = capture_step(h, bp)) != EMPPP_OK) return st;
+  long long pairs_per_step = 0;
+  if (h->opt.pair_fields)
+    for (int b = 0; b < h->nbunch; b++) pairs_per_step += (long long)h->hb[b].n * (h->hb[b].n - 1);
   for (int64_t k = 0; k < nsteps; k++) {
-    cudaEvent_t* ev = nullptr;
-    if (h->opt.timing && h->ev_used < emppp_ctx::kTimedSteps) ev = &h->events[4 * h->ev_used++];
-    if (ev) CU(cudaEventRecord(ev[0], h->stream));
-    CU(launch_prep(h->ds, h->stream));
-    h->launches += 1;
-    if (h->opt.pair_fields && h->opt.precision == EMPPP_MIXED) {
-      CU(launch_target_order(h->ds, h->ord_scratch, h->ord_scratch + 6, h->ord_key, h->order, h->stream));
-      h->launches += 5;
-    }
-    if (ev) CU(cudaEventRecord(ev[1], h->stream));
-    if (h->opt.pair_fields) {
-      if (h->opt.precision == EMPPP_MIXED)
-        CU(launch_pair_mixed(h->ds, h->order, h->opt.proposal, sc, h->stream));
-      else
-        CU(launch_pair_fp64(h->ds, h->opt.proposal, sc, h->stream));
-      h->launches += 1;
-      if (sc.nchunk > 1) {
-        CU(launch_reduce_partials(h->ds, sc.nchunk, h->stream));
-        h->launches += 1;
-      }
-      h->pairs_acc += h->N * (h->N - 1);
+    int nk = 0;
+    if (use_graph) {
+      CU(cudaGraphLaunch(h->graph_exec, h->stream));
+      nk = h->graph_launches;
     } else {
-      CU(launch_zero_self(h->ds, h->stream));
-      h->launches += 1;
+      cudaEvent_t* ev = nullptr;
+      if (h->opt.timing && h->ev_used < emppp_ctx::kTimedSteps) ev = &h->events[4 * h->ev_used++];
+      if ((st = enqueue_step(h, bp, ev, &nk)) != EMPPP_OK) return st;
     }
-    if (ev) CU(cudaEventRecord(ev[2], h->stream));
-    CU(launch_push(h->ds, bp, h->stream));
-    CU(launch_advance(h->ds, h->stream));
-    h->launches += 2;
-    if (ev) CU(cudaEventRecord(ev[3], h->stream));
+    h->launches += nk;
+    h->pairs_acc += pairs_per_step;
     h->steps_acc += 1;
     h->n += 1;
     h->t = h->t + h->dt;
   }
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_handoff(emppp_handle h, const double* center) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if (!center) return fail(EMPPP_ERR_ARG, "center is NULL");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  CU(launch_bunch_sums(h->ds, h->stream));
+  std::vector<double> sums((size_t)h->nbunch * 4);
+  CU(cudaMemcpyAsync(sums.data(), h->ds.bsum, sizeof(double) * sums.size(), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  std::vector<double> shifts((size_t)h->nbunch * 3);
+  for (int b = 0; b < h->nbunch; b++) {
+    const double wsum = sums[4 * b + 3];
+    if (!(wsum != 0.0)) return fail(EMPPP_ERR_NUMERIC, "bunch %d has zero total weight", b);
+    for (int c = 0; c < 3; c++) {
+      shifts[3 * b + c] = center[c] - sums[4 * b + c] / wsum;
+      h->hb[b].origin[c] += shifts[3 * b + c];  // keeps x - origin unchanged
+    }
+  }
+  CU(cudaMemcpyAsync(h->d_bunches, h->hb.data(), sizeof(BunchDesc) * h->nbunch, cudaMemcpyHostToDevice, h->stream));
+  CU(cudaMemcpyAsync(h->ds.bsum, shifts.data(), sizeof(double) * shifts.size(), cudaMemcpyHostToDevice, h->stream));
+  CU(launch_translate(h->ds, h->ds.bsum, h->stream));
+  h->launches += 2;
+  CU(cudaStreamSynchronize(h->stream));
+  h->hist_start = h->n;
+  invalidate_graph(h);
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_transport(emppp_handle h, int64_t nsteps, double dt, const emppp_bext* bext) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if (nsteps < 0) return fail(EMPPP_ERR_ARG, "nsteps must be >= 0");
+  if (!(dt > 0.0) || !(dt < 1e300)) return fail(EMPPP_ERR_ARG, "dt must be positive and finite");
+  BextParams bp;
+  if ((st = convert_bext(bext, &bp)) != EMPPP_OK) return st;
+  const int64_t kChunk = 4096;
+  for (int64_t done = 0; done < nsteps;) {
+    const int k = (int)(nsteps - done < kChunk ? nsteps - done : kChunk);
+    double t = h->t;
+    for (int s = 0; s < k; s++) t = t + dt;
+    CU(launch_transport_chunk(h->ds, bp, dt, k, t, h->stream));
+    h->launches += 2;
+    h->n += k;
+    h->t = t;
+    h->hist_start = h->n;
+    done += k;
+  }
+  invalidate_graph(h);
   return EMPPP_OK;
 }
 
@@ -593,7 +800,8 @@ EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* op
   if (!opt) return fail(EMPPP_ERR_ARG, "opt is NULL");
   if ((st = validate_options(opt)) != EMPPP_OK) return st;
   h->opt = *opt;
-  return ensure_events(h);
+  if ((st = ensure_events(h)) != EMPPP_OK) return st;
+  return update_schedule(h);
 }
 
 EMPPP_API emppp_status emppp_set_stream(emppp_handle h, void* cuda_stream) {
@@ -601,6 +809,7 @@ EMPPP_API emppp_status emppp_set_stream(emppp_handle h, void* cuda_stream) {
   if (st != EMPPP_OK) return st;
   CU(cudaStreamSynchronize(h->stream));
   h->stream = static_cast<cudaStream_t>(cuda_stream);
+  invalidate_graph(h);
   return EMPPP_OK;
 }
 

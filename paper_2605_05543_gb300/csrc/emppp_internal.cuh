@@ -1,17 +1,24 @@
 // Internal declarations of the EM-PP CUDA library (not part of the C ABI).
 //
+// A solver holds one or more independent bunches (particles interact only within their bunch); a
+// single-bunch solver is the case nbunch = 1. Particles of all bunches are concatenated: bunch b owns
+// global indices off_b .. off_b + n_b - 1. All bunches share the step, time and history depth.
+//
 // Device data layout (one GPU, all resident in HBM):
 //   rec64  [N][D][6] double   history ring, source-major: slot p of particle j holds the position
 //                             w (3) and velocity v (3) at the time slot_t[p]; slots are used
 //                             modulo D, so one particle's whole history is one contiguous 48*D-byte
 //                             run (pair gathers of one source stay within a few cache lines).
 //   rec32  [N][D][12] float   FP32 shadow of rec64 (shadow.cuh): hi(3) 1/gamma^2 | lo(3) 0 |
-//                             beta - beta_ref (3) gamma^2; 48-byte records, three 16-byte loads each.
+//                             beta - beta_ref (3) gamma^2; 48-byte records, three 16-byte loads each;
+//                             origin and beta_ref are per bunch.
 //   slot_t [D]                time stamp of each physical slot.
 //   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
 //                             1 / (t_{k+1} - t_k) in FP64 and 1 / (c (t_{k+1} - t_k)) in FP32.
 //   u      [N][3]             present proper velocities (FP64).
 //   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
+//   bunches [nbunch]          offsets, sizes, FP32-split origins and reference velocities.
+//   sched   [nbunch]          work split of the pair kernels (target tiles, source chunks, items).
 //   StepState (device)        present step n, t_n, dt and the derived window k0..n; kernels read it
 //                             so that one captured step can be replayed.
 #pragma once
@@ -38,18 +45,19 @@ enum : int {
 };
 
 struct StepState {
-  long long n;   // present (absolute) step index
-  double t;      // t_n
-  double dt;     // step of the next push
-  long long k0;  // earliest usable slot max(0, n - D + 1)
-  int p0;        // physical slot of k0
-  int pn;        // physical slot of n
+  long long n;           // present (absolute) step index
+  double t;              // t_n
+  double dt;             // step of the next push
+  long long hist_start;  // earliest slot stored since the history was (re)started
+  long long k0;          // earliest usable slot max(hist_start, n - D + 1)
+  int p0;                // physical slot of k0
+  int pn;                // physical slot of n
 };
 
 // retarded-time search proposals (values of emppp_proposal)
 enum { kPropBisect = 0, kPropClosedForm = 1, kPropMlp = 2 };
 
-// counters, reset by the prep kernel of every step
+// counters, accumulated until reset by the host
 enum { kStatOOH = 0, kStatShortcut = 1, kStatBisect = 2, kStatNodeTests = 3, kStatGuard = 4, kStatCount = 8 };
 
 struct SlotTables {
@@ -60,9 +68,31 @@ struct SlotTables {
   float* icdt32;    // [D] 1 / (c (t_{k+1} - t_k)), FP32
 };
 
+struct BunchDesc {
+  long long off;       // first particle
+  int n;               // particles
+  int pad_;
+  double origin[3];    // origin of the FP32 hi/lo position split
+  double beta_ref[3];  // reference velocity / c of the FP32 velocities
+};
+
+// Work split of the persistent pair kernels, per bunch: items are (source chunk, target tile of 128)
+// pairs taken chunk-major from an atomic counter by resident blocks; per-chunk partial sums are
+// reduced in a fixed order afterwards (nchunk > 1).
+struct BunchSched {
+  int ntb;       // target tiles
+  int nchunk;    // source chunks
+  int chunk;     // sources per chunk
+  int item_off;  // first work item of the bunch (items of all bunches are numbered consecutively)
+};
+
 struct DeviceState {
-  long long N;
+  long long N;  // particles of all bunches
   int D;
+  int nbunch;
+  const BunchDesc* bunches;  // [nbunch]
+  const BunchSched* sched;   // [nbunch]
+  const int* bunch_of;       // [N] bunch of each particle
   double* rec64;
   float* rec32;
   double* slot_t;
@@ -79,8 +109,7 @@ struct DeviceState {
   StepState* state;
   unsigned long long* stats;  // [kStatCount]
   int* err;
-  double origin[3];    // origin of the FP32 hi/lo split
-  double beta_ref[3];  // reference velocity / c of the FP32 shadow's velocities
+  double* bsum;     // [nbunch][4] per-bunch reductions (weighted position sums and weight)
 };
 
 struct BextParams {
@@ -90,16 +119,28 @@ struct BextParams {
   double center[3];
 };
 
-// Work split of a persistent pair kernel: items are (source chunk, target tile of 128) pairs taken
-// chunk-major from an atomic counter by `grid` resident blocks; per-chunk partial sums are reduced in a
-// fixed order afterwards (nchunk > 1).
-struct PairSchedule {
-  int ntb;     // target tiles
-  int nchunk;  // source chunks
-  int chunk;   // sources per chunk
-  int nitems;  // ntb * nchunk
+// launch configuration of a persistent pair kernel
+struct PairLaunch {
+  int nitems;  // work items of all bunches
   int grid;    // blocks launched
 };
+
+// item -> (bunch, chunk, target tile): bunches are searched by their first item
+__device__ __forceinline__ void decode_item(const BunchSched* __restrict__ sched, int nbunch, int item, int& b,
+                                            int& chunk_id, int& tb) {
+  int lo = 0, hi = nbunch - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sched[mid].item_off <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  b = lo;
+  const int local = item - sched[b].item_off;
+  chunk_id = local / sched[b].ntb;
+  tb = local - chunk_id * sched[b].ntb;
+}
 
 // ---- launchers (each in its own translation unit) ------------------------------------------
 // ring.cu
@@ -107,25 +148,29 @@ cudaError_t launch_init_slot0(const DeviceState& s, const double* x, const doubl
                               cudaStream_t st);
 cudaError_t launch_scatter_slot(const DeviceState& s, int p, const double* W, const double* V, cudaStream_t st);
 cudaError_t launch_gather_slot(const DeviceState& s, int p, double* W, double* V, cudaStream_t st);
-cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, const double* u,
-                             const double* w, cudaStream_t st);
+cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, long long hist_start,
+                             const double* u, const double* w, cudaStream_t st);
 cudaError_t launch_prep(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_advance(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st);
 // pair_fp64.cu
 int max_blocks_pair_fp64(int proposal);
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairSchedule& sc, cudaStream_t st);
-cudaError_t launch_reduce_partials(const DeviceState& s, int nchunk, cudaStream_t st);
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunch& pl, cudaStream_t st);
+cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
 cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st);
+// stage2.cu
+cudaError_t launch_bunch_sums(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_translate(const DeviceState& s, const double* shifts, cudaStream_t st);
+cudaError_t launch_transport_chunk(const DeviceState& s, const BextParams& b, double dt, int nsteps, double t_end,
+                                   cudaStream_t st);
 // order.cu
-size_t order_scratch_ints();
-cudaError_t launch_target_order(const DeviceState& s, int* bbox, int* hist, unsigned short* key, int* order,
-                                cudaStream_t st);
+cudaError_t prepare_target_order();
+cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, cudaStream_t st);
 // pair_mixed.cu
 int max_blocks_pair_mixed(int proposal);
-cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairSchedule& sc,
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairLaunch& pl,
                               cudaStream_t st);
 
 }  // namespace emppp

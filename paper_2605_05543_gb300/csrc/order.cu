@@ -1,48 +1,52 @@
 // Spatial order of the targets for the mixed-precision pair kernel.
 //
-// The particles' present positions are binned into a 32 x 32 x 32 grid over the bunch's bounding box,
-// the cells are numbered along a Morton (Z-order) curve, and a counting sort lists the particles cell
-// by cell. Threads then take targets in this order, so the 32 targets of a warp are close in space and
-// their retarded slots of any one source lie within a few cache lines. The order is a permutation of
-// 0..N-1 (each target is evaluated exactly once whatever the order); the order inside a cell comes from
-// atomics and may differ run to run, which changes which thread evaluates a target but not its result.
+// Each bunch's present positions are binned into a 2^b x 2^b x 2^b grid over the bunch's bounding box
+// (b = 2..5 from the bunch size), the cells are numbered along a Morton (Z-order) curve, and a
+// counting sort lists the bunch's particles cell by cell. Threads then take targets in this order, so
+// the 32 targets of a warp are close in space and their retarded slots of any one source lie within a
+// few cache lines. One block of 1024 threads sorts one bunch entirely in shared memory. The order is a
+// permutation of each bunch's index range (each target is evaluated exactly once whatever the order);
+// the order inside a cell comes from shared-memory atomics and may differ run to run, which changes
+// which thread evaluates a target but not its result.
 #include "emppp_internal.cuh"
 
 namespace emppp {
 
 namespace {
 
-constexpr int kCellBits = 5;                    // per axis
-constexpr int kCells = 1 << (3 * kCellBits);    // 32768
+constexpr int kThreads = 1024;
+constexpr int kMaxBits = 5;
 
-__device__ __forceinline__ int ordered_int(float f) {
-  const int i = __float_as_int(f);
-  return i >= 0 ? i : i ^ 0x7fffffff;
-}
-
-__device__ __forceinline__ float from_ordered_int(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
-
-__device__ __forceinline__ unsigned spread3(unsigned v) {  // 5 bits -> every third bit
+__device__ __forceinline__ unsigned spread3(unsigned v, int bits) {  // bit k -> bit 3k
   unsigned r = 0;
-#pragma unroll
-  for (int b = 0; b < kCellBits; b++) r |= ((v >> b) & 1u) << (3 * b);
+  for (int k = 0; k < bits; k++) r |= ((v >> k) & 1u) << (3 * k);
   return r;
 }
 
-__global__ void bbox_init_kernel(int* __restrict__ bbox) {
-  if (threadIdx.x < 3) {
-    bbox[threadIdx.x] = ordered_int(3.0e38f);
-    bbox[3 + threadIdx.x] = ordered_int(-3.0e38f);
-  }
+__host__ __device__ __forceinline__ int cell_bits(int n) {
+  int lg = 0;
+  while ((1 << (lg + 1)) <= n) lg++;
+  int b = lg / 3;
+  return b < 2 ? 2 : (b > kMaxBits ? kMaxBits : b);
 }
 
-// present positions are the FP32 hi parts of slot n (relative to the split origin)
-__global__ void bbox_kernel(const float* __restrict__ rec32, const StepState* __restrict__ state, long long N, int D,
-                            int* __restrict__ bbox) {
-  const int pn = (int)(state->n % D);
+__global__ void __launch_bounds__(kThreads) order_kernel(DeviceState s, unsigned* __restrict__ key,
+                                                         int* __restrict__ order) {
+  extern __shared__ int hist[];
+  __shared__ float s_lo[3][32], s_hi[3][32];
+  __shared__ int s_warp[32];
+  const BunchDesc bd = s.bunches[blockIdx.x];
+  const int n = bd.n;
+  const long long off = bd.off;
+  const int bits = cell_bits(n);
+  const int cells = 1 << (3 * bits);
+  const int pn = (int)(s.state->n % s.D);
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+  // bounding box of the present FP32 positions
   float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const float* q = rec32 + ((size_t)i * D + pn) * 12;
+  for (int k = tid; k < n; k += kThreads) {
+    const float* q = s.rec32 + ((size_t)(off + k) * s.D + pn) * 12;
     for (int c = 0; c < 3; c++) {
       const float x = q[c];
       if (x == x) {
@@ -52,100 +56,89 @@ __global__ void bbox_kernel(const float* __restrict__ rec32, const StepState* __
     }
   }
   for (int c = 0; c < 3; c++) {
-    for (int off = 16; off > 0; off >>= 1) {
-      lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], off));
-      hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], off));
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[c] = fminf(lo[c], __shfl_xor_sync(0xffffffffu, lo[c], o));
+      hi[c] = fmaxf(hi[c], __shfl_xor_sync(0xffffffffu, hi[c], o));
+    }
+    if (lane == 0) {
+      s_lo[c][wid] = lo[c];
+      s_hi[c][wid] = hi[c];
     }
   }
-  if ((threadIdx.x & 31) == 0) {
-    for (int c = 0; c < 3; c++) {
-      atomicMin(bbox + c, ordered_int(lo[c]));
-      atomicMax(bbox + 3 + c, ordered_int(hi[c]));
-    }
-  }
-}
-
-__global__ void key_hist_kernel(const float* __restrict__ rec32, const StepState* __restrict__ state, long long N,
-                                int D, const int* __restrict__ bbox, unsigned short* __restrict__ key,
-                                int* __restrict__ hist) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int pn = (int)(state->n % D);
-  const float* q = rec32 + ((size_t)i * D + pn) * 12;
-  unsigned cell[3];
+  for (int k = tid; k < cells; k += kThreads) hist[k] = 0;
+  __syncthreads();
+  float blo[3], bw[3];
   for (int c = 0; c < 3; c++) {
-    const float lo = from_ordered_int(bbox[c]), hi = from_ordered_int(bbox[3 + c]);
-    const float w = hi - lo;
-    float f = w > 0.f ? (q[c] - lo) / w : 0.f;
-    f = (f == f) ? fminf(fmaxf(f, 0.f), 1.f) : 0.f;
-    const int k = (int)(f * (float)(1 << kCellBits));
-    cell[c] = (unsigned)(k >= (1 << kCellBits) ? (1 << kCellBits) - 1 : k);
-  }
-  const unsigned m = spread3(cell[0]) | (spread3(cell[1]) << 1) | (spread3(cell[2]) << 2);
-  key[i] = (unsigned short)m;
-  atomicAdd(hist + m, 1);
-}
-
-// exclusive scan of kCells counts in one block of 1024 threads (32 cells each)
-__global__ void __launch_bounds__(1024) scan_kernel(int* __restrict__ hist) {
-  __shared__ int warp_tot[32];
-  constexpr int per = kCells / 1024;
-  const int t = threadIdx.x;
-  int v[per];
-  int sum = 0;
-#pragma unroll
-  for (int k = 0; k < per; k++) {
-    v[k] = hist[t * per + k];
-    sum += v[k];
-  }
-  // inclusive scan of the per-thread sums across the block
-  int x = sum;
-  for (int off = 1; off < 32; off <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, off);
-    if ((t & 31) >= off) x += y;
-  }
-  if ((t & 31) == 31) warp_tot[t >> 5] = x;
-  __syncthreads();
-  if (t < 32) {
-    int w = warp_tot[t];
-    for (int off = 1; off < 32; off <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, w, off);
-      if (t >= off) w += y;
+    float a = 3.0e38f, b2 = -3.0e38f;
+    for (int w = 0; w < kThreads / 32; w++) {
+      a = fminf(a, s_lo[c][w]);
+      b2 = fmaxf(b2, s_hi[c][w]);
     }
-    warp_tot[t] = w;
+    blo[c] = a;
+    bw[c] = b2 - a;
+  }
+  // cell keys and histogram
+  const float side = (float)(1 << bits);
+  for (int k = tid; k < n; k += kThreads) {
+    const float* q = s.rec32 + ((size_t)(off + k) * s.D + pn) * 12;
+    unsigned cc[3];
+    for (int c = 0; c < 3; c++) {
+      float f = bw[c] > 0.f ? (q[c] - blo[c]) / bw[c] : 0.f;
+      f = (f == f) ? fminf(fmaxf(f, 0.f), 1.f) : 0.f;
+      const int m = (int)(f * side);
+      cc[c] = (unsigned)(m >= (1 << bits) ? (1 << bits) - 1 : m);
+    }
+    const unsigned m = spread3(cc[0], bits) | (spread3(cc[1], bits) << 1) | (spread3(cc[2], bits) << 2);
+    key[off + k] = m;
+    atomicAdd(hist + m, 1);
   }
   __syncthreads();
-  int base = x - sum + ((t >> 5) > 0 ? warp_tot[(t >> 5) - 1] : 0);
-#pragma unroll
-  for (int k = 0; k < per; k++) {
-    hist[t * per + k] = base;
-    base += v[k];
+  // exclusive scan of the cell counts: each thread owns a contiguous run of cells
+  const int per = (cells + kThreads - 1) / kThreads;
+  const int c0 = tid * per, c1 = min(cells, c0 + per);
+  int sum = 0;
+  for (int k = c0; k < c1; k++) sum += hist[k];
+  int x = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-}
-
-__global__ void scatter_order_kernel(const unsigned short* __restrict__ key, long long N, int* __restrict__ offs,
-                                     int* __restrict__ order) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  const int pos = atomicAdd(offs + key[i], 1);
-  order[pos] = (int)i;
+  if (lane == 31) s_warp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = s_warp[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  int base = x - sum + (wid > 0 ? s_warp[wid - 1] : 0);
+  for (int k = c0; k < c1; k++) {
+    const int v = hist[k];
+    hist[k] = base;
+    base += v;
+  }
+  __syncthreads();
+  // scatter
+  for (int k = tid; k < n; k += kThreads) {
+    const int pos = atomicAdd(hist + key[off + k], 1);
+    order[off + pos] = (int)(off + k);
+  }
 }
 
 }  // namespace
 
-size_t order_scratch_ints() { return 6 + kCells; }
+constexpr size_t kSmem = sizeof(int) << (3 * kMaxBits);
 
-// bbox: int[6], hist: int[kCells], key: ushort[N], order: int[N]
-cudaError_t launch_target_order(const DeviceState& s, int* bbox, int* hist, unsigned short* key, int* order,
-                                cudaStream_t st) {
-  bbox_init_kernel<<<1, 32, 0, st>>>(bbox);
-  cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * kCells, st);
-  if (e != cudaSuccess) return e;
-  bbox_kernel<<<152, 256, 0, st>>>(s.rec32, s.state, s.N, s.D, bbox);
-  const unsigned nb = (unsigned)((s.N + 255) / 256);
-  key_hist_kernel<<<nb, 256, 0, st>>>(s.rec32, s.state, s.N, s.D, bbox, key, hist);
-  scan_kernel<<<1, 1024, 0, st>>>(hist);
-  scatter_order_kernel<<<nb, 256, 0, st>>>(key, s.N, hist, order);
+// allows the kernel its shared-memory histogram on the current device (call before launching)
+cudaError_t prepare_target_order() {
+  return cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+}
+
+cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, cudaStream_t st) {
+  order_kernel<<<s.nbunch, kThreads, kSmem, st>>>(s, key, order);
   return cudaGetLastError();
 }
 

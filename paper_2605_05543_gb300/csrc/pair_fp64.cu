@@ -41,11 +41,11 @@ struct PairArgs {
   int* err;
   long long N;
   int D;
-  long long chunk;  // sources per work item
-  int ntb;          // target tiles
-  int nitems;       // work items = source chunks x target tiles, chunk-major
-  int* work;        // work-item counter (zero at launch)
-  double beta_ref[3];
+  int nbunch;
+  const BunchDesc* __restrict__ bunches;
+  const BunchSched* __restrict__ sched;
+  int nitems;  // work items of all bunches
+  int* work;   // work-item counter (zero at launch)
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   win.D = D;
   const int pn = a.state->pn;
   const double t = a.state->t;
-  const float3 bref = make_float3((float)a.beta_ref[0], (float)a.beta_ref[1], (float)a.beta_ref[2]);
   const float inv_cdt = PROP == kPropClosedForm ? (float)(1.0 / (kC * a.state->dt)) : 0.f;
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
@@ -95,11 +94,15 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   __syncthreads();
   const int item = s_item;
   if (item >= a.nitems) break;
-  const int chunk_id = item / a.ntb;
-  const int tb = item - chunk_id * a.ntb;
-  const long long i = (long long)tb * kBlock + threadIdx.x;
-  const bool active = i < N;
-  const long long ic = active ? i : 0;
+  int b, chunk_id, tb;
+  decode_item(a.sched, a.nbunch, item, b, chunk_id, tb);
+  const BunchDesc& bd = a.bunches[b];
+  const BunchSched& bs = a.sched[b];
+  const float3 bref = make_float3((float)bd.beta_ref[0], (float)bd.beta_ref[1], (float)bd.beta_ref[2]);
+  const long long i_loc = (long long)tb * kBlock + threadIdx.x;
+  const bool active = i_loc < bd.n;
+  const long long i = bd.off + (active ? i_loc : 0);
+  const long long ic = i;
 
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
@@ -111,8 +114,8 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     rh2 = q[2];
   }
 
-  const long long j_begin = (long long)chunk_id * a.chunk;
-  const long long j_end = min(N, j_begin + a.chunk);
+  const long long j_begin = bd.off + (long long)chunk_id * bs.chunk;
+  const long long j_end = min(bd.off + bd.n, j_begin + bs.chunk);
 
   double Et[3] = {0, 0, 0}, Bt[3] = {0, 0, 0};
   double Ep[3] = {0, 0, 0}, Bp[3] = {0, 0, 0};
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     Bt[c] += Bp[c];
   }
   if (active) {
-    if (a.nitems == a.ntb) {
+    if (bs.nchunk == 1) {
       for (int c = 0; c < 3; c++) {
         a.E[3 * i + c] = Et[c];
         a.B[3 * i + c] = Bt[c];
@@ -327,16 +330,19 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   }
 }
 
-// E_i = sum over slices s of partial[s][i] (fixed order).
-__global__ void reduce_partials_kernel(const double* __restrict__ part, int S, long long N, double* __restrict__ E,
+// E_i = sum over the source chunks c of partial[c][i] (fixed order), for bunches split in chunks
+__global__ void reduce_partials_kernel(const double* __restrict__ part, const BunchSched* __restrict__ sched,
+                                       const int* __restrict__ bunch_of, long long N, double* __restrict__ E,
                                        double* __restrict__ B) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
+  const int S = sched[bunch_of[i]].nchunk;
+  if (S == 1) return;  // written directly by the pair kernel
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int s = 0; s < S; s++) {
-    const double* o = part + ((size_t)s * N + i) * 6;
+  for (int c = 0; c < S; c++) {
+    const double* o = part + ((size_t)c * N + i) * 6;
 #pragma unroll
-    for (int c = 0; c < 6; c++) acc[c] += o[c];
+    for (int k = 0; k < 6; k++) acc[k] += o[k];
   }
   for (int c = 0; c < 3; c++) {
     E[3 * i + c] = acc[c];
@@ -361,7 +367,7 @@ int max_blocks_pair_fp64(int proposal) {
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairSchedule& sc, cudaStream_t st) {
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunch& pl, cudaStream_t st) {
   PairArgs a;
   a.rec64 = s.rec64;
   a.rec32 = s.rec32;
@@ -377,22 +383,23 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairSched
   a.err = s.err;
   a.N = s.N;
   a.D = s.D;
-  a.chunk = sc.chunk;
-  a.ntb = sc.ntb;
-  a.nitems = sc.nitems;
+  a.nbunch = s.nbunch;
+  a.bunches = s.bunches;
+  a.sched = s.sched;
+  a.nitems = pl.nitems;
   a.work = s.work;
-  for (int c = 0; c < 3; c++) a.beta_ref[c] = s.beta_ref[c];
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)
-    pair_fp64_kernel<kPropClosedForm><<<sc.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropClosedForm><<<pl.grid, kBlock, 0, st>>>(a);
   else
-    pair_fp64_kernel<kPropBisect><<<sc.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropBisect><<<pl.grid, kBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_partials(const DeviceState& s, int nchunk, cudaStream_t st) {
-  reduce_partials_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s.partial, nchunk, s.N, s.Eself, s.Bself);
+cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st) {
+  reduce_partials_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s.partial, s.sched, s.bunch_of, s.N, s.Eself,
+                                                                          s.Bself);
   return cudaGetLastError();
 }
 

@@ -58,11 +58,11 @@ struct MixedArgs {
   int* err;
   int N;
   int D;
-  int chunk;   // sources per work item
-  int ntb;     // target tiles (kBlock targets each)
-  int nitems;  // work items = source chunks x target tiles, chunk-major
+  int nbunch;
+  const BunchDesc* __restrict__ bunches;
+  const BunchSched* __restrict__ sched;
+  int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
-  float bref[3];  // reference velocity of the shadow's dbeta
 };
 
 struct Target {
@@ -172,11 +172,16 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
   __syncthreads();
   const int item = s_item;
   if (item >= a.nitems) break;
-  const int chunk_id = item / a.ntb;
-  const int tb = item - chunk_id * a.ntb;
-  const int t = tb * kBlock + threadIdx.x;
-  const bool active = t < N;
-  const int i = active ? (a.order ? a.order[t] : t) : 0;
+  int b, chunk_id, tb;
+  decode_item(a.sched, a.nbunch, item, b, chunk_id, tb);
+  const BunchDesc& bd = a.bunches[b];
+  const BunchSched& bs = a.sched[b];
+  const int boff = (int)bd.off;
+  const float bref0 = (float)bd.beta_ref[0], bref1 = (float)bd.beta_ref[1], bref2 = (float)bd.beta_ref[2];
+  const int t_loc = tb * kBlock + threadIdx.x;
+  const bool active = t_loc < bd.n;
+  const int t = boff + (active ? t_loc : 0);
+  const int i = a.order ? a.order[t] : t;
 
   Target r;
   {
@@ -195,8 +200,8 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
 
-  const int j_begin = chunk_id * a.chunk;
-  const int j_end = min(N, j_begin + a.chunk);
+  const int j_begin = boff + chunk_id * bs.chunk;
+  const int j_end = min(boff + bd.n, j_begin + bs.chunk);
 
   float Es[3] = {0.f, 0.f, 0.f}, Ec[3] = {0.f, 0.f, 0.f}, Bs[3] = {0.f, 0.f, 0.f}, Bc[3] = {0.f, 0.f, 0.f};
   const float ic = (float)(1.0 / kC);
@@ -209,7 +214,7 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
       const float4* q = a.rec32 + ((size_t)j * D + pn) * 3;
       s_q0[threadIdx.x] = q[0];
       const float4 q2 = q[2];
-      s_q2[threadIdx.x] = make_float4(a.bref[0] + q2.x, a.bref[1] + q2.y, a.bref[2] + q2.z, q2.w);
+      s_q2[threadIdx.x] = make_float4(bref0 + q2.x, bref1 + q2.y, bref2 + q2.z, q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
     }
     __syncthreads();
@@ -373,7 +378,7 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
         const int p1 = win.phys(l1);
         const float d0 = dA.x, d1 = dA.y, d2 = dA.z;
         const float L1 = __ldg(a.ct32 + p1);
-        const float b10 = a.bref[0] + A.q2.x, b11 = a.bref[1] + A.q2.y, b12 = a.bref[2] + A.q2.z;
+        const float b10 = bref0 + A.q2.x, b11 = bref1 + A.q2.y, b12 = bref2 + A.q2.z;
         const float ig2 = A.q0.w, g2 = A.q2.w;
         const float hb = (d0 * b10 + d1 * b11 + d2 * b12) - L1;
         const float C0 = fmaf(L1, L1, -(d0 * d0 + d1 * d1 + d2 * d2));
@@ -450,7 +455,7 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
       Et[c] = (double)Es[c] - (double)Ec[c];
       Bt[c] = (double)Bs[c] - (double)Bc[c];
     }
-    if (a.nitems == a.ntb) {
+    if (bs.nchunk == 1) {
       for (int c = 0; c < 3; c++) {
         a.E[3 * i + c] = Et[c];
         a.B[3 * i + c] = Bt[c];
@@ -489,7 +494,7 @@ int max_blocks_pair_mixed(int proposal) {
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairSchedule& sc,
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairLaunch& pl,
                               cudaStream_t st) {
   MixedArgs a;
   a.rec32 = reinterpret_cast<const float4*>(s.rec32);
@@ -508,17 +513,17 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.err = s.err;
   a.N = (int)s.N;
   a.D = s.D;
-  a.chunk = sc.chunk;
-  a.ntb = sc.ntb;
-  a.nitems = sc.nitems;
+  a.nbunch = s.nbunch;
+  a.bunches = s.bunches;
+  a.sched = s.sched;
+  a.nitems = pl.nitems;
   a.work = s.work;
-  for (int c = 0; c < 3; c++) a.bref[c] = (float)s.beta_ref[c];
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)
-    pair_mixed_kernel<kPropClosedForm><<<sc.grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropClosedForm><<<pl.grid, kBlock, 0, st>>>(a);
   else
-    pair_mixed_kernel<kPropBisect><<<sc.grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropBisect><<<pl.grid, kBlock, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -13,7 +13,8 @@ __device__ __forceinline__ void write_record(const DeviceState& s, long long j, 
   reinterpret_cast<double2*>(r)[1] = make_double2(w2, v0);
   reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
   float4 q[3];
-  shadow_record(s.origin, s.beta_ref, w0, w1, w2, v0, v1, v2, gamma2_of_v(v0, v1, v2), q);
+  const BunchDesc& bd = s.bunches[s.bunch_of[j]];
+  shadow_record(bd.origin, bd.beta_ref, w0, w1, w2, v0, v1, v2, gamma2_of_v(v0, v1, v2), q);
   float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)j * s.D + p) * 12);
   o[0] = q[0];
   o[1] = q[1];
@@ -64,13 +65,14 @@ __global__ void gather_slot_kernel(DeviceState s, int p, double* __restrict__ W,
   }
 }
 
-__global__ void set_state_kernel(DeviceState s, long long n, double t, double dt, const double* __restrict__ u,
-                                 const double* __restrict__ w) {
+__global__ void set_state_kernel(DeviceState s, long long n, double t, double dt, long long hist_start,
+                                 const double* __restrict__ u, const double* __restrict__ w) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i == 0) {
     s.state->n = n;
     s.state->t = t;
     s.state->dt = dt;
+    s.state->hist_start = hist_start;
     *s.err = 0;
   }
   if (i >= s.N) return;
@@ -89,7 +91,8 @@ __global__ void set_state_kernel(DeviceState s, long long n, double t, double dt
 __global__ void prep_kernel(DeviceState s) {
   const long long n = s.state->n;
   const double t_n = s.state->t;
-  const long long k0 = n - s.D + 1 > 0 ? n - s.D + 1 : 0;
+  const long long hs = s.state->hist_start;
+  const long long k0 = n - s.D + 1 > hs ? n - s.D + 1 : hs;
   const int p0 = (int)(k0 % s.D);
   const int pn = (int)(n % s.D);
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -152,9 +155,9 @@ cudaError_t launch_gather_slot(const DeviceState& s, int p, double* W, double* V
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, const double* u,
-                             const double* w, cudaStream_t st) {
-  set_state_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, n, t, dt, u, w);
+cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, long long hist_start,
+                             const double* u, const double* w, cudaStream_t st) {
+  set_state_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s, n, t, dt, hist_start, u, w);
   return cudaGetLastError();
 }
 

@@ -33,7 +33,8 @@ class EmpppError(RuntimeError):
 
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("pair_fields", ctypes.c_int32),
-                ("source_split", ctypes.c_int32), ("timing", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("source_split", ctypes.c_int32), ("timing", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Bext(ctypes.Structure):
@@ -56,7 +57,11 @@ SIGNATURES = {
     "emppp_default_options": (None, [ctypes.POINTER(Options)]),
     "emppp_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(Options), _vp,
                                     ctypes.POINTER(_H)]),
+    "emppp_create_batch": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                          ctypes.c_double, ctypes.POINTER(Options), _vp, ctypes.POINTER(_H)]),
     "emppp_destroy": (None, [_H]),
+    "emppp_handoff": (ctypes.c_int, [_H, ctypes.POINTER(ctypes.c_double)]),
+    "emppp_transport": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(Bext)]),
     "emppp_set_particles": (ctypes.c_int, [_H, _vp, _vp, _vp, ctypes.c_int32]),
     "emppp_set_history": (ctypes.c_int, [_H, ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp,
                                          ctypes.c_int32]),
@@ -161,9 +166,11 @@ def bext_dipole(m0: float, center=(0.0, 0.0, 0.0)) -> Bext:
     return e
 
 
-def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_split=0, timing=False) -> Options:
+def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_split=0, timing=False,
+                 graphs=True) -> Options:
     o = Options()
     load().emppp_default_options(ctypes.byref(o))
+    o.graphs = 1 if graphs else 0
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.proposal = PROPOSAL[proposal] if isinstance(proposal, str) else int(proposal)
     o.pair_fields = 1 if pair_fields else 0
@@ -173,18 +180,27 @@ def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_s
 
 
 class Solver:
-    """One EM-PP system of n particles with history depth `depth` and step dt (all on one GPU)."""
+    """An EM-PP system on one GPU: n particles (or, with `bunches`, several independent bunches whose
+    particles are concatenated in every per-particle array), history depth `depth` and step dt."""
 
     def __init__(self, n: int, depth: int, dt: float, precision="fp64", proposal="bisect", pair_fields=True,
-                 source_split=0, stream=None, timing=False):
+                 source_split=0, stream=None, timing=False, graphs=True, bunches=None):
         self.lib = load()
-        self.n = int(n)
         self.depth = int(depth)
         self.dt = float(dt)
         self._h = _H()
-        self._opt = make_options(precision, proposal, pair_fields, source_split, timing)
-        _check(self.lib.emppp_create(self.n, self.depth, self.dt, ctypes.byref(self._opt),
-                                     _stream_handle(stream), ctypes.byref(self._h)))
+        self._opt = make_options(precision, proposal, pair_fields, source_split, timing, graphs)
+        if bunches is None:
+            self.n = int(n)
+            self.bunches = [self.n]
+            _check(self.lib.emppp_create(self.n, self.depth, self.dt, ctypes.byref(self._opt),
+                                         _stream_handle(stream), ctypes.byref(self._h)))
+        else:
+            self.bunches = [int(b) for b in bunches]
+            self.n = sum(self.bunches)
+            arr = (ctypes.c_int64 * len(self.bunches))(*self.bunches)
+            _check(self.lib.emppp_create_batch(len(self.bunches), arr, self.depth, self.dt, ctypes.byref(self._opt),
+                                               _stream_handle(stream), ctypes.byref(self._h)))
 
     def close(self):
         if self._h:
@@ -207,8 +223,11 @@ class Solver:
     def handle(self):
         return self._h
 
-    def set_options(self, precision=None, proposal=None, pair_fields=None, source_split=None, timing=None):
+    def set_options(self, precision=None, proposal=None, pair_fields=None, source_split=None, timing=None,
+                    graphs=None):
         o = self._opt
+        if graphs is not None:
+            o.graphs = 1 if graphs else 0
         if timing is not None:
             o.timing = 1 if timing else 0
         if precision is not None:
@@ -256,6 +275,15 @@ class Solver:
 
     def step(self, nsteps=1, bext=None):
         _check(self.lib.emppp_step(self._h, int(nsteps), None if bext is None else ctypes.byref(bext)))
+
+    def handoff(self, center):
+        """Translate every bunch so its weighted centroid sits at `center`; history restarts."""
+        c = (ctypes.c_double * 3)(*[float(v) for v in center])
+        _check(self.lib.emppp_handoff(self._h, c))
+
+    def transport(self, nsteps, dt, bext=None):
+        """Stage-2 transport: nsteps steps of dt in the background field only (no pair fields)."""
+        _check(self.lib.emppp_transport(self._h, int(nsteps), float(dt), None if bext is None else ctypes.byref(bext)))
 
     def get_state(self, x=None, u=None):
         """Returns (x, u, t, n). Pass preallocated host arrays or CUDA tensors to fill them in place."""
