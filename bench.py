@@ -65,6 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--proposal", choices=["bisect", "closed_form", "mlp"], default="closed_form")
+    ap.add_argument("--ablation", action="store_true", help="also time the other proposals on the same state")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -239,7 +240,38 @@ def cpu_baseline(h, wl, seconds, E_gpu=None, B_gpu=None, seed=1):
     return base, parity
 
 
-def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True):
+def train_proposal(wl, win, n_hist, samples=65536, epochs=60, seed=3):
+    """Trains the proposal network on (feature, delay) samples of random pairs of the workload's stored
+    state, drawn with the library's exact retarded-time search; returns (params, report)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_05543_gb300 import emppp, inputs
+
+    N, D = wl["N"], wl["depth"]
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, N, samples)
+    j = rng.integers(0, N - 1, samples)
+    j = np.where(j >= i, j + 1, j)
+    pairs = np.stack([i, j], axis=1).astype(np.int32)
+    T, W, V, u = win
+    t0 = time.perf_counter()
+    with emppp.Solver(N, D, wl["dt"]) as s:
+        s.set_history(n_hist, T, W, V, u)
+        feat, delay, z = s.sample_delays(pairs)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    p0 = inputs.mlp_init_params(seed)
+    loss0, _ = emppp.mlp_gradient(p0, feat, z)
+    p, losses = emppp.mlp_train(p0, feat, z, epochs=epochs, batch=512, lr=3e-3, lr_final=1e-5)
+    loss1, _ = emppp.mlp_gradient(p, feat, z)
+    t2 = time.perf_counter()
+    return p, {"samples": samples, "epochs": epochs, "batch": 512, "lr": "3e-3 -> 1e-5 (cosine)", "loss_initial": loss0,
+               "loss_final": loss1, "sample_seconds": t1 - t0, "train_seconds": t2 - t1,
+               "target": "z = log(c (t - t_r) / |r - w_n|), MSE"}
+
+
+def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True, net=None):
     import numpy as np
     import torch
 
@@ -251,6 +283,8 @@ def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, ke
     out = {}
     with emppp.Solver(N, D, wl["dt"], precision=path, proposal=proposal, stream=stream, timing=True) as s:
         s.set_history(h.n, T, W, V, u)
+        if net is not None:
+            s.set_proposal(net)
         # warm-up; the first step's fields are those of the stored state
         s.step(1)
         if keep_fields and rank == 0:
@@ -315,7 +349,10 @@ def run_ours(args):
     steps = args.steps if args.steps is not None else (5 if args.path == "fp64" else 50)
     warmup = max(args.warmup, 1)
     dev = torch.device("cuda", local)
-    res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e)
+    net, net_report = None, None
+    if args.proposal == "mlp":
+        net, net_report = train_proposal(wl, win, h.n)
+    res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e, net=net)
     ms = max_over_ranks(res["ms"], dev)
     pairs_per_step = wl["N"] * (wl["N"] - 1)
     total_pairs = sum_over_ranks(pairs_per_step * steps, dev)
@@ -346,6 +383,22 @@ def run_ours(args):
         "branch_mix": {k: st[k] / max(st["pairs"], 1) for k in ("out_of_history", "shortcut", "bisection")},
         "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
     }
+    if net_report is not None:
+        line["proposal_net"] = net_report
+    if args.proposal == "mlp" or args.ablation:
+        # the same state and path under each proposal: mean node tests per pair (identical brackets)
+        abl = {}
+        for prop in ("bisect", "closed_form", "mlp"):
+            if prop == args.proposal:
+                r = res
+            elif prop == "mlp" and net is None:
+                continue
+            else:
+                r = run_path(args, args.path, prop, 2 if args.path == "fp64" else 5, 1, wl, h, win, rank, e2e=False,
+                             keep_fields=False, net=net if prop == "mlp" else None)
+            abl[prop] = {"node_tests_per_pair": r["stats"]["node_tests"] / max(r["stats"]["pairs"], 1),
+                         "ms_per_step": r["ms"]}
+        line["proposal_ablation"] = abl
     if "e2e" in res:
         e = res["e2e"]
         el = max_over_ranks(e["seconds"], dev)

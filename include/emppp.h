@@ -101,6 +101,21 @@ typedef struct {
   int64_t timed_steps;     /* steps whose events were recorded (the event pool holds 4096 steps) */
 } emppp_stats;
 
+/* Work split of the pair kernel: items_per_block work items (bunch, source chunk, target tile) per
+ * resident block, which sets the sources per chunk; target_order 1 sorts the targets spatially each
+ * step (mixed path). Chosen by emppp_autotune or set with emppp_set_tuning. */
+typedef struct {
+  int32_t items_per_block; /* default 16 */
+  int32_t target_order;    /* default 1 */
+  double ms;               /* measured time of one field evaluation (emppp_autotune), else 0 */
+} emppp_tuning;
+
+typedef struct {
+  int32_t ncand;           /* candidates timed */
+  int32_t best;            /* index of the chosen one */
+  emppp_tuning cand[16];
+} emppp_tuning_report;
+
 /* Fills *out with the defaults listed above. */
 EMPPP_API void emppp_default_options(emppp_options* out);
 
@@ -179,6 +194,15 @@ EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out);
 /* Zeroes the accumulated counters and recorded times (not kernel_launches). */
 EMPPP_API emppp_status emppp_reset_stats(emppp_handle h);
 
+/* Times the pair-field evaluation of the present state (slot tables, target order, pair kernel and
+ * partial-sum reduction; the state is not advanced) for items_per_block in {4, 8, 16, 32, 64} and,
+ * on the mixed path, with and without the spatial target order; keeps the fastest for later steps of
+ * the current precision and proposal. report may be NULL. Synchronises the stream; resets the stats. */
+EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* report);
+
+/* Sets the work split directly (e.g. a tuning found earlier). items_per_block in 1..256. */
+EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning);
+
 /* Replaces the options (precision, proposal, pair_fields, source_split, timing) for later steps. */
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt);
 
@@ -207,6 +231,55 @@ EMPPP_API emppp_status emppp_synchronize(emppp_handle h);
 EMPPP_API emppp_status emppp_fields_noalloc(int64_t n, int32_t nslots, const double* T, const double* W,
                                             const double* V, const double* w, double* E, double* B,
                                             void* cuda_stream);
+
+/* ---- Learned retarded-time proposal --------------------------------------------------------------
+ * A 10-64-64-1 perceptron with SiLU activations predicts z = log(c (t - t_r) / |d|) for a target and a
+ * source (d = r - w_n, the present separation); the search then starts at the slot the predicted
+ * delay points at and finishes with the guarded search, so brackets and fields are those of the
+ * paper's search whatever the network predicts (no counterpart in the paper: it is a proposal for
+ * the bracketing of Sec. 2.2).
+ * Features, per pair (FP32): d / |d| (3), |d| / L (1), beta_n (3), (beta_n - beta_{n-1}) D (3) with
+ * L = c dt D, beta = v / c of the source at its present slot n and the slot before.
+ * Parameters (FP32, EMPPP_MLP_NUM_PARAMS values): W1[10][64] (feature, unit), b1[64], W2[64][64] (in,
+ * out), b2[64], w3[64], b3. Tensor-core passes round X, W1, silu(H1) and W2 to BF16 and accumulate in
+ * FP32. */
+#define EMPPP_MLP_NUM_PARAMS 4929
+
+typedef struct {
+  int32_t epochs;   /* passes over the data */
+  int32_t batch;    /* rows per Adam step */
+  float lr;         /* Adam step size */
+  float beta1;      /* Adam first-moment decay (0.9) */
+  float beta2;      /* Adam second-moment decay (0.999) */
+  float eps;        /* Adam epsilon (1e-8) */
+  float lr_final;   /* step size of the last Adam step: cosine decay from lr; 0 (or >= lr) keeps lr */
+  int32_t reserved;
+} emppp_mlp_config;
+
+/* Training data from the method itself: for m (target, source) pairs (pairs[2k], pairs[2k+1], indices
+ * into the present particles, target != source) at the present state, the features [m][10], the exact
+ * retarded delay t - t_r [m] (FP64 bracket of Sec. 2.2 and the smaller root of eq:dt) and the training
+ * target z = log(c (t - t_r) / |d|) [m]. All arrays host or device. */
+EMPPP_API emppp_status emppp_sample_delays(emppp_handle h, const int32_t* pairs, int64_t m, float* features,
+                                           double* delays, float* targets, int32_t is_device_ptr);
+
+/* z [m] of the network with parameters params for features [m][10]. Device pointers; synchronous. */
+EMPPP_API emppp_status emppp_mlp_forward(const float* params, const float* features, int64_t m, float* z,
+                                         void* cuda_stream);
+
+/* Loss sum_r (z_r - targets_r)^2 / m and its gradient grad [EMPPP_MLP_NUM_PARAMS] for one batch of m
+ * rows. Device pointers (loss on the host); synchronous. */
+EMPPP_API emppp_status emppp_mlp_gradient(const float* params, const float* features, const float* targets,
+                                          int64_t m, float* grad, double* loss, void* cuda_stream);
+
+/* Trains params (device, in place) with Adam on m rows of (features, targets) (device), in consecutive
+ * batches of cfg->batch rows, cfg->epochs passes; loss_per_epoch [epochs] (host, may be NULL) receives
+ * the mean loss of each pass. Synchronous. */
+EMPPP_API emppp_status emppp_mlp_train(float* params, const float* features, const float* targets, int64_t m,
+                                       const emppp_mlp_config* cfg, float* loss_per_epoch, void* cuda_stream);
+
+/* Sets the network used by EMPPP_PROPOSAL_MLP (params host or device, EMPPP_MLP_NUM_PARAMS values). */
+EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, int32_t is_device_ptr);
 
 /* Text of the last failing call on this thread ("" if none). Valid until the next call. */
 EMPPP_API const char* emppp_last_error(void);

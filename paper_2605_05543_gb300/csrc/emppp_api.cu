@@ -64,13 +64,18 @@ struct emppp_ctx {
   BunchSched* d_sched = nullptr;
   int* d_bunch_of = nullptr;
   PairLaunch launch{};
-  int sched_key = -1;  // configuration the uploaded schedule belongs to
+  long long sched_key = -1;  // configuration the uploaded schedule belongs to
+  int items_per_block = 16;  // work items per resident block of the pair kernel
+  int target_order = 1;      // spatial target order on the mixed path
+  // proposal network image (EMPPP_PROPOSAL_MLP)
+  void* mlp_image = nullptr;
+  bool has_mlp = false;
   // spatial target order of the mixed path
   unsigned* ord_key = nullptr;
   int* order = nullptr;
   // resident blocks per SM of the pair kernels (queried on first use), per proposal
-  int blocks_fp64[2] = {0, 0};
-  int blocks_mixed[2] = {0, 0};
+  int blocks_fp64[3] = {0, 0, 0};
+  int blocks_mixed[3] = {0, 0, 0};
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
   int64_t steps_acc = 0;  // steps since the last stats reset
@@ -112,8 +117,9 @@ emppp_status dalloc(emppp_ctx* c, T** p, size_t count) {
 emppp_status validate_options(const emppp_options* o) {
   if (o->precision != EMPPP_FP64 && o->precision != EMPPP_MIXED)
     return fail(EMPPP_ERR_ARG, "unknown precision %d", o->precision);
-  if (o->proposal != EMPPP_PROPOSAL_BISECT && o->proposal != EMPPP_PROPOSAL_CLOSED_FORM)
-    return fail(EMPPP_ERR_ARG, "proposal %d is not available in this build", o->proposal);
+  if (o->proposal != EMPPP_PROPOSAL_BISECT && o->proposal != EMPPP_PROPOSAL_CLOSED_FORM &&
+      o->proposal != EMPPP_PROPOSAL_MLP)
+    return fail(EMPPP_ERR_ARG, "unknown proposal %d", o->proposal);
   if (o->pair_fields != 0 && o->pair_fields != 1) return fail(EMPPP_ERR_ARG, "pair_fields must be 0 or 1");
   if (o->source_split < 0) return fail(EMPPP_ERR_ARG, "source_split must be >= 0");
   if (o->timing != 0 && o->timing != 1) return fail(EMPPP_ERR_ARG, "timing must be 0 or 1");
@@ -137,9 +143,10 @@ void invalidate_graph(emppp_handle h) {
 // sources. Uploaded when the configuration changes.
 emppp_status update_schedule(emppp_handle c) {
   const bool mixed = c->opt.precision == EMPPP_MIXED;
-  const int key = (mixed ? 1 : 0) | ((c->opt.proposal & 1) << 1) | (c->opt.source_split << 2);
+  const long long key = (mixed ? 1 : 0) | ((long long)(c->opt.proposal & 3) << 1) |
+                        ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13);
   if (key == c->sched_key) return EMPPP_OK;
-  int& nb = mixed ? c->blocks_mixed[c->opt.proposal & 1] : c->blocks_fp64[c->opt.proposal & 1];
+  int& nb = mixed ? c->blocks_mixed[c->opt.proposal % 3] : c->blocks_fp64[c->opt.proposal % 3];
   if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal) : max_blocks_pair_fp64(c->opt.proposal);
   const long long R = (long long)nb * c->num_sms;
   long long total_tiles = 0;
@@ -153,7 +160,7 @@ emppp_status update_schedule(emppp_handle c) {
     if (c->opt.source_split > 0) {
       nchunk = c->opt.source_split;
     } else {
-      nchunk = (16 * R + total_tiles - 1) / total_tiles;
+      nchunk = ((long long)c->items_per_block * R + total_tiles - 1) / total_tiles;
       const long long by_size = (n + 255) / 256;
       if (nchunk > by_size) nchunk = by_size;
     }
@@ -275,14 +282,15 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   if (ev) CU(cudaEventRecord(ev[0], h->stream));
   CU(launch_prep(h->ds, h->stream));
   k += 1;
-  if (h->opt.pair_fields && h->opt.precision == EMPPP_MIXED) {
+  const bool ordered = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED && h->target_order;
+  if (ordered) {
     CU(launch_target_order(h->ds, h->ord_key, h->order, h->stream));
     k += 1;
   }
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
     if (h->opt.precision == EMPPP_MIXED)
-      CU(launch_pair_mixed(h->ds, h->order, h->opt.proposal, h->launch, h->stream));
+      CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->launch, h->stream));
     else
       CU(launch_pair_fp64(h->ds, h->opt.proposal, h->launch, h->stream));
     k += 1;
@@ -422,10 +430,16 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(c->d_bunches, (size_t)nbunch);
   ALLOC(c->d_sched, (size_t)nbunch);
   ALLOC(c->d_bunch_of, N);
+  {
+    unsigned char* img = nullptr;
+    ALLOC(img, mlp_image_bytes());
+    c->mlp_image = img;
+  }
 #undef ALLOC
   s.bunches = c->d_bunches;
   s.sched = c->d_sched;
   s.bunch_of = c->d_bunch_of;
+  s.mlp_image = c->mlp_image;
   e = cudaMemcpyAsync(c->d_bunch_of, bunch_of.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_bunches, c->hb.data(), sizeof(BunchDesc) * nbunch, cudaMemcpyHostToDevice, c->stream);
@@ -645,6 +659,8 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
   if (nsteps < 0) return fail(EMPPP_ERR_ARG, "nsteps must be >= 0");
   BextParams bp;
   if ((st = convert_bext(bext, &bp)) != EMPPP_OK) return st;
+  if (h->opt.proposal == EMPPP_PROPOSAL_MLP && h->opt.pair_fields && !h->has_mlp)
+    return fail(EMPPP_ERR_STATE, "the MLP proposal needs a network: call emppp_set_proposal first");
   if ((st = update_schedule(h)) != EMPPP_OK) return st;
   const bool use_graph = h->opt.graphs && !h->opt.timing && h->stream != nullptr && nsteps > 1;
   if (use_graph && (st = capture_step(h, bp)) != EMPPP_OK) return st;
@@ -792,6 +808,274 @@ EMPPP_API emppp_status emppp_reset_stats(emppp_handle h) {
   emppp_status st = check_handle(h);
   if (st != EMPPP_OK) return st;
   return reset_counters(h);
+}
+
+// one evaluation of the self fields of the present state: slot tables, target order, pair kernel,
+// reduction (no push: the state does not change)
+emppp_status enqueue_fields(emppp_handle h) {
+  CU(launch_prep(h->ds, h->stream));
+  const bool ordered = h->opt.precision == EMPPP_MIXED && h->target_order;
+  if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->stream));
+  if (h->opt.precision == EMPPP_MIXED)
+    CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->launch, h->stream));
+  else
+    CU(launch_pair_fp64(h->ds, h->opt.proposal, h->launch, h->stream));
+  if (any_chunked(h)) CU(launch_reduce_partials(h->ds, h->stream));
+  h->launches += 3 + (ordered ? 1 : 0);
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* report) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if (!h->opt.pair_fields) return fail(EMPPP_ERR_STATE, "pair fields are off: nothing to tune");
+  if (h->opt.proposal == EMPPP_PROPOSAL_MLP && !h->has_mlp)
+    return fail(EMPPP_ERR_STATE, "the MLP proposal needs a network: call emppp_set_proposal first");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  const int ipb[5] = {4, 8, 16, 32, 64};
+  const int norders = h->opt.precision == EMPPP_MIXED ? 2 : 1;
+  emppp_tuning_report rep;
+  memset(&rep, 0, sizeof(rep));
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  double best_ms = 1e300;
+  for (int o = 0; o < norders; o++) {
+    for (int k = 0; k < 5; k++) {
+      h->items_per_block = ipb[k];
+      h->target_order = 1 - o;
+      if ((st = update_schedule(h)) != EMPPP_OK) break;
+      if ((st = enqueue_fields(h)) != EMPPP_OK) break;  // warm-up
+      float best = 3.4e38f;
+      for (int rpt = 0; rpt < 2 && st == EMPPP_OK; rpt++) {
+        cudaEventRecord(e0, h->stream);
+        st = enqueue_fields(h);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) best = ms;
+      }
+      if (st != EMPPP_OK) break;
+      emppp_tuning& c = rep.cand[rep.ncand];
+      c.items_per_block = ipb[k];
+      c.target_order = 1 - o;
+      c.ms = best;
+      if (best < best_ms) {
+        best_ms = best;
+        rep.best = rep.ncand;
+      }
+      rep.ncand++;
+    }
+    if (st != EMPPP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != EMPPP_OK) return st;
+  h->items_per_block = rep.cand[rep.best].items_per_block;
+  h->target_order = rep.cand[rep.best].target_order;
+  invalidate_graph(h);
+  if ((st = update_schedule(h)) != EMPPP_OK) return st;
+  if ((st = reset_counters(h)) != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  if (report) *report = rep;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!tuning || tuning->items_per_block < 1 || tuning->items_per_block > 256 ||
+      (tuning->target_order != 0 && tuning->target_order != 1))
+    return fail(EMPPP_ERR_ARG, "items_per_block must be in 1..256 and target_order 0 or 1");
+  h->items_per_block = tuning->items_per_block;
+  h->target_order = tuning->target_order;
+  invalidate_graph(h);
+  return update_schedule(h);
+}
+
+// ---- learned proposal ------------------------------------------------------------------------
+EMPPP_API emppp_status emppp_sample_delays(emppp_handle h, const int32_t* pairs, int64_t m, float* features,
+                                           double* delays, float* targets, int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if (m < 0 || (m > 0 && (!pairs || !features || !delays || !targets))) return fail(EMPPP_ERR_ARG, "bad arguments");
+  if (m == 0) return EMPPP_OK;
+  std::vector<int32_t> hp;
+  const int32_t* pp = pairs;
+  if (!is_device_ptr) {
+    hp.assign(pairs, pairs + 2 * m);
+  } else {
+    hp.resize((size_t)(2 * m));
+    CU(cudaMemcpyAsync(hp.data(), pairs, sizeof(int32_t) * 2 * m, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  for (int64_t k = 0; k < m; k++) {
+    const int32_t i = hp[2 * k], j = hp[2 * k + 1];
+    if (i < 0 || j < 0 || i >= h->N || j >= h->N || i == j)
+      return fail(EMPPP_ERR_ARG, "pair %lld = (%d, %d) is not two different particles", (long long)k, i, j);
+  }
+  // device buffers for this call (one-off training-data generation, not the step path)
+  void *dp = nullptr, *df = nullptr, *dd = nullptr, *dz = nullptr;
+  auto cleanup = [&]() {
+    if (!is_device_ptr) {
+      cudaFree(dp);
+      cudaFree(df);
+      cudaFree(dd);
+      cudaFree(dz);
+    }
+  };
+  if (!is_device_ptr) {
+    if (cudaMalloc(&dp, sizeof(int32_t) * 2 * m) != cudaSuccess || cudaMalloc(&df, sizeof(float) * 10 * m) != cudaSuccess ||
+        cudaMalloc(&dd, sizeof(double) * m) != cudaSuccess || cudaMalloc(&dz, sizeof(float) * m) != cudaSuccess) {
+      cudaGetLastError();
+      cleanup();
+      return fail(EMPPP_ERR_OOM, "device buffers for %lld samples", (long long)m);
+    }
+    cudaMemcpyAsync(dp, hp.data(), sizeof(int32_t) * 2 * m, cudaMemcpyHostToDevice, h->stream);
+    pp = static_cast<int32_t*>(dp);
+  } else {
+    df = features;
+    dd = delays;
+    dz = targets;
+  }
+  cudaError_t e = launch_prep(h->ds, h->stream);
+  if (e == cudaSuccess)
+    e = launch_sample(h->ds, pp, m, static_cast<float*>(df), static_cast<double*>(dd), static_cast<float*>(dz),
+                      h->stream);
+  if (e == cudaSuccess && !is_device_ptr) {
+    e = cudaMemcpyAsync(features, df, sizeof(float) * 10 * m, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(delays, dd, sizeof(double) * m, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(targets, dz, sizeof(float) * m, cudaMemcpyDeviceToHost, h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cleanup();
+  h->launches += 2;
+  if (e != cudaSuccess) return fail(EMPPP_ERR_CUDA, "sampling: %s", cudaGetErrorString(e));
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, int32_t is_device_ptr) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!params) return fail(EMPPP_ERR_ARG, "params is NULL");
+  float* dparams = nullptr;
+  if (cudaMalloc(&dparams, sizeof(float) * EMPPP_MLP_NUM_PARAMS) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EMPPP_ERR_OOM, "parameter buffer");
+  }
+  cudaError_t e = cudaMemcpyAsync(dparams, params, sizeof(float) * EMPPP_MLP_NUM_PARAMS,
+                                  is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = launch_build_image(dparams, h->mlp_image, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  cudaFree(dparams);
+  if (e != cudaSuccess) return fail(EMPPP_ERR_CUDA, "set_proposal: %s", cudaGetErrorString(e));
+  h->has_mlp = true;
+  h->launches += 1;
+  return EMPPP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// temporary device buffers of the handle-free network calls
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  bool alloc(size_t n) {
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    return true;
+  }
+};
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+EMPPP_API emppp_status emppp_mlp_forward(const float* params, const float* features, int64_t m, float* z,
+                                         void* cuda_stream) {
+  if (!params || !features || !z || m < 0) return fail(EMPPP_ERR_ARG, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DevBuf img;
+  if (!img.alloc(mlp_image_bytes())) return fail(EMPPP_ERR_OOM, "network image");
+  CU(launch_build_image(params, img.p, s));
+  CU(launch_mlp_forward(img.p, features, m, z, s));
+  CU(cudaStreamSynchronize(s));
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_mlp_gradient(const float* params, const float* features, const float* targets,
+                                          int64_t m, float* grad, double* loss, void* cuda_stream) {
+  if (!params || !features || !targets || !grad || m < 1) return fail(EMPPP_ERR_ARG, "bad arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DevBuf img, dl;
+  if (!img.alloc(mlp_image_bytes()) || !dl.alloc(sizeof(float))) return fail(EMPPP_ERR_OOM, "network buffers");
+  CU(launch_build_image(params, img.p, s));
+  CU(cudaMemsetAsync(grad, 0, sizeof(float) * EMPPP_MLP_NUM_PARAMS, s));
+  CU(cudaMemsetAsync(dl.p, 0, sizeof(float), s));
+  CU(launch_mlp_train_pass(img.p, features, targets, 0, m, (float)m, grad, static_cast<float*>(dl.p), device_sms(), s));
+  float hl = 0.f;
+  CU(cudaMemcpyAsync(&hl, dl.p, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (loss) *loss = (double)hl / (double)m;
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_mlp_train(float* params, const float* features, const float* targets, int64_t m,
+                                       const emppp_mlp_config* cfg, float* loss_per_epoch, void* cuda_stream) {
+  if (!params || !features || !targets || !cfg || m < 1) return fail(EMPPP_ERR_ARG, "bad arguments");
+  if (cfg->epochs < 0 || cfg->batch < 16 || !(cfg->lr > 0.f)) return fail(EMPPP_ERR_ARG, "bad training config");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  DevBuf img, grad, m1, m2, dl;
+  const size_t P = sizeof(float) * EMPPP_MLP_NUM_PARAMS;
+  if (!img.alloc(mlp_image_bytes()) || !grad.alloc(P) || !m1.alloc(P) || !m2.alloc(P) || !dl.alloc(sizeof(float)))
+    return fail(EMPPP_ERR_OOM, "training buffers");
+  CU(cudaMemsetAsync(m1.p, 0, P, s));
+  CU(cudaMemsetAsync(m2.p, 0, P, s));
+  const int sms = device_sms();
+  int step = 0;
+  const long long batches = (m + cfg->batch - 1) / cfg->batch;
+  const long long total = batches * cfg->epochs;
+  const bool decay = cfg->lr_final > 0.f && cfg->lr_final < cfg->lr && total > 1;
+  for (int ep = 0; ep < cfg->epochs; ep++) {
+    CU(cudaMemsetAsync(dl.p, 0, sizeof(float), s));
+    for (int64_t r0 = 0; r0 < m; r0 += cfg->batch) {
+      const int64_t rows = (m - r0 < cfg->batch) ? m - r0 : cfg->batch;
+      CU(launch_build_image(params, img.p, s));
+      CU(cudaMemsetAsync(grad.p, 0, P, s));
+      CU(launch_mlp_train_pass(img.p, features, targets, r0, rows, (float)rows, static_cast<float*>(grad.p),
+                               static_cast<float*>(dl.p), sms, s));
+      // cosine schedule from lr (first step) to lr_final (last step)
+      const double frac = decay ? (double)step / (double)(total - 1) : 0.0;
+      const float lr = decay ? (float)(cfg->lr_final + 0.5 * (cfg->lr - cfg->lr_final) * (1.0 + cos(3.14159265358979323846 * frac)))
+                             : cfg->lr;
+      CU(launch_adam(params, static_cast<float*>(grad.p), static_cast<float*>(m1.p), static_cast<float*>(m2.p), lr,
+                     cfg->beta1, cfg->beta2, cfg->eps, ++step, s));
+    }
+    float hl = 0.f;
+    CU(cudaMemcpyAsync(&hl, dl.p, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (loss_per_epoch) loss_per_epoch[ep] = hl / (float)m;
+  }
+  CU(cudaStreamSynchronize(s));
+  return EMPPP_OK;
 }
 
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt) {

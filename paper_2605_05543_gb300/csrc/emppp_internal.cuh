@@ -110,6 +110,7 @@ struct DeviceState {
   unsigned long long* stats;  // [kStatCount]
   int* err;
   double* bsum;     // [nbunch][4] per-bunch reductions (weighted position sums and weight)
+  const void* mlp_image;  // BF16 image of the proposal network (EMPPP_PROPOSAL_MLP), or null
 };
 
 struct BextParams {
@@ -168,6 +169,16 @@ cudaError_t launch_transport_chunk(const DeviceState& s, const BextParams& b, do
 // order.cu
 cudaError_t prepare_target_order();
 cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, cudaStream_t st);
+// mlp.cu
+size_t mlp_image_bytes();
+cudaError_t launch_build_image(const float* params, void* image, cudaStream_t st);
+cudaError_t launch_sample(const DeviceState& s, const int* pairs, long long m, float* feat, double* delay, float* zt,
+                          cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* image, const float* X, long long m, float* z, cudaStream_t st);
+cudaError_t launch_mlp_train_pass(const void* image, const float* X, const float* T, long long row0, long long rows,
+                                  float norm, float* grad, float* loss, int num_sms, cudaStream_t st);
+cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float lr, float b1, float b2, float eps,
+                        int step, cudaStream_t st);
 // pair_mixed.cu
 int max_blocks_pair_mixed(int proposal);
 cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairLaunch& pl,

@@ -16,6 +16,7 @@
 // The arithmetic is FP64-pipe bound (GB300: 2 DFMA/clk/SM); everything that is not an FP64 result
 // (the guess, indices, loads) runs on the FP32/INT pipes beside it.
 #include "emppp_internal.cuh"
+#include "mlp.cuh"
 #include "shadow.cuh"
 
 namespace emppp {
@@ -46,6 +47,7 @@ struct PairArgs {
   const BunchSched* __restrict__ sched;
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
+  const mlp::NetImage* __restrict__ net;  // proposal network (EMPPP_PROPOSAL_MLP)
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -72,6 +74,9 @@ struct Window {
 template <int PROP>
 __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   __shared__ int s_item;
+  __shared__ mlp::NetImage s_net[PROP == kPropMlp ? 1 : 1];
+  __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
+  if (PROP == kPropMlp) mlp::load_image(s_net[0], a.net);
   const long long N = a.N;
   const int D = a.D;
 
@@ -82,7 +87,9 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   win.D = D;
   const int pn = a.state->pn;
   const double t = a.state->t;
-  const float inv_cdt = PROP == kPropClosedForm ? (float)(1.0 / (kC * a.state->dt)) : 0.f;
+  const float inv_cdt = PROP != kPropBisect ? (float)(1.0 / (kC * a.state->dt)) : 0.f;
+  const float invL = (float)(1.0 / (kC * a.state->dt * D));
+  const int pprev = win.n > win.k0 ? win.phys(win.n - 1) : pn;  // slot n - 1 (or n)
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
   int errbits = 0;
@@ -107,7 +114,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
   float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f;
-  if (PROP == kPropClosedForm) {
+  if (PROP != kPropBisect) {
     const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
     rh0 = q[0];
     rh1 = q[1];
@@ -122,7 +129,23 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   int in_block = 0;
 
   const double c2 = kC * kC;
-  for (long long j = j_begin; active && j < j_end; ++j) {
+  for (long long j = j_begin; (PROP == kPropMlp || active) && j < j_end; ++j) {
+    long long kg_mlp = 0;
+    if (PROP == kPropMlp) {
+      // every lane of the warp takes part in the tensor-core evaluation, then idle lanes skip the pair
+      const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
+      const float4 q0n = __ldg(qn), q2n = __ldg(qn + 2);
+      const float4 q2p = __ldg(reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pprev) * 12) + 2);
+      const float x0 = rh0 - q0n.x, x1 = rh1 - q0n.y, x2 = rh2 - q0n.z;
+      float f[mlp::kIn];
+      mlp::features(x0, x1, x2, bref.x + q2n.x, bref.y + q2n.y, bref.z + q2n.z, q2n.x - q2p.x, q2n.y - q2p.y,
+                    q2n.z - q2p.z, invL, (float)D, f);
+      const float z = mlp::infer_warp(s_net[0], f, s_stage[threadIdx.x >> 5]);
+      const float steps = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 1e9f);
+      long long k = win.n - 1 - (long long)steps;
+      kg_mlp = k < win.k0 ? win.k0 : (k > win.n - 1 ? win.n - 1 : k);
+    }
+    if (!active) continue;  // and stay in the loop for the next source's evaluation
     if (j == i) continue;
     const double* src = a.rec64 + (size_t)j * D * 6;
     // ---- 1. bracket ------------------------------------------------------------------------
@@ -161,8 +184,13 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
         br = 0;
         n_tests += 1;
       } else {
-        const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
-        const long long kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), bref, inv_cdt, win.k0, win.n);
+        long long kg;
+        if (PROP == kPropMlp) {
+          kg = kg_mlp;
+        } else {
+          const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
+          kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), bref, inv_cdt, win.k0, win.n);
+        }
         long long lo, hi;
         bool ooh = false;
         n_tests += 1;
@@ -362,6 +390,8 @@ int max_blocks_pair_fp64(int proposal) {
   int nb = 0;
   if (proposal == kPropClosedForm)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm>, kBlock, 0);
+  else if (proposal == kPropMlp)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp>, kBlock, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect>, kBlock, 0);
   return nb > 0 ? nb : 1;
@@ -388,10 +418,13 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunc
   a.sched = s.sched;
   a.nitems = pl.nitems;
   a.work = s.work;
+  a.net = static_cast<const mlp::NetImage*>(s.mlp_image);
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)
     pair_fp64_kernel<kPropClosedForm><<<pl.grid, kBlock, 0, st>>>(a);
+  else if (proposal == kPropMlp)
+    pair_fp64_kernel<kPropMlp><<<pl.grid, kBlock, 0, st>>>(a);
   else
     pair_fp64_kernel<kPropBisect><<<pl.grid, kBlock, 0, st>>>(a);
   return cudaGetLastError();

@@ -26,6 +26,7 @@
 // memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
 // source are close together in the source-major FP32 shadow ring.
 #include "emppp_internal.cuh"
+#include "mlp.cuh"
 #include "shadow.cuh"
 
 namespace emppp {
@@ -63,6 +64,7 @@ struct MixedArgs {
   const BunchSched* __restrict__ sched;
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
+  const mlp::NetImage* __restrict__ net;  // proposal network (EMPPP_PROPOSAL_MLP)
 };
 
 struct Target {
@@ -98,6 +100,14 @@ __device__ __forceinline__ bool exact_test(const Target& r, const double* __rest
   const double d2 = __dsub_rn(r.r2, __ldg(w + 2));
   const double rhs = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
   return lhs <= rhs;
+}
+
+// a0 b0 + a1 b1 + a2 b2 and a0 b1 - a1 b0 in a fixed rounding sequence (no compiler contraction)
+__device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return __fmaf_rn(a2, b2, __fmaf_rn(a1, b1, __fmul_rn(a0, b0)));
+}
+__device__ __forceinline__ float cross1(float a0, float a1, float b0, float b1) {
+  return __fmaf_rn(a0, b1, -__fmul_rn(a1, b0));
 }
 
 // r - w of a record, from the hi and lo parts (each component exact to two roundings)
@@ -144,10 +154,14 @@ __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict_
 }  // namespace
 
 template <int PROP>
-__global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
+__global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
+  __shared__ float4 s_db[PROP == kPropMlp ? kTile : 1];  // beta_n - beta_{n-1} of the tile's sources
+  __shared__ mlp::NetImage s_net[1];
+  __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
+  if (PROP == kPropMlp) mlp::load_image(s_net[0], a.net);
 
   __shared__ int s_item;
   const int N = a.N;
@@ -161,6 +175,8 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
   win.nw = (int)(n_abs - k0_abs) + 1;
   const int pn = a.state->pn;
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
+  const int pprev = win.nw > 1 ? win.phys(win.nw - 2) : pn;  // slot n - 1 (or n)
+  const float invL = (float)(1.0 / (kC * a.state->dt * D));
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   int errbits = 0;
@@ -216,13 +232,28 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
       const float4 q2 = q[2];
       s_q2[threadIdx.x] = make_float4(bref0 + q2.x, bref1 + q2.y, bref2 + q2.z, q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
+      if (PROP == kPropMlp) {
+        const float4 q2p = a.rec32[((size_t)j * D + pprev) * 3 + 2];
+        s_db[threadIdx.x] = make_float4(q2.x - q2p.x, q2.y - q2p.y, q2.z - q2p.z, 0.f);
+      }
     }
     __syncthreads();
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
-      for (int jj = jj0; active && jj < jend; ++jj) {
+      for (int jj = jj0; (PROP == kPropMlp || active) && jj < jend; ++jj) {
         const int j = tile + jj;
+        float steps_mlp = 0.f;
+        if (PROP == kPropMlp) {
+          // every lane of the warp takes part in the tensor-core evaluation, then idle lanes skip the pair
+          const float4 g0 = s_q0[jj], g2 = s_q2[jj], gd = s_db[jj];
+          const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
+          float f[mlp::kIn];
+          mlp::features(x0, x1, x2, g2.x, g2.y, g2.z, gd.x, gd.y, gd.z, invL, (float)D, f);
+          const float z = mlp::infer_warp(s_net[0], f, s_stage[threadIdx.x >> 5]);
+          steps_mlp = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 2.0e9f);
+        }
+        if (!active) continue;  // and stay in the loop for the next source's evaluation
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
@@ -261,14 +292,19 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
             fast = (l1 == 0);
           }
         } else {
-          // uniform-motion guess of the older node from the staged present record of the source
-          const float4 g0 = s_q0[jj], g2 = s_q2[jj];
-          const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
-          const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
-          const float dd = x0 * x0 + x1 * x1 + x2 * x2;
-          const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
-          const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
-          const float steps = fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
+          float steps;
+          if (PROP == kPropMlp) {
+            steps = steps_mlp;
+          } else {
+            // uniform-motion guess of the older node from the staged present record of the source
+            const float4 g0 = s_q0[jj], g2 = s_q2[jj];
+            const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
+            const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
+            const float dd = x0 * x0 + x1 * x1 + x2 * x2;
+            const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
+            const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
+            steps = fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
+          }
           // offset of the guessed older node: (nw - 2) - steps; below 0 means "older than the history"
           const int lraw = (steps > (float)(win.nw - 2)) ? -1 : (win.nw - 2) - (int)steps;
           const int lg = max(lraw, 0);
@@ -375,65 +411,70 @@ __global__ void __launch_bounds__(kBlock, EMPPP_MIXED_MIN_BLOCKS) pair_mixed_ker
           n_bi++;
 
         // ---- retarded state (light units) --------------------------------------------------------
+        // Written with explicit round-to-nearest intrinsics: the compiler may not fuse or regroup any
+        // of it, so every search variant (whose own arithmetic shares subexpressions with this code
+        // in different ways) computes the same fields from the same bracket, bit for bit.
         const int p1 = win.phys(l1);
         const float d0 = dA.x, d1 = dA.y, d2 = dA.z;
         const float L1 = __ldg(a.ct32 + p1);
-        const float b10 = bref0 + A.q2.x, b11 = bref1 + A.q2.y, b12 = bref2 + A.q2.z;
+        const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
         const float ig2 = A.q0.w, g2 = A.q2.w;
-        const float hb = (d0 * b10 + d1 * b11 + d2 * b12) - L1;
-        const float C0 = fmaf(L1, L1, -(d0 * d0 + d1 * d1 + d2 * d2));
-        const float qd = fmaf(hb, hb, -ig2 * C0);
-        const float sq = qd * rsqrtf(fmaxf(qd, 1e-37f));
-        const float s = (hb <= 0.f) ? __fdividef(C0, sq - hb) : -(hb + sq) * g2;
-        const float e0 = fmaf(-b10, s, d0), e1 = fmaf(-b11, s, d1), e2 = fmaf(-b12, s, d2);
+        const float hb = __fsub_rn(dot3(d0, d1, d2, b10, b11, b12), L1);
+        const float C0 = __fmaf_rn(L1, L1, -dot3(d0, d1, d2, d0, d1, d2));
+        const float qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
+        const float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
+        const float s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
+        const float e0 = __fmaf_rn(-b10, s, d0), e1 = __fmaf_rn(-b11, s, d1), e2 = __fmaf_rn(-b12, s, d2);
         float be0 = b10, be1 = b11, be2 = b12, al0 = 0.f, al1 = 0.f, al2 = 0.f, ug = ig2;
         if (br != 0) {
           if (!have_b) q2b = __ldg(src32 + 3 * win.phys(l1 + 1) + 2);
           const float icdt = __ldg(a.icdt32 + p1);
-          const float db0 = q2b.x - A.q2.x, db1 = q2b.y - A.q2.y, db2 = q2b.z - A.q2.z;
-          al0 = db0 * icdt;
-          al1 = db1 * icdt;
-          al2 = db2 * icdt;
-          const float df = s * icdt;
-          const float x0 = db0 * df, x1 = db1 * df, x2 = db2 * df;
-          be0 = b10 + x0;
-          be1 = b11 + x1;
-          be2 = b12 + x2;
-          ug = ig2 - (x0 * (2.f * b10 + x0) + x1 * (2.f * b11 + x1) + x2 * (2.f * b12 + x2));
+          const float db0 = __fsub_rn(q2b.x, A.q2.x), db1 = __fsub_rn(q2b.y, A.q2.y), db2 = __fsub_rn(q2b.z, A.q2.z);
+          al0 = __fmul_rn(db0, icdt);
+          al1 = __fmul_rn(db1, icdt);
+          al2 = __fmul_rn(db2, icdt);
+          const float df = __fmul_rn(s, icdt);
+          const float x0 = __fmul_rn(db0, df), x1 = __fmul_rn(db1, df), x2 = __fmul_rn(db2, df);
+          be0 = __fadd_rn(b10, x0);
+          be1 = __fadd_rn(b11, x1);
+          be2 = __fadd_rn(b12, x2);
+          // 1 - beta^2 = (1 - beta1^2) - x.(2 beta1 + x)
+          ug = __fsub_rn(ig2, dot3(x0, x1, x2, __fmaf_rn(2.f, b10, x0), __fmaf_rn(2.f, b11, x1),
+                                   __fmaf_rn(2.f, b12, x2)));
         }
         // ---- Lienard-Wiechert fields ---------------------------------------------------------------
-        const float R2 = e0 * e0 + e1 * e1 + e2 * e2;
+        const float R2 = dot3(e0, e1, e2, e0, e1, e2);
         const float invR = rsqrtf(R2);
-        const float R = R2 * invR;
-        const float n0 = e0 * invR, n1 = e1 * invR, n2 = e2 * invR;
-        const float u0 = n0 - be0, u1 = n1 - be1, u2 = n2 - be2;
-        const float eb = e0 * be0 + e1 * be1 + e2 * be2;
+        const float R = __fmul_rn(R2, invR);
+        const float n0 = __fmul_rn(e0, invR), n1 = __fmul_rn(e1, invR), n2 = __fmul_rn(e2, invR);
+        const float u0 = __fsub_rn(n0, be0), u1 = __fsub_rn(n1, be1), u2 = __fsub_rn(n2, be2);
+        const float eb = dot3(e0, e1, e2, be0, be1, be2);
         // 1 / (eta . u'): R - eta.beta directly when eta.beta <= 0, else the rationalised form
-        const float xb0 = e1 * be2 - e2 * be1, xb1 = e2 * be0 - e0 * be2, xb2 = e0 * be1 - e1 * be0;
-        const float rat = fmaf(R2, ug, xb0 * xb0 + xb1 * xb1 + xb2 * xb2);
+        const float xb0 = cross1(e1, e2, be1, be2), xb1 = cross1(e2, e0, be2, be0), xb2 = cross1(e0, e1, be0, be1);
+        const float rat = __fmaf_rn(R2, ug, dot3(xb0, xb1, xb2, xb0, xb1, xb2));
         const bool fw = eb > 0.f;
-        const float ieu = __fdividef(fw ? (R + eb) : 1.f, fw ? rat : (R - eb));
+        const float ieu = __fdividef(fw ? __fadd_rn(R, eb) : 1.f, fw ? rat : __fsub_rn(R, eb));
         const bool root_ok = (qd >= 0.f) && (ig2 > 0.f);
         if (!(root_ok && R2 > 0.f && ieu > 0.f && ieu < 3.0e38f)) {
           errbits |= root_ok ? kErrCoincide : kErrDisc;
           continue;
         }
-        const float pref = s_kq[jj] * (R * ieu) * ieu * ieu;
-        float F0 = ug * u0, F1 = ug * u1, F2 = ug * u2;
+        const float pref = __fmul_rn(__fmul_rn(__fmul_rn(s_kq[jj], __fmul_rn(R, ieu)), ieu), ieu);
+        float F0 = __fmul_rn(ug, u0), F1 = __fmul_rn(ug, u1), F2 = __fmul_rn(ug, u2);
         if (br != 0) {
           // eta x (u' x alpha)
-          const float c0 = u1 * al2 - u2 * al1, c1 = u2 * al0 - u0 * al2, c2 = u0 * al1 - u1 * al0;
-          F0 += e1 * c2 - e2 * c1;
-          F1 += e2 * c0 - e0 * c2;
-          F2 += e0 * c1 - e1 * c0;
+          const float c0 = cross1(u1, u2, al1, al2), c1 = cross1(u2, u0, al2, al0), c2 = cross1(u0, u1, al0, al1);
+          F0 = __fadd_rn(F0, cross1(e1, e2, c1, c2));
+          F1 = __fadd_rn(F1, cross1(e2, e0, c2, c0));
+          F2 = __fadd_rn(F2, cross1(e0, e1, c0, c1));
         }
-        const float E0 = pref * F0, E1 = pref * F1, E2 = pref * F2;
-        P[0] += E0;
-        P[1] += E1;
-        P[2] += E2;
-        P[3] += (n1 * E2 - n2 * E1) * ic;
-        P[4] += (n2 * E0 - n0 * E2) * ic;
-        P[5] += (n0 * E1 - n1 * E0) * ic;
+        const float E0 = __fmul_rn(pref, F0), E1 = __fmul_rn(pref, F1), E2 = __fmul_rn(pref, F2);
+        P[0] = __fadd_rn(P[0], E0);
+        P[1] = __fadd_rn(P[1], E1);
+        P[2] = __fadd_rn(P[2], E2);
+        P[3] = __fadd_rn(P[3], __fmul_rn(cross1(n1, n2, E1, E2), ic));
+        P[4] = __fadd_rn(P[4], __fmul_rn(cross1(n2, n0, E2, E0), ic));
+        P[5] = __fadd_rn(P[5], __fmul_rn(cross1(n0, n1, E0, E1), ic));
       }
       // Kahan-add the partial sums of these kSub sources
 #pragma unroll
@@ -489,6 +530,8 @@ int max_blocks_pair_mixed(int proposal) {
   int nb = 0;
   if (proposal == kPropClosedForm)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropClosedForm>, kBlock, 0);
+  else if (proposal == kPropMlp)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropMlp>, kBlock, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropBisect>, kBlock, 0);
   return nb > 0 ? nb : 1;
@@ -518,10 +561,13 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.sched = s.sched;
   a.nitems = pl.nitems;
   a.work = s.work;
+  a.net = static_cast<const mlp::NetImage*>(s.mlp_image);
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)
     pair_mixed_kernel<kPropClosedForm><<<pl.grid, kBlock, 0, st>>>(a);
+  else if (proposal == kPropMlp)
+    pair_mixed_kernel<kPropMlp><<<pl.grid, kBlock, 0, st>>>(a);
   else
     pair_mixed_kernel<kPropBisect><<<pl.grid, kBlock, 0, st>>>(a);
   return cudaGetLastError();

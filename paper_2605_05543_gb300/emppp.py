@@ -42,6 +42,23 @@ class Bext(ctypes.Structure):
                 ("m0", ctypes.c_double), ("center", ctypes.c_double * 3)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("items_per_block", ctypes.c_int32), ("target_order", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+
+class TuningReport(ctypes.Structure):
+    _fields_ = [("ncand", ctypes.c_int32), ("best", ctypes.c_int32), ("cand", Tuning * 16)]
+
+
+class MlpConfig(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("lr_final", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+MLP_NUM_PARAMS = 4929
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("pairs", ctypes.c_int64), ("out_of_history", ctypes.c_int64),
                 ("shortcut", ctypes.c_int64), ("bisection", ctypes.c_int64), ("node_tests", ctypes.c_int64),
@@ -74,9 +91,16 @@ SIGNATURES = {
     "emppp_get_stats": (ctypes.c_int, [_H, ctypes.POINTER(Stats)]),
     "emppp_reset_stats": (ctypes.c_int, [_H]),
     "emppp_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
+    "emppp_autotune": (ctypes.c_int, [_H, ctypes.POINTER(TuningReport)]),
+    "emppp_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
     "emppp_set_stream": (ctypes.c_int, [_H, _vp]),
     "emppp_synchronize": (ctypes.c_int, [_H]),
     "emppp_fields_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "emppp_sample_delays": (ctypes.c_int, [_H, _vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32]),
+    "emppp_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "emppp_mlp_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
+    "emppp_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(MlpConfig), _vp, _vp]),
+    "emppp_set_proposal": (ctypes.c_int, [_H, _vp, ctypes.c_int32]),
     "emppp_last_error": (ctypes.c_char_p, []),
     "emppp_version": (ctypes.c_char_p, []),
 }
@@ -316,8 +340,38 @@ class Solver:
     def reset_stats(self):
         _check(self.lib.emppp_reset_stats(self._h))
 
+    def autotune(self) -> dict:
+        """Time the candidate work splits on the present state and keep the fastest."""
+        r = TuningReport()
+        _check(self.lib.emppp_autotune(self._h, ctypes.byref(r)))
+        cands = [dict(items_per_block=r.cand[k].items_per_block, target_order=r.cand[k].target_order,
+                      ms=r.cand[k].ms) for k in range(r.ncand)]
+        return dict(best=cands[r.best], candidates=cands)
+
+    def set_tuning(self, items_per_block=16, target_order=1):
+        t = Tuning(items_per_block=int(items_per_block), target_order=int(target_order), ms=0.0)
+        _check(self.lib.emppp_set_tuning(self._h, ctypes.byref(t)))
+
     def synchronize(self):
         _check(self.lib.emppp_synchronize(self._h))
+
+    def sample_delays(self, pairs):
+        """Features [m, 10], exact delays t - t_r [m] and targets z [m] of (target, source) pairs."""
+        pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        m = pairs.shape[0]
+        feat = np.zeros((m, 10), dtype=np.float32)
+        delay = np.zeros(m)
+        z = np.zeros(m, dtype=np.float32)
+        _check(self.lib.emppp_sample_delays(self._h, pairs.ctypes.data, m, feat.ctypes.data, delay.ctypes.data,
+                                            z.ctypes.data, 0))
+        return feat, delay, z
+
+    def set_proposal(self, params):
+        """Network used by the "mlp" proposal (EMPPP_MLP_NUM_PARAMS float32 values)."""
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != MLP_NUM_PARAMS:
+            raise ValueError(f"expected {MLP_NUM_PARAMS} parameters")
+        _check(self.lib.emppp_set_proposal(self._h, p.ctypes.data, 0))
 
 
 def fields_noalloc(T, W, V, E, B, w=None, stream=None):
@@ -332,6 +386,53 @@ def fields_noalloc(T, W, V, E, B, w=None, stream=None):
         raise ValueError("fields_noalloc takes device (CUDA tensor) arrays only")
     pT, pW, pV, pw, pE, pB = (p for p, _ in ptrs)
     _check(load().emppp_fields_noalloc(n, nslots, pT, pW, pV, pw, pE, pB, _stream_handle(stream)))
+
+
+def _dev_f32(a):
+    import torch
+
+    if _is_torch(a):
+        return a.to(device="cuda", dtype=torch.float32).contiguous()
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def mlp_forward(params, features):
+    """z of the proposal network for features [m, 10] (host arrays or CUDA tensors); returns numpy."""
+    import torch
+
+    p, X = _dev_f32(params), _dev_f32(features)
+    m = X.shape[0]
+    z = torch.empty(m, dtype=torch.float32, device="cuda")
+    _check(load().emppp_mlp_forward(p.data_ptr(), X.data_ptr(), m, z.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream))
+    return z.cpu().numpy()
+
+
+def mlp_gradient(params, features, targets):
+    """(mean squared error, gradient [4929]) of one batch."""
+    import torch
+
+    p, X, T = _dev_f32(params), _dev_f32(features), _dev_f32(targets)
+    g = torch.empty(MLP_NUM_PARAMS, dtype=torch.float32, device="cuda")
+    loss = ctypes.c_double()
+    _check(load().emppp_mlp_gradient(p.data_ptr(), X.data_ptr(), T.data_ptr(), X.shape[0], g.data_ptr(),
+                                     ctypes.byref(loss), torch.cuda.current_stream().cuda_stream))
+    return loss.value, g.cpu().numpy()
+
+
+def mlp_train(params, features, targets, epochs=4, batch=4096, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+              lr_final=0.0):
+    """Adam training on the GPU (cosine step-size decay to lr_final when 0 < lr_final < lr); returns
+    (trained params as numpy float32, mean loss per epoch)."""
+    import torch
+
+    p, X, T = _dev_f32(params).clone(), _dev_f32(features), _dev_f32(targets)
+    cfg = MlpConfig(epochs=int(epochs), batch=int(batch), lr=float(lr), beta1=float(beta1), beta2=float(beta2),
+                    eps=float(eps), lr_final=float(lr_final))
+    losses = np.zeros(max(int(epochs), 1), dtype=np.float32)
+    _check(load().emppp_mlp_train(p.data_ptr(), X.data_ptr(), T.data_ptr(), X.shape[0], ctypes.byref(cfg),
+                                  losses.ctypes.data, torch.cuda.current_stream().cuda_stream))
+    return p.cpu().numpy(), losses[:int(epochs)]
 
 
 def version() -> str:

@@ -182,3 +182,22 @@ def batch_bunches(nbunch: int = 64, nmin: int = 512, nmax: int = 16384, smin: fl
         N = nmin + int(r[0] * (nmax - nmin + 1))
         out.append((min(N, nmax), smin + r[1] * (smax - smin), gmin + r[2] * (gmax - gmin), b))
     return out
+
+
+# ------------------------------------------------------------------------------------------------
+# Proposal network (10-64-64-1): seeded initial parameters
+# ------------------------------------------------------------------------------------------------
+MLP_IN, MLP_H = 10, 64
+MLP_NUM_PARAMS = MLP_IN * MLP_H + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Initial parameters, float32: W1 and W2 and w3 uniform in +-1/sqrt(fan in), biases zero, in the
+    layout W1[10][64], b1[64], W2[64][64], b2[64], w3[64], b3."""
+    u = uniforms(2000 + seed, MLP_IN * MLP_H + MLP_H * MLP_H + MLP_H)
+    k = MLP_IN * MLP_H
+    W1 = (2 * u[:k] - 1) / math.sqrt(MLP_IN)
+    W2 = (2 * u[k:k + MLP_H * MLP_H] - 1) / math.sqrt(MLP_H)
+    w3 = (2 * u[k + MLP_H * MLP_H:] - 1) / math.sqrt(MLP_H)
+    z = np.zeros(MLP_H)
+    return np.concatenate([W1, z, W2, z, w3, [0.0]]).astype(np.float32)

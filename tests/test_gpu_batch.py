@@ -194,3 +194,28 @@ def test_two_stage_pipeline_batched_equals_single():
         assert np.array_equal(xb[off:off + N], x1) and np.array_equal(ub[off:off + N], u1)
         off += N
     assert nb == 2020
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_state_and_results(precision):
+    from gpu_helpers import history_case, window
+
+    h = history_case(3000, 80, sigma=10e-6, seed=21)
+    T, W, V, u = window(h, 128)
+    with emppp.Solver(3000, 128, DT, precision=precision, proposal="closed_form") as s:
+        s.set_history(80, T, W, V, u)
+        rep = s.autotune()
+        _, _, t0, n0 = s.get_state()
+        assert n0 == 80 and len(rep["candidates"]) == (10 if precision == "mixed" else 5)
+        assert all(c["ms"] > 0 for c in rep["candidates"])
+        s.step(1)
+        Ea, Ba = s.get_fields()
+        s.set_history(80, T, W, V, u)
+        s.set_tuning(items_per_block=4, target_order=0)
+        s.step(1)
+        Eb, Bb = s.get_fields()
+    E_ref, B_ref, _, M = oracle.self_fields(h.T, h.W, h.V, 80, 128, mags=True)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for E, B in ((Ea, Ba), (Eb, Bb)):
+        eE, eB = field_errors(E, B, E_ref, B_ref, M)
+        assert eE <= tol and eB <= tol
