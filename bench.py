@@ -65,7 +65,11 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--proposal", choices=["bisect", "closed_form", "mlp"], default="closed_form")
-    ap.add_argument("--ablation", action="store_true", help="also time the other proposals on the same state")
+    ap.add_argument("--workload", choices=["bunch", "batch"], default="bunch",
+                    help="bunch: the N = 65536 bunch (default); batch: 64 bunches, stage 1 then stage 2")
+    ap.add_argument("--stage2-steps", type=int, default=100000, help="stage-2 steps of the batch workload")
+    ap.add_argument("--no-ablation", action="store_true",
+                    help="skip the other proposals (node tests per pair and ms/step on the same state)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -193,16 +197,22 @@ def workload(small=False, rank=0, args=None):
     return wl, h, win
 
 
-def kernel_traffic_record(path_name):
+def workload_name(wl):
+    if wl["N"] == WL["N"] and wl["n0"] == WL["n0"] and wl["depth"] == WL["depth"]:
+        return WORKLOAD_NAME
+    return f"reduced case N={wl['N']} depth={wl['depth']} history slots={wl['n0'] + 1}"
+
+
+def kernel_traffic_record(path_name, proposal):
     """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it was taken on the
-    kernel source as it is now (else None)."""
+    same kernel instance and on the kernel source as it is now (else None)."""
     rec = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     if not os.path.exists(rec):
         return None
     try:
         d = json.load(open(rec))
         ent = d.get(path_name)
-        if not ent:
+        if not ent or ent.get("proposal") != proposal:
             return None
         src = os.path.join(ROOT, "paper_2605_05543_gb300", "csrc", ent["source"])
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
@@ -350,9 +360,10 @@ def run_ours(args):
     warmup = max(args.warmup, 1)
     dev = torch.device("cuda", local)
     net, net_report = None, None
-    if args.proposal == "mlp":
+    if args.proposal == "mlp" or not args.no_ablation:
         net, net_report = train_proposal(wl, win, h.n)
-    res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e, net=net)
+    res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e,
+                   net=net if args.proposal == "mlp" else None)
     ms = max_over_ranks(res["ms"], dev)
     pairs_per_step = wl["N"] * (wl["N"] - 1)
     total_pairs = sum_over_ranks(pairs_per_step * steps, dev)
@@ -367,14 +378,13 @@ def run_ours(args):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.path == "fp64" else "f32+f64",
         "data": "synthetic (seeded Gaussian bunch and stored history; no dataset)",
-        "config": {"workload": WORKLOAD_NAME if wl["N"] == WL["N"] and wl["n0"] == WL["n0"] else
-                   f"reduced case N={wl['N']} depth={wl['depth']} history slots={wl['n0'] + 1}", "path": args.path, "proposal": args.proposal,
+        "config": {"workload": workload_name(wl), "path": args.path, "proposal": args.proposal,
                    "N": wl["N"], "history_depth": wl["depth"], "history_slots": wl["n0"] + 1, "dt": wl["dt"],
                    "pairs_per_step": pairs_per_step, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2: 0.79 GB of history window read per step (L2 129 MB)"},
         "roofline": {"bound": "alu", "kernel": "pair_fp64_kernel" if args.path == "fp64" else "pair_mixed_kernel",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic_record(args.path),
+                     "traffic": kernel_traffic_record(args.path, args.proposal),
                      "peak_note": ("FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz" if args.path == "fp64"
                                    else "FP32: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
                      "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1)},
@@ -385,7 +395,7 @@ def run_ours(args):
     }
     if net_report is not None:
         line["proposal_net"] = net_report
-    if args.proposal == "mlp" or args.ablation:
+    if not args.no_ablation:
         # the same state and path under each proposal: mean node tests per pair (identical brackets)
         abl = {}
         for prop in ("bisect", "closed_form", "mlp"):
@@ -395,9 +405,13 @@ def run_ours(args):
                 continue
             else:
                 r = run_path(args, args.path, prop, 2 if args.path == "fp64" else 5, 1, wl, h, win, rank, e2e=False,
-                             keep_fields=False, net=net if prop == "mlp" else None)
+                             keep_fields=True, net=net if prop == "mlp" else None)
             abl[prop] = {"node_tests_per_pair": r["stats"]["node_tests"] / max(r["stats"]["pairs"], 1),
-                         "ms_per_step": r["ms"]}
+                         "ms_per_step": r["ms"], "pairs_per_s": pairs_per_step / (r["ms"] / 1e3)}
+            if rank == 0 and "fields0" in r and "fields0" in res:
+                # same brackets, same arithmetic after them: the first step's fields agree bit for bit
+                abl[prop]["fields_identical_to_main_path"] = bool(
+                    np.array_equal(r["fields0"][0], res["fields0"][0]) and np.array_equal(r["fields0"][1], res["fields0"][1]))
         line["proposal_ablation"] = abl
     if "e2e" in res:
         e = res["e2e"]
@@ -413,11 +427,120 @@ def run_ours(args):
         line["fp64_plain_path"] = {"proposal": "bisect", "ms_per_step": ref_ms,
                                    "value": pairs_per_step * world / (ref_ms / 1e3), "unit": UNIT, "steps": 2}
         line["speedup_vs_fp64_plain"] = ref_ms / ms
+        for v in line.get("proposal_ablation", {}).values():
+            v["speedup_vs_fp64_plain"] = ref_ms / v["ms_per_step"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         E0, B0 = res.get("fields0", (None, None))
         line["cpu_baseline"], parity = cpu_baseline(h, wl, args.cpu_seconds, E0, B0)
         if parity:
             line["rel_field_err_vs_fp64_oracle"] = parity
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+BATCH_NAME = ("batched two-stage transport: 64 bunches, N ~ U[512, 16384], sigma ~ U[5, 50] um, gamma0 ~ U[2, 20]; "
+              "stage 1 self fields dt=1e-15s depth=1024 from t=0; stage 2 centred dipole (3.1e-5 T at 1 R_E) from "
+              "(-4 R_E, 0, 0), dt=1e-9s")
+
+
+def run_batch(args):
+    """The batched two-stage workload: 64 independent bunches in one handle (one persistent pair launch per
+    step, the step replayed from a CUDA graph, tiles from the autotuner), stage 1 from t = 0, the handoff
+    to 4 Earth radii, and stage-2 transport in the dipole field."""
+    import numpy as np
+    import torch
+
+    from paper_2605_05543_gb300 import emppp, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    dev = torch.device("cuda", local)
+    emppp.load(build_if_missing=True)
+    nb = 8 if args.small else 64
+    spec = inputs.batch_bunches(nb, nmax=2048 if args.small else 16384)
+    xs, us = [], []
+    for N, sigma, g0, seed in spec:
+        b = inputs.gaussian_bunch(N, sigma, g0, seed=seed + 1000 * rank)
+        xs.append(b.x)
+        us.append(b.u)
+    sizes = [x.shape[0] for x in xs]
+    X, U = np.concatenate(xs), np.concatenate(us)
+    pairs_per_step = sum(n * (n - 1) for n in sizes)
+    steps = args.steps if args.steps is not None else 100
+    s2_steps = args.stage2_steps
+    warmup = max(args.warmup, 1)
+    stream = torch.cuda.current_stream()
+    RE = inputs.R_EARTH
+    m0 = 3.1e-5 * 4 * math.pi * RE ** 3 / 1.25663706212e-6
+    with emppp.Solver(0, WL["depth"], WL["dt"], precision=args.path, proposal=args.proposal, stream=stream,
+                      graphs=True, bunches=sizes) as s:
+        s.set_particles(X, U)
+        s.step(warmup)
+        tune = s.autotune()
+        s.synchronize()
+        s.reset_stats()
+        barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1) / steps
+        st = s.stats()
+        # one step with the library's in-step events for the pair kernel's own duration
+        s.set_options(timing=True)
+        s.reset_stats()
+        s.step(2)
+        s.synchronize()
+        stt = s.stats()
+        s.set_options(timing=False)
+        # stage 2
+        s.handoff((-4 * RE, 0.0, 0.0))
+        torch.cuda.synchronize()
+        l0 = s.stats()["kernel_launches"]
+        e0.record(stream)
+        s.transport(s2_steps, 1e-9, emppp.bext_dipole(m0))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s2_ms = e0.elapsed_time(e1)
+        s2_launches = s.stats()["kernel_launches"] - l0
+    ms = max_over_ranks(ms, dev)
+    s2_ms = max_over_ranks(s2_ms, dev)
+    total_pairs = sum_over_ranks(pairs_per_step * steps, dev)
+    flops = algorithmic_flops(stt)
+    pair_ms = stt["pair_ms"] / max(stt["timed_steps"], 1)
+    achieved = flops / max(stt["timed_steps"], 1) / (pair_ms / 1e3) / 1e12
+    peak = PEAK_FP64_TFLOPS if args.path == "fp64" else PEAK_FP32_TFLOPS
+    npart = sum(sizes)
+    best = tune["best"]
+    line = {
+        "metric": METRIC, "value": total_pairs / (ms * steps / 1e3), "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.path == "fp64" else "f32+f64",
+        "data": "synthetic (seeded Gaussian bunches; no dataset)",
+        "config": {"workload": BATCH_NAME if not args.small else "reduced batch: 8 bunches, N <= 2048",
+                   "path": args.path, "proposal": args.proposal, "bunches": len(sizes), "particles": npart,
+                   "pairs_per_step": pairs_per_step, "stage1_steps_timed": steps,
+                   "stage1_first_step": warmup, "history_depth": WL["depth"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "stage-1 history windows grow from 1 slot (2 x 48 B x particles x slots; > L2 after ~1 step)"},
+        "roofline": {"bound": "alu", "kernel": "pair_fp64_kernel" if args.path == "fp64" else "pair_mixed_kernel",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "pair_kernel_ms": pair_ms, "flops_per_pair": flops / max(stt["pairs"], 1)},
+        "clocks": clocks,
+        "gpu_launches": st["kernel_launches"],
+        "autotune": {"items_per_block": best["items_per_block"], "target_order": best["target_order"],
+                     "candidates": len(tune["candidates"])},
+        "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
+        "stage2": {"particle_steps_per_s": npart * s2_steps * world / (s2_ms / 1e3), "steps": s2_steps,
+                   "ms": s2_ms, "particles": npart, "gpu_launches": s2_launches, "dt": 1e-9},
+    }
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -458,7 +581,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
             "warmup": warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Gaussian bunch and stored history)",
-            "config": {"workload": WORKLOAD_NAME, "path": "cpu oracle", "N": N, "history_depth": wl["depth"],
+            "config": {"workload": workload_name(wl), "path": "cpu oracle", "N": N, "history_depth": wl["depth"],
                        "parallelism": "host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
@@ -472,6 +595,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
     try:

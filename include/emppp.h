@@ -263,9 +263,12 @@ typedef struct {
 EMPPP_API emppp_status emppp_sample_delays(emppp_handle h, const int32_t* pairs, int64_t m, float* features,
                                            double* delays, float* targets, int32_t is_device_ptr);
 
-/* z [m] of the network with parameters params for features [m][10]. Device pointers; synchronous. */
+/* z [m] of the network with parameters params for features [m][10]. mode 0: the reference form that
+ * training differentiates (FP32 SiLU, BF16 GEMM operands); mode 1: the inference form the pair kernels
+ * evaluate (hidden layers scaled by 1/2, SiLU on packed BF16 pairs via tanh, output layer on the tensor
+ * cores). Device pointers; synchronous. */
 EMPPP_API emppp_status emppp_mlp_forward(const float* params, const float* features, int64_t m, float* z,
-                                         void* cuda_stream);
+                                         int32_t mode, void* cuda_stream);
 
 /* Loss sum_r (z_r - targets_r)^2 / m and its gradient grad [EMPPP_MLP_NUM_PARAMS] for one batch of m
  * rows. Device pointers (loss on the host); synchronous. */

@@ -148,7 +148,14 @@ emppp_status update_schedule(emppp_handle c) {
   if (key == c->sched_key) return EMPPP_OK;
   int& nb = mixed ? c->blocks_mixed[c->opt.proposal % 3] : c->blocks_fp64[c->opt.proposal % 3];
   if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal) : max_blocks_pair_fp64(c->opt.proposal);
+  // The source chunking (and with it the order of every target's sum) follows the closed-form
+  // variant's residency whatever the proposal, so that all proposals give identical fields; only the
+  // number of persistent blocks follows the variant that runs.
+  int& nref = mixed ? c->blocks_mixed[EMPPP_PROPOSAL_CLOSED_FORM] : c->blocks_fp64[EMPPP_PROPOSAL_CLOSED_FORM];
+  if (nref <= 0)
+    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM) : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM);
   const long long R = (long long)nb * c->num_sms;
+  const long long Rsched = (long long)nref * c->num_sms;
   long long total_tiles = 0;
   for (int b = 0; b < c->nbunch; b++) total_tiles += (c->hb[b].n + 127) / 128;
   int item = 0;
@@ -160,7 +167,7 @@ emppp_status update_schedule(emppp_handle c) {
     if (c->opt.source_split > 0) {
       nchunk = c->opt.source_split;
     } else {
-      nchunk = ((long long)c->items_per_block * R + total_tiles - 1) / total_tiles;
+      nchunk = ((long long)c->items_per_block * Rsched + total_tiles - 1) / total_tiles;
       const long long by_size = (n + 255) / 256;
       if (nchunk > by_size) nchunk = by_size;
     }
@@ -1010,13 +1017,13 @@ int device_sms() {
 extern "C" {
 
 EMPPP_API emppp_status emppp_mlp_forward(const float* params, const float* features, int64_t m, float* z,
-                                         void* cuda_stream) {
-  if (!params || !features || !z || m < 0) return fail(EMPPP_ERR_ARG, "bad arguments");
+                                         int32_t mode, void* cuda_stream) {
+  if (!params || !features || !z || m < 0 || mode < 0 || mode > 1) return fail(EMPPP_ERR_ARG, "bad arguments");
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   DevBuf img;
   if (!img.alloc(mlp_image_bytes())) return fail(EMPPP_ERR_OOM, "network image");
   CU(launch_build_image(params, img.p, s));
-  CU(launch_mlp_forward(img.p, features, m, z, s));
+  CU(launch_mlp_forward(img.p, features, m, z, mode, s));
   CU(cudaStreamSynchronize(s));
   return EMPPP_OK;
 }

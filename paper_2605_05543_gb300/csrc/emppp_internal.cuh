@@ -174,7 +174,7 @@ size_t mlp_image_bytes();
 cudaError_t launch_build_image(const float* params, void* image, cudaStream_t st);
 cudaError_t launch_sample(const DeviceState& s, const int* pairs, long long m, float* feat, double* delay, float* zt,
                           cudaStream_t st);
-cudaError_t launch_mlp_forward(const void* image, const float* X, long long m, float* z, cudaStream_t st);
+cudaError_t launch_mlp_forward(const void* image, const float* X, long long m, float* z, int mode, cudaStream_t st);
 cudaError_t launch_mlp_train_pass(const void* image, const float* X, const float* T, long long row0, long long rows,
                                   float norm, float* grad, float* loss, int num_sms, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float lr, float b1, float b2, float eps,

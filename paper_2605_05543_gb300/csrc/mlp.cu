@@ -34,8 +34,37 @@ constexpr int kWarps = 4;  // warps per training block
 // ---------------------------------------------------------------------------------------------
 // network image
 // ---------------------------------------------------------------------------------------------
-__global__ void build_image_kernel(const float* __restrict__ p, NetImage* __restrict__ img) {
+__global__ void build_image_kernel(const float* __restrict__ p, void* __restrict__ image) {
+  NetImage* __restrict__ img = static_cast<NetImage*>(image);
+  InferImage* __restrict__ inf = reinterpret_cast<InferImage*>(static_cast<char*>(image) + sizeof(NetImage));
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  // inference image: halved hidden layers, lane-major B fragments (mlp.cuh)
+  auto w1h = [&](int f, int n) { return f < kIn ? 0.5f * p[kOffW1 + f * kH + n] : 0.f; };
+  auto w2h = [&](int i, int o) { return 0.5f * p[kOffW2 + i * kH + o]; };
+  if (k < (kH / 8) * 32) {
+    const int nt = k / 32, lane = k % 32, g = lane >> 2, t = lane & 3, n = 8 * nt + g;
+    inf->w1[nt][lane] = make_uint2(pack_bf16x2(w1h(2 * t, n), w1h(2 * t + 1, n)),
+                                   pack_bf16x2(w1h(2 * t + 8, n), w1h(2 * t + 9, n)));
+  }
+  if (k < (kH / 8) * (kH / 16) * 32) {
+    const int nt = k / 128, kk = (k / 32) % 4, lane = k % 32, g = lane >> 2, t = lane & 3;
+    const int n = 8 * nt + g, ki = 16 * kk + 2 * t;
+    inf->w2[nt][kk][lane] = make_uint2(pack_bf16x2(w2h(ki, n), w2h(ki + 1, n)), pack_bf16x2(w2h(ki + 8, n), w2h(ki + 9, n)));
+  }
+  if (k < (kH / 8) * 4) {
+    const int nt = k / 4, t = k % 4, o = 8 * nt + 2 * t;
+    inf->b1[nt][t] = make_float2(0.5f * p[kOffB1 + o], 0.5f * p[kOffB1 + o + 1]);
+    inf->b2[nt][t] = make_float2(0.5f * p[kOffB2 + o], 0.5f * p[kOffB2 + o + 1]);
+  }
+  if (k < (kH / 16) * 4) {
+    const int ko = k / 4, t = k % 4, i = 16 * ko + 2 * t;
+    inf->w3[ko][t] = make_uint2(pack_bf16x2(p[kOffW3 + i], p[kOffW3 + i + 1]), pack_bf16x2(p[kOffW3 + i + 8], p[kOffW3 + i + 9]));
+  }
+  if (k == 0) {
+    inf->b3 = p[kOffB3];
+    inf->pad_[0] = inf->pad_[1] = inf->pad_[2] = 0.f;
+  }
+  // reference image
   if (k < kH * (kInPad / 2)) {
     const int n = k / (kInPad / 2), kp = k % (kInPad / 2);
     const int f0 = 2 * kp, f1 = 2 * kp + 1;
@@ -142,6 +171,7 @@ __global__ void sample_kernel(DeviceState s, const int* __restrict__ pairs, long
 // ---------------------------------------------------------------------------------------------
 // forward pass of many rows (tests and evaluation)
 // ---------------------------------------------------------------------------------------------
+// the reference form (training's forward pass)
 __global__ void forward_kernel(const NetImage* __restrict__ img, const float* __restrict__ X, long long m,
                                float* __restrict__ z) {
   __shared__ NetImage net;
@@ -156,11 +186,30 @@ __global__ void forward_kernel(const NetImage* __restrict__ img, const float* __
                            pack_bf16x2(feat(r0, 2 * t + 8), feat(r0, 2 * t + 9)),
                            pack_bf16x2(feat(r1, 2 * t + 8), feat(r1, 2 * t + 9))};
     float zg, zg8;
-    forward_tile<false>(net, a, zg, zg8);
+    forward_tile(net, a, zg, zg8);
     if (t == 0) {
       if (r0 < m) z[r0] = zg;
       if (r1 < m) z[r1] = zg8;
     }
+  }
+}
+
+// the inference form, exactly as the pair kernels evaluate it: one row per lane, 32 rows per warp
+__global__ void forward_infer_kernel(const InferImage* __restrict__ img, const float* __restrict__ X, long long m,
+                                     float* __restrict__ z) {
+  __shared__ InferImage net;
+  __shared__ uint32_t stage[4][32][8];
+  load_image(net, img);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long base = warp * 32; base < m; base += nwarps * 32) {
+    const long long r = base + lane;
+    float f[kIn];
+#pragma unroll
+    for (int k = 0; k < kIn; k++) f[k] = r < m ? X[r * kIn + k] : 0.f;
+    const float zr = infer_warp(net, f, stage[w]);
+    if (r < m) z[r] = zr;
   }
 }
 
@@ -368,10 +417,11 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gra
 
 namespace emppp {
 
-size_t mlp_image_bytes() { return sizeof(NetImage); }
+size_t mlp_image_bytes() { return kImageBytes; }
 
 cudaError_t launch_build_image(const float* params, void* image, cudaStream_t st) {
-  build_image_kernel<<<(kH * (kH / 2) + 255) / 256, 256, 0, st>>>(params, static_cast<NetImage*>(image));
+  static_assert(kH * (kH / 2) >= (kH / 8) * (kH / 16) * 32, "build grid covers every image entry");
+  build_image_kernel<<<(kH * (kH / 2) + 255) / 256, 256, 0, st>>>(params, image);
   return cudaGetLastError();
 }
 
@@ -382,12 +432,18 @@ cudaError_t launch_sample(const DeviceState& s, const int* pairs, long long m, f
   return cudaGetLastError();
 }
 
-cudaError_t launch_mlp_forward(const void* image, const float* X, long long m, float* z, cudaStream_t st) {
+cudaError_t launch_mlp_forward(const void* image, const float* X, long long m, float* z, int mode, cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
-  long long tiles = (m + 15) / 16;
-  long long blocks = (tiles + 3) / 4;
-  if (blocks > 4096) blocks = 4096;
-  forward_kernel<<<(unsigned)blocks, 128, 0, st>>>(static_cast<const NetImage*>(image), X, m, z);
+  if (mode == 0) {
+    long long tiles = (m + 15) / 16;
+    long long blocks = (tiles + 3) / 4;
+    if (blocks > 4096) blocks = 4096;
+    forward_kernel<<<(unsigned)blocks, 128, 0, st>>>(static_cast<const NetImage*>(image), X, m, z);
+  } else {
+    long long blocks = (m + 127) / 128;
+    if (blocks > 4096) blocks = 4096;
+    forward_infer_kernel<<<(unsigned)blocks, 128, 0, st>>>(infer_image(image), X, m, z);
+  }
   return cudaGetLastError();
 }
 

@@ -7,6 +7,16 @@
 // Tensor-core arithmetic: mma.sync m16n8k16 with BF16 operands and FP32 accumulation, one warp per 16
 // (or 32) rows. Hidden layers are chained from the accumulator layout of one GEMM to the operand
 // layout of the next without data movement.
+//
+// Two forms of the forward pass:
+//   reference form (forward_tile; training and emppp_mlp_forward mode 0): FP32 SiLU of each hidden
+//     value, BF16 rounding of the GEMM operands only, FP32 output layer;
+//   inference form (infer_warp; the pair kernels and emppp_mlp_forward mode 1): weights and biases of
+//     the hidden layers pre-scaled by 1/2 so that the accumulator holds h = x / 2, SiLU evaluated on
+//     packed BF16 pairs as h + h tanh(h) (one tanh.approx.bf16x2 and one fma.rn.bf16x2 per two values),
+//     and the output layer as one more tensor-core product against w3, so that each hidden value
+//     costs about one and a half instructions. Its z differs from the reference form by BF16 rounding
+//     of the activations (a few 1e-3), which only moves the starting slot of the guarded search.
 #pragma once
 
 #include <stdint.h>
@@ -42,6 +52,29 @@ struct __align__(16) NetImage {  // copied with 16-byte vector loads and stores
   float pad_[3];
 };
 
+// Inference image (the pair kernels' form), lane-major B fragments so that a warp's fragment load is
+// one contiguous 256-byte row:
+//   w1[nt][lane]      B fragment of W1 / 2 for hidden units 8 nt .. 8 nt + 7
+//   w2[nt][kk][lane]  B fragment of W2 / 2, output units 8 nt .., input units 16 kk ..
+//   b1[nt][t], b2[nt][t]  halved biases of units 8 nt + 2t, 8 nt + 2t + 1
+//   w3[kk][t]         B fragment of the output layer (w3 in every column), input units 16 kk ..
+struct __align__(16) InferImage {
+  uint2 w1[kH / 8][32];
+  uint2 w2[kH / 8][kH / 16][32];
+  float2 b1[kH / 8][4];
+  float2 b2[kH / 8][4];
+  uint2 w3[kH / 16][4];
+  float b3;
+  float pad_[3];
+};
+
+// the device image of a network: NetImage (training, reference form) followed by InferImage
+constexpr size_t kImageBytes = sizeof(NetImage) + sizeof(InferImage);
+static_assert(sizeof(NetImage) % 16 == 0, "InferImage must start 16-byte aligned");
+__host__ __device__ inline const InferImage* infer_image(const void* image) {
+  return reinterpret_cast<const InferImage*>(static_cast<const char*>(image) + sizeof(NetImage));
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
@@ -68,11 +101,13 @@ __device__ __forceinline__ float dsilu(float x) {
   const float s = sigmoid(x);
   return s * (1.f + x * (1.f - s));
 }
-// inference form: silu(x) = x (1 + tanh(x / 2)) / 2 with the hardware tanh approximation
-__device__ __forceinline__ float silu_fast(float x) {
-  float th;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(th) : "f"(0.5f * x));
-  return 0.5f * x * (1.f + th);
+// inference form: silu(x) = h + h tanh(h) with h = x / 2, on two packed BF16 values
+__device__ __forceinline__ uint32_t silu_half_bf16x2(float h_lo, float h_hi) {
+  const uint32_t h = pack_bf16x2(h_lo, h_hi);
+  uint32_t th, r;
+  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(th) : "r"(h));
+  asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(r) : "r"(h), "r"(th), "r"(h));
+  return r;
 }
 
 // Features of a (target, source) pair: the direction d / |d| of d = r - w_n (3), |d| / L with
@@ -98,7 +133,6 @@ __device__ __forceinline__ void features(float d0, float d1, float d2, float b0,
 
 // Forward pass of one 16-row tile held by a warp: a_in is the A fragment of the padded 16 x 16 input
 // tile (rows g and g + 8 of lane (g, t)); returns z of rows g and g + 8 (all four lanes of a quad).
-template <bool FAST>
 __device__ __forceinline__ void forward_tile(const NetImage& net, const uint32_t a_in[4], float& z_g, float& z_g8) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   uint32_t a1[4][4];
@@ -111,7 +145,7 @@ __device__ __forceinline__ void forward_tile(const NetImage& net, const uint32_t
     const float bc = net.b1[8 * (nt + 1) + 2 * t], bd = net.b1[8 * (nt + 1) + 2 * t + 1];
     float h[8] = {c0[0] + ba, c0[1] + bb, c0[2] + ba, c0[3] + bb, c1[0] + bc, c1[1] + bd, c1[2] + bc, c1[3] + bd};
 #pragma unroll
-    for (int k = 0; k < 8; k++) h[k] = FAST ? silu_fast(h[k]) : silu(h[k]);
+    for (int k = 0; k < 8; k++) h[k] = silu(h[k]);
     const int kk = nt >> 1;
     a1[kk][0] = pack_bf16x2(h[0], h[1]);
     a1[kk][1] = pack_bf16x2(h[2], h[3]);
@@ -127,13 +161,8 @@ __device__ __forceinline__ void forward_tile(const NetImage& net, const uint32_t
     const int o = 8 * nt + 2 * t;
     const float h0 = c[0] + net.b2[o], h1 = c[1] + net.b2[o + 1], h2 = c[2] + net.b2[o], h3 = c[3] + net.b2[o + 1];
     const float w0 = net.w3[o], w1 = net.w3[o + 1];
-    if (FAST) {
-      zg += silu_fast(h0) * w0 + silu_fast(h1) * w1;
-      zg8 += silu_fast(h2) * w0 + silu_fast(h3) * w1;
-    } else {
-      zg += silu(h0) * w0 + silu(h1) * w1;
-      zg8 += silu(h2) * w0 + silu(h3) * w1;
-    }
+    zg += silu(h0) * w0 + silu(h1) * w1;
+    zg8 += silu(h2) * w0 + silu(h3) * w1;
   }
   zg += __shfl_xor_sync(0xffffffffu, zg, 1);
   zg += __shfl_xor_sync(0xffffffffu, zg, 2);
@@ -143,19 +172,22 @@ __device__ __forceinline__ void forward_tile(const NetImage& net, const uint32_t
   z_g8 = zg8 + net.b3;
 }
 
-// Copies the network image from global memory into shared memory (whole block, then a barrier). Both
-// addresses are 16-byte aligned: NetImage is declared with that alignment and the global image comes
-// from cudaMalloc.
-__device__ __forceinline__ void load_image(NetImage& dst, const NetImage* __restrict__ src) {
+// Copies an image (NetImage or InferImage) from global memory into shared memory (whole block, then a
+// barrier). Both addresses are 16-byte aligned: the images are declared with that alignment and the
+// global image comes from cudaMalloc (InferImage at a multiple of 16 bytes after it).
+template <class Image>
+__device__ __forceinline__ void load_image(Image& dst, const Image* __restrict__ src) {
+  static_assert(sizeof(Image) % 16 == 0, "image size must be a multiple of 16 bytes");
   const uint4* s = reinterpret_cast<const uint4*>(src);
   uint4* d = reinterpret_cast<uint4*>(&dst);
-  for (int k = threadIdx.x; k < (int)(sizeof(NetImage) / 16); k += blockDim.x) d[k] = s[k];
+  for (int k = threadIdx.x; k < (int)(sizeof(Image) / 16); k += blockDim.x) d[k] = s[k];
   __syncthreads();
 }
 
-// Warp-wide inference for the 32 rows held one per lane: f are this lane's features, stage is a per-warp
-// shared buffer of 32 x 8 uint32; returns z of this lane's row. Every lane of the warp must call it.
-__device__ __forceinline__ float infer_warp(const NetImage& net, const float f[kIn], uint32_t (*stage)[8]) {
+// Inference form of the forward pass for the 32 rows held one per lane: f are this lane's features,
+// stage is a per-warp shared buffer of 32 x 8 uint32; returns z of this lane's row. Every lane of the
+// warp must call it (converged). Both 16-row tiles share each B-fragment load.
+__device__ __forceinline__ float infer_warp(const InferImage& net, const float f[kIn], uint32_t (*stage)[8]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   stage[lane][0] = pack_bf16x2(f[0], f[1]);
   stage[lane][1] = pack_bf16x2(f[2], f[3]);
@@ -166,17 +198,62 @@ __device__ __forceinline__ float infer_warp(const NetImage& net, const float f[k
   stage[lane][6] = 0u;
   stage[lane][7] = 0u;
   __syncwarp();
-  float z[2][2];
+  uint32_t a_in[2][4];
 #pragma unroll
   for (int m = 0; m < 2; m++) {
-    const uint32_t a[4] = {stage[16 * m + g][t], stage[16 * m + g + 8][t], stage[16 * m + g][4 + t],
-                           stage[16 * m + g + 8][4 + t]};
-    forward_tile<true>(net, a, z[m][0], z[m][1]);
+    a_in[m][0] = stage[16 * m + g][t];
+    a_in[m][1] = stage[16 * m + g + 8][t];
+    a_in[m][2] = stage[16 * m + g][4 + t];
+    a_in[m][3] = stage[16 * m + g + 8][4 + t];
   }
   __syncwarp();
+  // layer 1: accumulators start at b1 / 2, activations packed straight into layer 2's A fragments
+  uint32_t a1[2][4][4];
+#pragma unroll
+  for (int nt = 0; nt < kH / 8; nt++) {
+    const uint2 bw = net.w1[nt][lane];
+    const float2 bb = net.b1[nt][t];
+#pragma unroll
+    for (int m = 0; m < 2; m++) {
+      float c[4] = {bb.x, bb.y, bb.x, bb.y};
+      mma_bf16(c, a_in[m], bw.x, bw.y);
+      const int kk = nt >> 1, o = (nt & 1) * 2;
+      a1[m][kk][o] = silu_half_bf16x2(c[0], c[1]);
+      a1[m][kk][o + 1] = silu_half_bf16x2(c[2], c[3]);
+    }
+  }
+  // layer 2, two n-tiles at a time = one k-step of the output layer
+  float zo[2][4];
+#pragma unroll
+  for (int m = 0; m < 2; m++) zo[m][0] = zo[m][1] = zo[m][2] = zo[m][3] = net.b3;
+#pragma unroll
+  for (int ko = 0; ko < kH / 16; ko++) {
+    uint32_t ao[2][4];
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+      const int nt = 2 * ko + half;
+      const float2 bb = net.b2[nt][t];
+      float c[2][4] = {{bb.x, bb.y, bb.x, bb.y}, {bb.x, bb.y, bb.x, bb.y}};
+#pragma unroll
+      for (int kk = 0; kk < kH / 16; kk++) {
+        const uint2 bw = net.w2[nt][kk][lane];
+        mma_bf16(c[0], a1[0][kk], bw.x, bw.y);
+        mma_bf16(c[1], a1[1][kk], bw.x, bw.y);
+      }
+#pragma unroll
+      for (int m = 0; m < 2; m++) {
+        ao[m][2 * half] = silu_half_bf16x2(c[m][0], c[m][1]);
+        ao[m][2 * half + 1] = silu_half_bf16x2(c[m][2], c[m][3]);
+      }
+    }
+    const uint2 w3 = net.w3[ko][t];
+    mma_bf16(zo[0], ao[0], w3.x, w3.y);
+    mma_bf16(zo[1], ao[1], w3.x, w3.y);
+  }
+  // every column of the output holds z: lane (g, t) has rows g (zo[m][0]) and g + 8 (zo[m][2]) of tile m
   const int m = lane >> 4, local = lane & 15, src = (local & 7) * 4;
-  const float v00 = __shfl_sync(0xffffffffu, z[0][0], src), v01 = __shfl_sync(0xffffffffu, z[0][1], src);
-  const float v10 = __shfl_sync(0xffffffffu, z[1][0], src), v11 = __shfl_sync(0xffffffffu, z[1][1], src);
+  const float v00 = __shfl_sync(0xffffffffu, zo[0][0], src), v01 = __shfl_sync(0xffffffffu, zo[0][2], src);
+  const float v10 = __shfl_sync(0xffffffffu, zo[1][0], src), v11 = __shfl_sync(0xffffffffu, zo[1][2], src);
   return m == 0 ? (local < 8 ? v00 : v01) : (local < 8 ? v10 : v11);
 }
 

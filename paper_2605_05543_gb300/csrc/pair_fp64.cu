@@ -47,7 +47,7 @@ struct PairArgs {
   const BunchSched* __restrict__ sched;
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
-  const mlp::NetImage* __restrict__ net;  // proposal network (EMPPP_PROPOSAL_MLP)
+  const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -74,7 +74,7 @@ struct Window {
 template <int PROP>
 __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   __shared__ int s_item;
-  __shared__ mlp::NetImage s_net[PROP == kPropMlp ? 1 : 1];
+  __shared__ mlp::InferImage s_net[1];
   __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
   if (PROP == kPropMlp) mlp::load_image(s_net[0], a.net);
   const long long N = a.N;
@@ -418,7 +418,7 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunc
   a.sched = s.sched;
   a.nitems = pl.nitems;
   a.work = s.work;
-  a.net = static_cast<const mlp::NetImage*>(s.mlp_image);
+  a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)

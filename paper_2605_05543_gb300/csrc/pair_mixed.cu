@@ -64,7 +64,7 @@ struct MixedArgs {
   const BunchSched* __restrict__ sched;
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
-  const mlp::NetImage* __restrict__ net;  // proposal network (EMPPP_PROPOSAL_MLP)
+  const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
 };
 
 struct Target {
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
   __shared__ float4 s_db[PROP == kPropMlp ? kTile : 1];  // beta_n - beta_{n-1} of the tile's sources
-  __shared__ mlp::NetImage s_net[1];
+  __shared__ mlp::InferImage s_net[1];
   __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
   if (PROP == kPropMlp) mlp::load_image(s_net[0], a.net);
 
@@ -561,7 +561,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.sched = s.sched;
   a.nitems = pl.nitems;
   a.work = s.work;
-  a.net = static_cast<const mlp::NetImage*>(s.mlp_image);
+  a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
   if (proposal == kPropClosedForm)

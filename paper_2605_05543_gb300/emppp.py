@@ -97,7 +97,7 @@ SIGNATURES = {
     "emppp_synchronize": (ctypes.c_int, [_H]),
     "emppp_fields_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "emppp_sample_delays": (ctypes.c_int, [_H, _vp, ctypes.c_int64, _vp, _vp, _vp, ctypes.c_int32]),
-    "emppp_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, _vp]),
+    "emppp_mlp_forward": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp, ctypes.c_int32, _vp]),
     "emppp_mlp_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "emppp_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(MlpConfig), _vp, _vp]),
     "emppp_set_proposal": (ctypes.c_int, [_H, _vp, ctypes.c_int32]),
@@ -396,14 +396,16 @@ def _dev_f32(a):
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def mlp_forward(params, features):
-    """z of the proposal network for features [m, 10] (host arrays or CUDA tensors); returns numpy."""
+def mlp_forward(params, features, mode="reference"):
+    """z of the proposal network for features [m, 10] (host arrays or CUDA tensors); returns numpy.
+    mode "reference": the form training differentiates; "inference": the form the pair kernels use."""
     import torch
 
     p, X = _dev_f32(params), _dev_f32(features)
     m = X.shape[0]
     z = torch.empty(m, dtype=torch.float32, device="cuda")
-    _check(load().emppp_mlp_forward(p.data_ptr(), X.data_ptr(), m, z.data_ptr(),
+    md = {"reference": 0, "inference": 1}[mode]
+    _check(load().emppp_mlp_forward(p.data_ptr(), X.data_ptr(), m, z.data_ptr(), md,
                                     torch.cuda.current_stream().cuda_stream))
     return z.cpu().numpy()
 

@@ -97,6 +97,21 @@ def test_forward_matches_reference(m):
         assert err < 0.25 * np.max(np.abs(zg - zu))  # the BF16 rounding points are the kernel's
 
 
+@pytest.mark.parametrize("m", [1, 31, 33, 5000])
+def test_inference_form_matches_reference(m):
+    """The pair kernels' form (halved hidden layers, packed BF16 SiLU, tensor-core output) stays within
+    BF16 activation rounding of the reference form."""
+    X, Tz = _dataset(max(m, 64), seed=42)
+    X = X[:m]
+    p = _params(4)
+    zi = emppp.mlp_forward(p, X, mode="inference")
+    zr, _ = mlp.forward(p, X, rounding=True)
+    scale = max(1.0, np.max(np.abs(zr)))
+    assert np.all(np.isfinite(zi))
+    assert np.max(np.abs(zi - zr)) <= 3e-2 * scale
+    assert np.sqrt(np.mean((zi - zr) ** 2)) <= 5e-3 * scale
+
+
 _BLOCKS = [(mlp.OFF_W1, mlp.OFF_B1), (mlp.OFF_B1, mlp.OFF_W2), (mlp.OFF_W2, mlp.OFF_B2), (mlp.OFF_B2, mlp.OFF_W3),
            (mlp.OFF_W3, mlp.OFF_B3), (mlp.OFF_B3, mlp.NUM_PARAMS)]
 
