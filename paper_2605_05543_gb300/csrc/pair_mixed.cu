@@ -33,6 +33,10 @@ namespace emppp {
 
 namespace {
 
+#ifndef EMPPP_MIXED_PREFETCH
+#define EMPPP_MIXED_PREFETCH 0
+#endif
+
 #ifndef EMPPP_MIXED_MIN_BLOCKS
 #define EMPPP_MIXED_MIN_BLOCKS 6  // resident blocks per SM the register budget is fitted to
 #endif
@@ -136,6 +140,24 @@ __device__ __forceinline__ bool node_test(const Target& r, const float4* __restr
   return node_test_d(r, separation(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1)), src64, p, a, n_fb);
 }
 
+// uniform-motion guess of the retarded delay in steps, from the staged present record of the source:
+// c tau = gamma^2 [d.beta + sqrt((d.beta)^2 + |d|^2 / gamma^2)] with d from the hi parts only
+__device__ __forceinline__ float closed_form_steps(const Target& r, float4 g0, float4 g2, float inv_cdt) {
+  const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
+  const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
+  const float dd = x0 * x0 + x1 * x1 + x2 * x2;
+  const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
+  const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
+  return fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
+}
+
+// offset of the guessed older node: (nw - 2) - steps; below 0 means "older than the history"
+__device__ __forceinline__ int guessed_offset(float steps, int nw) {
+  return (steps > (float)(nw - 2)) ? -1 : (nw - 2) - (int)steps;
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // bisection between offsets lo (P false) and hi (P true); returns lo
 __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict__ src32, const double* __restrict__ src64,
                                       const Window& w, int lo, int hi, const MixedArgs& a, unsigned& n_tests,
@@ -238,6 +260,10 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
       }
     }
     __syncthreads();
+    // closed-form guess of the next source, computed one source ahead so that its records can be
+    // prefetched into L1 while the present pair is evaluated
+    float steps_next = 0.f;
+    if (PROP == kPropClosedForm && EMPPP_MIXED_PREFETCH && active) steps_next = closed_form_steps(r, s_q0[0], s_q2[0], inv_cdt);
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
@@ -254,6 +280,17 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           steps_mlp = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 2.0e9f);
         }
         if (!active) continue;  // and stay in the loop for the next source's evaluation
+        float steps_cf = 0.f;
+        if (PROP == kPropClosedForm && EMPPP_MIXED_PREFETCH) {
+          steps_cf = steps_next;
+          if (jj + 1 < tn) {
+            steps_next = closed_form_steps(r, s_q0[jj + 1], s_q2[jj + 1], inv_cdt);
+            const int pq = win.phys(max(guessed_offset(steps_next, win.nw), 0));
+            const float4* nx = a.rec32 + ((size_t)(j + 1) * D + pq) * 3;
+            prefetch_l1(nx);                   // record of the guessed older slot
+            if (pq + 1 < D) prefetch_l1(nx + 5);  // end of the next slot's record, in the same source
+          }
+        }
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
@@ -293,20 +330,13 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           }
         } else {
           float steps;
-          if (PROP == kPropMlp) {
+          if (PROP == kPropMlp)
             steps = steps_mlp;
-          } else {
-            // uniform-motion guess of the older node from the staged present record of the source
-            const float4 g0 = s_q0[jj], g2 = s_q2[jj];
-            const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
-            const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
-            const float dd = x0 * x0 + x1 * x1 + x2 * x2;
-            const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
-            const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
-            steps = fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
-          }
-          // offset of the guessed older node: (nw - 2) - steps; below 0 means "older than the history"
-          const int lraw = (steps > (float)(win.nw - 2)) ? -1 : (win.nw - 2) - (int)steps;
+          else if (EMPPP_MIXED_PREFETCH)
+            steps = steps_cf;
+          else
+            steps = closed_form_steps(r, s_q0[jj], s_q2[jj], inv_cdt);
+          const int lraw = guessed_offset(steps, win.nw);
           const int lg = max(lraw, 0);
           const int pg = win.phys(lg);
           A = load_rec(src32, pg);
