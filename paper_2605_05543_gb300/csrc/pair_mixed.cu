@@ -33,12 +33,8 @@ namespace emppp {
 
 namespace {
 
-#ifndef EMPPP_MIXED_PREFETCH
-#define EMPPP_MIXED_PREFETCH 0
-#endif
-
 #ifndef EMPPP_MIXED_MIN_BLOCKS
-#define EMPPP_MIXED_MIN_BLOCKS 6  // resident blocks per SM the register budget is fitted to
+#define EMPPP_MIXED_MIN_BLOCKS 7  // resident blocks per SM the register budget is fitted to (72 registers)
 #endif
 
 constexpr int kBlock = 128;
@@ -156,8 +152,6 @@ __device__ __forceinline__ int guessed_offset(float steps, int nw) {
   return (steps > (float)(nw - 2)) ? -1 : (nw - 2) - (int)steps;
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
-
 // bisection between offsets lo (P false) and hi (P true); returns lo
 __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict__ src32, const double* __restrict__ src64,
                                       const Window& w, int lo, int hi, const MixedArgs& a, unsigned& n_tests,
@@ -241,8 +235,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   const int j_begin = boff + chunk_id * bs.chunk;
   const int j_end = min(boff + bd.n, j_begin + bs.chunk);
 
+  // compensated running sums of E and of c B
   float Es[3] = {0.f, 0.f, 0.f}, Ec[3] = {0.f, 0.f, 0.f}, Bs[3] = {0.f, 0.f, 0.f}, Bc[3] = {0.f, 0.f, 0.f};
-  const float ic = (float)(1.0 / kC);
 
   for (int tile = j_begin; tile < j_end; tile += kTile) {
     const int tn = min(kTile, j_end - tile);
@@ -260,10 +254,6 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
       }
     }
     __syncthreads();
-    // closed-form guess of the next source, computed one source ahead so that its records can be
-    // prefetched into L1 while the present pair is evaluated
-    float steps_next = 0.f;
-    if (PROP == kPropClosedForm && EMPPP_MIXED_PREFETCH && active) steps_next = closed_form_steps(r, s_q0[0], s_q2[0], inv_cdt);
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
@@ -280,17 +270,6 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           steps_mlp = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 2.0e9f);
         }
         if (!active) continue;  // and stay in the loop for the next source's evaluation
-        float steps_cf = 0.f;
-        if (PROP == kPropClosedForm && EMPPP_MIXED_PREFETCH) {
-          steps_cf = steps_next;
-          if (jj + 1 < tn) {
-            steps_next = closed_form_steps(r, s_q0[jj + 1], s_q2[jj + 1], inv_cdt);
-            const int pq = win.phys(max(guessed_offset(steps_next, win.nw), 0));
-            const float4* nx = a.rec32 + ((size_t)(j + 1) * D + pq) * 3;
-            prefetch_l1(nx);                   // record of the guessed older slot
-            if (pq + 1 < D) prefetch_l1(nx + 5);  // end of the next slot's record, in the same source
-          }
-        }
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
@@ -332,8 +311,6 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           float steps;
           if (PROP == kPropMlp)
             steps = steps_mlp;
-          else if (EMPPP_MIXED_PREFETCH)
-            steps = steps_cf;
           else
             steps = closed_form_steps(r, s_q0[jj], s_q2[jj], inv_cdt);
           const int lraw = guessed_offset(steps, win.nw);
@@ -476,8 +453,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
         const float R2 = dot3(e0, e1, e2, e0, e1, e2);
         const float invR = rsqrtf(R2);
         const float R = __fmul_rn(R2, invR);
-        const float n0 = __fmul_rn(e0, invR), n1 = __fmul_rn(e1, invR), n2 = __fmul_rn(e2, invR);
-        const float u0 = __fsub_rn(n0, be0), u1 = __fsub_rn(n1, be1), u2 = __fsub_rn(n2, be2);
+        // u' = eta / R - beta
+        const float u0 = __fmaf_rn(e0, invR, -be0), u1 = __fmaf_rn(e1, invR, -be1), u2 = __fmaf_rn(e2, invR, -be2);
         const float eb = dot3(e0, e1, e2, be0, be1, be2);
         // 1 / (eta . u'): R - eta.beta directly when eta.beta <= 0, else the rationalised form
         const float xb0 = cross1(e1, e2, be1, be2), xb1 = cross1(e2, e0, be2, be0), xb2 = cross1(e0, e1, be0, be1);
@@ -498,13 +475,14 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           F1 = __fadd_rn(F1, cross1(e2, e0, c2, c0));
           F2 = __fadd_rn(F2, cross1(e0, e1, c0, c1));
         }
-        const float E0 = __fmul_rn(pref, F0), E1 = __fmul_rn(pref, F1), E2 = __fmul_rn(pref, F2);
-        P[0] = __fadd_rn(P[0], E0);
-        P[1] = __fadd_rn(P[1], E1);
-        P[2] = __fadd_rn(P[2], E2);
-        P[3] = __fadd_rn(P[3], __fmul_rn(cross1(n1, n2, E1, E2), ic));
-        P[4] = __fadd_rn(P[4], __fmul_rn(cross1(n2, n0, E2, E0), ic));
-        P[5] = __fadd_rn(P[5], __fmul_rn(cross1(n0, n1, E0, E1), ic));
+        // E = pref F; c B = eta_hat x E = (pref / R) (eta x F), with 1 / c applied once per target
+        P[0] = __fmaf_rn(pref, F0, P[0]);
+        P[1] = __fmaf_rn(pref, F1, P[1]);
+        P[2] = __fmaf_rn(pref, F2, P[2]);
+        const float pb = __fmul_rn(pref, invR);
+        P[3] = __fmaf_rn(pb, cross1(e1, e2, F1, F2), P[3]);
+        P[4] = __fmaf_rn(pb, cross1(e2, e0, F2, F0), P[4]);
+        P[5] = __fmaf_rn(pb, cross1(e0, e1, F0, F1), P[5]);
       }
       // Kahan-add the partial sums of these kSub sources
 #pragma unroll
@@ -524,7 +502,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
     double Et[3], Bt[3];
     for (int c = 0; c < 3; c++) {
       Et[c] = (double)Es[c] - (double)Ec[c];
-      Bt[c] = (double)Bs[c] - (double)Bc[c];
+      Bt[c] = ((double)Bs[c] - (double)Bc[c]) * (1.0 / kC);
     }
     if (bs.nchunk == 1) {
       for (int c = 0; c < 3; c++) {

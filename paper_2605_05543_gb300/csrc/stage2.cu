@@ -75,7 +75,7 @@ __global__ void transport_kernel(DeviceState s, BextParams bp, double dt, int ns
   double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
   const double E[3] = {0.0, 0.0, 0.0};
   double v[3] = {rec[3], rec[4], rec[5]}, B[3] = {0.0, 0.0, 0.0};
-  for (int k = 0; k < nsteps; k++) push_particle(x, u, E, E, bp, dt, v, B);
+  for (int k = 0; k < nsteps; k++) push_particle<false>(x, u, E, E, bp, dt, v, B);
   if (!isfinite(x[0] + x[1] + x[2] + u[0] + u[1] + u[2])) atomicOr(s.err, kErrNonFinite);
   for (int c = 0; c < 3; c++) {
     s.u[3 * i + c] = u[c];
