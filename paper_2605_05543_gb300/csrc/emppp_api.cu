@@ -415,10 +415,8 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.rec32, N * D * 12);
   ALLOC(s.slot_t, D);
   ALLOC(s.tab.lhs64, D);
-  ALLOC(s.tab.lhs32, D);
-  ALLOC(s.tab.ct32, D);
   ALLOC(s.tab.inv_dtk, D);
-  ALLOC(s.tab.icdt32, D);
+  ALLOC(s.tab.tab32, D);
   ALLOC(s.u, N * 3);
   ALLOC(s.wts, N);
   ALLOC(s.kq32, N);

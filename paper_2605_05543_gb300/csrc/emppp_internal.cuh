@@ -60,12 +60,20 @@ enum { kPropBisect = 0, kPropClosedForm = 1, kPropMlp = 2 };
 // counters, accumulated until reset by the host
 enum { kStatOOH = 0, kStatShortcut = 1, kStatBisect = 2, kStatNodeTests = 3, kStatGuard = 4, kStatCount = 8 };
 
+// Guard band of the FP32 node test of the mixed path. The FP32 value of |r - w|^2 formed from hi/lo
+// coordinates carries a relative error below 7u (u = 2^-24; two roundings in each component of d,
+// one in each square and two in the sum). With the thresholds L^2 (1 + k) / (1 - k) and
+// L^2 (1 - k) / (1 + k), each rounded outward to FP32, and k = 32u, a computed |d|^2 beyond a threshold
+// puts the exact margin |d|^2 - L^2 beyond about 24u (|d|^2 + L^2), far above the FP64 test's own
+// rounding, so the FP32 decision is the FP64 one; between the thresholds the FP64 test decides.
+constexpr double kGuardBand = 32.0 * 5.9604644775390625e-08;
+
 struct SlotTables {
   double* lhs64;    // [D] (c (t_n - t_k))^2, formed as c*(t_n - t_k) then squared (no FMA)
-  float* lhs32;     // [D] same, FP32
-  float* ct32;      // [D] c (t_n - t_k), FP32
   double* inv_dtk;  // [D] 1 / (t_{k+1} - t_k) for k < n
-  float* icdt32;    // [D] 1 / (c (t_{k+1} - t_k)), FP32
+  // [D] FP32 per slot: (upper threshold of (c (t_n - t_k))^2, lower threshold, c (t_n - t_k),
+  // 1 / (c (t_{k+1} - t_k)))
+  float4* tab32;
 };
 
 struct BunchDesc {

@@ -3,11 +3,10 @@
 //
 // Per pair (target i at r = x_i^n, t = t_n; source j):
 //   bracket   the node test P(k): (c (t - t_k))^2 <= |r - w_k|^2 is evaluated in FP32 on hi/lo split
-//             coordinates; the FP32 margin M = |d|^2 - L^2 carries an error below 8u (|d|^2 + L^2)
-//             (u = 2^-24: two roundings in each component of d, three in |d|^2, one in the table value
-//             L^2 and one in M), so |M| > kBand (|d|^2 + L^2) with kBand = 32u decides exactly as the
-//             FP64 test would; otherwise the FP64 test itself (reference operation order) decides. The
-//             bracket is therefore the FP64 one. Search: the paper's bisection, or the guarded galloping
+//             coordinates against two per-slot thresholds, L^2 widened and narrowed by the guard band
+//             (kGuardBand, emppp_internal.cuh); beyond them the FP32 decision is the FP64 one, between
+//             them the FP64 test itself (reference operation order) decides. The bracket is therefore
+//             the FP64 one. Search: the paper's bisection, or the guarded galloping
 //             search from the uniform-motion guess; with the guess, the records of the one or two slots
 //             the guess points at are loaded together, so a correct guess needs a single gather round.
 //   retarded  in light units (lengths in m, velocities as beta = v/c): with L1 = c (t - t1) and d = r - w1,
@@ -40,15 +39,12 @@ namespace {
 constexpr int kBlock = 128;
 constexpr int kTile = 128;
 constexpr int kSub = 8;  // sources per FP32 partial sum
-constexpr float kBand = 32.0f * 5.9604645e-8f;  // 32 u, u = 2^-24
 
 struct MixedArgs {
   const float4* __restrict__ rec32;
   const double* __restrict__ rec64;
   const double* __restrict__ lhs64;
-  const float* __restrict__ lhs32;
-  const float* __restrict__ ct32;
-  const float* __restrict__ icdt32;
+  const float4* __restrict__ tab32;  // per slot: guard-band thresholds of L^2, c (t - t_k), 1 / (c dt_k)
   const float* __restrict__ kq32;  // -e w_j / (4 pi eps0), FP32
   const int* __restrict__ order;
   const StepState* __restrict__ state;
@@ -115,16 +111,13 @@ __device__ __forceinline__ float3 separation(const Target& r, float4 q0, float4 
   return make_float3((r.h0 - q0.x) + (r.l0 - q1.x), (r.h1 - q0.y) + (r.l1 - q1.y), (r.h2 - q0.z) + (r.l2 - q1.z));
 }
 
-// P(k) from a separation d already formed at physical slot p
-__device__ __forceinline__ bool node_test_d(const Target& r, float3 d, const double* __restrict__ src64, int p,
-                                            const MixedArgs& a, unsigned& n_fb) {
+// P(k) from a separation d already formed at physical slot p, with that slot's table entry tab
+__device__ __forceinline__ bool node_test_d(const Target& r, float3 d, float4 tab, const double* __restrict__ src64,
+                                            int p, const MixedArgs& a, unsigned& n_fb) {
   const float D2 = d.x * d.x + d.y * d.y + d.z * d.z;
-  const float L2 = __ldg(a.lhs32 + p);
-  const float M = D2 - L2;
-  const float band = kBand * (D2 + L2);
   if (!r.exact_only) {
-    if (M > band) return true;
-    if (M < -band) return false;
+    if (D2 > tab.x) return true;
+    if (D2 < tab.y) return false;
   }
   n_fb++;
   return exact_test(r, src64 + 6 * p, __ldg(a.lhs64 + p));
@@ -133,7 +126,8 @@ __device__ __forceinline__ bool node_test_d(const Target& r, float3 d, const dou
 __device__ __forceinline__ bool node_test(const Target& r, const float4* __restrict__ src32,
                                           const double* __restrict__ src64, int p, const MixedArgs& a,
                                           unsigned& n_fb) {
-  return node_test_d(r, separation(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1)), src64, p, a, n_fb);
+  return node_test_d(r, separation(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1)), __ldg(a.tab32 + p), src64, p,
+                     a, n_fb);
 }
 
 // uniform-motion guess of the retarded delay in steps, from the staged present record of the source:
@@ -240,6 +234,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
 
   for (int tile = j_begin; tile < j_end; tile += kTile) {
     const int tn = min(kTile, j_end - tile);
+    unsigned brc = 0;  // out-of-history, shortcut and bisection counts of this tile (at most kTile each)
     __syncthreads();
     if (threadIdx.x < tn) {
       const int j = tile + threadIdx.x;
@@ -273,27 +268,32 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
-        // ---- bracket: offset l1 of the older node, its record A and separation dA --------------------
+        // ---- bracket: offset l1 of the older node, its slot pA, record A, separation dA and table -------
         int l1;
         int br;
+        int pA;         // physical slot of the older node
         Rec A;          // record of the older node
         float3 dA;      // r - w at the older node
+        float4 tabA;    // slot table entry of the older node
         float4 q2b;     // (dbeta, gamma^2) of the newer node (regular brackets)
         bool have_b = false;
-        bool fast = true;  // A and dA already belong to l1
+        bool fast = true;  // pA, A, dA and tabA already belong to l1
         if (win.nw == 1) {
           // n = k0: only the present slot exists; every pair is out of history
           n_tests += 1;
           l1 = 0;
           br = 0;
-          A = load_rec(src32, win.phys(0));
+          pA = win.phys(0);
+          A = load_rec(src32, pA);
           dA = separation(r, A.q0, A.q1);
+          tabA = __ldg(a.tab32 + pA);
         } else if (PROP == kPropBisect) {
           n_tests += 1;
-          const int pa = win.phys(0);
-          A = load_rec(src32, pa);
+          pA = win.phys(0);
+          A = load_rec(src32, pA);
           dA = separation(r, A.q0, A.q1);
-          if (node_test_d(r, dA, src64, pa, a, n_fb)) {
+          tabA = __ldg(a.tab32 + pA);
+          if (node_test_d(r, dA, tabA, src64, pA, a, n_fb)) {
             l1 = 0;
             br = 0;
           } else {
@@ -315,13 +315,14 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
             steps = closed_form_steps(r, s_q0[jj], s_q2[jj], inv_cdt);
           const int lraw = guessed_offset(steps, win.nw);
           const int lg = max(lraw, 0);
-          const int pg = win.phys(lg);
-          A = load_rec(src32, pg);
+          pA = win.phys(lg);
+          A = load_rec(src32, pA);
           dA = separation(r, A.q0, A.q1);
+          tabA = __ldg(a.tab32 + pA);
           if (lraw < 0) {
             // predicted out of history: the only record needed is the oldest slot's
             n_tests += 1;
-            if (node_test_d(r, dA, src64, pg, a, n_fb)) {
+            if (node_test_d(r, dA, tabA, src64, pA, a, n_fb)) {
               l1 = 0;
               br = 0;
             } else {
@@ -344,15 +345,15 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
             }
           } else {
             // predicted bracket [lg, lg + 1]: both records are loaded at once
-            const int pg1 = win.phys(lg + 1);
+            const int pg1 = pA + 1 == D ? 0 : pA + 1;  // slot of offset lg + 1
             const Rec Bn = load_rec(src32, pg1);
             n_tests += 1;
-            const bool tA = node_test_d(r, dA, src64, pg, a, n_fb);
+            const bool tA = node_test_d(r, dA, tabA, src64, pA, a, n_fb);
             if (!tA) {
               bool tB = true;  // P(n) is always true
               if (lg + 1 < win.nw - 1) {
                 n_tests += 1;
-                tB = node_test_d(r, separation(r, Bn.q0, Bn.q1), src64, pg1, a, n_fb);
+                tB = node_test_d(r, separation(r, Bn.q0, Bn.q1), __ldg(a.tab32 + pg1), src64, pg1, a, n_fb);
               }
               if (tB) {
                 l1 = lg;
@@ -407,23 +408,19 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           }
         }
         if (!fast) {
-          A = load_rec(src32, win.phys(l1));
+          pA = win.phys(l1);
+          A = load_rec(src32, pA);
           dA = separation(r, A.q0, A.q1);
+          tabA = __ldg(a.tab32 + pA);
         }
-        if (br == 0)
-          n_ooh++;
-        else if (br == 1)
-          n_sc++;
-        else
-          n_bi++;
+        brc += 1u << (10 * br);  // branch counts of this tile, 10 bits each
 
         // ---- retarded state (light units) --------------------------------------------------------
         // Written with explicit round-to-nearest intrinsics: the compiler may not fuse or regroup any
         // of it, so every search variant (whose own arithmetic shares subexpressions with this code
         // in different ways) computes the same fields from the same bracket, bit for bit.
-        const int p1 = win.phys(l1);
         const float d0 = dA.x, d1 = dA.y, d2 = dA.z;
-        const float L1 = __ldg(a.ct32 + p1);
+        const float L1 = tabA.z;
         const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
         const float ig2 = A.q0.w, g2 = A.q2.w;
         const float hb = __fsub_rn(dot3(d0, d1, d2, b10, b11, b12), L1);
@@ -434,8 +431,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
         const float e0 = __fmaf_rn(-b10, s, d0), e1 = __fmaf_rn(-b11, s, d1), e2 = __fmaf_rn(-b12, s, d2);
         float be0 = b10, be1 = b11, be2 = b12, al0 = 0.f, al1 = 0.f, al2 = 0.f, ug = ig2;
         if (br != 0) {
-          if (!have_b) q2b = __ldg(src32 + 3 * win.phys(l1 + 1) + 2);
-          const float icdt = __ldg(a.icdt32 + p1);
+          if (!have_b) q2b = __ldg(src32 + 3 * (pA + 1 == D ? 0 : pA + 1) + 2);
+          const float icdt = tabA.w;
           const float db0 = __fsub_rn(q2b.x, A.q2.x), db1 = __fsub_rn(q2b.y, A.q2.y), db2 = __fsub_rn(q2b.z, A.q2.z);
           al0 = __fmul_rn(db0, icdt);
           al1 = __fmul_rn(db1, icdt);
@@ -497,6 +494,9 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
         Bs[c] = tb;
       }
     }
+    n_ooh += brc & 1023u;
+    n_sc += (brc >> 10) & 1023u;
+    n_bi += brc >> 20;
   }
   if (active) {
     double Et[3], Bt[3];
@@ -551,9 +551,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.rec32 = reinterpret_cast<const float4*>(s.rec32);
   a.rec64 = s.rec64;
   a.lhs64 = s.tab.lhs64;
-  a.lhs32 = s.tab.lhs32;
-  a.ct32 = s.tab.ct32;
-  a.icdt32 = s.tab.icdt32;
+  a.tab32 = s.tab.tab32;
   a.kq32 = s.kq32;
   a.order = order;
   a.state = s.state;

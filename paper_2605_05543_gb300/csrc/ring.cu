@@ -108,17 +108,17 @@ __global__ void prep_kernel(DeviceState s) {
     const double ct = __dmul_rn(kC, __dsub_rn(t_n, tk));
     const double lhs = __dmul_rn(ct, ct);
     s.tab.lhs64[p] = lhs;
-    s.tab.lhs32[p] = (float)lhs;
-    s.tab.ct32[p] = (float)ct;
+    float icdt = 0.f;
     if (l + 1 < nwin) {
       int q = p + 1 == s.D ? 0 : p + 1;
       const double dtk = s.slot_t[q] - tk;
       s.tab.inv_dtk[p] = 1.0 / dtk;
-      s.tab.icdt32[p] = (float)(1.0 / (kC * dtk));
+      icdt = (float)(1.0 / (kC * dtk));
     } else {
       s.tab.inv_dtk[p] = 0.0;
-      s.tab.icdt32[p] = 0.f;
     }
+    const double qhi = (1.0 + kGuardBand) / (1.0 - kGuardBand), qlo = (1.0 - kGuardBand) / (1.0 + kGuardBand);
+    s.tab.tab32[p] = make_float4(__double2float_ru(lhs * qhi), __double2float_rd(lhs * qlo), (float)ct, icdt);
   }
 }
 
