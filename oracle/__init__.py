@@ -72,6 +72,14 @@ def _bind(lib):
     lib.orc_step.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                              _d, ctypes.c_int, _d, ctypes.c_int, _d, _d, _i64]
     lib.orc_step.restype = ctypes.c_int
+    lib.orc_interaction_scale.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                          _d]
+    lib.orc_interaction_scale.restype = ctypes.c_int
+    lib.orc_adaptive_dt.argtypes = [ctypes.c_double] * 5
+    lib.orc_adaptive_dt.restype = ctypes.c_double
+    lib.orc_step_adaptive.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _d,
+                                      ctypes.c_int, _d, _d, _d, _i64, _d]
+    lib.orc_step_adaptive.restype = ctypes.c_int
     return lib
 
 
@@ -202,6 +210,25 @@ def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None, mags=False)
     return (E, B, sd, M) if mags else (E, B, sd)
 
 
+def interaction_scale(T, W, V, n, D, eta_allow=0.0, lib=None):
+    """(eta_min, v_max) of the adaptive time step (Sec. 2.4) at step n."""
+    lib = lib or load()
+    T, W, V = _f64(T), _f64(W), _f64(V)
+    out = np.zeros(2)
+    _check(lib.orc_interaction_scale(W.shape[1], _p(T), _p(W), _p(V), int(n), int(D), float(eta_allow), _p(out)),
+           "interaction_scale")
+    return float(out[0]), float(out[1])
+
+
+def adaptive_dt(eta_min, v_max, c_dt=0.05, dt_min=1e-15, dt_max=1e-12, lib=None):
+    """dt = c_dt eta_min / v_max clamped to [dt_min, dt_max] (Sec. 2.4)."""
+    lib = lib or load()
+    return float(lib.orc_adaptive_dt(float(eta_min), float(v_max), float(c_dt), float(dt_min), float(dt_max)))
+
+
+ADAPTIVE_PAPER = dict(c_dt=0.05, eta_allow=0.0, dt_min=1e-15, dt_max=1e-12)
+
+
 def velocity(u):
     """v = u / gamma with gamma = sqrt(1 + u.u / c^2), the way the oracle forms it."""
     c = constants()["c"]
@@ -239,6 +266,7 @@ class Run:
         self.E = None
         self.B = None
         self.stats = None
+        self.adaptive_log = []
 
     @property
     def x(self):
@@ -248,17 +276,29 @@ class Run:
     def t(self):
         return self.T[self.n]
 
-    def step(self, nsteps=1, bkind=0, bpar=None, self_on=True):
+    def step(self, nsteps=1, bkind=0, bpar=None, self_on=True, adaptive=None):
+        """nsteps steps; adaptive = dict(c_dt, eta_allow, dt_min, dt_max) chooses each step's dt by the
+        rule of Sec. 2.4 (self fields on) and appends (dt, eta_min, v_max) to self.adaptive_log."""
         bpar = bext_params() if bpar is None else _f64(bpar, 7)
         E = np.zeros((self.N, 3))
         B = np.zeros((self.N, 3))
         stats = np.zeros(4, dtype=np.int64)
+        wp = None if self.weights is None else _p(self.weights)
+        if adaptive is not None:
+            par = np.array([adaptive["c_dt"], adaptive["eta_allow"], adaptive["dt_min"], adaptive["dt_max"]], dtype=float)
+            info = np.zeros(3)
         for _ in range(int(nsteps)):
             if self.n + 1 >= self.T.shape[0]:
                 raise OracleError("history capacity exhausted")
-            st = self.lib.orc_step(self.N, _p(self.T), _p(self.W), _p(self.V), _p(self.u), self.n, self.D,
-                                   self.dt, None if self.weights is None else _p(self.weights), int(bkind),
-                                   _p(bpar), 1 if self_on else 0, _p(E), _p(B), _pi(stats))
+            if adaptive is None:
+                st = self.lib.orc_step(self.N, _p(self.T), _p(self.W), _p(self.V), _p(self.u), self.n, self.D,
+                                       self.dt, wp, int(bkind), _p(bpar), 1 if self_on else 0, _p(E), _p(B),
+                                       _pi(stats))
+            else:
+                st = self.lib.orc_step_adaptive(self.N, _p(self.T), _p(self.W), _p(self.V), _p(self.u), self.n,
+                                                self.D, _p(par), wp, int(bkind), _p(bpar), _p(E), _p(B), _pi(stats),
+                                                _p(info))
+                self.adaptive_log.append(tuple(info.tolist()))
             _check(st, "step")
             self.n += 1
         self.E, self.B = E, B

@@ -34,6 +34,9 @@
  *   - self fields are evaluated at the present positions x^n and time t_n; the background field
  *     at the half-step position x^{n+1/2}; the push is drift (dt/2) - HC kick - drift (dt/2).
  *   - charge of particle j is -e w_j and its mass m_e w_j.
+ *   - adaptive time step (Sec. 2.4): eta_min and v_max come from the retarded solve of step n, with
+ *     v_i(t) the target's stored velocity at slot n; the resulting dt is the one the push from n to
+ *     n+1 uses; with no qualifying pair, or v_max = 0, dt = dt_max.
  */
 #include <math.h>
 #include <stdint.h>
@@ -449,4 +452,71 @@ int orc_step(int64_t N, double* T, double* W, double* V, double* u, int64_t n, i
   free(Bs);
   free(x);
   return st;
+}
+
+/* Interaction scale of the adaptive time step (Sec. 2.4) at step n, from the same retarded solve as the
+   fields: over ordered pairs i != j whose retarded separation |eta_ij| = |x_i^n - w_j(t_r)| is at least
+   eta_allow, eta_min = min |eta_ij| and v_max = max |v_i(t_n) - v_j(t_r)|, with v_i(t_n) the target's
+   stored velocity at slot n and v_j(t_r) the reconstructed retarded velocity (eq:linear, eq:linear2).
+   out[0] = eta_min (+inf when no pair qualifies), out[1] = v_max (0 when none). */
+int orc_interaction_scale(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D,
+                          double eta_allow, double* out) {
+  if (N < 1 || n < 0 || D < 1 || !out) return ORC_ERR_ARG;
+  history h = {N, T, W, V};
+  int64_t k0 = n - D + 1 > 0 ? n - D + 1 : 0;
+  double t = T[n];
+  double emin = INFINITY, vmax = 0.0;
+  int err = ORC_OK;
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : emin) reduction(max : vmax) reduction(| : err)
+  for (int64_t i = 0; i < N; i++) {
+    const double* r = hist_w(&h, n, i);
+    const double* vi = hist_v(&h, n, i);
+    for (int64_t j = 0; j < N; j++) {
+      if (j == i) continue;
+      double w[3], v[3], a[3], tr;
+      int br, nt;
+      int64_t k1;
+      int st = retarded_state(&h, j, r, t, k0, n, w, v, a, &tr, &br, &k1, &nt);
+      if (st != ORC_OK) {
+        err |= st;
+        continue;
+      }
+      double eta[3] = {r[0] - w[0], r[1] - w[1], r[2] - w[2]};
+      double R = sqrt(dot3(eta, eta));
+      if (R < eta_allow) continue;
+      double dv[3] = {vi[0] - v[0], vi[1] - v[1], vi[2] - v[2]};
+      double vr = sqrt(dot3(dv, dv));
+      if (R < emin) emin = R;
+      if (vr > vmax) vmax = vr;
+    }
+  }
+  out[0] = emin;
+  out[1] = vmax;
+  return err;
+}
+
+/* Step size of Sec. 2.4: dt = c_dt eta_min / v_max, then dt <- min(dt_max, max(dt_min, dt)); when no pair
+   qualifies or v_max = 0 the interaction time is unbounded and dt = dt_max. */
+double orc_adaptive_dt(double eta_min, double v_max, double c_dt, double dt_min, double dt_max) {
+  double dt = (v_max > 0.0 && isfinite(eta_min)) ? c_dt * eta_min / v_max : dt_max;
+  return fmin(dt_max, fmax(dt_min, dt));
+}
+
+/* orc_step with the step size of the adaptive rule of Sec. 2.4, computed from the state at step n and
+   used for the push from n to n+1: par = {c_dt, eta_allow, dt_min, dt_max}; info (may be NULL) receives
+   {dt, eta_min, v_max}. */
+int orc_step_adaptive(int64_t N, double* T, double* W, double* V, double* u, int64_t n, int64_t D,
+                      const double* par, const double* wts, int bkind, const double* bpar, double* E, double* B,
+                      int64_t* stats, double* info) {
+  if (!par) return ORC_ERR_ARG;
+  double sc[2];
+  int st = orc_interaction_scale(N, T, W, V, n, D, par[1], sc);
+  if (st != ORC_OK) return st;
+  double dt = orc_adaptive_dt(sc[0], sc[1], par[0], par[2], par[3]);
+  if (info) {
+    info[0] = dt;
+    info[1] = sc[0];
+    info[2] = sc[1];
+  }
+  return orc_step(N, T, W, V, u, n, D, dt, wts, bkind, bpar, 1, E, B, stats);
 }

@@ -529,6 +529,145 @@ def pin_invariances(lib):
     assert np.array_equal(E5[0], E[0]) and np.array_equal(B5[0], B[0])
 
 
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.4 adaptive time step: for charges in uniform motion, with stored slots sampled exactly
+# on their lines, the retarded separation of target i from source j is c tau_ij, where tau_ij is the
+# root of (c^2 - v_j^2) tau^2 - 2 (d.v_j) tau - |d|^2 = 0 (d = x_i^n - x_j^n), and the relative
+# velocity is v_i - v_j; eta_min, v_max and dt = clip(0.05 eta_min / v_max) follow in closed form
+# ---------------------------------------------------------------------------------------------
+def _uniform_history(x_now, v, n, dt, tstamps=None):
+    """Slots 0..n of particles moving on straight lines through x_now at t_n with velocities v."""
+    T = np.array([k * dt for k in range(n + 1)]) if tstamps is None else np.asarray(tstamps, dtype=float)
+    W = x_now[None] + v[None] * (T - T[n])[:, None, None]
+    V = np.broadcast_to(v[None], W.shape).copy()
+    return T, W, V
+
+
+def _uniform_delay(d, v):
+    """Retarded delay tau of a source in uniform motion at present offset d from the target (mp)."""
+    dv = mp.fsum(mp.mpf(float(a)) * mp.mpf(float(b)) for a, b in zip(d, v))
+    dd = mp.fsum(mp.mpf(float(a)) ** 2 for a in d)
+    vv = mp.fsum(mp.mpf(float(a)) ** 2 for a in v)
+    c = mp.mpf(C)
+    return (dv + mp.sqrt(dv * dv + (c * c - vv) * dd)) / (c * c - vv)
+
+
+def _expected_scale(x_now, v, eta_allow):
+    N = x_now.shape[0]
+    emin, vmax = math.inf, 0.0
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                continue
+            R = float(C * _uniform_delay(x_now[i] - x_now[j], v[j]))
+            if R < eta_allow:
+                continue
+            emin = min(emin, R)
+            vmax = max(vmax, float(np.linalg.norm(v[i] - v[j])))
+    return emin, vmax
+
+
+def pin_adaptive_dt_uniform_motion(lib):
+    mp.mp.dps = 40
+    rng = np.random.default_rng(11)
+    n, dt = 30, 1e-15
+    done = 0
+    while done < 10:
+        N = 2 + done % 2
+        x_now = rng.normal(size=(N, 3)) * 3e-5
+        v = rng.normal(size=(N, 3))
+        v *= (rng.uniform(0.05, 0.9, size=N) * C / np.linalg.norm(v, axis=1))[:, None]
+        eta_ref, v_ref = _expected_scale(x_now, v, 0.0)
+        dt_ref = 0.05 * eta_ref / v_ref
+        if not 1e-15 < dt_ref < 1e-12:
+            continue  # the clamps are pinned below; here the step must come from the formula itself
+        done += 1
+        T, W, V = _uniform_history(x_now, v, n, dt)
+        eta, vm = oracle.interaction_scale(T, W, V, n, 64, 0.0, lib=lib)
+        assert abs(eta - eta_ref) <= 1e-12 * eta_ref, (eta, eta_ref)
+        assert abs(vm - v_ref) <= 1e-13 * v_ref, (vm, v_ref)
+        u = v / np.sqrt(1.0 - np.sum(v * v, axis=1) / C ** 2)[:, None]
+        run = oracle.Run(None, u, 64, 1e-15, nmax=1, T0=T, W0=W, V0=V, lib=lib)
+        run.step(1, adaptive=oracle.ADAPTIVE_PAPER)
+        assert abs((run.T[n + 1] - run.T[n]) - dt_ref) <= 1e-12 * dt_ref + 1e-29
+        assert abs(run.adaptive_log[0][0] - dt_ref) <= 1e-12 * dt_ref
+
+
+def pin_adaptive_dt_present_target_velocity(lib):
+    """A charge whose stored velocity changed at the present slot (a kick in the last step): as a target
+    it moves with the new velocity, while its retarded states as a source lie many slots back on its
+    old straight line, so both ends of v_max are known in closed form."""
+    mp.mp.dps = 40
+    n, dt = 40, 1e-15
+    x_now = np.array([[0.0, 0.0, 0.0], [2.0e-6, 1.0e-6, -1.5e-6]])
+    v_old = np.array([[0.0, 0.0, 0.2 * C], [0.1 * C, 0.0, 0.0]])
+    T, W, V = _uniform_history(x_now, v_old, n, dt)
+    v_new = np.array([0.0, -0.7 * C, 0.0])
+    V[n, 0] = v_new
+    tau01 = float(_uniform_delay(x_now[0] - x_now[1], v_old[1]))
+    tau10 = float(_uniform_delay(x_now[1] - x_now[0], v_old[0]))
+    assert min(tau01, tau10) > 3 * dt  # both retarded times lie before slot n - 2
+    eta_ref = C * min(tau01, tau10)
+    v_ref = max(np.linalg.norm(v_new - v_old[1]), np.linalg.norm(v_old[1] - v_old[0]))
+    eta, vm = oracle.interaction_scale(T, W, V, n, 64, 0.0, lib=lib)
+    assert abs(eta - eta_ref) <= 1e-12 * eta_ref and abs(vm - v_ref) <= 1e-13 * v_ref, (eta, eta_ref, vm, v_ref)
+
+
+def pin_adaptive_dt_cutoff_and_clamps(lib):
+    mp.mp.dps = 40
+    n, dt = 20, 1e-15
+    # three charges: 0 and 1 close together, 2 far away; eta_allow between the separations
+    x_now = np.array([[0.0, 0.0, 0.0], [0.4e-6, 0.1e-6, 0.0], [5e-6, -3e-6, 2e-6]])
+    v = np.array([[0.0, 0.0, 0.6 * C], [0.3 * C, 0.0, 0.0], [0.0, 0.1 * C, 0.0]])
+    T, W, V = _uniform_history(x_now, v, n, dt)
+    for eta_allow in (0.0, 2e-6):
+        eta_ref, v_ref = _expected_scale(x_now, v, eta_allow)
+        eta, vm = oracle.interaction_scale(T, W, V, n, 64, eta_allow, lib=lib)
+        assert abs(eta - eta_ref) <= 1e-12 * eta_ref and abs(vm - v_ref) <= 1e-13 * v_ref, (eta_allow, eta, vm)
+    e0, _ = oracle.interaction_scale(T, W, V, n, 64, 0.0, lib=lib)
+    e1, _ = oracle.interaction_scale(T, W, V, n, 64, 2e-6, lib=lib)
+    assert e1 > 2e-6 > e0
+    # every pair below the cutoff: no interaction scale, the step is dt_max
+    eta, vm = oracle.interaction_scale(T, W, V, n, 64, 1.0, lib=lib)
+    assert eta == math.inf and vm == 0.0
+    assert oracle.adaptive_dt(eta, vm, lib=lib) == 1e-12
+    # equal velocities: v_max = 0, the step is dt_max
+    vs = np.broadcast_to(v[0], v.shape).copy()
+    T2, W2, V2 = _uniform_history(x_now, vs, n, dt)
+    eta, vm = oracle.interaction_scale(T2, W2, V2, n, 64, 0.0, lib=lib)
+    assert vm == 0.0 and oracle.adaptive_dt(eta, vm, lib=lib) == 1e-12
+    # a very close, fast pair: 0.05 eta / v far below 1e-15 s, the step is dt_min
+    xc = np.array([[0.0, 0.0, 0.0], [2e-12, 0.0, 0.0]])
+    vc = np.array([[0.0, 0.0, 0.5 * C], [0.0, 0.0, -0.5 * C]])
+    T3, W3, V3 = _uniform_history(xc, vc, n, dt)
+    eta, vm = oracle.interaction_scale(T3, W3, V3, n, 64, 0.0, lib=lib)
+    assert 0.05 * eta / vm < 1e-15 and oracle.adaptive_dt(eta, vm, lib=lib) == 1e-15
+    assert oracle.adaptive_dt(1e-6, 1e3, lib=lib) == 1e-12 and oracle.adaptive_dt(1e-8, 1e5, lib=lib) == 0.05 * 1e-8 / 1e5
+
+
+def pin_heaviside_nonuniform_slots(lib):
+    """Heaviside's field with stored slots at uneven times (the spacing an adaptive step leaves)."""
+    rng = np.random.default_rng(12)
+    n = 40
+    for beta in (0.5, 0.95):
+        for trial in range(6):
+            steps = rng.uniform(0.2e-15, 3e-15, size=n)
+            tst = np.concatenate([[0.0], np.cumsum(steps)])
+            bdir = rng.normal(size=3)
+            bdir /= np.linalg.norm(bdir)
+            vsrc = beta * C * bdir
+            d = rng.normal(size=3)
+            d *= rng.uniform(0.3e-6, 6e-6) / np.linalg.norm(d)
+            x_now = np.stack([d, np.zeros(3)])
+            v = np.stack([np.zeros(3), vsrc])
+            T, W, V = _uniform_history(x_now, v, n, None, tstamps=tst)
+            E, B, _ = _field_on_target(lib, T, W, V, n, 128)
+            Eref, Bref = _heaviside(-QE, vsrc / C, d)
+            scale = np.linalg.norm(Eref)
+            assert np.max(np.abs(E - Eref)) <= 1e-12 * scale, (beta, E, Eref)
+            assert np.max(np.abs(B - Bref)) <= 1e-12 * scale / C
+
+
 PINS = [
     pin_hc_pure_electric,
     pin_hc_pure_magnetic,
@@ -545,4 +684,8 @@ PINS = [
     pin_acceleration_field_from_potentials,
     pin_slow_pair_energy,
     pin_hc_exb_drift,
+    pin_adaptive_dt_uniform_motion,
+    pin_adaptive_dt_cutoff_and_clamps,
+    pin_adaptive_dt_present_target_velocity,
+    pin_heaviside_nonuniform_slots,
 ]

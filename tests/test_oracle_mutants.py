@@ -39,6 +39,14 @@ MUTANTS = [
      "if (!node_test(r, t, h->T[n - 1], hist_w(h, n, j))) {"),
     ("half_width_test", "double ct = C_LIGHT * (t - tk);", "double ct = 0.5 * C_LIGHT * (t - tk);"),
     ("special_keeps_accel", "      a[c] = 0.0;\n", "      a[c] = v1[c] * 1e3;\n"),
+    # Sec. 2.4 adaptive time step
+    ("adapt_target_velocity_old_slot", "const double* vi = hist_v(&h, n, i);", "const double* vi = hist_v(&h, k0, i);"),
+    ("adapt_cutoff_ignored", "if (R < eta_allow) continue;", "if (R < 0.0) continue;"),
+    ("adapt_vrel_sum", "double dv[3] = {vi[0] - v[0], vi[1] - v[1], vi[2] - v[2]};",
+     "double dv[3] = {vi[0] + v[0], vi[1] + v[1], vi[2] + v[2]};"),
+    ("adapt_no_clamp_low", "return fmin(dt_max, fmax(dt_min, dt));", "return fmin(dt_max, dt);"),
+    ("adapt_present_separation", "double eta[3] = {r[0] - w[0], r[1] - w[1], r[2] - w[2]};\n      double R",
+     "double eta[3] = {r[0] - hist_w(&h, n, j)[0], r[1] - hist_w(&h, n, j)[1], r[2] - hist_w(&h, n, j)[2]};\n      double R"),
     # Sec. 2.6 dipole
     ("dipole_factor", "B[c] = k * (3.0 * Mr * rhat[c] - M[c]);", "B[c] = k * (2.0 * Mr * rhat[c] - M[c]);"),
     ("dipole_power", "double k = MU0 / (4.0 * PI) / (r * r * r);", "double k = MU0 / (4.0 * PI) / (r * r);"),
