@@ -99,6 +99,9 @@ typedef struct {
   double pair_ms;          /* device time of the pair evaluations (timing option on, else 0) */
   double step_ms;          /* device time of whole steps (timing option on, else 0) */
   int64_t timed_steps;     /* steps whose events were recorded (the event pool holds 4096 steps) */
+  double dt_last;          /* step size of the last step (s) */
+  double eta_min;          /* adaptive step: min |eta_ij| of the last step's pairs above the cutoff (m), else 0 */
+  double v_max;            /* adaptive step: max |v_i - v_j(t_r)| of the same pairs (m/s), else 0 */
 } emppp_stats;
 
 /* Work split of the pair kernel: items_per_block work items (bunch, source chunk, target tile) per
@@ -280,6 +283,29 @@ EMPPP_API emppp_status emppp_mlp_gradient(const float* params, const float* feat
  * the mean loss of each pass. Synchronous. */
 EMPPP_API emppp_status emppp_mlp_train(float* params, const float* features, const float* targets, int64_t m,
                                        const emppp_mlp_config* cfg, float* loss_per_epoch, void* cuda_stream);
+
+/* ---- adaptive time step (Sec. 2.4) ------------------------------------------------------------------
+ * With enable = 1 every stage-1 step chooses its own size from the retarded solve of its pair
+ * evaluation: over ordered pairs i != j with |eta_ij| >= eta_allow (eta_ij = x_i^n - w_j(t_r)),
+ * eta_min = min |eta_ij| and v_max = max |v_i(t_n) - v_j(t_r)|, and the push from n to n+1 uses
+ * dt = min(dt_max, max(dt_min, c_dt eta_min / v_max)) (dt_max when no pair qualifies or v_max = 0).
+ * The history then holds unevenly spaced slots, which the retarded-time search handles by their time
+ * stamps. The mixed path forms eta_min and v_max in FP32. emppp_stats reports the last step's dt,
+ * eta_min and v_max; emppp_get_state the accumulated time. enable = 0 (or cfg = NULL) returns to the
+ * fixed dt of emppp_create. In a batch the step is common to all bunches (the smallest of theirs); with
+ * pair fields off no pair qualifies and every step is dt_max. Returns EMPPP_ERR_ARG unless c_dt > 0,
+ * eta_allow >= 0 and 0 < dt_min <= dt_max, all finite. The setting is kept until changed, across
+ * emppp_set_particles and emppp_set_history. */
+typedef struct {
+  int32_t enable;
+  int32_t reserved;
+  double c_dt;      /* safety factor C (0.05 in the paper) */
+  double eta_allow; /* lower cutoff of |eta_ij| (m); the paper leaves it open */
+  double dt_min;    /* 1e-15 s in the paper */
+  double dt_max;    /* 1e-12 s in the paper */
+} emppp_adaptive_dt;
+
+EMPPP_API emppp_status emppp_set_adaptive_dt(emppp_handle h, const emppp_adaptive_dt* cfg);
 
 /* Sets the network used by EMPPP_PROPOSAL_MLP (params host or device, EMPPP_MLP_NUM_PARAMS values). */
 EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, int32_t is_device_ptr);

@@ -2,6 +2,7 @@
 // and transport. Every entry point validates its arguments, enqueues work on the handle's stream and
 // returns a status; nothing here aborts or prints.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -74,8 +75,11 @@ struct emppp_ctx {
   unsigned* ord_key = nullptr;
   int* order = nullptr;
   // resident blocks per SM of the pair kernels (queried on first use), per proposal
-  int blocks_fp64[3] = {0, 0, 0};
-  int blocks_mixed[3] = {0, 0, 0};
+  int blocks_fp64[2][3] = {{0, 0, 0}, {0, 0, 0}};   // [adaptive time step][proposal]
+  int blocks_mixed[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  // adaptive time step (Sec. 2.4): the rule, and whether the host mirror of t lags the device
+  AdaptParams adapt{0, 0.05, 0.0, 1e-15, 1e-12};
+  bool t_stale = false;
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
   int64_t steps_acc = 0;  // steps since the last stats reset
@@ -88,7 +92,7 @@ struct emppp_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_launches = 0;        // kernels per replayed step
-  unsigned char graph_key[sizeof(emppp_options) + sizeof(BextParams)];  // configuration of the graph
+  unsigned char graph_key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams)];  // graph's configuration
   bool graph_valid = false;
 };
 
@@ -143,17 +147,20 @@ void invalidate_graph(emppp_handle h) {
 // sources. Uploaded when the configuration changes.
 emppp_status update_schedule(emppp_handle c) {
   const bool mixed = c->opt.precision == EMPPP_MIXED;
+  const int ad = c->adapt.on ? 1 : 0;
   const long long key = (mixed ? 1 : 0) | ((long long)(c->opt.proposal & 3) << 1) |
-                        ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13);
+                        ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13) |
+                        ((long long)ad << 40);
   if (key == c->sched_key) return EMPPP_OK;
-  int& nb = mixed ? c->blocks_mixed[c->opt.proposal % 3] : c->blocks_fp64[c->opt.proposal % 3];
-  if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal) : max_blocks_pair_fp64(c->opt.proposal);
+  int& nb = mixed ? c->blocks_mixed[ad][c->opt.proposal % 3] : c->blocks_fp64[ad][c->opt.proposal % 3];
+  if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal, ad) : max_blocks_pair_fp64(c->opt.proposal, ad);
   // The source chunking (and with it the order of every target's sum) follows the closed-form
   // variant's residency whatever the proposal, so that all proposals give identical fields; only the
   // number of persistent blocks follows the variant that runs.
-  int& nref = mixed ? c->blocks_mixed[EMPPP_PROPOSAL_CLOSED_FORM] : c->blocks_fp64[EMPPP_PROPOSAL_CLOSED_FORM];
+  int& nref = mixed ? c->blocks_mixed[ad][EMPPP_PROPOSAL_CLOSED_FORM] : c->blocks_fp64[ad][EMPPP_PROPOSAL_CLOSED_FORM];
   if (nref <= 0)
-    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM) : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM);
+    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM, ad)
+                 : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM, ad);
   const long long R = (long long)nb * c->num_sms;
   const long long Rsched = (long long)nref * c->num_sms;
   long long total_tiles = 0;
@@ -205,6 +212,17 @@ emppp_status read_err(emppp_handle h) {
                 "4 = non-finite state, 8 = wait limit)",
                 herr);
   }
+  return EMPPP_OK;
+}
+
+// with the adaptive time step the device chooses each step's size: refresh the host mirror of t_n
+emppp_status sync_time(emppp_handle h) {
+  if (!h->t_stale) return EMPPP_OK;
+  StepState hs;
+  CU(cudaMemcpyAsync(&hs, h->ds.state, sizeof(StepState), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  h->t = hs.t;
+  h->t_stale = false;
   return EMPPP_OK;
 }
 
@@ -296,10 +314,14 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   }
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
+    if (h->opt.precision == EMPPP_MIXED) {
+      CU(launch_extrap(h->ds, h->stream));
+      k += 1;
+    }
     if (h->opt.precision == EMPPP_MIXED)
-      CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->launch, h->stream));
+      CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
     else
-      CU(launch_pair_fp64(h->ds, h->opt.proposal, h->launch, h->stream));
+      CU(launch_pair_fp64(h->ds, h->opt.proposal, h->adapt, h->launch, h->stream));
     k += 1;
     if (any_chunked(h)) {
       CU(launch_reduce_partials(h->ds, h->stream));
@@ -307,6 +329,11 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
     }
   } else {
     CU(launch_zero_self(h->ds, h->stream));
+    k += 1;
+  }
+  if (h->adapt.on) {
+    // step size of this step's push from the pair evaluation's interaction scale (Sec. 2.4)
+    CU(launch_adaptive_dt(h->ds, h->adapt, h->stream));
     k += 1;
   }
   if (ev) CU(cudaEventRecord(ev[2], h->stream));
@@ -320,9 +347,11 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
 
 // captures one step into a CUDA graph for the current configuration (options and background field)
 emppp_status capture_step(emppp_handle h, const BextParams& bp) {
-  unsigned char key[sizeof(emppp_options) + sizeof(BextParams)];
+  unsigned char key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams)];
+  memset(key, 0, sizeof(key));
   memcpy(key, &h->opt, sizeof(emppp_options));
   memcpy(key + sizeof(emppp_options), &bp, sizeof(BextParams));
+  memcpy(key + sizeof(emppp_options) + sizeof(BextParams), &h->adapt, sizeof(AdaptParams));
   if (h->graph_valid && memcmp(key, h->graph_key, sizeof(key)) == 0) return EMPPP_OK;
   invalidate_graph(h);
   CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -429,6 +458,9 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.stats, kStatCount);
   ALLOC(s.err, 1);
   ALLOC(s.bsum, (size_t)nbunch * 4);
+  ALLOC(s.scale, 2);
+  ALLOC(s.adapt_info, 3);
+  ALLOC(s.ext32, N * 2);
   ALLOC(c->staging, N * 7);
   ALLOC(c->ord_key, N);
   ALLOC(c->order, N);
@@ -536,7 +568,9 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
   if ((st = set_bunch_frames(h, x, u, true, is_device_ptr)) != EMPPP_OK) return st;
   CU(launch_set_state(h->ds, 0, 0.0, h->dt, 0, du, dw, h->stream));
   CU(launch_init_slot0(h->ds, dx, du, dw, h->stream));
-  h->launches += 2;
+  CU(launch_reset_scale(h->ds, h->stream));
+  h->launches += 3;
+  h->t_stale = false;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
   CU(cudaMemsetAsync(h->ds.Bout, 0, sizeof(double) * N * 3, h->stream));
@@ -602,7 +636,9 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
   }
   const int64_t hs = n - nslots + 1;
   CU(launch_set_state(h->ds, n, hT[nslots - 1], h->dt, hs, du, dw, h->stream));
-  h->launches += 1;
+  CU(launch_reset_scale(h->ds, h->stream));
+  h->launches += 2;
+  h->t_stale = false;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
   CU(cudaMemsetAsync(h->ds.Bout, 0, sizeof(double) * N * 3, h->stream));
@@ -686,7 +722,10 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
     h->pairs_acc += pairs_per_step;
     h->steps_acc += 1;
     h->n += 1;
-    h->t = h->t + h->dt;
+    if (h->adapt.on)
+      h->t_stale = true;  // each step's size is chosen on the device
+    else
+      h->t = h->t + h->dt;
   }
   return EMPPP_OK;
 }
@@ -728,6 +767,7 @@ EMPPP_API emppp_status emppp_transport(emppp_handle h, int64_t nsteps, double dt
   if (!(dt > 0.0) || !(dt < 1e300)) return fail(EMPPP_ERR_ARG, "dt must be positive and finite");
   BextParams bp;
   if ((st = convert_bext(bext, &bp)) != EMPPP_OK) return st;
+  if ((st = sync_time(h)) != EMPPP_OK) return st;
   const int64_t kChunk = 4096;
   for (int64_t done = 0; done < nsteps;) {
     const int k = (int)(nsteps - done < kChunk ? nsteps - done : kChunk);
@@ -762,6 +802,7 @@ EMPPP_API emppp_status emppp_get_state(emppp_handle h, double* x, double* u, dou
   }
   if (u && (st = from_device(h, u, h->ds.u, 3 * N, is_device_ptr)) != EMPPP_OK) return st;
   CU(cudaStreamSynchronize(h->stream));
+  if ((st = sync_time(h)) != EMPPP_OK) return st;
   if (t_now) *t_now = h->t;
   if (n_now) *n_now = h->n;
   return EMPPP_OK;
@@ -806,6 +847,14 @@ EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out) {
   out->pair_ms = pair_ms;
   out->step_ms = step_ms;
   out->timed_steps = h->ev_used;
+  double ai[3] = {h->dt, 0.0, 0.0};
+  if (h->has_state) {
+    CU(cudaMemcpyAsync(ai, h->ds.adapt_info, sizeof(ai), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  out->dt_last = ai[0];
+  out->eta_min = ai[1];
+  out->v_max = ai[2];
   return EMPPP_OK;
 }
 
@@ -821,12 +870,14 @@ emppp_status enqueue_fields(emppp_handle h) {
   CU(launch_prep(h->ds, h->stream));
   const bool ordered = h->opt.precision == EMPPP_MIXED && h->target_order;
   if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->stream));
-  if (h->opt.precision == EMPPP_MIXED)
-    CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->launch, h->stream));
-  else
-    CU(launch_pair_fp64(h->ds, h->opt.proposal, h->launch, h->stream));
+  if (h->opt.precision == EMPPP_MIXED) {
+    CU(launch_extrap(h->ds, h->stream));
+    CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
+  } else {
+    CU(launch_pair_fp64(h->ds, h->opt.proposal, h->adapt, h->launch, h->stream));
+  }
   if (any_chunked(h)) CU(launch_reduce_partials(h->ds, h->stream));
-  h->launches += 3 + (ordered ? 1 : 0);
+  h->launches += 3 + (ordered ? 1 : 0) + (h->opt.precision == EMPPP_MIXED ? 1 : 0);
   return EMPPP_OK;
 }
 
@@ -1081,6 +1132,39 @@ EMPPP_API emppp_status emppp_mlp_train(float* params, const float* features, con
   }
   CU(cudaStreamSynchronize(s));
   return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_set_adaptive_dt(emppp_handle h, const emppp_adaptive_dt* cfg) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  AdaptParams ap;
+  memset(&ap, 0, sizeof(ap));
+  ap.c_dt = 0.05;
+  ap.dt_min = 1e-15;
+  ap.dt_max = 1e-12;
+  if (cfg && cfg->enable) {
+    const bool ok = cfg->c_dt > 0.0 && cfg->c_dt < 1e300 && cfg->eta_allow >= 0.0 && cfg->eta_allow < 1e300 &&
+                    cfg->dt_min > 0.0 && cfg->dt_max >= cfg->dt_min && cfg->dt_max < 1e300;
+    if (!ok) return fail(EMPPP_ERR_ARG, "adaptive step: need c_dt > 0, eta_allow >= 0, 0 < dt_min <= dt_max, all finite");
+    ap.on = 1;
+    ap.c_dt = cfg->c_dt;
+    ap.eta_allow = cfg->eta_allow;
+    ap.dt_min = cfg->dt_min;
+    ap.dt_max = cfg->dt_max;
+  }
+  if ((st = sync_time(h)) != EMPPP_OK) return st;
+  const bool was_on = h->adapt.on != 0;
+  h->adapt = ap;
+  if (was_on && !ap.on && h->has_state) {
+    // back to the fixed step of emppp_create
+    CU(cudaMemcpyAsync(reinterpret_cast<char*>(h->ds.state) + offsetof(StepState, dt), &h->dt, sizeof(double),
+                       cudaMemcpyHostToDevice, h->stream));
+    CU(launch_reset_scale(h->ds, h->stream));  // the reported step size becomes the fixed one
+    h->launches += 1;
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  invalidate_graph(h);
+  return update_schedule(h);
 }
 
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt) {

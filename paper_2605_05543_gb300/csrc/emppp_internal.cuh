@@ -15,6 +15,7 @@
 //   slot_t [D]                time stamp of each physical slot.
 //   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
 //                             1 / (t_{k+1} - t_k) in FP64 and 1 / (c (t_{k+1} - t_k)) in FP32.
+//   ext32  [N][2] float4      per step (mixed path): hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) - origin.
 //   u      [N][3]             present proper velocities (FP64).
 //   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
 //   bunches [nbunch]          offsets, sizes, FP32-split origins and reference velocities.
@@ -119,7 +120,35 @@ struct DeviceState {
   int* err;
   double* bsum;     // [nbunch][4] per-bunch reductions (weighted position sums and weight)
   const void* mlp_image;  // BF16 image of the proposal network (EMPPP_PROPOSAL_MLP), or null
+  // [N][2] FP32 hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) relative to the bunch origin: the end of the
+  // last history segment of eq:linear, from which the mixed path forms near-field retarded points
+  float4* ext32;
+  // adaptive time step (Sec. 2.4)
+  unsigned long long* scale;  // [2] bit patterns of eta_min (m, reduced by min) and v_max^2 ((m/s)^2, by max)
+  double* adapt_info;         // [3] dt, eta_min, v_max of the last adaptive step
 };
+
+// adaptive time-step rule (Sec. 2.4)
+struct AdaptParams {
+  int on;
+  double c_dt, eta_allow, dt_min, dt_max;
+};
+
+// Warp-wide min of eta and max of dv^2, then one atomic per warp into scale. Non-negative doubles order
+// like their bit patterns read as unsigned integers, so the min and max are exact and independent of
+// the order of the pairs. Every lane of the warp must call it.
+__device__ __forceinline__ void reduce_scale(unsigned long long* scale, double emin, double vmax2) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    emin = fmin(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+    vmax2 = fmax(vmax2, __shfl_xor_sync(0xffffffffu, vmax2, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (emin < __longlong_as_double(0x7ff0000000000000LL))
+      atomicMin(scale, (unsigned long long)__double_as_longlong(emin));
+    if (vmax2 > 0.0) atomicMax(scale + 1, (unsigned long long)__double_as_longlong(vmax2));
+  }
+}
 
 struct BextParams {
   int kind;
@@ -161,10 +190,14 @@ cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double
                              const double* u, const double* w, cudaStream_t st);
 cudaError_t launch_prep(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_advance(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_adaptive_dt(const DeviceState& s, const AdaptParams& ap, cudaStream_t st);
+cudaError_t launch_extrap(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_reset_scale(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st);
 // pair_fp64.cu
-int max_blocks_pair_fp64(int proposal);
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunch& pl, cudaStream_t st);
+int max_blocks_pair_fp64(int proposal, bool adapt);
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptParams& ap, const PairLaunch& pl,
+                             cudaStream_t st);
 cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
@@ -188,8 +221,8 @@ cudaError_t launch_mlp_train_pass(const void* image, const float* X, const float
 cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float lr, float b1, float b2, float eps,
                         int step, cudaStream_t st);
 // pair_mixed.cu
-int max_blocks_pair_mixed(int proposal);
-cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairLaunch& pl,
-                              cudaStream_t st);
+int max_blocks_pair_mixed(int proposal, bool adapt);
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const AdaptParams& ap,
+                              const PairLaunch& pl, cudaStream_t st);
 
 }  // namespace emppp

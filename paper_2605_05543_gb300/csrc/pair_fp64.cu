@@ -62,6 +62,8 @@ struct PairArgs {
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
   const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
+  unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
+  double eta_allow;
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -85,7 +87,7 @@ struct Window {
 
 }  // namespace
 
-template <int PROP>
+template <int PROP, bool ADAPT>
 __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   __shared__ int s_item;
   __shared__ mlp::InferImage s_net[1];
@@ -106,6 +108,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const int pprev = win.n > win.k0 ? win.phys(win.n - 1) : pn;  // slot n - 1 (or n)
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
+  double emin = __longlong_as_double(0x7ff0000000000000LL), vmax2 = 0.0;  // adaptive time step (Sec. 2.4)
   int errbits = 0;
 
   // persistent blocks pull (source chunk, target tile) items, chunk-major, until none is left
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
 
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
+  const double vi0 = ADAPT ? rr[3] : 0.0, vi1 = ADAPT ? rr[4] : 0.0, vi2 = ADAPT ? rr[5] : 0.0;  // v_i(t_n)
   float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f;
   if (PROP != kPropBisect) {
     const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
@@ -320,6 +324,12 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     const double pref = kCoulomb * q * R * (ievp * ievp * ievp);
     const double E0 = pref * (c2mv2 * vp0 + ac0), E1 = pref * (c2mv2 * vp1 + ac1), E2 = pref * (c2mv2 * vp2 + ac2);
     const double bs = invR * (1.0 / kC);
+    if (ADAPT && R >= a.eta_allow) {
+      // interaction scale of the adaptive step: |eta_ij| and |v_i(t_n) - v_j(t_r)|
+      emin = fmin(emin, R);
+      const double dv0 = vi0 - v0, dv1 = vi1 - v1, dv2 = vi2 - v2;
+      vmax2 = fmax(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+    }
     Ep[0] += E0;
     Ep[1] += E1;
     Ep[2] += E2;
@@ -357,6 +367,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     }
   }
   }  // work items
+  if (ADAPT) reduce_scale(a.scale, emin, vmax2);
   // counters: one atomic per warp and counter
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
@@ -400,18 +411,34 @@ __global__ void zero_kernel(double* __restrict__ a, double* __restrict__ b, long
   }
 }
 
-int max_blocks_pair_fp64(int proposal) {
+template <bool ADAPT>
+int max_blocks_fp64(int proposal) {
   int nb = 0;
   if (proposal == kPropClosedForm)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm, ADAPT>, kBlock, 0);
   else if (proposal == kPropMlp)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp, ADAPT>, kBlock, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect, ADAPT>, kBlock, 0);
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunch& pl, cudaStream_t st) {
+int max_blocks_pair_fp64(int proposal, bool adapt) {
+  return adapt ? max_blocks_fp64<true>(proposal) : max_blocks_fp64<false>(proposal);
+}
+
+template <bool ADAPT>
+void launch_fp64(int proposal, const PairLaunch& pl, const PairArgs& a, cudaStream_t st) {
+  if (proposal == kPropClosedForm)
+    pair_fp64_kernel<kPropClosedForm, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+  else if (proposal == kPropMlp)
+    pair_fp64_kernel<kPropMlp, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+  else
+    pair_fp64_kernel<kPropBisect, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+}
+
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptParams& ap, const PairLaunch& pl,
+                             cudaStream_t st) {
   PairArgs a;
   a.rec64 = s.rec64;
   a.rec32 = s.rec32;
@@ -433,14 +460,14 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const PairLaunc
   a.nitems = pl.nitems;
   a.work = s.work;
   a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
+  a.scale = s.scale;
+  a.eta_allow = ap.eta_allow;
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  if (proposal == kPropClosedForm)
-    pair_fp64_kernel<kPropClosedForm><<<pl.grid, kBlock, 0, st>>>(a);
-  else if (proposal == kPropMlp)
-    pair_fp64_kernel<kPropMlp><<<pl.grid, kBlock, 0, st>>>(a);
+  if (ap.on)
+    launch_fp64<true>(proposal, pl, a, st);
   else
-    pair_fp64_kernel<kPropBisect><<<pl.grid, kBlock, 0, st>>>(a);
+    launch_fp64<false>(proposal, pl, a, st);
   return cudaGetLastError();
 }
 

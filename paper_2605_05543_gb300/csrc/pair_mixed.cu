@@ -12,6 +12,9 @@
 //   retarded  in light units (lengths in m, velocities as beta = v/c): with L1 = c (t - t1) and d = r - w1,
 //             (1 - beta1^2) s^2 + 2 (d.beta1 - L1) s + (L1^2 - |d|^2) = 0 for s = c (t_r - t1) (eq:dt),
 //             smaller root without cancellation; eta = d - beta1 s (eq:linear, retarded position w1 + v1 dt);
+//             in the near-field shortcut bracket the same point is formed from the segment's end
+//             P = w1 + v1 (t_n - t1) as eta = (r - P) + beta1 tau, tau = c (t_n - t_r) = R, which avoids the
+//             cancellation in L1^2 - |d|^2 when R is far below c (t_n - t_{n-1});
 //             beta = beta1 + (s / (c dt)) (beta2 - beta1), alpha = a / c^2 = (beta2 - beta1) / (c dt)
 //             (eq:linear2 out of history: beta = beta1, alpha = 0); 1 - beta^2 = 1/gamma1^2 - dbeta.(2 beta1
 //             + dbeta), so 1 - beta^2 is never formed by cancellation.
@@ -61,6 +64,9 @@ struct MixedArgs {
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
   const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
+  unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
+  float eta_allow;
+  const float4* __restrict__ ext32;  // [N][2] hi/lo of the end of each source's last history segment
 };
 
 struct Target {
@@ -163,7 +169,7 @@ __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict_
 
 }  // namespace
 
-template <int PROP>
+template <int PROP, bool ADAPT>
 __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
@@ -189,6 +195,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   const float invL = (float)(1.0 / (kC * a.state->dt * D));
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
+  float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
   int errbits = 0;
 
   // persistent blocks pull (source chunk, target tile) items, chunk-major, until none is left
@@ -224,6 +231,15 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
     r.r1 = rr[1];
     r.r2 = rr[2];
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
+  }
+  // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
+  // so relative velocities are formed from these small differences at full FP32 relative precision)
+  float bi0 = 0.f, bi1 = 0.f, bi2 = 0.f;
+  if (ADAPT) {
+    const float4 q2 = a.rec32[((size_t)i * D + pn) * 3 + 2];
+    bi0 = q2.x;
+    bi1 = q2.y;
+    bi2 = q2.z;
   }
 
   const int j_begin = boff + chunk_id * bs.chunk;
@@ -423,13 +439,35 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
         const float L1 = tabA.z;
         const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
         const float ig2 = A.q0.w, g2 = A.q2.w;
-        const float hb = __fsub_rn(dot3(d0, d1, d2, b10, b11, b12), L1);
-        const float C0 = __fmaf_rn(L1, L1, -dot3(d0, d1, d2, d0, d1, d2));
-        const float qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
-        const float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
-        const float s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
-        const float e0 = __fmaf_rn(-b10, s, d0), e1 = __fmaf_rn(-b11, s, d1), e2 = __fmaf_rn(-b12, s, d2);
+        float e0, e1, e2, qd, df;  // eta, the discriminant, and (t_r - t1) / (t2 - t1)
+        if (br == 1) {
+          // near-field shortcut, t_r in [t_{n-1}, t_n]: the retarded point is P - beta1 tau with P the end
+          // of the segment (ext32) and tau = c (t_n - t_r) = R, the positive root of
+          // (1 - beta1^2) tau^2 - 2 (p.beta1) tau - |p|^2 = 0, p = r - P (eq:dt about t_n). Formed this
+          // way, eta keeps FP32 precision when R is far below c (t_n - t_{n-1}).
+          const float3 dp = separation(r, __ldg(a.ext32 + 2 * j), __ldg(a.ext32 + 2 * j + 1));
+          const float pb = dot3(dp.x, dp.y, dp.z, b10, b11, b12);
+          const float pp = dot3(dp.x, dp.y, dp.z, dp.x, dp.y, dp.z);
+          qd = __fmaf_rn(pb, pb, __fmul_rn(ig2, pp));
+          const float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
+          const float tau = (pb <= 0.f) ? __fdividef(pp, __fsub_rn(sq, pb)) : __fmul_rn(__fadd_rn(pb, sq), g2);
+          e0 = __fmaf_rn(b10, tau, dp.x);
+          e1 = __fmaf_rn(b11, tau, dp.y);
+          e2 = __fmaf_rn(b12, tau, dp.z);
+          df = __fmaf_rn(-tau, tabA.w, 1.f);
+        } else {
+          const float hb = __fsub_rn(dot3(d0, d1, d2, b10, b11, b12), L1);
+          const float C0 = __fmaf_rn(L1, L1, -dot3(d0, d1, d2, d0, d1, d2));
+          qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
+          const float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
+          const float s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
+          e0 = __fmaf_rn(-b10, s, d0);
+          e1 = __fmaf_rn(-b11, s, d1);
+          e2 = __fmaf_rn(-b12, s, d2);
+          df = __fmul_rn(s, tabA.w);
+        }
         float be0 = b10, be1 = b11, be2 = b12, al0 = 0.f, al1 = 0.f, al2 = 0.f, ug = ig2;
+        float xs0 = 0.f, xs1 = 0.f, xs2 = 0.f;  // beta(t_r) - beta1 (eq:linear)
         if (br != 0) {
           if (!have_b) q2b = __ldg(src32 + 3 * (pA + 1 == D ? 0 : pA + 1) + 2);
           const float icdt = tabA.w;
@@ -437,8 +475,12 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           al0 = __fmul_rn(db0, icdt);
           al1 = __fmul_rn(db1, icdt);
           al2 = __fmul_rn(db2, icdt);
-          const float df = __fmul_rn(s, icdt);
           const float x0 = __fmul_rn(db0, df), x1 = __fmul_rn(db1, df), x2 = __fmul_rn(db2, df);
+          if (ADAPT) {
+            xs0 = x0;
+            xs1 = x1;
+            xs2 = x2;
+          }
           be0 = __fadd_rn(b10, x0);
           be1 = __fadd_rn(b11, x1);
           be2 = __fadd_rn(b12, x2);
@@ -473,6 +515,13 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           F2 = __fadd_rn(F2, cross1(e0, e1, c0, c1));
         }
         // E = pref F; c B = eta_hat x E = (pref / R) (eta x F), with 1 / c applied once per target
+        if (ADAPT && R >= a.eta_allow) {
+          // interaction scale of the adaptive step: |eta_ij| and |beta_i(t_n) - beta_j(t_r)|, with
+          // beta_j(t_r) - beta_ref = (beta1 - beta_ref) + (beta(t_r) - beta1)
+          emin = fminf(emin, R);
+          const float dv0 = (bi0 - A.q2.x) - xs0, dv1 = (bi1 - A.q2.y) - xs1, dv2 = (bi2 - A.q2.z) - xs2;
+          vmax2 = fmaxf(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+        }
         P[0] = __fmaf_rn(pref, F0, P[0]);
         P[1] = __fmaf_rn(pref, F1, P[1]);
         P[2] = __fmaf_rn(pref, F2, P[2]);
@@ -518,6 +567,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
     }
   }
   }  // work items
+  if (ADAPT) reduce_scale(a.scale, (double)emin, (double)vmax2 * (kC * kC));
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
   n_bi = __reduce_add_sync(0xffffffffu, n_bi);
@@ -534,19 +584,34 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   }
 }
 
-int max_blocks_pair_mixed(int proposal) {
+template <bool ADAPT>
+int max_blocks_mixed(int proposal) {
   int nb = 0;
   if (proposal == kPropClosedForm)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropClosedForm>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropClosedForm, ADAPT>, kBlock, 0);
   else if (proposal == kPropMlp)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropMlp>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropMlp, ADAPT>, kBlock, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropBisect>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropBisect, ADAPT>, kBlock, 0);
   return nb > 0 ? nb : 1;
 }
 
-cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const PairLaunch& pl,
-                              cudaStream_t st) {
+int max_blocks_pair_mixed(int proposal, bool adapt) {
+  return adapt ? max_blocks_mixed<true>(proposal) : max_blocks_mixed<false>(proposal);
+}
+
+template <bool ADAPT>
+void launch_mixed(int proposal, const PairLaunch& pl, const MixedArgs& a, cudaStream_t st) {
+  if (proposal == kPropClosedForm)
+    pair_mixed_kernel<kPropClosedForm, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+  else if (proposal == kPropMlp)
+    pair_mixed_kernel<kPropMlp, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+  else
+    pair_mixed_kernel<kPropBisect, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+}
+
+cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const AdaptParams& ap,
+                              const PairLaunch& pl, cudaStream_t st) {
   MixedArgs a;
   a.rec32 = reinterpret_cast<const float4*>(s.rec32);
   a.rec64 = s.rec64;
@@ -568,14 +633,15 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.nitems = pl.nitems;
   a.work = s.work;
   a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
+  a.scale = s.scale;
+  a.eta_allow = (float)ap.eta_allow;
+  a.ext32 = s.ext32;
   cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  if (proposal == kPropClosedForm)
-    pair_mixed_kernel<kPropClosedForm><<<pl.grid, kBlock, 0, st>>>(a);
-  else if (proposal == kPropMlp)
-    pair_mixed_kernel<kPropMlp><<<pl.grid, kBlock, 0, st>>>(a);
+  if (ap.on)
+    launch_mixed<true>(proposal, pl, a, st);
   else
-    pair_mixed_kernel<kPropBisect><<<pl.grid, kBlock, 0, st>>>(a);
+    launch_mixed<false>(proposal, pl, a, st);
   return cudaGetLastError();
 }
 

@@ -122,6 +122,52 @@ __global__ void prep_kernel(DeviceState s) {
   }
 }
 
+// Adaptive time step (Sec. 2.4): dt = c_dt eta_min / v_max from the pair kernel's reduction, clamped to
+// [dt_min, dt_max] (dt_max when no pair qualified or v_max = 0); it becomes the step size of this step's
+// push. The reduction is then reset for the next step.
+__global__ void adaptive_dt_kernel(DeviceState s, AdaptParams ap) {
+  const double eta_min = __longlong_as_double((long long)s.scale[0]);
+  const double v_max = sqrt(__longlong_as_double((long long)s.scale[1]));
+  const bool bounded = v_max > 0.0 && eta_min < __longlong_as_double(0x7ff0000000000000LL);
+  const double dt = fmin(ap.dt_max, fmax(ap.dt_min, bounded ? ap.c_dt * eta_min / v_max : ap.dt_max));
+  s.state->dt = dt;
+  s.adapt_info[0] = dt;
+  s.adapt_info[1] = bounded ? eta_min : 0.0;
+  s.adapt_info[2] = v_max;
+  s.scale[0] = (unsigned long long)0x7ff0000000000000ULL;  // +inf
+  s.scale[1] = 0ull;
+}
+
+// End of the last history segment of each source, P_j = w_{j,n-1} + v_{j,n-1} (t_n - t_{n-1}) (eq:linear at
+// t_n), split hi/lo about the bunch origin. For a pair in the near-field shortcut bracket [n-1, n] the
+// mixed path writes the retarded point as P_j - v_{j,n-1} tau with tau = t_n - t_r, which is the same point
+// as w_{j,n-1} + v_{j,n-1} (t_r - t_{n-1}) but keeps FP32 precision when c tau is far below c (t_n - t_{n-1}).
+__global__ void extrap_kernel(DeviceState s) {
+  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= s.N) return;
+  const StepState st = *s.state;
+  if (st.n <= st.k0) return;  // no segment [n-1, n] in the window
+  const int pn = st.pn;
+  const int p1 = pn == 0 ? s.D - 1 : pn - 1;
+  const double dtl = s.slot_t[pn] - s.slot_t[p1];
+  const double* r = s.rec64 + ((size_t)j * s.D + p1) * 6;
+  const BunchDesc& bd = s.bunches[s.bunch_of[j]];
+  const double d0 = (r[0] + r[3] * dtl) - bd.origin[0];
+  const double d1 = (r[1] + r[4] * dtl) - bd.origin[1];
+  const double d2 = (r[2] + r[5] * dtl) - bd.origin[2];
+  const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
+  s.ext32[2 * j] = make_float4(h0, h1, h2, 0.f);
+  s.ext32[2 * j + 1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.f);
+}
+
+__global__ void reset_scale_kernel(DeviceState s) {
+  s.scale[0] = (unsigned long long)0x7ff0000000000000ULL;
+  s.scale[1] = 0ull;
+  s.adapt_info[0] = s.state->dt;
+  s.adapt_info[1] = 0.0;
+  s.adapt_info[2] = 0.0;
+}
+
 __global__ void advance_kernel(StepState* state) {
   state->n = state->n + 1;
   state->t = state->t + state->dt;
@@ -168,6 +214,21 @@ cudaError_t launch_prep(const DeviceState& s, cudaStream_t st) {
 
 cudaError_t launch_advance(const DeviceState& s, cudaStream_t st) {
   advance_kernel<<<1, 1, 0, st>>>(s.state);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adaptive_dt(const DeviceState& s, const AdaptParams& ap, cudaStream_t st) {
+  adaptive_dt_kernel<<<1, 1, 0, st>>>(s, ap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_extrap(const DeviceState& s, cudaStream_t st) {
+  extrap_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reset_scale(const DeviceState& s, cudaStream_t st) {
+  reset_scale_kernel<<<1, 1, 0, st>>>(s);
   return cudaGetLastError();
 }
 

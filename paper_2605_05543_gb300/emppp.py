@@ -63,7 +63,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int64), ("pairs", ctypes.c_int64), ("out_of_history", ctypes.c_int64),
                 ("shortcut", ctypes.c_int64), ("bisection", ctypes.c_int64), ("node_tests", ctypes.c_int64),
                 ("guard_fallbacks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("pair_ms", ctypes.c_double),
-                ("step_ms", ctypes.c_double), ("timed_steps", ctypes.c_int64)]
+                ("step_ms", ctypes.c_double), ("timed_steps", ctypes.c_int64), ("dt_last", ctypes.c_double),
+                ("eta_min", ctypes.c_double), ("v_max", ctypes.c_double)]
+
+
+class AdaptiveDt(ctypes.Structure):
+    _fields_ = [("enable", ctypes.c_int32), ("reserved", ctypes.c_int32), ("c_dt", ctypes.c_double),
+                ("eta_allow", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double)]
 
 
 _vp = ctypes.c_void_p
@@ -101,6 +107,7 @@ SIGNATURES = {
     "emppp_mlp_gradient": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, _vp, ctypes.POINTER(ctypes.c_double), _vp]),
     "emppp_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(MlpConfig), _vp, _vp]),
     "emppp_set_proposal": (ctypes.c_int, [_H, _vp, ctypes.c_int32]),
+    "emppp_set_adaptive_dt": (ctypes.c_int, [_H, ctypes.POINTER(AdaptiveDt)]),
     "emppp_last_error": (ctypes.c_char_p, []),
     "emppp_version": (ctypes.c_char_p, []),
 }
@@ -336,6 +343,13 @@ class Solver:
         s = Stats()
         _check(self.lib.emppp_get_stats(self._h, ctypes.byref(s)))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def set_adaptive_dt(self, enable=True, c_dt=0.05, eta_allow=0.0, dt_min=1e-15, dt_max=1e-12):
+        """Adaptive time step of Sec. 2.4 (the paper's C = 0.05 and [1e-15, 1e-12] s by default); enable=False
+        returns to the fixed dt."""
+        cfg = AdaptiveDt(enable=1 if enable else 0, c_dt=float(c_dt), eta_allow=float(eta_allow), dt_min=float(dt_min),
+                         dt_max=float(dt_max))
+        _check(self.lib.emppp_set_adaptive_dt(self._h, ctypes.byref(cfg)))
 
     def reset_stats(self):
         _check(self.lib.emppp_reset_stats(self._h))
