@@ -80,6 +80,10 @@ def _bind(lib):
     lib.orc_step_adaptive.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _d,
                                       ctypes.c_int, _d, _d, _d, _i64, _d]
     lib.orc_step_adaptive.restype = ctypes.c_int
+    lib.orc_mean_kinetic_energy.argtypes = [ctypes.c_int64, _d, _d]
+    lib.orc_mean_kinetic_energy.restype = ctypes.c_double
+    lib.orc_energy_switch.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_double, ctypes.c_int64, _d]
+    lib.orc_energy_switch.restype = ctypes.c_int64
     return lib
 
 
@@ -227,6 +231,24 @@ def adaptive_dt(eta_min, v_max, c_dt=0.05, dt_min=1e-15, dt_max=1e-12, lib=None)
 
 
 ADAPTIVE_PAPER = dict(c_dt=0.05, eta_allow=0.0, dt_min=1e-15, dt_max=1e-12)
+
+
+def mean_kinetic_energy(u, weights=None, lib=None):
+    """Weighted mean kinetic energy per electron (J) of Sec. 2.7."""
+    lib = lib or load()
+    u = _f64(u)
+    w = None if weights is None else _f64(weights)
+    return float(lib.orc_mean_kinetic_energy(u.shape[0], _p(u), None if w is None else _p(w)))
+
+
+def energy_switch(T, E, eps, hold=1, lib=None):
+    """(n_sw, rates) of the switching criterion |dE/dt| < eps of Sec. 2.7 on a record E(T); n_sw = -1
+    when the criterion never holds for `hold` consecutive steps."""
+    lib = lib or load()
+    T, E = _f64(T), _f64(E)
+    rate = np.zeros(T.shape[0])
+    n = int(lib.orc_energy_switch(T.shape[0], _p(T), _p(E), float(eps), int(hold), _p(rate)))
+    return n, rate
 
 
 def velocity(u):

@@ -37,6 +37,12 @@
  *   - adaptive time step (Sec. 2.4): eta_min and v_max come from the retarded solve of step n, with
  *     v_i(t) the target's stored velocity at slot n; the resulting dt is the one the push from n to
  *     n+1 uses; with no qualifying pair, or v_max = 0, dt = dt_max.
+ *   - stage switch (Sec. 2.7): E_i is the kinetic energy (gamma_i - 1) m_e c^2 per represented
+ *     electron, so the weighted mean is the mean energy per electron; dE/dt at step n is the backward
+ *     difference (E_n - E_{n-1}) / (t_n - t_{n-1}); the criterion arms once |dE/dt| >= eps_E (the rate
+ *     "falls below" the threshold, so a bunch at rest does not switch at once); the switch step is the
+ *     first n at which |dE/dt| < eps_E has held, after arming, for `hold` consecutive steps, n being the
+ *     last of them.
  */
 #include <math.h>
 #include <stdint.h>
@@ -519,4 +525,38 @@ int orc_step_adaptive(int64_t N, double* T, double* W, double* V, double* u, int
     info[2] = sc[1];
   }
   return orc_step(N, T, W, V, u, n, D, dt, wts, bkind, bpar, 1, E, B, stats);
+}
+
+/* Mean kinetic energy of Sec. 2.7: E = sum_i w_i E_i / sum_i w_i with E_i = (gamma_i - 1) m_e c^2 and
+   gamma_i = sqrt(1 + u_i.u_i / c^2); w = NULL means unit weights. Returns J (per electron). gamma - 1 is
+   written as (u.u / c^2) / (gamma + 1), the same quantity without the cancellation of 1 from gamma. */
+double orc_mean_kinetic_energy(int64_t N, const double* u, const double* w) {
+  csum num = {0.0, 0.0}, den = {0.0, 0.0};
+  for (int64_t i = 0; i < N; i++) {
+    double wi = w ? w[i] : 1.0;
+    double uu = dot3(u + 3 * i, u + 3 * i) / (C_LIGHT * C_LIGHT);
+    double Ei = uu / (gamma_of_u(u + 3 * i) + 1.0) * M_E * C_LIGHT * C_LIGHT;
+    csum_add(&num, wi * Ei);
+    csum_add(&den, wi);
+  }
+  return csum_get(&num) / csum_get(&den);
+}
+
+/* Switching step of Sec. 2.7 from a record of the mean energy E[0..m-1] at times T[0..m-1], with the
+   backward difference r_k = (E[k] - E[k-1]) / (T[k] - T[k-1]): the criterion arms at the first k with
+   |r_k| >= eps; the switch step is the first n at which |r_k| < eps held for the `hold` steps
+   k = n - hold + 1 .. n, all after arming. rate[k] (may be NULL) receives r_k (rate[0] = 0). Returns -1
+   when no step qualifies. */
+int64_t orc_energy_switch(int64_t m, const double* T, const double* E, double eps, int64_t hold, double* rate) {
+  int64_t run = 0, found = -1;
+  int armed = 0;
+  if (rate && m > 0) rate[0] = 0.0;
+  for (int64_t n = 1; n < m; n++) {
+    double r = (E[n] - E[n - 1]) / (T[n] - T[n - 1]);
+    if (rate) rate[n] = r;
+    if (fabs(r) >= eps) armed = 1;
+    run = (armed && fabs(r) < eps) ? run + 1 : 0;
+    if (found < 0 && run >= hold) found = n;
+  }
+  return found;
 }

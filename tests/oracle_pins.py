@@ -668,6 +668,100 @@ def pin_heaviside_nonuniform_slots(lib):
             assert np.max(np.abs(B - Bref)) <= 1e-12 * scale / C
 
 
+# ---------------------------------------------------------------------------------------------
+# Sec. 2.7 stage switch: the mean kinetic energy per electron and the criterion |dE/dt| < eps_E
+# ---------------------------------------------------------------------------------------------
+def pin_mean_energy_closed_forms(lib):
+    mc2 = ME * C * C
+    # gamma = 3 exactly: u = c sqrt(8)
+    u = np.array([[0.0, 0.0, C * math.sqrt(8.0)], [C * math.sqrt(8.0), 0.0, 0.0]])
+    assert abs(oracle.mean_kinetic_energy(u, lib=lib) - 2.0 * mc2) <= 1e-15 * 2.0 * mc2
+    # non-relativistic limit: (gamma - 1) m c^2 = m u^2 / 2 (1 - (3/4) u^2 / c^2 + ...)
+    rng = np.random.default_rng(21)
+    u = rng.normal(size=(50, 3)) * 1e3
+    ek = 0.5 * ME * np.sum(u * u, axis=1)
+    assert abs(oracle.mean_kinetic_energy(u, lib=lib) - ek.mean()) <= 1e-9 * ek.mean()
+    # weights: a particle of weight 2 counts as two copies of itself
+    u = rng.normal(size=(7, 3)) * 1e8
+    w = np.ones(7)
+    w[3] = 2.0
+    dup = np.concatenate([u, u[3:4]])
+    a = oracle.mean_kinetic_energy(u, w, lib=lib)
+    b = oracle.mean_kinetic_energy(dup, lib=lib)
+    assert abs(a - b) <= 1e-15 * b, (a, b)
+    g = np.sqrt(1.0 + np.sum(u * u, axis=1) / C ** 2)
+    assert ((g - 1).min() * mc2) <= a <= ((g - 1).max() * mc2)
+
+
+def pin_energy_switch_semantics(lib):
+    """Arming, hold and the absolute value, on records whose backward differences are set by hand."""
+    def record(rates):
+        T = np.arange(len(rates) + 1, dtype=float) * 2.0
+        E = np.concatenate([[10.0], 10.0 + np.cumsum(np.asarray(rates) * 2.0)])
+        return T, E
+    T, E = record([5, 5, 0.5, 0.5, 5, 0.5, 0.5, 0.5])
+    assert [oracle.energy_switch(T, E, 1.0, h, lib=lib)[0] for h in (1, 2, 3, 4)] == [3, 4, 8, -1]
+    T, E = record([-5, -5, -0.5, -0.5])           # a decreasing energy falls below the threshold too
+    assert oracle.energy_switch(T, E, 1.0, 1, lib=lib)[0] == 3
+    T, E = record([0.1, 0.2, 5, 0.3])             # below the threshold before arming does not count
+    assert oracle.energy_switch(T, E, 1.0, 1, lib=lib)[0] == 4
+    n, rate = oracle.energy_switch(T, E, 1.0, 1, lib=lib)
+    assert np.allclose(rate[1:], [0.1, 0.2, 5, 0.3], rtol=1e-12, atol=0)
+
+
+def pin_energy_switch_magnetic(lib):
+    """A magnetic field does no work: in a uniform B the mean energy stays constant to rounding, the
+    rate never reaches the threshold, and the criterion never arms."""
+    u = np.array([[0.3 * C, 0.0, 2.0 * C], [0.0, -0.4 * C, 1.5 * C]])
+    x = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])  # far apart: self fields negligible
+    run = oracle.Run(x, u, D=4, dt=1e-12, nmax=50, lib=lib)
+    par = oracle.bext_params(1, b=(0.0, 0.3, 1.0))
+    T, E = [0.0], [oracle.mean_kinetic_energy(run.u, lib=lib)]
+    for _ in range(50):
+        run.step(1, bkind=1, bpar=par, self_on=False)
+        T.append(run.t)
+        E.append(oracle.mean_kinetic_energy(run.u, lib=lib))
+    E = np.array(E)
+    assert np.max(np.abs(E - E[0])) <= 1e-13 * E[0]
+    eps = 1e-3 * E[0] / 1e-12  # a rate that changes E by 1e-3 of itself per step
+    assert oracle.energy_switch(np.array(T), E, eps, 1, lib=lib)[0] == -1
+
+
+def pin_energy_switch_coulomb_pair(lib):
+    """Two electrons released at rest 10 nm apart. Each gains half the Coulomb energy released,
+    E(r) = (k e^2 / 2)(1/d0 - 1/r), and m rdot^2 / 4 = k e^2 (1/d0 - 1/r), so dE/dt = (k e^2 / 2) rdot / r^2
+    is a function of r alone: zero at rest, a peak, then a decay. With eps at a fifth of the peak, the
+    switch step is where that rate, at the run's own separation, has decayed to eps."""
+    d0 = 1e-8
+    ke2 = K_C * QE * QE
+    x = np.array([[0.0, 0.0, -d0 / 2], [0.0, 0.0, d0 / 2]])
+    u = np.zeros((2, 3))
+    t_dyn = d0 / math.sqrt(ke2 / d0 / ME)
+    dt = 2e-3 * t_dyn
+    steps = 4000
+
+    def rate_of_r(r):
+        return 0.5 * ke2 * np.sqrt(4.0 * ke2 / ME * (1.0 / d0 - 1.0 / r)) / r ** 2
+
+    rs = d0 * np.linspace(1.0, 40.0, 400001)[1:]
+    eps = 0.2 * rate_of_r(rs).max()
+    run = oracle.Run(x, u, D=16, dt=dt, nmax=steps, lib=lib)
+    T, E, R = [0.0], [0.0], [d0]
+    for _ in range(steps):
+        run.step(1)
+        T.append(run.t)
+        E.append(oracle.mean_kinetic_energy(run.u, lib=lib))
+        R.append(float(np.linalg.norm(run.x[1] - run.x[0])))
+    T, E, R = np.array(T), np.array(E), np.array(R)
+    Eref = 0.5 * ke2 * (1.0 / d0 - 1.0 / R)
+    assert np.max(np.abs(E - Eref)) <= 5e-3 * 0.5 * ke2 / d0
+    n, rate = oracle.energy_switch(T, E, eps, 1, lib=lib)
+    assert 10 < n < steps, n
+    assert R[n] > 1.5 * d0  # past the peak of the rate
+    assert rate_of_r(R[n]) <= 1.02 * eps and rate_of_r(R[n - 1]) >= 0.98 * eps, (rate_of_r(R[n]) / eps,
+                                                                             rate_of_r(R[n - 1]) / eps)
+
+
 PINS = [
     pin_hc_pure_electric,
     pin_hc_pure_magnetic,
@@ -688,4 +782,8 @@ PINS = [
     pin_adaptive_dt_cutoff_and_clamps,
     pin_adaptive_dt_present_target_velocity,
     pin_heaviside_nonuniform_slots,
+    pin_mean_energy_closed_forms,
+    pin_energy_switch_semantics,
+    pin_energy_switch_magnetic,
+    pin_energy_switch_coulomb_pair,
 ]

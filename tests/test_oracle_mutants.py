@@ -47,6 +47,14 @@ MUTANTS = [
     ("adapt_no_clamp_low", "return fmin(dt_max, fmax(dt_min, dt));", "return fmin(dt_max, dt);"),
     ("adapt_present_separation", "double eta[3] = {r[0] - w[0], r[1] - w[1], r[2] - w[2]};\n      double R",
      "double eta[3] = {r[0] - hist_w(&h, n, j)[0], r[1] - hist_w(&h, n, j)[1], r[2] - hist_w(&h, n, j)[2]};\n      double R"),
+    # Sec. 2.7 stage switch
+    ("energy_includes_rest_mass", "double Ei = uu / (gamma_of_u(u + 3 * i) + 1.0) * M_E * C_LIGHT * C_LIGHT;",
+     "double Ei = (uu / (gamma_of_u(u + 3 * i) + 1.0) + 1.0) * M_E * C_LIGHT * C_LIGHT;"),
+    ("energy_weight_squared", "csum_add(&num, wi * Ei);", "csum_add(&num, wi * wi * Ei);"),
+    ("switch_not_armed", "run = (armed && fabs(r) < eps) ? run + 1 : 0;", "run = (fabs(r) < eps) ? run + 1 : 0;"),
+    ("switch_signed_rate", "run = (armed && fabs(r) < eps) ? run + 1 : 0;", "run = (armed && r < eps) ? run + 1 : 0;"),
+    ("switch_time_base", "double r = (E[n] - E[n - 1]) / (T[n] - T[n - 1]);", "double r = (E[n] - E[n - 1]) / (T[n] - T[0]);"),
+    ("switch_first_of_hold", "if (found < 0 && run >= hold) found = n;", "if (found < 0 && run >= hold) found = n - hold + 1;"),
     # Sec. 2.6 dipole
     ("dipole_factor", "B[c] = k * (3.0 * Mr * rhat[c] - M[c]);", "B[c] = k * (2.0 * Mr * rhat[c] - M[c]);"),
     ("dipole_power", "double k = MU0 / (4.0 * PI) / (r * r * r);", "double k = MU0 / (4.0 * PI) / (r * r);"),
