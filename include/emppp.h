@@ -307,6 +307,74 @@ typedef struct {
 
 EMPPP_API emppp_status emppp_set_adaptive_dt(emppp_handle h, const emppp_adaptive_dt* cfg);
 
+/* ---- stage switch by the energy criterion (Sec. 2.7) -------------------------------------------------
+ * With enable = 1, after every stage-1 step the device forms each bunch's mean kinetic energy per
+ * electron, E(t) = sum_i w_i (gamma_i - 1) m_e c^2 / sum_i w_i, and its backward difference
+ * dE/dt = (E_n - E_{n-1}) / (t_n - t_{n-1}). The criterion arms once |dE/dt| >= eps_E; the bunch's switch
+ * step is then the first step at which |dE/dt| < eps_E has held for `hold` consecutive steps. Enabling
+ * starts the record at the present state; emppp_set_particles and emppp_set_history restart it. The paper
+ * takes eps_E = 30 keV/s or less: 30e3 * 1.602176634e-19 J/s. Returns EMPPP_ERR_ARG unless eps_E > 0 and
+ * hold >= 1; enable = 0 (or cfg = NULL) turns the monitor off. */
+typedef struct {
+  int32_t enable;
+  int32_t hold;
+  double eps_E; /* J/s per electron */
+} emppp_energy_monitor;
+
+typedef struct {
+  double ebar;      /* mean kinetic energy per electron at the present step (J) */
+  double rate;      /* dE/dt over the last step (J/s); 0 right after the record starts */
+  double t_sw;      /* time of the switch step (s), 0 before */
+  int64_t n_sw;     /* switch step, -1 before */
+  int32_t armed;    /* |dE/dt| has reached eps_E */
+  int32_t switched; /* the criterion has held */
+} emppp_energy_state;
+
+EMPPP_API emppp_status emppp_set_energy_monitor(emppp_handle h, const emppp_energy_monitor* cfg);
+/* Per-bunch record (out: one entry per bunch). EMPPP_ERR_STATE while the monitor is off. Synchronises. */
+EMPPP_API emppp_status emppp_get_energy(emppp_handle h, emppp_energy_state* out);
+
+/* The two-stage procedure of Sec. 2.7 on this handle:
+ *   1. from the initial state (x0, u0, w0; host or device, as emppp_set_particles takes them) step the
+ *      full EM-PP model with the energy monitor on, checking every check_every steps, until every bunch
+ *      has met the criterion or max_stage1_steps have run. The threshold step n_th (time t_th, the
+ *      paper's first crossing) is the latest of the bunches' criterion steps (max_stage1_steps when one
+ *      never meets it);
+ *   2. restart from the same initial state and step the full model past the threshold to the switch
+ *      time t_sw = t_th + t_after (the paper keeps the coupled model on for some time after the first
+ *      crossing: t_sw > t_th); the first n_th steps reproduce the monitoring run bit for bit;
+ *   3. if do_handoff, translate each bunch so that its centroid sits at `center` (emppp_handoff); then
+ *      push steps2 steps of dt2 in the background field bext2 alone (emppp_transport).
+ * The adaptive time step, options and tuning of the handle apply to both stage-1 runs. The energy
+ * monitor stays on afterwards with eps_E and hold. Returns the first failing status of the calls above. */
+typedef struct {
+  double eps_E;
+  int32_t hold;
+  int32_t do_handoff;
+  int64_t max_stage1_steps;
+  int64_t check_every;
+  double t_after;     /* coupled time kept after the threshold (s, >= 0) */
+  emppp_bext bext1;   /* stage-1 background field */
+  double center[3];   /* handoff target of each bunch's centroid */
+  double dt2;         /* stage-2 step (s) */
+  int64_t steps2;
+  emppp_bext bext2;   /* stage-2 background field (the dipole, Sec. 2.6) */
+} emppp_two_stage_config;
+
+typedef struct {
+  int64_t n_th;                    /* threshold step (first crossing) */
+  double t_th;                     /* its time (s) */
+  int64_t n_sw;                    /* stage-1 steps of the re-run: the first step with t >= t_th + t_after */
+  double t_sw;                     /* time at n_sw (s) */
+  int64_t stage1_steps_first_run;  /* steps of the monitoring run */
+  int32_t switched;                /* 1 if every bunch met the criterion before the cap */
+  int32_t pad_;
+} emppp_two_stage_report;
+
+EMPPP_API emppp_status emppp_two_stage(emppp_handle h, const double* x0, const double* u0, const double* w0,
+                                       int32_t is_device_ptr, const emppp_two_stage_config* cfg,
+                                       emppp_two_stage_report* rep);
+
 /* Sets the network used by EMPPP_PROPOSAL_MLP (params host or device, EMPPP_MLP_NUM_PARAMS values). */
 EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, int32_t is_device_ptr);
 

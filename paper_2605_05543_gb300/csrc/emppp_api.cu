@@ -80,6 +80,9 @@ struct emppp_ctx {
   // adaptive time step (Sec. 2.4): the rule, and whether the host mirror of t lags the device
   AdaptParams adapt{0, 0.05, 0.0, 1e-15, 1e-12};
   bool t_stale = false;
+  // stage-switch monitor (Sec. 2.7): criterion and per-bunch device record
+  EnergyParams energy{0, 1, 0.0};
+  EnergyMon* d_mon = nullptr;
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
   int64_t steps_acc = 0;  // steps since the last stats reset
@@ -92,7 +95,8 @@ struct emppp_ctx {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_launches = 0;        // kernels per replayed step
-  unsigned char graph_key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams)];  // graph's configuration
+  unsigned char graph_key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams) +
+                          sizeof(EnergyParams)];  // configuration of the graph
   bool graph_valid = false;
 };
 
@@ -340,6 +344,11 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   CU(launch_push(h->ds, bp, h->stream));
   CU(launch_advance(h->ds, h->stream));
   k += 2;
+  if (h->energy.on) {
+    // mean energy of the new state and the switch criterion (Sec. 2.7)
+    CU(launch_energy(h->ds, h->energy, h->d_mon, false, h->stream));
+    k += 1;
+  }
   if (ev) CU(cudaEventRecord(ev[3], h->stream));
   *nkernels = k;
   return EMPPP_OK;
@@ -347,11 +356,12 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
 
 // captures one step into a CUDA graph for the current configuration (options and background field)
 emppp_status capture_step(emppp_handle h, const BextParams& bp) {
-  unsigned char key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams)];
+  unsigned char key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams) + sizeof(EnergyParams)];
   memset(key, 0, sizeof(key));
   memcpy(key, &h->opt, sizeof(emppp_options));
   memcpy(key + sizeof(emppp_options), &bp, sizeof(BextParams));
   memcpy(key + sizeof(emppp_options) + sizeof(BextParams), &h->adapt, sizeof(AdaptParams));
+  memcpy(key + sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams), &h->energy, sizeof(EnergyParams));
   if (h->graph_valid && memcmp(key, h->graph_key, sizeof(key)) == 0) return EMPPP_OK;
   invalidate_graph(h);
   CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
@@ -461,6 +471,7 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.scale, 2);
   ALLOC(s.adapt_info, 3);
   ALLOC(s.ext32, N * 2);
+  ALLOC(c->d_mon, (size_t)nbunch);
   ALLOC(c->staging, N * 7);
   ALLOC(c->ord_key, N);
   ALLOC(c->order, N);
@@ -570,6 +581,10 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
   CU(launch_init_slot0(h->ds, dx, du, dw, h->stream));
   CU(launch_reset_scale(h->ds, h->stream));
   h->launches += 3;
+  if (h->energy.on) {
+    CU(launch_energy(h->ds, h->energy, h->d_mon, true, h->stream));
+    h->launches += 1;
+  }
   h->t_stale = false;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
@@ -638,6 +653,10 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
   CU(launch_set_state(h->ds, n, hT[nslots - 1], h->dt, hs, du, dw, h->stream));
   CU(launch_reset_scale(h->ds, h->stream));
   h->launches += 2;
+  if (h->energy.on) {
+    CU(launch_energy(h->ds, h->energy, h->d_mon, true, h->stream));
+    h->launches += 1;
+  }
   h->t_stale = false;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
   CU(cudaMemsetAsync(h->ds.Eself, 0, sizeof(double) * N * 3, h->stream));
@@ -1165,6 +1184,112 @@ EMPPP_API emppp_status emppp_set_adaptive_dt(emppp_handle h, const emppp_adaptiv
   }
   invalidate_graph(h);
   return update_schedule(h);
+}
+
+EMPPP_API emppp_status emppp_set_energy_monitor(emppp_handle h, const emppp_energy_monitor* cfg) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  EnergyParams ep{0, 1, 0.0};
+  if (cfg && cfg->enable) {
+    if (!(cfg->eps_E > 0.0 && cfg->eps_E < 1e300) || cfg->hold < 1)
+      return fail(EMPPP_ERR_ARG, "energy monitor: need eps_E > 0 (finite) and hold >= 1");
+    ep.on = 1;
+    ep.hold = cfg->hold;
+    ep.eps = cfg->eps_E;
+  }
+  h->energy = ep;
+  invalidate_graph(h);
+  if (ep.on && h->has_state) {
+    // the record starts at the present state
+    CU(launch_energy(h->ds, h->energy, h->d_mon, true, h->stream));
+    h->launches += 1;
+    CU(cudaStreamSynchronize(h->stream));
+  }
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_get_energy(emppp_handle h, emppp_energy_state* out) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!out) return fail(EMPPP_ERR_ARG, "out is NULL");
+  if (!h->energy.on || !h->has_state) return fail(EMPPP_ERR_STATE, "energy monitor off or no state");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  std::vector<EnergyMon> m((size_t)h->nbunch);
+  CU(cudaMemcpyAsync(m.data(), h->d_mon, sizeof(EnergyMon) * m.size(), cudaMemcpyDeviceToHost, h->stream));
+  CU(cudaStreamSynchronize(h->stream));
+  for (int b = 0; b < h->nbunch; b++) {
+    out[b].ebar = m[b].ebar;
+    out[b].rate = m[b].rate;
+    out[b].t_sw = m[b].t_sw;
+    out[b].n_sw = m[b].n_sw;
+    out[b].armed = m[b].armed;
+    out[b].switched = m[b].switched;
+  }
+  return EMPPP_OK;
+}
+
+EMPPP_API emppp_status emppp_two_stage(emppp_handle h, const double* x0, const double* u0, const double* w0,
+                                       int32_t is_device_ptr, const emppp_two_stage_config* cfg,
+                                       emppp_two_stage_report* rep) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!cfg || !rep || !x0 || !u0) return fail(EMPPP_ERR_ARG, "x0, u0, cfg and rep must not be NULL");
+  if (cfg->max_stage1_steps < 1 || cfg->check_every < 1 || cfg->steps2 < 0 || !(cfg->dt2 > 0.0) ||
+      !(cfg->t_after >= 0.0 && cfg->t_after < 1e300))
+    return fail(EMPPP_ERR_ARG,
+                "two-stage: need max_stage1_steps >= 1, check_every >= 1, steps2 >= 0, dt2 > 0, t_after >= 0");
+  memset(rep, 0, sizeof(*rep));
+  emppp_energy_monitor mon;
+  memset(&mon, 0, sizeof(mon));
+  mon.enable = 1;
+  mon.hold = cfg->hold;
+  mon.eps_E = cfg->eps_E;
+  if ((st = emppp_set_energy_monitor(h, &mon)) != EMPPP_OK) return st;
+  // 1. full EM-PP from the initial state until every bunch has met the criterion (or the cap)
+  if ((st = emppp_set_particles(h, x0, u0, w0, is_device_ptr)) != EMPPP_OK) return st;
+  std::vector<emppp_energy_state> es((size_t)h->nbunch);
+  int64_t done = 0;
+  bool all = false;
+  while (done < cfg->max_stage1_steps && !all) {
+    const int64_t k = cfg->max_stage1_steps - done < cfg->check_every ? cfg->max_stage1_steps - done : cfg->check_every;
+    if ((st = emppp_step(h, k, &cfg->bext1)) != EMPPP_OK) return st;
+    done += k;
+    if ((st = emppp_get_energy(h, es.data())) != EMPPP_OK) return st;
+    all = true;
+    for (int b = 0; b < h->nbunch; b++) all = all && es[b].switched;
+  }
+  int64_t n_th = 0;
+  double t_th = 0.0;
+  for (int b = 0; b < h->nbunch; b++) {
+    if (es[b].switched && es[b].n_sw > n_th) {
+      n_th = es[b].n_sw;
+      t_th = es[b].t_sw;
+    }
+  }
+  if (!all) {  // the cap ends the search
+    n_th = done;
+    if ((st = emppp_get_state(h, nullptr, nullptr, &t_th, nullptr, 0)) != EMPPP_OK) return st;
+  }
+  rep->switched = all ? 1 : 0;
+  rep->n_th = n_th;
+  rep->t_th = t_th;
+  rep->stage1_steps_first_run = done;
+  // 2. the re-run from the same initial state: full EM-PP through the threshold, then on to t_th + t_after
+  if ((st = emppp_set_particles(h, x0, u0, w0, is_device_ptr)) != EMPPP_OK) return st;
+  if ((st = emppp_step(h, n_th, &cfg->bext1)) != EMPPP_OK) return st;
+  const double t_target = t_th + cfg->t_after;
+  int64_t n_sw = n_th;
+  double t_sw = t_th;
+  while (t_sw < t_target) {  // one step at a time: with the adaptive step only the device knows dt
+    if ((st = emppp_step(h, 1, &cfg->bext1)) != EMPPP_OK) return st;
+    if ((st = emppp_get_state(h, nullptr, nullptr, &t_sw, &n_sw, 0)) != EMPPP_OK) return st;
+  }
+  rep->n_sw = n_sw;
+  rep->t_sw = t_sw;
+  // 3. stage 2: pair fields off, background field only, larger step
+  if (cfg->do_handoff && (st = emppp_handoff(h, cfg->center)) != EMPPP_OK) return st;
+  if ((st = emppp_transport(h, cfg->steps2, cfg->dt2, &cfg->bext2)) != EMPPP_OK) return st;
+  return emppp_synchronize(h);
 }
 
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt) {

@@ -150,6 +150,24 @@ __device__ __forceinline__ void reduce_scale(unsigned long long* scale, double e
   }
 }
 
+// stage-switch monitor (Sec. 2.7): the criterion, and the per-bunch record the device keeps
+struct EnergyParams {
+  int on;
+  int hold;    // consecutive steps below eps
+  double eps;  // threshold on |dE/dt| (J/s per electron)
+};
+struct EnergyMon {
+  double ebar;    // mean kinetic energy per electron at the present step (J)
+  double rate;    // backward difference of ebar over the last step (J/s)
+  double t_prev;  // time of ebar
+  double t_sw;    // time of the switch step
+  long long n_sw; // switch step, -1 before
+  int armed;      // the rate has reached eps
+  int run;        // consecutive steps below eps since arming
+  int switched;
+  int pad_;
+};
+
 struct BextParams {
   int kind;
   double b[3];
@@ -220,6 +238,8 @@ cudaError_t launch_mlp_train_pass(const void* image, const float* X, const float
                                   float norm, float* grad, float* loss, int num_sms, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float lr, float b1, float b2, float eps,
                         int step, cudaStream_t st);
+// energy.cu
+cudaError_t launch_energy(const DeviceState& s, const EnergyParams& ep, EnergyMon* mon, bool reset, cudaStream_t st);
 // pair_mixed.cu
 int max_blocks_pair_mixed(int proposal, bool adapt);
 cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const AdaptParams& ap,

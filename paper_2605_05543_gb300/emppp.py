@@ -72,6 +72,30 @@ class AdaptiveDt(ctypes.Structure):
                 ("eta_allow", ctypes.c_double), ("dt_min", ctypes.c_double), ("dt_max", ctypes.c_double)]
 
 
+class EnergyMonitor(ctypes.Structure):
+    _fields_ = [("enable", ctypes.c_int32), ("hold", ctypes.c_int32), ("eps_E", ctypes.c_double)]
+
+
+class EnergyState(ctypes.Structure):
+    _fields_ = [("ebar", ctypes.c_double), ("rate", ctypes.c_double), ("t_sw", ctypes.c_double),
+                ("n_sw", ctypes.c_int64), ("armed", ctypes.c_int32), ("switched", ctypes.c_int32)]
+
+
+class TwoStageConfig(ctypes.Structure):
+    _fields_ = [("eps_E", ctypes.c_double), ("hold", ctypes.c_int32), ("do_handoff", ctypes.c_int32),
+                ("max_stage1_steps", ctypes.c_int64), ("check_every", ctypes.c_int64), ("t_after", ctypes.c_double),
+                ("bext1", Bext),
+                ("center", ctypes.c_double * 3), ("dt2", ctypes.c_double), ("steps2", ctypes.c_int64),
+                ("bext2", Bext)]
+
+
+class TwoStageReport(ctypes.Structure):
+    _fields_ = [("n_th", ctypes.c_int64), ("t_th", ctypes.c_double), ("n_sw", ctypes.c_int64), ("t_sw", ctypes.c_double),
+                ("stage1_steps_first_run", ctypes.c_int64), ("switched", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+EV = 1.602176634e-19  # J per eV (the paper quotes eps_E in keV/s)
+
 _vp = ctypes.c_void_p
 _H = ctypes.c_void_p
 
@@ -108,6 +132,10 @@ SIGNATURES = {
     "emppp_mlp_train": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(MlpConfig), _vp, _vp]),
     "emppp_set_proposal": (ctypes.c_int, [_H, _vp, ctypes.c_int32]),
     "emppp_set_adaptive_dt": (ctypes.c_int, [_H, ctypes.POINTER(AdaptiveDt)]),
+    "emppp_set_energy_monitor": (ctypes.c_int, [_H, ctypes.POINTER(EnergyMonitor)]),
+    "emppp_get_energy": (ctypes.c_int, [_H, ctypes.POINTER(EnergyState)]),
+    "emppp_two_stage": (ctypes.c_int, [_H, _vp, _vp, _vp, ctypes.c_int32, ctypes.POINTER(TwoStageConfig),
+                                       ctypes.POINTER(TwoStageReport)]),
     "emppp_last_error": (ctypes.c_char_p, []),
     "emppp_version": (ctypes.c_char_p, []),
 }
@@ -350,6 +378,36 @@ class Solver:
         cfg = AdaptiveDt(enable=1 if enable else 0, c_dt=float(c_dt), eta_allow=float(eta_allow), dt_min=float(dt_min),
                          dt_max=float(dt_max))
         _check(self.lib.emppp_set_adaptive_dt(self._h, ctypes.byref(cfg)))
+
+    def set_energy_monitor(self, eps_E, hold=1, enable=True):
+        """Stage-switch monitor of Sec. 2.7: eps_E in J/s per electron (30 keV/s = 30e3 * EV)."""
+        cfg = EnergyMonitor(enable=1 if enable else 0, hold=int(hold), eps_E=float(eps_E))
+        _check(self.lib.emppp_set_energy_monitor(self._h, ctypes.byref(cfg)))
+
+    def get_energy(self) -> list:
+        """Per-bunch dicts: ebar (J), rate (J/s), n_sw, t_sw, armed, switched."""
+        arr = (EnergyState * len(self.bunches))()
+        _check(self.lib.emppp_get_energy(self._h, arr))
+        return [{k: getattr(e, k) for k, _ in EnergyState._fields_} for e in arr]
+
+    def two_stage(self, x0, u0, eps_E, max_stage1_steps, dt2, steps2, w0=None, hold=1, check_every=50,
+                  t_after=0.0, bext1=None, bext2=None, center=None) -> dict:
+        """The two-stage procedure of Sec. 2.7 (emppp_two_stage); center=None skips the handoff."""
+        cfg = TwoStageConfig(eps_E=float(eps_E), hold=int(hold), do_handoff=0 if center is None else 1,
+                             max_stage1_steps=int(max_stage1_steps), check_every=int(check_every),
+                             t_after=float(t_after), dt2=float(dt2), steps2=int(steps2))
+        cfg.bext1 = bext1 if bext1 is not None else bext_none()
+        cfg.bext2 = bext2 if bext2 is not None else bext_none()
+        if center is not None:
+            for c in range(3):
+                cfg.center[c] = float(center[c])
+        px, kx = _ptr(x0, 3 * self.n, "x0")
+        pu, ku = _ptr(u0, 3 * self.n, "u0")
+        pw, kw = _ptr(w0, self.n, "w0")
+        dev = _same_kind((px, kx), (pu, ku), (pw, kw))
+        rep = TwoStageReport()
+        _check(self.lib.emppp_two_stage(self._h, px, pu, pw, dev, ctypes.byref(cfg), ctypes.byref(rep)))
+        return {k: getattr(rep, k) for k, _ in TwoStageReport._fields_ if k != "pad_"}
 
     def reset_stats(self):
         _check(self.lib.emppp_reset_stats(self._h))
