@@ -65,7 +65,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--proposal", choices=["bisect", "closed_form", "mlp"], default="closed_form")
-    ap.add_argument("--workload", choices=["bunch", "batch"], default="bunch",
+    ap.add_argument("--workload", choices=["bunch", "batch", "paper"], default="bunch",
                     help="bunch: the N = 65536 bunch (default); batch: 64 bunches, stage 1 then stage 2")
     ap.add_argument("--stage2-steps", type=int, default=100000, help="stage-2 steps of the batch workload")
     ap.add_argument("--no-ablation", action="store_true",
@@ -470,7 +470,7 @@ def run_batch(args):
     steps = args.steps if args.steps is not None else 100
     s2_steps = args.stage2_steps
     warmup = max(args.warmup, 1)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a stream of its own: the library replays each step from a CUDA graph
     RE = inputs.R_EARTH
     m0 = 3.1e-5 * 4 * math.pi * RE ** 3 / 1.25663706212e-6
     with emppp.Solver(0, WL["depth"], WL["dt"], precision=args.path, proposal=args.proposal, stream=stream,
@@ -545,6 +545,101 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
 
 
+PAPER_NAME = ("the paper's own runs (Sec. 2.5, Sec. 3.1): 2 mm Gaussian bunches of N_p macroparticles "
+              "(weight 1e6 electrons), E0 = 1 MeV at N_p = 400, 800, 1600 and E0 = 10, 100 MeV at N_p = 1600, "
+              "injected at (-10 R_E, 0, 0) in the 8.6e22 A m^2 dipole (simulated in the bunch frame), adaptive "
+              "dt in [1e-15, 1e-12] s, energy monitor at 30 keV/s, depth 1024; then the two-stage procedure "
+              "of the N_p = 400, 1 MeV case")
+PAPER_CASES = [(400, 1.0), (800, 1.0), (1600, 1.0), (1600, 10.0), (1600, 100.0)]
+
+
+def run_paper(args):
+    """The paper's own workload: stage 1 of each case, timed step by step (CUDA graph replay on the
+    solver's stream), then the full two-stage procedure (monitoring run, re-run, handoff, dipole
+    transport) of the N_p = 400, 1 MeV case."""
+    import torch
+
+    from paper_2605_05543_gb300 import emppp, inputs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    dev = torch.device("cuda", local)
+    emppp.load(build_if_missing=True)
+    steps = args.steps if args.steps is not None else (20 if args.small else 400)
+    warmup = max(args.warmup, 3)
+    cases = PAPER_CASES[:2] if args.small else PAPER_CASES
+    center = tuple(-c for c in inputs.PAPER_R0)
+    bext = emppp.bext_dipole(inputs.PAPER_M0, center)
+    eps = 30e3 * emppp.EV
+    stream = torch.cuda.Stream()  # a stream of its own: the library replays each step from a CUDA graph
+    out, total_pairs, total_ms, launches = [], 0, 0.0, 0
+    clk = ClockSampler(local)
+    barrier()
+    clk.start()
+    for Np, E0 in cases:
+        b = inputs.paper_bunch(Np, E0, seed=11 + rank, weight=1e6)
+        with emppp.Solver(Np, 1024, 1e-15, precision=args.path, proposal=args.proposal, stream=stream,
+                          graphs=True) as s:
+            s.set_particles(b.x.copy(), b.u.copy(), b.weights.copy())
+            s.set_adaptive_dt()
+            s.set_energy_monitor(eps)
+            s.step(warmup, bext)
+            s.synchronize()
+            s.reset_stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(steps, bext)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = s.stats()
+            _, _, t, n = s.get_state()
+            en = s.get_energy()[0]
+        pairs = Np * (Np - 1) * steps
+        total_pairs += pairs
+        total_ms += ms
+        launches += st["kernel_launches"]
+        out.append({"N_p": Np, "E0_MeV": E0, "ms_per_step": ms / steps, "pairs_per_s": pairs / (ms / 1e3),
+                    "steps_per_s": steps / (ms / 1e3), "dt_last": st["dt_last"], "t_end": t,
+                    "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
+                    "ebar_MeV": en["ebar"] / (1e6 * emppp.EV), "rate_keV_per_s": en["rate"] / (1e3 * emppp.EV)})
+    clocks = clk.stop()
+    # the two-stage procedure of Sec. 2.7 on the N_p = 400, 1 MeV case (untimed by CUDA events: host wall time)
+    b = inputs.paper_bunch(400, 1.0, seed=11 + rank, weight=1e6)
+    s1_cap = 200 if args.small else 20000
+    s2_steps = 1000 if args.small else 100000
+    with emppp.Solver(400, 1024, 1e-15, precision=args.path, proposal=args.proposal, stream=stream,
+                      graphs=True) as s:
+        s.set_adaptive_dt()
+        t0 = time.perf_counter()
+        # stage 2 stays in the bunch frame of stage 1 (dipole centre at +10 R_E), so no handoff is needed
+        rep = s.two_stage(b.x.copy(), b.u.copy(), eps, max_stage1_steps=s1_cap, dt2=1e-6, steps2=s2_steps,
+                          w0=b.weights.copy(), check_every=500, t_after=0.0, bext1=bext, bext2=bext)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms_step = max_over_ranks(total_ms, dev) / (steps * len(cases))
+    value = sum_over_ranks(total_pairs, dev) / (max_over_ranks(total_ms, dev) / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.path == "fp64" else "f32+f64",
+        "data": "synthetic (the paper's bunch sampler, seeded; no dataset)",
+        "config": {"workload": PAPER_NAME, "path": args.path, "proposal": args.proposal,
+                   "steps_per_case": steps, "parallelism": f"replicas x{world}",
+                   "l2": "small working sets (< 20 MB): L2-resident; no flush (launch- and latency-bound regime)"},
+        "cases": out,
+        "two_stage_400_1MeV": {"threshold_step": rep["n_th"], "t_th": rep["t_th"], "switch_step": rep["n_sw"],
+                               "t_sw": rep["t_sw"], "switched": bool(rep["switched"]),
+                               "stage1_cap": s1_cap, "stage2_steps": s2_steps, "stage2_dt": 1e-6,
+                               "wall_s": wall},
+        "clocks": clocks,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: each step is a bounded sample of the workload (the fields
     of a fixed random subset of targets against all N sources)."""
@@ -597,6 +692,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "paper":
+        run_paper(args)
     else:
         run_ours(args)
     try:

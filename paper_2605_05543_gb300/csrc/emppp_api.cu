@@ -147,8 +147,11 @@ void invalidate_graph(emppp_handle h) {
 
 // Work split of the persistent pair kernel, per bunch: one block per resident slot of the kernel that
 // is launched (occupancy query) and about 16 work items per block over all bunches, so that the uneven
-// cost of the items (the branch mix differs across a bunch) evens out; chunks hold at least 256
-// sources. Uploaded when the configuration changes.
+// cost of the items (the branch mix differs across a bunch) evens out; small systems instead get one
+// round of items with short chunks. Chunks hold at least 8 sources (whole 128-source tiles once they
+// reach 128), at most max_split chunks per bunch. Uploaded when the configuration changes.
+constexpr long long kMinChunk = 8;  // fewest sources per chunk
+
 emppp_status update_schedule(emppp_handle c) {
   const bool mixed = c->opt.precision == EMPPP_MIXED;
   const int ad = c->adapt.on ? 1 : 0;
@@ -179,13 +182,17 @@ emppp_status update_schedule(emppp_handle c) {
       nchunk = c->opt.source_split;
     } else {
       nchunk = ((long long)c->items_per_block * Rsched + total_tiles - 1) / total_tiles;
-      const long long by_size = (n + 255) / 256;
+      // A small system has few target tiles: there one round of items (one per resident block) with
+      // the shortest chunks finishes first, since each block's time is its chunk length.
+      if (n / nchunk < 128) nchunk = Rsched / total_tiles > 1 ? Rsched / total_tiles : 1;
+      const long long by_size = (n + kMinChunk - 1) / kMinChunk;
       if (nchunk > by_size) nchunk = by_size;
     }
     if (nchunk > c->ds.max_split) nchunk = c->ds.max_split;
     if (nchunk < 1) nchunk = 1;
     long long chunk = (n + nchunk - 1) / nchunk;
-    chunk = (chunk + 127) / 128 * 128;
+    // whole 128-source tiles where chunks are large, multiples of 8 sources below that
+    chunk = chunk >= 128 ? (chunk + 127) / 128 * 128 : (chunk + kMinChunk - 1) / kMinChunk * kMinChunk;
     s.chunk = (int)chunk;
     s.nchunk = (int)((n + chunk - 1) / chunk);
     s.item_off = item;
@@ -438,9 +445,13 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   s.nbunch = nbunch;
   const size_t N = (size_t)n, D = (size_t)history_depth;
   {
-    // partial sums of up to 64 source chunks, within 1 GiB
+    // partial sums of up to 64 source chunks within 1 GiB, or up to 256 chunks for small systems, whose
+    // few target tiles need many chunks to fill the GPU (within 256 MiB)
     const long long by_mem = (1LL << 30) / ((long long)n * 48);
-    s.max_split = (int)(by_mem < 1 ? 1 : (by_mem > 64 ? 64 : by_mem));
+    const long long small = (256LL << 20) / ((long long)n * 48);
+    long long ms = by_mem > 64 ? 64 : by_mem;
+    if (small > ms) ms = small > 256 ? 256 : small;
+    s.max_split = (int)(ms < 1 ? 1 : ms);
   }
 #define ALLOC(p, cnt)            \
   do {                           \

@@ -97,6 +97,60 @@ def gaussian_bunch(N: int, sigma: float, gamma0: float, dE_rel: float = 1e-3, du
     return Bunch(x=x, u=u, sigma=sigma, gamma0=gamma0, seed=seed)
 
 
+def beam_kinematics(E0: float):
+    """gamma0 = 1 + E0 / (m_e c^2) and beta = sqrt(1 - 1 / gamma0^2) of a kinetic energy E0 (J) (Sec. 2.5)."""
+    g0 = 1.0 + E0 / (M_E * C_LIGHT * C_LIGHT)
+    return g0, math.sqrt(1.0 - 1.0 / (g0 * g0))
+
+
+def rotation(theta: float, phi: float) -> np.ndarray:
+    """R(theta, phi) = R_z(phi) R_y(theta): beam frame to laboratory frame (Sec. 2.5)."""
+    ct, st, cp, sp = math.cos(theta), math.sin(theta), math.cos(phi), math.sin(phi)
+    Ry = np.array([[ct, 0.0, st], [0.0, 1.0, 0.0], [-st, 0.0, ct]])
+    Rz = np.array([[cp, -sp, 0.0], [sp, cp, 0.0], [0.0, 0.0, 1.0]])
+    return Rz @ Ry
+
+
+def paper_bunch(Np: int, E0_MeV: float, r_perp: float = 2e-3, r_par: float = 2e-3, delta_E: float = 0.01,
+                eps_r: float = 1e-6, theta: float = 0.0, phi: float = 0.0, center=(0.0, 0.0, 0.0), seed: int = 0,
+                weight: float = 1.0) -> Bunch:
+    """The paper's own bunch (Sec. 2.5, Table 1): Np macroparticles with
+    x, y ~ N(0, r_perp^2), z ~ N(0, r_par^2); v_x, v_y ~ N(0, sigma_perp^2) with sigma_perp = eps_r v0 / r_perp;
+    E ~ N(E0, (delta_E E0)^2), gamma(E) = 1 + E / (m_e c^2), v_z = c sqrt(1 - 1 / gamma(E)^2); then v_z is
+    shifted so that its sample mean is v0, and positions and velocities are rotated by R(theta, phi) and
+    the positions translated to `center`. Particle i consumes normals 6i..6i+5 in the order x, y, z, v_x,
+    v_y, E. The returned u is the proper velocity v / sqrt(1 - v.v / c^2). `weight` is the number of
+    electrons per macroparticle (w_p = n0 V / Np; the paper does not state n0)."""
+    g = normals(seed, 6 * Np).reshape(Np, 6)
+    mc2 = M_E * C_LIGHT * C_LIGHT
+    E0 = E0_MeV * 1e6 * Q_E
+    g0, beta0 = beam_kinematics(E0)
+    v0 = beta0 * C_LIGHT
+    sig_perp = eps_r * v0 / r_perp
+    x = np.stack([r_perp * g[:, 0], r_perp * g[:, 1], r_par * g[:, 2]], axis=1)
+    E = E0 + delta_E * E0 * g[:, 5]
+    gam = 1.0 + E / mc2
+    vz = C_LIGHT * np.sqrt(1.0 - 1.0 / (gam * gam))
+    vz = vz - (vz.mean() - v0)
+    v = np.stack([sig_perp * g[:, 3], sig_perp * g[:, 4], vz], axis=1)
+    R = rotation(theta, phi)
+    x = x @ R.T + np.asarray(center, dtype=float)[None, :]
+    v = v @ R.T
+    vv = np.sum(v * v, axis=1) / (C_LIGHT * C_LIGHT)
+    if np.any(vv >= 1.0):
+        raise ValueError("sampled speed at or above c")
+    u = v / np.sqrt(1.0 - vv)[:, None]
+    b = Bunch(x=x, u=u, sigma=r_perp, gamma0=g0, seed=seed)
+    b.weights = np.full(Np, float(weight))
+    return b
+
+
+# Geometry of the paper's runs (Sec. 2.5, Sec. 2.6): injection at (-10 R_E, 0, 0) in a centred dipole of
+# moment 8.6e22 A m^2 along +z.
+PAPER_M0 = 8.6e22
+PAPER_R0 = (-10.0 * R_EARTH, 0.0, 0.0)
+
+
 def velocity_of(u: np.ndarray) -> np.ndarray:
     """v = u / sqrt(1 + u.u / c^2): the relativistic relation the recipe needs to lay out a history."""
     uu = np.sum(u * u, axis=-1)

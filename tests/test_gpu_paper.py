@@ -1,0 +1,82 @@
+"""The paper's own workload (Sec. 2.5, Sec. 3.1) on the GPU against the oracle (GB300): a 2 mm bunch of
+N_p macroparticles at 1-100 MeV, injected at 10 Earth radii in the centred dipole with a tilt, advanced
+with the adaptive time step and the energy monitor.
+
+The bunch is simulated in its own frame: it is centred at the origin and the dipole's centre sits at
+-r0 = (+10 R_E, 0, 0), which is the paper's geometry translated by -r0. In absolute coordinates at
+6.4e7 m a double resolves 7.5 nm, so every push would round positions to that grain; in the bunch frame
+positions keep their full relative precision.
+
+Bar (FP64 path): each step's size within 1e-12 relative of the oracle's on the first step and within
+the run bar 1e-9 after it, positions within 1e-9 of the bunch size, mean energy within 1e-12 relative.
+Mixed path: step sizes within 1e-5.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2605_05543_gb300 import emppp, inputs  # noqa: E402
+
+ADAPT = dict(oracle.ADAPTIVE_PAPER)
+CENTER = tuple(-c for c in inputs.PAPER_R0)
+
+
+def _rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def _runs(Np, E0, weight, steps, D, precision="fp64"):
+    b = inputs.paper_bunch(Np, E0, theta=math.radians(30), phi=math.radians(45), seed=7, weight=weight)
+    par = oracle.bext_params(2, m0=inputs.PAPER_M0, center=CENTER)
+    run = oracle.Run(b.x, b.u, D, 1e-15, weights=b.weights, nmax=steps)
+    T, E = [0.0], [oracle.mean_kinetic_energy(b.u, b.weights)]
+    for _ in range(steps):
+        run.step(1, bkind=2, bpar=par, adaptive=ADAPT)
+        T.append(run.t)
+        E.append(oracle.mean_kinetic_energy(run.u, b.weights))
+    log = []
+    with emppp.Solver(Np, D, 1e-15, precision=precision, proposal="closed_form") as s:
+        s.set_particles(b.x.copy(), b.u.copy(), b.weights.copy())
+        s.set_adaptive_dt(**ADAPT)
+        s.set_energy_monitor(30e3 * emppp.EV)
+        Eg = [s.get_energy()[0]["ebar"]]
+        for _ in range(steps):
+            s.step(1, emppp.bext_dipole(inputs.PAPER_M0, CENTER))
+            st = s.stats()
+            log.append((st["dt_last"], st["eta_min"], st["v_max"]))
+            Eg.append(s.get_energy()[0]["ebar"])
+        x, u, t, n = s.get_state()
+    return b, run, np.array(run.adaptive_log), np.array(log), np.array(E), np.array(Eg), x, u, t
+
+
+@pytest.mark.parametrize("Np,E0,weight", [(400, 1.0, 1e6), (800, 10.0, 1e6), (400, 100.0, 1e7)])
+def test_paper_workload_fp64(Np, E0, weight):
+    steps = 25
+    b, run, ref, log, E, Eg, x, u, t = _runs(Np, E0, weight, steps, 64)
+    assert all(_rel(log[0, c], ref[0, c]) <= 1e-12 for c in range(3))
+    worst = max(_rel(log[k, c], ref[k, c]) for k in range(steps) for c in range(3))
+    assert worst <= 1e-9, worst
+    assert _rel(t, run.t) <= 1e-9
+    sig = float(np.sqrt(np.mean(np.sum((run.x - run.x.mean(axis=0)) ** 2, axis=1))))
+    err = np.max(np.linalg.norm(x - run.x, axis=1)) / sig
+    assert err <= 1e-9, err
+    assert np.max(np.abs(Eg - E) / E) <= 1e-12
+    print(f"paper Np={Np} E0={E0} MeV w={weight:g}: dt {ref[0, 0]:.3e}..{ref[-1, 0]:.3e} s, worst step err "
+          f"{worst:.1e}, positions {err:.1e}")
+
+
+def test_paper_workload_mixed():
+    steps = 25
+    b, run, ref, log, E, Eg, x, u, t = _runs(800, 1.0, 1e6, steps, 64, precision="mixed")
+    worst = max(_rel(log[k, c], ref[k, c]) for k in range(steps) for c in range(3))
+    print(f"paper mixed: worst step err {worst:.1e}")
+    assert worst <= 1e-5, worst

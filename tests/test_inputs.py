@@ -69,3 +69,36 @@ def test_batch_bunches_ranges():
     assert len(bb) == 64
     for N, s, g, seed in bb:
         assert 512 <= N <= 16384 and 5e-6 <= s <= 50e-6 and 2 <= g <= 20
+
+
+def test_paper_bunch_recipe():
+    """Sec. 2.5: the paper's own sampler (Table 1 widths, v_z mean shift, beam-to-lab rotation)."""
+    vals = {r[0]: float(r[1]) for r in _rows("beam_params_1MeV.txt")}
+    g0, beta = inputs.beam_kinematics(vals["E0_MeV"] * 1e6 * inputs.Q_E)
+    assert round(g0, 2) == vals["gamma0"] and round(beta, 3) == vals["beta"]
+    v0 = beta * inputs.C_LIGHT
+    b = inputs.paper_bunch(20000, 1.0, seed=2)
+    v = inputs.velocity_of(b.u)
+    # the shifted longitudinal mean is v0 (to rounding), the transverse spread eps_r v0 / r_perp
+    assert abs(v[:, 2].mean() - v0) <= 1e-9 * v0
+    assert np.allclose(v[:, :2].std(axis=0), 1e-6 * v0 / 2e-3, rtol=2e-2)
+    assert np.allclose(b.x.std(axis=0), 2e-3, rtol=2e-2)
+    assert np.all(np.linalg.norm(v, axis=1) < inputs.C_LIGHT)
+    mc2 = inputs.M_E * inputs.C_LIGHT ** 2
+    # energy spread from gamma(E): relative spread delta_E of E0, before the speed adjustment
+    gz = 1.0 / np.sqrt(1.0 - (v[:, 2] / inputs.C_LIGHT) ** 2)
+    K = (gz - 1) * mc2 / (1e6 * inputs.Q_E)
+    assert abs(np.median(K) - 1.0) < 2e-3
+    # rotation: theta = 90 deg turns the beam axis onto +x; phi = 90 deg then onto +y; norms are kept
+    for theta, phi, axis in ((math.pi / 2, 0.0, 0), (math.pi / 2, math.pi / 2, 1), (0.0, 1.3, 2)):
+        r = inputs.paper_bunch(500, 10.0, theta=theta, phi=phi, center=inputs.PAPER_R0, seed=4)
+        r0 = inputs.paper_bunch(500, 10.0, seed=4)
+        vr = inputs.velocity_of(r.u)
+        assert np.all(vr[:, axis] > 0.99 * inputs.C_LIGHT)
+        d = r.x - np.asarray(inputs.PAPER_R0)
+        assert np.allclose(np.linalg.norm(d, axis=1), np.linalg.norm(r0.x, axis=1), rtol=1e-12)
+        assert np.allclose(np.linalg.norm(r.u, axis=1), np.linalg.norm(r0.u, axis=1), rtol=1e-12)
+    R = inputs.rotation(0.4, -1.1)
+    assert np.allclose(R @ R.T, np.eye(3), atol=1e-15) and abs(np.linalg.det(R) - 1) < 1e-15
+    w = inputs.paper_bunch(10, 1.0, weight=2.5e6).weights
+    assert w.shape == (10,) and np.all(w == 2.5e6)
