@@ -22,8 +22,9 @@
 //             (eq:LW_E with v' = c u', a = c^2 alpha), B = eta_hat x E / c (eq:LW_B). eta.u' = R - eta.beta
 //             cancels for a source moving towards the target; there it is formed as
 //             [R^2 (1 - beta^2) + |eta x beta|^2] / (R + eta.beta), a sum of non-negative terms.
-//   sums      FP32 partial sums over 8 sources, added with Kahan compensation into FP32 running totals,
-//             converted to FP64 at the end.
+//   sums      FP32 partial sums over 8 sources, added with Kahan compensation into FP32 running totals
+//             (kept in shared memory, which leaves the registers to the pair loop: 64 registers, 8 blocks
+//             of 128 threads per SM), converted to FP64 at the end.
 // Sources are walked in tiles of kTile whose present records and FP32 charges are staged in shared
 // memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
 // source are close together in the source-major FP32 shadow ring.
@@ -36,7 +37,7 @@ namespace emppp {
 namespace {
 
 #ifndef EMPPP_MIXED_MIN_BLOCKS
-#define EMPPP_MIXED_MIN_BLOCKS 7  // resident blocks per SM the register budget is fitted to (72 registers)
+#define EMPPP_MIXED_MIN_BLOCKS 8  // resident blocks per SM the register budget is fitted to (64 registers)
 #endif
 
 constexpr int kBlock = 128;
@@ -71,8 +72,8 @@ struct MixedArgs {
 
 struct Target {
   float h0, h1, h2, l0, l1, l2;
-  double r0, r1, r2;
-  bool exact_only;  // coordinates too far from the split origin for the FP32 band: FP64 tests only
+  const double* rr;  // FP64 present position, read only by the rare FP64 node tests
+  bool exact_only;   // coordinates too far from the split origin for the FP32 band: FP64 tests only
 };
 
 // slots of the usable window k0..n are addressed by their offset l = k - k0 (0..nw-1)
@@ -97,9 +98,9 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ src32, int p)
 }
 
 __device__ __forceinline__ bool exact_test(const Target& r, const double* __restrict__ w, double lhs) {
-  const double d0 = __dsub_rn(r.r0, __ldg(w + 0));
-  const double d1 = __dsub_rn(r.r1, __ldg(w + 1));
-  const double d2 = __dsub_rn(r.r2, __ldg(w + 2));
+  const double d0 = __dsub_rn(__ldg(r.rr + 0), __ldg(w + 0));
+  const double d1 = __dsub_rn(__ldg(r.rr + 1), __ldg(w + 1));
+  const double d2 = __dsub_rn(__ldg(r.rr + 2), __ldg(w + 2));
   const double rhs = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
   return lhs <= rhs;
 }
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
+  __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
   __shared__ float4 s_db[PROP == kPropMlp ? kTile : 1];  // beta_n - beta_{n-1} of the tile's sources
   __shared__ mlp::InferImage s_net[1];
   __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
@@ -226,10 +228,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
     r.l0 = q1.x;
     r.l1 = q1.y;
     r.l2 = q1.z;
-    const double* rr = a.rec64 + ((size_t)i * D + pn) * 6;
-    r.r0 = rr[0];
-    r.r1 = rr[1];
-    r.r2 = rr[2];
+    r.rr = a.rec64 + ((size_t)i * D + pn) * 6;
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
   // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
@@ -245,8 +244,10 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   const int j_begin = boff + chunk_id * bs.chunk;
   const int j_end = min(boff + bd.n, j_begin + bs.chunk);
 
-  // compensated running sums of E and of c B
-  float Es[3] = {0.f, 0.f, 0.f}, Ec[3] = {0.f, 0.f, 0.f}, Bs[3] = {0.f, 0.f, 0.f}, Bc[3] = {0.f, 0.f, 0.f};
+  // compensated running sums of E and of c B, kept in shared memory (rows: E sums, E compensations,
+  // c B sums, c B compensations) to leave registers to the pair loop
+#pragma unroll
+  for (int c = 0; c < 12; c++) s_acc[c][threadIdx.x] = 0.f;
 
   for (int tile = j_begin; tile < j_end; tile += kTile) {
     const int tn = min(kTile, j_end - tile);
@@ -533,14 +534,16 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
       // Kahan-add the partial sums of these kSub sources
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        const float y = P[c] - Ec[c];
-        const float tt = Es[c] + y;
-        Ec[c] = (tt - Es[c]) - y;
-        Es[c] = tt;
-        const float yb = P[3 + c] - Bc[c];
-        const float tb = Bs[c] + yb;
-        Bc[c] = (tb - Bs[c]) - yb;
-        Bs[c] = tb;
+        const float es = s_acc[c][threadIdx.x], ec = s_acc[3 + c][threadIdx.x];
+        const float y = P[c] - ec;
+        const float tt = es + y;
+        s_acc[3 + c][threadIdx.x] = (tt - es) - y;
+        s_acc[c][threadIdx.x] = tt;
+        const float bsv = s_acc[6 + c][threadIdx.x], bcv = s_acc[9 + c][threadIdx.x];
+        const float yb = P[3 + c] - bcv;
+        const float tb = bsv + yb;
+        s_acc[9 + c][threadIdx.x] = (tb - bsv) - yb;
+        s_acc[6 + c][threadIdx.x] = tb;
       }
     }
     n_ooh += brc & 1023u;
@@ -550,8 +553,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   if (active) {
     double Et[3], Bt[3];
     for (int c = 0; c < 3; c++) {
-      Et[c] = (double)Es[c] - (double)Ec[c];
-      Bt[c] = ((double)Bs[c] - (double)Bc[c]) * (1.0 / kC);
+      Et[c] = (double)s_acc[c][threadIdx.x] - (double)s_acc[3 + c][threadIdx.x];
+      Bt[c] = ((double)s_acc[6 + c][threadIdx.x] - (double)s_acc[9 + c][threadIdx.x]) * (1.0 / kC);
     }
     if (bs.nchunk == 1) {
       for (int c = 0; c < 3; c++) {
