@@ -15,7 +15,8 @@
 //   slot_t [D]                time stamp of each physical slot.
 //   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
 //                             1 / (t_{k+1} - t_k) in FP64 and 1 / (c (t_{k+1} - t_k)) in FP32.
-//   ext32  [N][2] float4      per step (mixed path): hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) - origin.
+//   ext32  [N][3] float4      per step (mixed path): hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) - origin,
+//                             and w_{k0} + v_{k0} (t_n - t_{k0}) - w_n.
 //   u      [N][3]             present proper velocities (FP64).
 //   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
 //   bunches [nbunch]          offsets, sizes, FP32-split origins and reference velocities.
@@ -120,8 +121,9 @@ struct DeviceState {
   int* err;
   double* bsum;     // [nbunch][4] per-bunch reductions (weighted position sums and weight)
   const void* mlp_image;  // BF16 image of the proposal network (EMPPP_PROPOSAL_MLP), or null
-  // [N][2] FP32 hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) relative to the bunch origin: the end of the
-  // last history segment of eq:linear, from which the mixed path forms near-field retarded points
+  // [N][3] FP32 hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) relative to the bunch origin (the end of the
+  // last history segment of eq:linear, from which the mixed path forms near-field retarded points), and
+  // w_{k0} + v_{k0} (t_n - t_{k0}) - w_n (where the out-of-history line of eq:linear2 is at t_n)
   float4* ext32;
   // adaptive time step (Sec. 2.4)
   unsigned long long* scale;  // [2] bit patterns of eta_min (m, reduced by min) and v_max^2 ((m/s)^2, by max)

@@ -67,7 +67,7 @@ struct MixedArgs {
   const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
   unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
   float eta_allow;
-  const float4* __restrict__ ext32;  // [N][2] hi/lo of the end of each source's last history segment
+  const float4* __restrict__ ext32;  // [N][3] per source: segment end hi/lo, out-of-history line offset
 };
 
 struct Target {
@@ -175,6 +175,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
+  __shared__ float4 s_q1[kTile];  // present record (lo, 0) of the tile's sources
+  __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position (ext32)
   __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
   __shared__ float4 s_db[PROP == kPropMlp ? kTile : 1];  // beta_n - beta_{n-1} of the tile's sources
   __shared__ mlp::InferImage s_net[1];
@@ -260,6 +262,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
       const float4 q2 = q[2];
       s_q2[threadIdx.x] = make_float4(bref0 + q2.x, bref1 + q2.y, bref2 + q2.z, q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
+      s_q1[threadIdx.x] = q[1];
+      s_x[threadIdx.x] = __ldg(a.ext32 + 3 * j + 2);
       if (PROP == kPropMlp) {
         const float4 q2p = a.rec32[((size_t)j * D + pprev) * 3 + 2];
         s_db[threadIdx.x] = make_float4(q2.x - q2p.x, q2.y - q2p.y, q2.z - q2p.z, 0.f);
@@ -432,6 +436,45 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
         }
         brc += 1u << (10 * br);  // branch counts of this tile, 10 bits each
 
+        if (br == 0) {
+          // ---- out of history (eq:linear2): the source moves uniformly with beta1 along the line through
+          // w1; its Lienard-Wiechert field is Heaviside's field about the line's point at t_n,
+          //   E = kq (1 - beta^2) X / [X^2 (1 - beta^2) + (X.beta)^2]^{3/2},  c B = beta x E,
+          // with X = (r - w_n) - (line at t_n - w_n) from the staged present record and line offset.
+          const float4 g0 = s_q0[jj], g1 = s_q1[jj], gx = s_x[jj];
+          const float X0 = __fsub_rn(__fadd_rn(__fsub_rn(r.h0, g0.x), __fsub_rn(r.l0, g1.x)), gx.x);
+          const float X1 = __fsub_rn(__fadd_rn(__fsub_rn(r.h1, g0.y), __fsub_rn(r.l1, g1.y)), gx.y);
+          const float X2 = __fsub_rn(__fadd_rn(__fsub_rn(r.h2, g0.z), __fsub_rn(r.l2, g1.z)), gx.z);
+          const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
+          const float ig2 = A.q0.w;
+          const float Xb = dot3(X0, X1, X2, b10, b11, b12);
+          const float Dh = __fmaf_rn(dot3(X0, X1, X2, X0, X1, X2), ig2, __fmul_rn(Xb, Xb));
+          const float iD = rsqrtf(Dh);
+          if (!(Dh > 0.f) || !(ig2 > 0.f)) {
+            errbits |= (ig2 > 0.f) ? kErrCoincide : kErrDisc;
+            continue;
+          }
+          const float pref = __fmul_rn(__fmul_rn(s_kq[jj], ig2), __fmul_rn(__fmul_rn(iD, iD), iD));
+          const float E0 = __fmul_rn(pref, X0), E1 = __fmul_rn(pref, X1), E2 = __fmul_rn(pref, X2);
+          if (ADAPT) {
+            // retarded distance c (t - t_r) = gamma^2 [X.beta + sqrt(Dh)], and v(t_r) = v1
+            const float sD = __fmul_rn(Dh, iD);
+            const float R = (Xb >= 0.f) ? __fmul_rn(__fadd_rn(Xb, sD), A.q2.w)
+                                        : __fdividef(dot3(X0, X1, X2, X0, X1, X2), __fsub_rn(sD, Xb));
+            if (R >= a.eta_allow) {
+              emin = fminf(emin, R);
+              const float dv0 = bi0 - A.q2.x, dv1 = bi1 - A.q2.y, dv2 = bi2 - A.q2.z;
+              vmax2 = fmaxf(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+            }
+          }
+          P[0] = __fadd_rn(P[0], E0);
+          P[1] = __fadd_rn(P[1], E1);
+          P[2] = __fadd_rn(P[2], E2);
+          P[3] = __fadd_rn(P[3], cross1(b11, b12, E1, E2));
+          P[4] = __fadd_rn(P[4], cross1(b12, b10, E2, E0));
+          P[5] = __fadd_rn(P[5], cross1(b10, b11, E0, E1));
+          continue;
+        }
         // ---- retarded state (light units) --------------------------------------------------------
         // Written with explicit round-to-nearest intrinsics: the compiler may not fuse or regroup any
         // of it, so every search variant (whose own arithmetic shares subexpressions with this code
@@ -446,7 +489,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           // of the segment (ext32) and tau = c (t_n - t_r) = R, the positive root of
           // (1 - beta1^2) tau^2 - 2 (p.beta1) tau - |p|^2 = 0, p = r - P (eq:dt about t_n). Formed this
           // way, eta keeps FP32 precision when R is far below c (t_n - t_{n-1}).
-          const float3 dp = separation(r, __ldg(a.ext32 + 2 * j), __ldg(a.ext32 + 2 * j + 1));
+          const float3 dp = separation(r, __ldg(a.ext32 + 3 * j), __ldg(a.ext32 + 3 * j + 1));
           const float pb = dot3(dp.x, dp.y, dp.z, b10, b11, b12);
           const float pp = dot3(dp.x, dp.y, dp.z, dp.x, dp.y, dp.z);
           qd = __fmaf_rn(pb, pb, __fmul_rn(ig2, pp));

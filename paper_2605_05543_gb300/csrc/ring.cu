@@ -138,16 +138,26 @@ __global__ void adaptive_dt_kernel(DeviceState s, AdaptParams ap) {
   s.scale[1] = 0ull;
 }
 
-// End of the last history segment of each source, P_j = w_{j,n-1} + v_{j,n-1} (t_n - t_{n-1}) (eq:linear at
-// t_n), split hi/lo about the bunch origin. For a pair in the near-field shortcut bracket [n-1, n] the
-// mixed path writes the retarded point as P_j - v_{j,n-1} tau with tau = t_n - t_r, which is the same point
-// as w_{j,n-1} + v_{j,n-1} (t_r - t_{n-1}) but keeps FP32 precision when c tau is far below c (t_n - t_{n-1}).
+// Per-source vectors of the mixed path, each step (eq:linear at t_n, eq:linear2):
+//   P_j = w_{j,n-1} + v_{j,n-1} (t_n - t_{n-1}), the end of the last history segment, split hi/lo about
+//     the bunch origin. For a pair in the near-field shortcut bracket [n-1, n] the retarded point is
+//     written as P_j - v_{j,n-1} tau with tau = t_n - t_r: the same point as w_{j,n-1} + v_{j,n-1}
+//     (t_r - t_{n-1}), with FP32 precision kept when c tau is far below c (t_n - t_{n-1}).
+//   X_j = w_{j,k0} + v_{j,k0} (t_n - t_{k0}) - w_{j,n}, where the straight line of eq:linear2 (the
+//     out-of-history case) is at t_n, relative to the source's present position. Along that line the
+//     source moves uniformly, so its field is Heaviside's field about the point w_{j,n} + X_j; the
+//     separation from a target is then (r - w_{j,n}) - X_j, formed without cancellation.
 __global__ void extrap_kernel(DeviceState s) {
   const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= s.N) return;
   const StepState st = *s.state;
-  if (st.n <= st.k0) return;  // no segment [n-1, n] in the window
   const int pn = st.pn;
+  const double* rn = s.rec64 + ((size_t)j * s.D + pn) * 6;
+  const double* r0 = s.rec64 + ((size_t)j * s.D + st.p0) * 6;
+  const double dt0 = s.slot_t[pn] - s.slot_t[st.p0];
+  s.ext32[3 * j + 2] = make_float4((float)((r0[0] + r0[3] * dt0) - rn[0]), (float)((r0[1] + r0[4] * dt0) - rn[1]),
+                                   (float)((r0[2] + r0[5] * dt0) - rn[2]), 0.f);
+  if (st.n <= st.k0) return;  // no segment [n-1, n] in the window
   const int p1 = pn == 0 ? s.D - 1 : pn - 1;
   const double dtl = s.slot_t[pn] - s.slot_t[p1];
   const double* r = s.rec64 + ((size_t)j * s.D + p1) * 6;
@@ -156,8 +166,8 @@ __global__ void extrap_kernel(DeviceState s) {
   const double d1 = (r[1] + r[4] * dtl) - bd.origin[1];
   const double d2 = (r[2] + r[5] * dtl) - bd.origin[2];
   const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-  s.ext32[2 * j] = make_float4(h0, h1, h2, 0.f);
-  s.ext32[2 * j + 1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.f);
+  s.ext32[3 * j] = make_float4(h0, h1, h2, 0.f);
+  s.ext32[3 * j + 1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.f);
 }
 
 __global__ void reset_scale_kernel(DeviceState s) {
