@@ -147,9 +147,9 @@ void invalidate_graph(emppp_handle h) {
 
 // Work split of the persistent pair kernel, per bunch: one block per resident slot of the kernel that
 // is launched (occupancy query) and about 16 work items per block over all bunches, so that the uneven
-// cost of the items (the branch mix differs across a bunch) evens out; small systems instead get one
-// round of items with short chunks. Chunks hold at least 8 sources (whole 128-source tiles once they
-// reach 128), at most max_split chunks per bunch. Uploaded when the configuration changes.
+// cost of the items (the branch mix differs across a bunch) evens out; systems too small for that get
+// one round of items with short chunks instead. At most max_split chunks per bunch. Uploaded when the
+// configuration changes.
 constexpr long long kMinChunk = 8;  // fewest sources per chunk
 
 emppp_status update_schedule(emppp_handle c) {
@@ -172,27 +172,41 @@ emppp_status update_schedule(emppp_handle c) {
   const long long Rsched = (long long)nref * c->num_sms;
   long long total_tiles = 0;
   for (int b = 0; b < c->nbunch; b++) total_tiles += (c->hb[b].n + 127) / 128;
-  int item = 0;
-  for (int b = 0; b < c->nbunch; b++) {
-    BunchSched& s = c->hs[b];
-    const long long n = c->hb[b].n;
-    s.ntb = (int)((n + 127) / 128);
+  // chunking of one bunch: about items_per_block items per resident block over all bunches, in
+  // whole 128-source tiles of at least 256 sources (small == false); or, for a system too small to fill
+  // the resident blocks that way, one round of items with chunks of 8k sources (small == true), since
+  // then each block's time is its own chunk length
+  auto chunks = [&](long long n, bool small) -> long long {
     long long nchunk;
     if (c->opt.source_split > 0) {
       nchunk = c->opt.source_split;
-    } else {
+    } else if (!small) {
       nchunk = ((long long)c->items_per_block * Rsched + total_tiles - 1) / total_tiles;
-      // A small system has few target tiles: there one round of items (one per resident block) with
-      // the shortest chunks finishes first, since each block's time is its chunk length.
-      if (n / nchunk < 128) nchunk = Rsched / total_tiles > 1 ? Rsched / total_tiles : 1;
+      const long long by_size = (n + 255) / 256;
+      if (nchunk > by_size) nchunk = by_size;
+    } else {
+      nchunk = Rsched / total_tiles > 1 ? Rsched / total_tiles : 1;
       const long long by_size = (n + kMinChunk - 1) / kMinChunk;
       if (nchunk > by_size) nchunk = by_size;
     }
     if (nchunk > c->ds.max_split) nchunk = c->ds.max_split;
     if (nchunk < 1) nchunk = 1;
     long long chunk = (n + nchunk - 1) / nchunk;
-    // whole 128-source tiles where chunks are large, multiples of 8 sources below that
-    chunk = chunk >= 128 ? (chunk + 127) / 128 * 128 : (chunk + kMinChunk - 1) / kMinChunk * kMinChunk;
+    return chunk >= 128 ? (chunk + 127) / 128 * 128 : (chunk + kMinChunk - 1) / kMinChunk * kMinChunk;
+  };
+  long long items_large = 0;
+  for (int b = 0; b < c->nbunch; b++) {
+    const long long n = c->hb[b].n;
+    const long long chunk = chunks(n, false);
+    items_large += ((n + 127) / 128) * ((n + chunk - 1) / chunk);
+  }
+  const bool small = items_large < Rsched;
+  int item = 0;
+  for (int b = 0; b < c->nbunch; b++) {
+    BunchSched& s = c->hs[b];
+    const long long n = c->hb[b].n;
+    s.ntb = (int)((n + 127) / 128);
+    const long long chunk = chunks(n, small);
     s.chunk = (int)chunk;
     s.nchunk = (int)((n + chunk - 1) / chunk);
     s.item_off = item;
