@@ -43,11 +43,16 @@ namespace {
 constexpr int kBlock = 128;
 constexpr int kTile = 128;
 constexpr int kSub = 8;  // sources per FP32 partial sum
+// FP64 recomputation of C0 when u L1^2 |s| / (C0 (L1 - s)) exceeds 2e-6: kC0Guard = 2e-6 / u
+constexpr float kC0Guard = 2.0e-6f / 5.9604644775390625e-08f;
+// FP64 recomputation of X.beta (out-of-history pairs) when 2 u |X| |X.beta| / denominator exceeds 1.3e-6
+constexpr float kXbGuard = 2.0f * 5.9604644775390625e-08f / 1.3e-6f;
 
 struct MixedArgs {
   const float4* __restrict__ rec32;
   const double* __restrict__ rec64;
   const double* __restrict__ lhs64;
+  const double* __restrict__ slot_t;  // time stamps of the physical slots
   const float4* __restrict__ tab32;  // per slot: guard-band thresholds of L^2, c (t - t_k), 1 / (c dt_k)
   const float* __restrict__ kq32;  // -e w_j / (4 pi eps0), FP32
   const int* __restrict__ order;
@@ -442,13 +447,32 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           //   E = kq (1 - beta^2) X / [X^2 (1 - beta^2) + (X.beta)^2]^{3/2},  c B = beta x E,
           // with X = (r - w_n) - (line at t_n - w_n) from the staged present record and line offset.
           const float4 g0 = s_q0[jj], g1 = s_q1[jj], gx = s_x[jj];
-          const float X0 = __fsub_rn(__fadd_rn(__fsub_rn(r.h0, g0.x), __fsub_rn(r.l0, g1.x)), gx.x);
-          const float X1 = __fsub_rn(__fadd_rn(__fsub_rn(r.h1, g0.y), __fsub_rn(r.l1, g1.y)), gx.y);
-          const float X2 = __fsub_rn(__fadd_rn(__fsub_rn(r.h2, g0.z), __fsub_rn(r.l2, g1.z)), gx.z);
+          float X0 = __fsub_rn(__fadd_rn(__fsub_rn(r.h0, g0.x), __fsub_rn(r.l0, g1.x)), gx.x);
+          float X1 = __fsub_rn(__fadd_rn(__fsub_rn(r.h1, g0.y), __fsub_rn(r.l1, g1.y)), gx.y);
+          float X2 = __fsub_rn(__fadd_rn(__fsub_rn(r.h2, g0.z), __fsub_rn(r.l2, g1.z)), gx.z);
           const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
           const float ig2 = A.q0.w;
-          const float Xb = dot3(X0, X1, X2, b10, b11, b12);
-          const float Dh = __fmaf_rn(dot3(X0, X1, X2, X0, X1, X2), ig2, __fmul_rn(Xb, Xb));
+          float Xb = dot3(X0, X1, X2, b10, b11, b12);
+          float XX = dot3(X0, X1, X2, X0, X1, X2);
+          // The FP32 rounding of X.beta (absolute about u |X|) moves the denominator by 2 u |X| |X.beta| /
+          // denominator relative, at most u gamma. Above 1.3e-6 (only for gamma above ~20, at directions
+          // near perpendicular to beta) X and X.beta are formed in FP64 from the FP64 records instead.
+          // (as the shift is at most u gamma, sources with gamma^2 < 100 never need it)
+          if (ig2 < 0.01f && __fmul_rn(kXbGuard, __fmul_rn(sqrtf(XX), fabsf(Xb))) > __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb))) {
+            const double* w0 = src64 + 6 * pA;  // FP64 record of slot k0: X = r - w_k0 - v_k0 (t_n - t_k0)
+            const double ct = kC * (a.state->t - __ldg(a.slot_t + pA));  // c (t_n - t_k0)
+            const double ic = 1.0 / kC;
+            const double y0 = (__ldg(r.rr + 0) - __ldg(w0 + 0)) - __ldg(w0 + 3) * ic * ct;
+            const double y1 = (__ldg(r.rr + 1) - __ldg(w0 + 1)) - __ldg(w0 + 4) * ic * ct;
+            const double y2 = (__ldg(r.rr + 2) - __ldg(w0 + 2)) - __ldg(w0 + 5) * ic * ct;
+            X0 = (float)y0;
+            X1 = (float)y1;
+            X2 = (float)y2;
+            Xb = (float)((y0 * __ldg(w0 + 3) + y1 * __ldg(w0 + 4) + y2 * __ldg(w0 + 5)) * ic);
+            XX = dot3(X0, X1, X2, X0, X1, X2);
+            n_fb++;
+          }
+          const float Dh = __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb));
           const float iD = rsqrtf(Dh);
           if (!(Dh > 0.f) || !(ig2 > 0.f)) {
             errbits |= (ig2 > 0.f) ? kErrCoincide : kErrDisc;
@@ -501,10 +525,27 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
           df = __fmaf_rn(-tau, tabA.w, 1.f);
         } else {
           const float hb = __fsub_rn(dot3(d0, d1, d2, b10, b11, b12), L1);
-          const float C0 = __fmaf_rn(L1, L1, -dot3(d0, d1, d2, d0, d1, d2));
+          float C0 = __fmaf_rn(L1, L1, -dot3(d0, d1, d2, d0, d1, d2));
           qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
-          const float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
-          const float s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
+          float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
+          float s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
+          // C0 = L1^2 - |d|^2 cancels when |d| is close to L1; its FP32 rounding moves eta by about
+          // u L1^2 s / C0, relative to R = L1 - s. That reaches 2e-6 only for sources moving nearly
+          // towards the target at high gamma (eta moves by ~ u / (1 - beta cos psi)); for those pairs
+          // C0 is formed again in FP64 from the reference quantities (c (t - t1))^2 and the FP64 positions.
+          // (the shift is below u / (1 - beta) < 2 u gamma^2, so sources with gamma^2 < 16 never need it)
+          if (br == 2 && ig2 < 0.0625f &&
+              __fmul_rn(__fmul_rn(L1, L1), fabsf(s)) > __fmul_rn(kC0Guard, __fmul_rn(C0, __fsub_rn(L1, s)))) {
+            const double* w64 = src64 + 6 * pA;
+            const double x0 = __dsub_rn(__ldg(r.rr + 0), __ldg(w64 + 0));
+            const double x1 = __dsub_rn(__ldg(r.rr + 1), __ldg(w64 + 1));
+            const double x2 = __dsub_rn(__ldg(r.rr + 2), __ldg(w64 + 2));
+            C0 = (float)(__ldg(a.lhs64 + pA) - (x0 * x0 + x1 * x1 + x2 * x2));
+            qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
+            sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
+            s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
+            n_fb++;
+          }
           e0 = __fmaf_rn(-b10, s, d0);
           e1 = __fmaf_rn(-b11, s, d1);
           e2 = __fmaf_rn(-b12, s, d2);
@@ -662,6 +703,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.rec32 = reinterpret_cast<const float4*>(s.rec32);
   a.rec64 = s.rec64;
   a.lhs64 = s.tab.lhs64;
+  a.slot_t = s.slot_t;
   a.tab32 = s.tab.tab32;
   a.kq32 = s.kq32;
   a.order = order;

@@ -80,3 +80,40 @@ def test_paper_workload_mixed():
     worst = max(_rel(log[k, c], ref[k, c]) for k in range(steps) for c in range(3))
     print(f"paper mixed: worst step err {worst:.1e}")
     assert worst <= 1e-5, worst
+
+
+@pytest.mark.parametrize("E0", [10.0, 100.0])
+def test_paper_workload_high_energy(E0):
+    """The paper's higher beam energies (gamma 20.6 and 196.7), one step from a 30-step history of the
+    paper's bunch, against the oracle. The retarded solve of a source moving towards the target is
+    conditioned like 1 / (1 - beta cos psi), up to 2 gamma^2: both the oracle and the FP64 path lose
+    digits in proportion (at gamma 196.7 the oracle itself is 2.4e-11 from a 40-digit evaluation of
+    the same formulas), so the FP64 bar is 1e-12 scaled by (gamma0 / 3)^2. The mixed path keeps 1e-5:
+    its C0 = L1^2 - |d|^2 is formed again in FP64 for the pairs where FP32 would lose that."""
+    b = inputs.paper_bunch(800, E0, theta=math.radians(30), phi=math.radians(45), seed=8, weight=1e6)
+    par = oracle.bext_params(2, m0=inputs.PAPER_M0, center=CENTER)
+    run = oracle.Run(b.x, b.u, 64, 1e-12, weights=b.weights, nmax=30)
+    run.step(29, bkind=2, bpar=par)
+    n = run.n
+    T, W, V = run.T[:n + 1], run.W[:n + 1], run.V[:n + 1]
+    E_ref, B_ref, st_ref, M = oracle.self_fields(T, W, V, n, 64, weights=b.weights, mags=True)
+    step = oracle.Run(None, run.u, 64, 1e-12, weights=b.weights, nmax=1, T0=T, W0=W, V0=V)
+    step.step(1, bkind=2, bpar=par)  # B of the step: self field plus the dipole at x^{n+1/2}
+    gamma0 = inputs.beam_kinematics(E0 * 1e6 * inputs.Q_E)[0]
+    tol = {"fp64": 1e-12 * max(1.0, (gamma0 / 3.0) ** 2), "mixed": 1e-5}
+    out = {}
+    for precision in ("fp64", "mixed"):
+        with emppp.Solver(800, 64, 1e-12, precision=precision, proposal="closed_form") as s:
+            s.set_history(n, T.copy(), W.copy(), V.copy(), run.u.copy(), b.weights.copy())
+            s.step(1, emppp.bext_dipole(inputs.PAPER_M0, CENTER))
+            E, B = s.get_fields()
+            st = s.stats()
+        eE = float(np.max(np.abs(E - E_ref) / np.maximum(M[:, 0:1], 1e-300)))
+        eB = float(np.max(np.abs(B - step.B) / np.maximum(M[:, 1:2], 1e-300)))
+        out[precision] = (eE, eB, st["guard_fallbacks"])
+        for k in ("out_of_history", "shortcut", "bisection"):
+            assert st[k] == st_ref[k], (precision, k, st, st_ref)
+    print(f"paper E0={E0} MeV (gamma {gamma0:.1f}): fp64 err {out['fp64'][0]:.1e}/{out['fp64'][1]:.1e}, mixed err "
+          f"{out['mixed'][0]:.1e}/{out['mixed'][1]:.1e} ({out['mixed'][2]} FP64 fallbacks); branches {st_ref}")
+    for p in ("fp64", "mixed"):
+        assert max(out[p][:2]) <= tol[p], (p, out[p], tol[p])
