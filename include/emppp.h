@@ -100,8 +100,9 @@ typedef struct {
   double step_ms;          /* device time of whole steps (timing option on, else 0) */
   int64_t timed_steps;     /* steps whose events were recorded (the event pool holds 4096 steps) */
   double dt_last;          /* step size of the last step (s) */
-  double eta_min;          /* adaptive step: min |eta_ij| of the last step's pairs above the cutoff (m), else 0 */
-  double v_max;            /* adaptive step: max |v_i - v_j(t_r)| of the same pairs (m/s), else 0 */
+  double eta_min;          /* adaptive step: min |eta_ij| over the last step's pairs above the cutoff (m), else 0;
+                              in a batch, of the bunch whose step is the smallest */
+  double v_max;            /* adaptive step: max |v_i - v_j(t_r)| over the same pairs (m/s), else 0 */
 } emppp_stats;
 
 /* Work split of the pair kernel: items_per_block work items (bunch, source chunk, target tile) per
@@ -292,7 +293,8 @@ EMPPP_API emppp_status emppp_mlp_train(float* params, const float* features, con
  * The history then holds unevenly spaced slots, which the retarded-time search handles by their time
  * stamps. The mixed path forms eta_min and v_max in FP32. emppp_stats reports the last step's dt,
  * eta_min and v_max; emppp_get_state the accumulated time. enable = 0 (or cfg = NULL) returns to the
- * fixed dt of emppp_create. In a batch the step is common to all bunches (the smallest of theirs); with
+ * fixed dt of emppp_create. In a batch each bunch's step comes from its own pairs, and the step taken,
+ * common to all bunches, is the smallest of them; with
  * pair fields off no pair qualifies and every step is dt_max. Returns EMPPP_ERR_ARG unless c_dt > 0,
  * eta_allow >= 0 and 0 < dt_min <= dt_max, all finite. The setting is kept until changed, across
  * emppp_set_particles and emppp_set_history. */

@@ -493,7 +493,7 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.stats, kStatCount);
   ALLOC(s.err, 1);
   ALLOC(s.bsum, (size_t)nbunch * 4);
-  ALLOC(s.scale, 2);
+  ALLOC(s.scale, (size_t)nbunch * 2);
   ALLOC(s.adapt_info, 3);
   ALLOC(s.ext32, N * 3);
   ALLOC(c->d_mon, (size_t)nbunch);

@@ -126,7 +126,7 @@ struct DeviceState {
   // w_{k0} + v_{k0} (t_n - t_{k0}) - w_n (where the out-of-history line of eq:linear2 is at t_n)
   float4* ext32;
   // adaptive time step (Sec. 2.4)
-  unsigned long long* scale;  // [2] bit patterns of eta_min (m, reduced by min) and v_max^2 ((m/s)^2, by max)
+  unsigned long long* scale;  // [nbunch][2] bit patterns of eta_min (m, by min) and v_max^2 ((m/s)^2, by max)
   double* adapt_info;         // [3] dt, eta_min, v_max of the last adaptive step
 };
 

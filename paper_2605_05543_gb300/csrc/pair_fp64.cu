@@ -366,8 +366,13 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
       }
     }
   }
+  if (ADAPT) {
+    // this item's interaction scale into its bunch's slots (every lane of the warp takes part)
+    reduce_scale(a.scale + 2 * b, emin, vmax2);
+    emin = __longlong_as_double(0x7ff0000000000000LL);
+    vmax2 = 0.0;
+  }
   }  // work items
-  if (ADAPT) reduce_scale(a.scale, emin, vmax2);
   // counters: one atomic per warp and counter
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);

@@ -653,8 +653,13 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN
       }
     }
   }
+  if (ADAPT) {
+    // this item's interaction scale into its bunch's slots (every lane of the warp takes part)
+    reduce_scale(a.scale + 2 * b, (double)emin, (double)vmax2 * (kC * kC));
+    emin = __int_as_float(0x7f800000);
+    vmax2 = 0.f;
+  }
   }  // work items
-  if (ADAPT) reduce_scale(a.scale, (double)emin, (double)vmax2 * (kC * kC));
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
   n_bi = __reduce_add_sync(0xffffffffu, n_bi);

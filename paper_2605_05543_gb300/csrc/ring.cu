@@ -122,20 +122,29 @@ __global__ void prep_kernel(DeviceState s) {
   }
 }
 
-// Adaptive time step (Sec. 2.4): dt = c_dt eta_min / v_max from the pair kernel's reduction, clamped to
-// [dt_min, dt_max] (dt_max when no pair qualified or v_max = 0); it becomes the step size of this step's
-// push. The reduction is then reset for the next step.
+// Adaptive time step (Sec. 2.4): each bunch's dt_b = c_dt eta_min,b / v_max,b from the pair kernel's
+// per-bunch reduction, clamped to [dt_min, dt_max] (dt_max when no pair qualified or v_max = 0); the
+// step of all bunches (one clock) is the smallest dt_b, and it becomes this step's push step. The
+// reported eta_min and v_max are those of the bunch that sets it. The reduction is then reset.
 __global__ void adaptive_dt_kernel(DeviceState s, AdaptParams ap) {
-  const double eta_min = __longlong_as_double((long long)s.scale[0]);
-  const double v_max = sqrt(__longlong_as_double((long long)s.scale[1]));
-  const bool bounded = v_max > 0.0 && eta_min < __longlong_as_double(0x7ff0000000000000LL);
-  const double dt = fmin(ap.dt_max, fmax(ap.dt_min, bounded ? ap.c_dt * eta_min / v_max : ap.dt_max));
+  double dt = ap.dt_max, eta_rep = 0.0, v_rep = 0.0;
+  for (int b = 0; b < s.nbunch; b++) {
+    const double eta_min = __longlong_as_double((long long)s.scale[2 * b]);
+    const double v_max = sqrt(__longlong_as_double((long long)s.scale[2 * b + 1]));
+    const bool bounded = v_max > 0.0 && eta_min < __longlong_as_double(0x7ff0000000000000LL);
+    const double dtb = fmin(ap.dt_max, fmax(ap.dt_min, bounded ? ap.c_dt * eta_min / v_max : ap.dt_max));
+    if (b == 0 || dtb < dt) {
+      dt = dtb;
+      eta_rep = bounded ? eta_min : 0.0;
+      v_rep = v_max;
+    }
+    s.scale[2 * b] = (unsigned long long)0x7ff0000000000000ULL;  // +inf
+    s.scale[2 * b + 1] = 0ull;
+  }
   s.state->dt = dt;
   s.adapt_info[0] = dt;
-  s.adapt_info[1] = bounded ? eta_min : 0.0;
-  s.adapt_info[2] = v_max;
-  s.scale[0] = (unsigned long long)0x7ff0000000000000ULL;  // +inf
-  s.scale[1] = 0ull;
+  s.adapt_info[1] = eta_rep;
+  s.adapt_info[2] = v_rep;
 }
 
 // Per-source vectors of the mixed path, each step (eq:linear at t_n, eq:linear2):
@@ -171,8 +180,10 @@ __global__ void extrap_kernel(DeviceState s) {
 }
 
 __global__ void reset_scale_kernel(DeviceState s) {
-  s.scale[0] = (unsigned long long)0x7ff0000000000000ULL;
-  s.scale[1] = 0ull;
+  for (int b = 0; b < s.nbunch; b++) {
+    s.scale[2 * b] = (unsigned long long)0x7ff0000000000000ULL;
+    s.scale[2 * b + 1] = 0ull;
+  }
   s.adapt_info[0] = s.state->dt;
   s.adapt_info[1] = 0.0;
   s.adapt_info[2] = 0.0;

@@ -214,3 +214,56 @@ def test_graph_replay_is_bitwise_identical(precision):
         out.append((x, u, t, T))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2] == out[1][2] and np.array_equal(out[0][3], out[1][3])
+
+
+def test_adaptive_with_ring_wrap_and_batch():
+    """Adaptive steps over a history ring that wraps (depth 8 for 20 steps) and in a two-bunch batch: each
+    bunch's state equals its own single-bunch run driven by the batch's common steps (the smaller of the
+    two bunches' steps), and the single-bunch FP64 run with depth 8 matches the oracle's."""
+    b1 = inputs.gaussian_bunch(150, 3e-6, 3.0, seed=21)
+    b2 = inputs.gaussian_bunch(90, 1e-6, 5.0, seed=22)
+    D, steps = 8, 20
+    # ring wrap, single bunch, against the oracle
+    run = _oracle_run(b1, D, steps, PAPER)
+    log, x, u, t, n, _ = _gpu_run(b1, D, steps, PAPER)
+    ref = np.array(run.adaptive_log)
+    worst = max(_rel(log[k, c], ref[k, c]) for k in range(steps) for c in range(3))
+    err = np.max(np.linalg.norm(x - run.x, axis=1)) / _sigma_rms(run.x)
+    assert worst <= 1e-9 and err <= 1e-9, (worst, err)
+    # the batch takes the smaller step of the two bunches at every step
+    with emppp.Solver(0, D, DT0, bunches=[150, 90]) as s:
+        s.set_particles(np.concatenate([b1.x, b2.x]), np.concatenate([b1.u, b2.u]))
+        s.set_adaptive_dt(**PAPER)
+        dts = []
+        for _ in range(steps):
+            s.step(1)
+            dts.append(s.stats()["dt_last"])
+        xb, ub, tb, nb = s.get_state()
+    log1 = _gpu_run(b1, D, steps, PAPER)[0]
+    log2 = _gpu_run(b2, D, steps, PAPER)[0]
+    assert _rel(dts[0], min(log1[0, 0], log2[0, 0])) <= 1e-15
+    # replaying the batch's steps on each bunch alone gives the batch's states
+    for (bb, lo, hi) in ((b1, 0, 150), (b2, 150, 240)):
+        r = oracle.Run(bb.x, bb.u, D, DT0, nmax=steps)
+        for dt in dts:
+            r.dt = dt
+            r.step(1)
+        e = np.max(np.linalg.norm(xb[lo:hi] - r.x, axis=1)) / _sigma_rms(r.x)
+        assert e <= 1e-9, e
+
+
+def test_adaptive_with_learned_proposal():
+    """The network proposal under the adaptive step: same states as the bisection proposal, bit for bit."""
+    b = inputs.gaussian_bunch(200, 5e-6, 3.0, seed=23)
+    params = inputs.mlp_init_params(0)
+    out = []
+    for proposal in ("bisect", "mlp"):
+        with emppp.Solver(200, 32, DT0, proposal=proposal) as s:
+            if proposal == "mlp":
+                s.set_proposal(params)
+            s.set_particles(b.x.copy(), b.u.copy())
+            s.set_adaptive_dt(**PAPER)
+            s.step(10)
+            x, u, t, n = s.get_state()
+        out.append((x, u, t))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1]) and out[0][2] == out[1][2]
