@@ -82,6 +82,7 @@ struct emppp_ctx {
   bool t_stale = false;
   // stage-switch monitor (Sec. 2.7): criterion and per-bunch device record
   EnergyParams energy{0, 1, 0.0};
+  long long max_bunch = 0;  // particles of the largest bunch
   EnergyMon* d_mon = nullptr;
   // counters
   int64_t launches = 0;   // kernels launched (cumulative)
@@ -330,41 +331,30 @@ emppp_status convert_bext(const emppp_bext* bext, BextParams* bp) {
 emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev, int* nkernels) {
   int k = 0;
   if (ev) CU(cudaEventRecord(ev[0], h->stream));
-  CU(launch_prep(h->ds, h->stream));
+  // window, slot tables, work counter and (mixed path) per-source segment vectors
+  const bool mixed_pairs = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED;
+  CU(launch_setup(h->ds, mixed_pairs, h->stream));
   k += 1;
-  const bool ordered = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED && h->target_order;
+  const bool ordered = mixed_pairs && h->target_order;
   if (ordered) {
-    CU(launch_target_order(h->ds, h->ord_key, h->order, h->stream));
+    CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
     k += 1;
   }
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
-    if (h->opt.precision == EMPPP_MIXED) {
-      CU(launch_extrap(h->ds, h->stream));
-      k += 1;
-    }
     if (h->opt.precision == EMPPP_MIXED)
       CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
     else
       CU(launch_pair_fp64(h->ds, h->opt.proposal, h->adapt, h->launch, h->stream));
     k += 1;
-    if (any_chunked(h)) {
-      CU(launch_reduce_partials(h->ds, h->stream));
-      k += 1;
-    }
   } else {
     CU(launch_zero_self(h->ds, h->stream));
     k += 1;
   }
-  if (h->adapt.on) {
-    // step size of this step's push from the pair evaluation's interaction scale (Sec. 2.4)
-    CU(launch_adaptive_dt(h->ds, h->adapt, h->stream));
-    k += 1;
-  }
   if (ev) CU(cudaEventRecord(ev[2], h->stream));
-  CU(launch_push(h->ds, bp, h->stream));
-  CU(launch_advance(h->ds, h->stream));
-  k += 2;
+  // partial sums, step size (Sec. 2.4), push and append (Sec. 2.3), clock advance: one launch
+  CU(launch_step_post(h->ds, bp, h->adapt, h->opt.pair_fields && any_chunked(h), h->stream));
+  k += 1;
   if (h->energy.on) {
     // mean energy of the new state and the switch criterion (Sec. 2.7)
     CU(launch_energy(h->ds, h->energy, h->d_mon, false, h->stream));
@@ -450,6 +440,7 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
     memset(&c->hb[b], 0, sizeof(BunchDesc));
     c->hb[b].off = off;
     c->hb[b].n = (int)nper[b];
+    if (nper[b] > c->max_bunch) c->max_bunch = nper[b];
     for (long long k = 0; k < nper[b]; k++) bunch_of[(size_t)(off + k)] = b;
     off += nper[b];
   }
@@ -490,6 +481,11 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.partial, (size_t)s.max_split * N * 6);
   ALLOC(s.state, 1);
   ALLOC(s.work, 1);
+  ALLOC(s.done, 1);
+  if (cudaMemset(s.done, 0, sizeof(unsigned)) != cudaSuccess || cudaMemset(s.work, 0, sizeof(int)) != cudaSuccess) {
+    emppp_destroy(c);
+    return fail(EMPPP_ERR_CUDA, "zeroing the launch counters failed");
+  }
   ALLOC(s.stats, kStatCount);
   ALLOC(s.err, 1);
   ALLOC(s.bsum, (size_t)nbunch * 4);
@@ -911,17 +907,16 @@ EMPPP_API emppp_status emppp_reset_stats(emppp_handle h) {
 // one evaluation of the self fields of the present state: slot tables, target order, pair kernel,
 // reduction (no push: the state does not change)
 emppp_status enqueue_fields(emppp_handle h) {
-  CU(launch_prep(h->ds, h->stream));
+  CU(launch_setup(h->ds, h->opt.precision == EMPPP_MIXED, h->stream));
   const bool ordered = h->opt.precision == EMPPP_MIXED && h->target_order;
-  if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->stream));
+  if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
   if (h->opt.precision == EMPPP_MIXED) {
-    CU(launch_extrap(h->ds, h->stream));
     CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
   } else {
     CU(launch_pair_fp64(h->ds, h->opt.proposal, h->adapt, h->launch, h->stream));
   }
   if (any_chunked(h)) CU(launch_reduce_partials(h->ds, h->stream));
-  h->launches += 3 + (ordered ? 1 : 0) + (h->opt.precision == EMPPP_MIXED ? 1 : 0);
+  h->launches += 2 + (ordered ? 1 : 0) + (any_chunked(h) ? 1 : 0);
   return EMPPP_OK;
 }
 

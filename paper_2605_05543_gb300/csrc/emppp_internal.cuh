@@ -115,7 +115,8 @@ struct DeviceState {
   double* Bout;
   double* partial;  // [C][N][6] per-source-chunk partial sums
   int max_split;    // chunks the partial buffer holds
-  int* work;        // work-item counter of the persistent pair kernels
+  int* work;        // work-item counter of the persistent pair kernels (zeroed by the set-up launch)
+  unsigned* done;   // blocks of the post-pair launch that have finished (reset by its last block)
   StepState* state;
   unsigned long long* stats;  // [kStatCount]
   int* err;
@@ -209,9 +210,7 @@ cudaError_t launch_gather_slot(const DeviceState& s, int p, double* W, double* V
 cudaError_t launch_set_state(const DeviceState& s, long long n, double t, double dt, long long hist_start,
                              const double* u, const double* w, cudaStream_t st);
 cudaError_t launch_prep(const DeviceState& s, cudaStream_t st);
-cudaError_t launch_advance(const DeviceState& s, cudaStream_t st);
-cudaError_t launch_adaptive_dt(const DeviceState& s, const AdaptParams& ap, cudaStream_t st);
-cudaError_t launch_extrap(const DeviceState& s, cudaStream_t st);
+cudaError_t launch_setup(const DeviceState& s, bool extrap, cudaStream_t st);
 cudaError_t launch_reset_scale(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st);
 // pair_fp64.cu
@@ -221,7 +220,8 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptPara
 cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
-cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st);
+cudaError_t launch_step_post(const DeviceState& s, const BextParams& b, const AdaptParams& ap, bool chunked,
+                             cudaStream_t st);
 // stage2.cu
 cudaError_t launch_bunch_sums(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_translate(const DeviceState& s, const double* shifts, cudaStream_t st);
@@ -229,7 +229,7 @@ cudaError_t launch_transport_chunk(const DeviceState& s, const BextParams& b, do
                                    cudaStream_t st);
 // order.cu
 cudaError_t prepare_target_order();
-cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, cudaStream_t st);
+cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, long long max_bunch, cudaStream_t st);
 // mlp.cu
 size_t mlp_image_bytes();
 cudaError_t launch_build_image(const float* params, void* image, cudaStream_t st);

@@ -137,8 +137,10 @@ cudaError_t prepare_target_order() {
   return cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
 }
 
-cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, cudaStream_t st) {
-  order_kernel<<<s.nbunch, kThreads, kSmem, st>>>(s, key, order);
+cudaError_t launch_target_order(const DeviceState& s, unsigned* key, int* order, long long max_bunch, cudaStream_t st) {
+  // histogram of the largest bunch's cells only: a small system does not reserve 128 KB of shared memory
+  const size_t smem = sizeof(int) << (3 * cell_bits((int)(max_bunch < (1LL << 30) ? max_bunch : (1LL << 30))));
+  order_kernel<<<s.nbunch, kThreads, smem, st>>>(s, key, order);
   return cudaGetLastError();
 }
 

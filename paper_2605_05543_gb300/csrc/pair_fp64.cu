@@ -467,8 +467,7 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptPara
   a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
   a.scale = s.scale;
   a.eta_allow = ap.eta_allow;
-  cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
+  // the work counter is zeroed by the set-up launch that precedes every pair launch
   if (ap.on)
     launch_fp64<true>(proposal, pl, a, st);
   else

@@ -729,8 +729,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.scale = s.scale;
   a.eta_allow = (float)ap.eta_allow;
   a.ext32 = s.ext32;
-  cudaError_t e = cudaMemsetAsync(s.work, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
+  // the work counter is zeroed by the set-up launch that precedes every pair launch
   if (ap.on)
     launch_mixed<true>(proposal, pl, a, st);
   else

@@ -8,48 +8,122 @@
 //   u^{n+1} = u^+ + h E + u^+ x t   (u^+ x t, not the u^- x t misprint the paper warns about);
 //   v^{n+1} = u^{n+1} / gamma^{n+1};  x^{n+1} = x^{n+1/2} + (dt/2) v^{n+1}.
 // Then slot n+1 (modulo D) receives (x^{n+1}, v^{n+1}) and the time stamp t_n + dt.
-// O(N) work; FP64 throughout (the momentum update needs it).
+// O(N) work; FP64 throughout (the momentum update needs it). The launch also sums the pair kernel's
+// per-chunk partial fields, picks the adaptive step and advances the clock, so that a step after the
+// pair kernel is one launch.
 #include "emppp_internal.cuh"
 #include "push_math.cuh"
 #include "shadow.cuh"
 
 namespace emppp {
 
-__global__ void push_kernel(DeviceState s, BextParams bp) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const StepState st = *s.state;
-  const int pnext = st.pn + 1 == s.D ? 0 : st.pn + 1;
-  if (i == 0) s.slot_t[pnext] = st.t + st.dt;
-  if (i >= s.N) return;
-  const double* rec = s.rec64 + ((size_t)i * s.D + st.pn) * 6;
-  double x[3] = {rec[0], rec[1], rec[2]};
-  double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
-  const double E[3] = {s.Eself[3 * i], s.Eself[3 * i + 1], s.Eself[3 * i + 2]};
-  const double Bs[3] = {s.Bself[3 * i], s.Bself[3 * i + 1], s.Bself[3 * i + 2]};
-  double v[3], B[3];
-  push_particle(x, u, E, Bs, bp, st.dt, v, B);
-  const double x0 = x[0], x1 = x[1], x2 = x[2], v0 = v[0], v1 = v[1], v2 = v[2];
-  if (!isfinite(x0 + x1 + x2 + u[0] + u[1] + u[2])) atomicOr(s.err, kErrNonFinite);
-  s.u[3 * i] = u[0];
-  s.u[3 * i + 1] = u[1];
-  s.u[3 * i + 2] = u[2];
-  for (int c = 0; c < 3; c++) s.Bout[3 * i + c] = B[c];
-  // append slot n+1 (both rings)
-  double* r = s.rec64 + ((size_t)i * s.D + pnext) * 6;
-  reinterpret_cast<double2*>(r)[0] = make_double2(x0, x1);
-  reinterpret_cast<double2*>(r)[1] = make_double2(x2, v0);
-  reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
-  float4 q[3];
-  const BunchDesc& bd = s.bunches[s.bunch_of[i]];
-  shadow_record(bd.origin, bd.beta_ref, x0, x1, x2, v0, v1, v2, gamma2_of_u(u[0], u[1], u[2]), q);
-  float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)i * s.D + pnext) * 12);
-  o[0] = q[0];
-  o[1] = q[1];
-  o[2] = q[2];
+// Step size of the push from the pair kernel's per-bunch interaction scales (Sec. 2.4): each bunch's
+// dt_b = c_dt eta_min,b / v_max,b clamped to [dt_min, dt_max] (dt_max when no pair qualified or v_max = 0);
+// the step of all bunches (one clock) is the smallest dt_b. eta_rep and v_rep are the binding bunch's.
+__device__ __forceinline__ double adaptive_step(const DeviceState& s, const AdaptParams& ap, double& eta_rep,
+                                                double& v_rep) {
+  double dt = ap.dt_max;
+  eta_rep = 0.0;
+  v_rep = 0.0;
+  for (int b = 0; b < s.nbunch; b++) {
+    const double eta_min = __longlong_as_double((long long)s.scale[2 * b]);
+    const double v_max = sqrt(__longlong_as_double((long long)s.scale[2 * b + 1]));
+    const bool bounded = v_max > 0.0 && eta_min < __longlong_as_double(0x7ff0000000000000LL);
+    const double dtb = fmin(ap.dt_max, fmax(ap.dt_min, bounded ? ap.c_dt * eta_min / v_max : ap.dt_max));
+    if (b == 0 || dtb < dt) {
+      dt = dtb;
+      eta_rep = bounded ? eta_min : 0.0;
+      v_rep = v_max;
+    }
+  }
+  return dt;
 }
 
-cudaError_t launch_push(const DeviceState& s, const BextParams& b, cudaStream_t st) {
-  push_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s, b);
+// The rest of a step after the pair kernel, in one launch: the sum of each target's per-chunk partial
+// fields (fixed chunk order), the adaptive step size, the push of every particle and the append of slot
+// n+1, then (by the last block to finish) the clock advance n -> n+1, t -> t + dt and the reset of the
+// interaction-scale reduction. The last block is found with a counter that every block increments once
+// after its work; nothing waits on it.
+__global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, int chunked) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const StepState st = *s.state;
+  double dt = st.dt, eta_rep = 0.0, v_rep = 0.0;
+  if (ap.on) dt = adaptive_step(s, ap, eta_rep, v_rep);
+  const int pnext = st.pn + 1 == s.D ? 0 : st.pn + 1;
+  if (i == 0) {
+    s.slot_t[pnext] = st.t + dt;
+    if (ap.on) {
+      s.adapt_info[0] = dt;
+      s.adapt_info[1] = eta_rep;
+      s.adapt_info[2] = v_rep;
+    }
+  }
+  if (i < s.N) {
+    if (chunked) {
+      // E_i = sum over the source chunks c of partial[c][i], in chunk order
+      const int S = s.sched[s.bunch_of[i]].nchunk;
+      if (S > 1) {
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < S; c++) {
+          const double* o = s.partial + ((size_t)c * s.N + i) * 6;
+#pragma unroll
+          for (int k = 0; k < 6; k++) acc[k] += o[k];
+        }
+        for (int c = 0; c < 3; c++) {
+          s.Eself[3 * i + c] = acc[c];
+          s.Bself[3 * i + c] = acc[3 + c];
+        }
+      }
+    }
+    const double* rec = s.rec64 + ((size_t)i * s.D + st.pn) * 6;
+    double x[3] = {rec[0], rec[1], rec[2]};
+    double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
+    const double E[3] = {s.Eself[3 * i], s.Eself[3 * i + 1], s.Eself[3 * i + 2]};
+    const double Bs[3] = {s.Bself[3 * i], s.Bself[3 * i + 1], s.Bself[3 * i + 2]};
+    double v[3], B[3];
+    push_particle(x, u, E, Bs, bp, dt, v, B);
+    const double x0 = x[0], x1 = x[1], x2 = x[2], v0 = v[0], v1 = v[1], v2 = v[2];
+    if (!isfinite(x0 + x1 + x2 + u[0] + u[1] + u[2])) atomicOr(s.err, kErrNonFinite);
+    s.u[3 * i] = u[0];
+    s.u[3 * i + 1] = u[1];
+    s.u[3 * i + 2] = u[2];
+    for (int c = 0; c < 3; c++) s.Bout[3 * i + c] = B[c];
+    // append slot n+1 (both rings)
+    double* r = s.rec64 + ((size_t)i * s.D + pnext) * 6;
+    reinterpret_cast<double2*>(r)[0] = make_double2(x0, x1);
+    reinterpret_cast<double2*>(r)[1] = make_double2(x2, v0);
+    reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
+    float4 q[3];
+    const BunchDesc& bd = s.bunches[s.bunch_of[i]];
+    shadow_record(bd.origin, bd.beta_ref, x0, x1, x2, v0, v1, v2, gamma2_of_u(u[0], u[1], u[2]), q);
+    float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)i * s.D + pnext) * 12);
+    o[0] = q[0];
+    o[1] = q[1];
+    o[2] = q[2];
+  }
+  // the last block to finish advances the clock and resets the reduction for the next step
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(s.done, 1u);
+    if (prev == gridDim.x - 1) {
+      s.state->n = st.n + 1;
+      s.state->t = st.t + dt;
+      s.state->dt = dt;
+      if (ap.on) {
+        for (int b = 0; b < s.nbunch; b++) {
+          s.scale[2 * b] = (unsigned long long)0x7ff0000000000000ULL;  // +inf
+          s.scale[2 * b + 1] = 0ull;
+        }
+      }
+      *s.done = 0u;
+    }
+  }
+}
+
+cudaError_t launch_step_post(const DeviceState& s, const BextParams& b, const AdaptParams& ap, bool chunked,
+                             cudaStream_t st) {
+  step_post_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s, b, ap, chunked ? 1 : 0);
   return cudaGetLastError();
 }
 

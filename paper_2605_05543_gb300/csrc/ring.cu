@@ -85,9 +85,31 @@ __global__ void set_state_kernel(DeviceState s, long long n, double t, double dt
   s.kq32[i] = (float)(-kQe * s.wts[i] / (4.0 * kPi * kEps0));
 }
 
-// Per-step slot tables over the usable window k0..n (Sec. 2.2): the squared light-travel distance
-// (c (t_n - t_k))^2 in exactly the operation order of the reference evaluation (so that the FP64
-// node test decides identically), its FP32 rounding, c (t_n - t_k) in FP32, and 1 / (t_{k+1} - t_k).
+// Slot-table entry of window offset l (slot p0 + l, modulo D) at time t_n (Sec. 2.2): the squared
+// light-travel distance (c (t_n - t_k))^2 in exactly the operation order of the reference evaluation
+// (so that the FP64 node test decides identically), its guard-band thresholds in FP32, c (t_n - t_k) in
+// FP32, and 1 / (t_{k+1} - t_k).
+__device__ __forceinline__ void slot_table(const DeviceState& s, int l, int p0, int nwin, double t_n) {
+  int p = p0 + l;
+  if (p >= s.D) p -= s.D;
+  const double tk = s.slot_t[p];
+  const double ct = __dmul_rn(kC, __dsub_rn(t_n, tk));
+  const double lhs = __dmul_rn(ct, ct);
+  s.tab.lhs64[p] = lhs;
+  float icdt = 0.f;
+  if (l + 1 < nwin) {
+    int q = p + 1 == s.D ? 0 : p + 1;
+    const double dtk = s.slot_t[q] - tk;
+    s.tab.inv_dtk[p] = 1.0 / dtk;
+    icdt = (float)(1.0 / (kC * dtk));
+  } else {
+    s.tab.inv_dtk[p] = 0.0;
+  }
+  const double qhi = (1.0 + kGuardBand) / (1.0 - kGuardBand), qlo = (1.0 - kGuardBand) / (1.0 + kGuardBand);
+  s.tab.tab32[p] = make_float4(__double2float_ru(lhs * qhi), __double2float_rd(lhs * qlo), (float)ct, icdt);
+}
+
+// Per-step slot tables over the usable window k0..n alone (used before the delay sampler).
 __global__ void prep_kernel(DeviceState s) {
   const long long n = s.state->n;
   const double t_n = s.state->t;
@@ -101,53 +123,12 @@ __global__ void prep_kernel(DeviceState s) {
     s.state->pn = pn;
   }
   const int nwin = (int)(n - k0 + 1);
-  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nwin; l += gridDim.x * blockDim.x) {
-    int p = p0 + l;
-    if (p >= s.D) p -= s.D;
-    const double tk = s.slot_t[p];
-    const double ct = __dmul_rn(kC, __dsub_rn(t_n, tk));
-    const double lhs = __dmul_rn(ct, ct);
-    s.tab.lhs64[p] = lhs;
-    float icdt = 0.f;
-    if (l + 1 < nwin) {
-      int q = p + 1 == s.D ? 0 : p + 1;
-      const double dtk = s.slot_t[q] - tk;
-      s.tab.inv_dtk[p] = 1.0 / dtk;
-      icdt = (float)(1.0 / (kC * dtk));
-    } else {
-      s.tab.inv_dtk[p] = 0.0;
-    }
-    const double qhi = (1.0 + kGuardBand) / (1.0 - kGuardBand), qlo = (1.0 - kGuardBand) / (1.0 + kGuardBand);
-    s.tab.tab32[p] = make_float4(__double2float_ru(lhs * qhi), __double2float_rd(lhs * qlo), (float)ct, icdt);
-  }
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nwin; l += gridDim.x * blockDim.x) slot_table(s, l, p0, nwin, t_n);
 }
 
-// Adaptive time step (Sec. 2.4): each bunch's dt_b = c_dt eta_min,b / v_max,b from the pair kernel's
-// per-bunch reduction, clamped to [dt_min, dt_max] (dt_max when no pair qualified or v_max = 0); the
-// step of all bunches (one clock) is the smallest dt_b, and it becomes this step's push step. The
-// reported eta_min and v_max are those of the bunch that sets it. The reduction is then reset.
-__global__ void adaptive_dt_kernel(DeviceState s, AdaptParams ap) {
-  double dt = ap.dt_max, eta_rep = 0.0, v_rep = 0.0;
-  for (int b = 0; b < s.nbunch; b++) {
-    const double eta_min = __longlong_as_double((long long)s.scale[2 * b]);
-    const double v_max = sqrt(__longlong_as_double((long long)s.scale[2 * b + 1]));
-    const bool bounded = v_max > 0.0 && eta_min < __longlong_as_double(0x7ff0000000000000LL);
-    const double dtb = fmin(ap.dt_max, fmax(ap.dt_min, bounded ? ap.c_dt * eta_min / v_max : ap.dt_max));
-    if (b == 0 || dtb < dt) {
-      dt = dtb;
-      eta_rep = bounded ? eta_min : 0.0;
-      v_rep = v_max;
-    }
-    s.scale[2 * b] = (unsigned long long)0x7ff0000000000000ULL;  // +inf
-    s.scale[2 * b + 1] = 0ull;
-  }
-  s.state->dt = dt;
-  s.adapt_info[0] = dt;
-  s.adapt_info[1] = eta_rep;
-  s.adapt_info[2] = v_rep;
-}
-
-// Per-source vectors of the mixed path, each step (eq:linear at t_n, eq:linear2):
+// Per-step set-up, one launch before the pair kernel: the window k0..n and its slot tables (as
+// prep_kernel), the pair kernel's work counter, and, for the mixed path, per-source vectors (eq:linear at
+// t_n):
 //   P_j = w_{j,n-1} + v_{j,n-1} (t_n - t_{n-1}), the end of the last history segment, split hi/lo about
 //     the bunch origin. For a pair in the near-field shortcut bracket [n-1, n] the retarded point is
 //     written as P_j - v_{j,n-1} tau with tau = t_n - t_r: the same point as w_{j,n-1} + v_{j,n-1}
@@ -156,17 +137,30 @@ __global__ void adaptive_dt_kernel(DeviceState s, AdaptParams ap) {
 //     out-of-history case) is at t_n, relative to the source's present position. Along that line the
 //     source moves uniformly, so its field is Heaviside's field about the point w_{j,n} + X_j; the
 //     separation from a target is then (r - w_{j,n}) - X_j, formed without cancellation.
-__global__ void extrap_kernel(DeviceState s) {
-  const long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= s.N) return;
-  const StepState st = *s.state;
-  const int pn = st.pn;
+__global__ void setup_kernel(DeviceState s, int extrap) {
+  const long long n = s.state->n;
+  const double t_n = s.state->t;
+  const long long hs = s.state->hist_start;
+  const long long k0 = n - s.D + 1 > hs ? n - s.D + 1 : hs;
+  const int p0 = (int)(k0 % s.D);
+  const int pn = (int)(n % s.D);
+  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid == 0) {
+    s.state->k0 = k0;
+    s.state->p0 = p0;
+    s.state->pn = pn;
+    *s.work = 0;
+  }
+  const int nwin = (int)(n - k0 + 1);
+  if (gid < nwin) slot_table(s, (int)gid, p0, nwin, t_n);
+  if (!extrap || gid >= s.N) return;
+  const long long j = gid;
   const double* rn = s.rec64 + ((size_t)j * s.D + pn) * 6;
-  const double* r0 = s.rec64 + ((size_t)j * s.D + st.p0) * 6;
-  const double dt0 = s.slot_t[pn] - s.slot_t[st.p0];
+  const double* r0 = s.rec64 + ((size_t)j * s.D + p0) * 6;
+  const double dt0 = s.slot_t[pn] - s.slot_t[p0];
   s.ext32[3 * j + 2] = make_float4((float)((r0[0] + r0[3] * dt0) - rn[0]), (float)((r0[1] + r0[4] * dt0) - rn[1]),
                                    (float)((r0[2] + r0[5] * dt0) - rn[2]), 0.f);
-  if (st.n <= st.k0) return;  // no segment [n-1, n] in the window
+  if (n <= k0) return;  // no segment [n-1, n] in the window
   const int p1 = pn == 0 ? s.D - 1 : pn - 1;
   const double dtl = s.slot_t[pn] - s.slot_t[p1];
   const double* r = s.rec64 + ((size_t)j * s.D + p1) * 6;
@@ -187,11 +181,6 @@ __global__ void reset_scale_kernel(DeviceState s) {
   s.adapt_info[0] = s.state->dt;
   s.adapt_info[1] = 0.0;
   s.adapt_info[2] = 0.0;
-}
-
-__global__ void advance_kernel(StepState* state) {
-  state->n = state->n + 1;
-  state->t = state->t + state->dt;
 }
 
 __global__ void gather_positions_kernel(DeviceState s, double* __restrict__ x) {
@@ -233,18 +222,9 @@ cudaError_t launch_prep(const DeviceState& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_advance(const DeviceState& s, cudaStream_t st) {
-  advance_kernel<<<1, 1, 0, st>>>(s.state);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adaptive_dt(const DeviceState& s, const AdaptParams& ap, cudaStream_t st) {
-  adaptive_dt_kernel<<<1, 1, 0, st>>>(s, ap);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_extrap(const DeviceState& s, cudaStream_t st) {
-  extrap_kernel<<<blocks_for(s.N, 256), 256, 0, st>>>(s);
+cudaError_t launch_setup(const DeviceState& s, bool extrap, cudaStream_t st) {
+  const long long n = extrap ? (s.N > s.D ? s.N : s.D) : s.D;
+  setup_kernel<<<blocks_for(n, 256), 256, 0, st>>>(s, extrap ? 1 : 0);
   return cudaGetLastError();
 }
 
