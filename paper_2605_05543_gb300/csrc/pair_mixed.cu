@@ -176,7 +176,7 @@ __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict_
 }  // namespace
 
 template <int PROP, bool ADAPT>
-__global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 3 : EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
+__global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
