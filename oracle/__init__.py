@@ -64,14 +64,23 @@ def _bind(lib):
     lib.orc_retarded.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                  _d, _d, _d, _i64]
     lib.orc_retarded.restype = ctypes.c_int
+    lib.orc_retarded_ex.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                    _d, ctypes.c_int, _d, _d, _i64]
+    lib.orc_retarded_ex.restype = ctypes.c_int
     lib.orc_self_fields.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _i64,
                                     ctypes.c_int64, _d, _d, _d, _i64]
     lib.orc_self_fields.restype = ctypes.c_int
+    lib.orc_self_fields_ex.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _i64,
+                                       ctypes.c_int64, ctypes.c_int, _d, _d, _d, _i64]
+    lib.orc_self_fields_ex.restype = ctypes.c_int
     lib.orc_push.argtypes = [ctypes.c_int64, ctypes.c_double, _d, _d, _d, _d, ctypes.c_int, _d, _d, _d]
     lib.orc_push.restype = ctypes.c_int
     lib.orc_step.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                              _d, ctypes.c_int, _d, ctypes.c_int, _d, _d, _i64]
     lib.orc_step.restype = ctypes.c_int
+    lib.orc_step_ex.argtypes = [ctypes.c_int64, _d, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                _d, ctypes.c_int, _d, ctypes.c_int, ctypes.c_int, _d, _d, _i64]
+    lib.orc_step_ex.restype = ctypes.c_int
     lib.orc_interaction_scale.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                                           _d]
     lib.orc_interaction_scale.restype = ctypes.c_int
@@ -173,23 +182,31 @@ def node_test(T, W, j, r, t, k, lib=None) -> bool:
     return bool(lib.orc_node_test(W.shape[1], _p(T), _p(W), int(j), _p(r), float(t), int(k)))
 
 
-def retarded(T, W, V, n, D, j, r, lib=None):
-    """Retarded state of source j seen from (r, T[n]): dict(w, v, a, tr, branch, k1, ntest)."""
+# step variants, kept as accuracy comparisons: the midpoint reconstruction of eq:mid and the self fields
+# at the half-step point (x^{n+1/2}, t_n + dt/2)
+MIDPOINT = 1
+HALF_STEP = 2
+
+
+def retarded(T, W, V, n, D, j, r, lib=None, variant=0):
+    """Retarded state of source j seen from (r, T[n]): dict(w, v, a, tr, branch, k1, ntest).
+    variant = MIDPOINT reconstructs bracketed pairs by eq:mid."""
     lib = lib or load()
     T, W, V, r = _f64(T), _f64(W), _f64(V), _f64(r, 3)
     out = np.zeros(9)
     tr = np.zeros(1)
     info = np.zeros(3, dtype=np.int64)
-    st = lib.orc_retarded(W.shape[1], _p(T), _p(W), _p(V), int(n), int(D), int(j), _p(r), _p(out), _p(tr),
-                          _pi(info))
+    st = lib.orc_retarded_ex(W.shape[1], _p(T), _p(W), _p(V), int(n), int(D), int(j), _p(r), int(variant),
+                             _p(out), _p(tr), _pi(info))
     _check(st, "retarded")
     return dict(w=out[0:3].copy(), v=out[3:6].copy(), a=out[6:9].copy(), tr=float(tr[0]),
                 branch=int(info[0]), k1=int(info[1]), ntest=int(info[2]))
 
 
-def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None, mags=False):
+def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None, mags=False, variant=0):
     """Self fields on targets (all if None) at step n. Returns (E, B, stats), or (E, B, stats, M) with
-    mags=True where M[:, 0] = sum_j |E_ij| and M[:, 1] = sum_j |B_ij| per target.
+    mags=True where M[:, 0] = sum_j |E_ij| and M[:, 1] = sum_j |B_ij| per target. variant = MIDPOINT
+    reconstructs bracketed pairs by eq:mid.
 
     stats = dict(out_of_history, shortcut, bisection, node_tests) over all evaluated pairs.
     """
@@ -207,8 +224,8 @@ def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None, mags=False)
     B = np.zeros((nt, 3))
     stats = np.zeros(4, dtype=np.int64)
     M = np.zeros((nt, 2))
-    st = lib.orc_self_fields(N, _p(T), _p(W), _p(V), int(n), int(D), None if wts is None else _p(wts),
-                             None if tg is None else _pi(tg), nt, _p(E), _p(B), _p(M), _pi(stats))
+    st = lib.orc_self_fields_ex(N, _p(T), _p(W), _p(V), int(n), int(D), None if wts is None else _p(wts),
+                                None if tg is None else _pi(tg), nt, int(variant), _p(E), _p(B), _p(M), _pi(stats))
     _check(st, "self_fields")
     sd = dict(zip(("out_of_history", "shortcut", "bisection", "node_tests"), stats.tolist()))
     return (E, B, sd, M) if mags else (E, B, sd)
@@ -298,9 +315,12 @@ class Run:
     def t(self):
         return self.T[self.n]
 
-    def step(self, nsteps=1, bkind=0, bpar=None, self_on=True, adaptive=None):
+    def step(self, nsteps=1, bkind=0, bpar=None, self_on=True, adaptive=None, variant=0):
         """nsteps steps; adaptive = dict(c_dt, eta_allow, dt_min, dt_max) chooses each step's dt by the
-        rule of Sec. 2.4 (self fields on) and appends (dt, eta_min, v_max) to self.adaptive_log."""
+        rule of Sec. 2.4 (self fields on) and appends (dt, eta_min, v_max) to self.adaptive_log.
+        variant (fixed dt only): MIDPOINT and/or HALF_STEP, the comparison variants of the step."""
+        if adaptive is not None and variant:
+            raise OracleError("the step variants run with a fixed dt")
         bpar = bext_params() if bpar is None else _f64(bpar, 7)
         E = np.zeros((self.N, 3))
         B = np.zeros((self.N, 3))
@@ -313,9 +333,9 @@ class Run:
             if self.n + 1 >= self.T.shape[0]:
                 raise OracleError("history capacity exhausted")
             if adaptive is None:
-                st = self.lib.orc_step(self.N, _p(self.T), _p(self.W), _p(self.V), _p(self.u), self.n, self.D,
-                                       self.dt, wp, int(bkind), _p(bpar), 1 if self_on else 0, _p(E), _p(B),
-                                       _pi(stats))
+                st = self.lib.orc_step_ex(self.N, _p(self.T), _p(self.W), _p(self.V), _p(self.u), self.n, self.D,
+                                          self.dt, wp, int(bkind), _p(bpar), 1 if self_on else 0, int(variant), _p(E),
+                                          _p(B), _pi(stats))
             else:
                 st = self.lib.orc_step_adaptive(self.N, _p(self.T), _p(self.W), _p(self.V), _p(self.u), self.n,
                                                 self.D, _p(par), wp, int(bkind), _p(bpar), _p(E), _p(B), _pi(stats),

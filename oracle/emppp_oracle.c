@@ -37,6 +37,13 @@
  *   - adaptive time step (Sec. 2.4): eta_min and v_max come from the retarded solve of step n, with
  *     v_i(t) the target's stored velocity at slot n; the resulting dt is the one the push from n to
  *     n+1 uses; with no qualifying pair, or v_max = 0, dt = dt_max.
+ *   - variants kept as accuracy comparisons (not the method): the midpoint reconstruction eq:mid of
+ *     the authors' earlier scheme applies to bracketed pairs only (t_r, w, v the bracket's midpoint
+ *     values, a the finite difference); out-of-history pairs keep eq:linear2, which eq:mid does not
+ *     cover. The half-step field point evaluates the self fields at (x^{n+1/2}, t_n + dt/2), the point
+ *     the pusher's kick uses: the history gains a provisional slot n+1 holding (t_n + dt/2, x^{n+1/2},
+ *     v^n), formed with the push's own half drift, and counted in the depth D; the push then replaces
+ *     it with slot n+1.
  *   - stage switch (Sec. 2.7): E_i is the kinetic energy (gamma_i - 1) m_e c^2 per represented
  *     electron, so the weighted mean is the mean energy per electron; dE/dt at step n is the backward
  *     difference (E_n - E_{n-1}) / (t_n - t_{n-1}); the criterion arms once |dE/dt| >= eps_E (the rate
@@ -66,6 +73,9 @@ enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_NUMERIC = 2 };
 
 /* branches of the retarded-time search */
 enum { BR_OUT_OF_HISTORY = 0, BR_SHORTCUT = 1, BR_BISECTION = 2 };
+
+/* step variants (bit mask): the midpoint reconstruction eq:mid, the half-step field point */
+enum { VAR_MIDPOINT = 1, VAR_HALF_STEP = 2 };
 
 /* ------------------------------------------------------------------------------------------ */
 /* small vector helpers                                                                         */
@@ -169,15 +179,32 @@ static int solve_dt(const double d[3], double T1, const double v1[3], double* dt
 }
 
 /* Retarded position, velocity and acceleration of source j seen from (r, t) at step n
-   (eq:linear for the shortcut and bisection branches, eq:linear2 out of history). */
+   (eq:linear for the shortcut and bisection branches, eq:linear2 out of history; with `midpoint`,
+   eq:mid for the shortcut and bisection branches). */
 static int retarded_state(const history* h, int64_t j, const double r[3], double t, int64_t k0, int64_t n,
-                          double w[3], double v[3], double a[3], double* tr, int* branch, int64_t* k1out,
-                          int* ntest) {
+                          int midpoint, double w[3], double v[3], double a[3], double* tr, int* branch,
+                          int64_t* k1out, int* ntest) {
   int64_t k1;
   int br = bracket(h, j, r, t, k0, n, &k1, ntest);
   const double* w1 = hist_w(h, k1, j);
   const double* v1 = hist_v(h, k1, j);
   double t1 = h->T[k1];
+  *branch = br;
+  *k1out = k1;
+  if (midpoint && br != BR_OUT_OF_HISTORY) {
+    /* eq:mid: the midpoint of the bracket [t1, t2] stands for the retarded time */
+    const double* w2 = hist_w(h, k1 + 1, j);
+    const double* v2 = hist_v(h, k1 + 1, j);
+    double t2 = h->T[k1 + 1];
+    double span = t2 - t1;
+    *tr = (t1 + t2) / 2.0;
+    for (int c = 0; c < 3; c++) {
+      w[c] = (w1[c] + w2[c]) / 2.0;
+      v[c] = (v1[c] + v2[c]) / 2.0;
+      a[c] = (v2[c] - v1[c]) / span;
+    }
+    return ORC_OK;
+  }
   double d[3] = {r[0] - w1[0], r[1] - w1[1], r[2] - w1[2]};
   double dt;
   int st = solve_dt(d, t - t1, v1, &dt);
@@ -198,8 +225,6 @@ static int retarded_state(const history* h, int64_t j, const double r[3], double
       a[c] = (v2[c] - v1[c]) / (t2 - t1);
     }
   }
-  *branch = br;
-  *k1out = k1;
   return ORC_OK;
 }
 
@@ -316,20 +341,27 @@ int orc_node_test(int64_t N, const double* T, const double* W, int64_t j, const 
   return node_test(r, t, T[k], hist_w(&h, k, j));
 }
 
-/* Retarded state of source j seen from (r, t = T[n]) with depth D.
-   out9 = {w[3], v[3], a[3]}; info = {branch, k1, ntest}; *tr = t_r. */
-int orc_retarded(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D, int64_t j,
-                 const double* r, double* out9, double* tr, int64_t* info) {
+/* Retarded state of source j seen from (r, t = T[n]) with depth D; variant & VAR_MIDPOINT selects
+   eq:mid. out9 = {w[3], v[3], a[3]}; info = {branch, k1, ntest}; *tr = t_r. */
+int orc_retarded_ex(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D, int64_t j,
+                    const double* r, int variant, double* out9, double* tr, int64_t* info) {
   if (N < 1 || n < 0 || D < 1 || j < 0 || j >= N) return ORC_ERR_ARG;
   history h = {N, T, W, V};
   int64_t k0 = n - D + 1 > 0 ? n - D + 1 : 0;
   int br, nt;
   int64_t k1;
-  int st = retarded_state(&h, j, r, T[n], k0, n, out9, out9 + 3, out9 + 6, tr, &br, &k1, &nt);
+  int st = retarded_state(&h, j, r, T[n], k0, n, variant & VAR_MIDPOINT, out9, out9 + 3, out9 + 6, tr, &br, &k1,
+                          &nt);
   info[0] = br;
   info[1] = k1;
   info[2] = nt;
   return st;
+}
+
+/* the same with the method's own reconstruction */
+int orc_retarded(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D, int64_t j,
+                 const double* r, double* out9, double* tr, int64_t* info) {
+  return orc_retarded_ex(N, T, W, V, n, D, j, r, 0, out9, tr, info);
 }
 
 /* Self fields (Sec. 2.1 superposition over j != i) at the present positions W[n][i] and time
@@ -337,10 +369,10 @@ int orc_retarded(int64_t N, const double* T, const double* W, const double* V, i
    slots k0..n, k0 = max(0, n - D + 1). q[j] = -e w[j] (wts NULL: w = 1).
    E, B: [ntgt][3]. mags (may be NULL): [ntgt][2] = {sum_j |E_ij|, sum_j |B_ij|}, the scale against
    which a per-component error of the sum is measured. stats (may be NULL): {out-of-history,
-   shortcut, bisection, node tests}. */
-int orc_self_fields(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D,
-                    const double* wts, const int64_t* tgt, int64_t ntgt, double* E, double* B, double* mags,
-                    int64_t* stats) {
+   shortcut, bisection, node tests}. variant & VAR_MIDPOINT selects eq:mid. */
+int orc_self_fields_ex(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D,
+                       const double* wts, const int64_t* tgt, int64_t ntgt, int variant, double* E, double* B,
+                       double* mags, int64_t* stats) {
   if (N < 1 || n < 0 || D < 1) return ORC_ERR_ARG;
   history h = {N, T, W, V};
   int64_t k0 = n - D + 1 > 0 ? n - D + 1 : 0;
@@ -359,7 +391,7 @@ int orc_self_fields(int64_t N, const double* T, const double* W, const double* V
       double w[3], v[3], a[3], tr, Ej[3], Bj[3];
       int br, nt;
       int64_t k1;
-      int st = retarded_state(&h, j, r, t, k0, n, w, v, a, &tr, &br, &k1, &nt);
+      int st = retarded_state(&h, j, r, t, k0, n, variant & VAR_MIDPOINT, w, v, a, &tr, &br, &k1, &nt);
       if (st == ORC_OK) {
         double eta[3] = {r[0] - w[0], r[1] - w[1], r[2] - w[2]};
         double q = -Q_E * (wts ? wts[j] : 1.0);
@@ -398,6 +430,13 @@ int orc_self_fields(int64_t N, const double* T, const double* W, const double* V
   return err;
 }
 
+/* the same with the method's own reconstruction */
+int orc_self_fields(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D,
+                    const double* wts, const int64_t* tgt, int64_t ntgt, double* E, double* B, double* mags,
+                    int64_t* stats) {
+  return orc_self_fields_ex(N, T, W, V, n, D, wts, tgt, ntgt, 0, E, B, mags, stats);
+}
+
 /* Push of Sec. 2.3 for all N particles with the given self fields: x^{n+1/2} = x^n + dt/2 v^n,
    B = Bself + B_geo(x^{n+1/2}), HC kick with h = -e dt / (2 m_e), x^{n+1} = x^{n+1/2} + dt/2 v^{n+1}.
    x, u are updated in place; v receives v^{n+1}; Btot (may be NULL) receives the B used. */
@@ -431,10 +470,14 @@ int orc_push(int64_t N, double dt, double* x, double* u, const double* Eself, co
    self fields at (W[n], T[n]) over slots k0..n, push with the background field, then append
    slot n+1: T[n+1] = T[n] + dt, W[n+1] = x^{n+1}, V[n+1] = v^{n+1}. u holds u^n on entry and
    u^{n+1} on return. self_on = 0 drops the pair fields (E = 0, B = B_geo).
+   variant: VAR_MIDPOINT reconstructs bracketed pairs by eq:mid; VAR_HALF_STEP evaluates the self
+   fields at (x^{n+1/2}, t_n + dt/2) from the history with the provisional slot n+1 = (t_n + dt/2,
+   x^n + (dt/2) v^n, v^n), v^n = u^n / gamma^n formed as the push's half drift forms it, over slots
+   max(0, n+2-D)..n+1; the push then overwrites slot n+1.
    E, B (may be NULL) receive the fields used (B including the background). */
-int orc_step(int64_t N, double* T, double* W, double* V, double* u, int64_t n, int64_t D, double dt,
-             const double* wts, int bkind, const double* bpar, int self_on, double* E, double* B,
-             int64_t* stats) {
+int orc_step_ex(int64_t N, double* T, double* W, double* V, double* u, int64_t n, int64_t D, double dt,
+                const double* wts, int bkind, const double* bpar, int self_on, int variant, double* E, double* B,
+                int64_t* stats) {
   double* Es = (double*)calloc((size_t)N * 3, sizeof(double));
   double* Bs = (double*)calloc((size_t)N * 3, sizeof(double));
   double* x = (double*)malloc((size_t)N * 3 * sizeof(double));
@@ -445,7 +488,22 @@ int orc_step(int64_t N, double* T, double* W, double* V, double* u, int64_t n, i
     return ORC_ERR_ARG;
   }
   int st = ORC_OK;
-  if (self_on) st = orc_self_fields(N, T, W, V, n, D, wts, NULL, 0, Es, Bs, NULL, stats);
+  if (self_on && (variant & VAR_HALF_STEP)) {
+    double* Wp = W + (n + 1) * N * 3;
+    double* Vp = V + (n + 1) * N * 3;
+    const double* Wn = W + n * N * 3;
+    for (int64_t i = 0; i < N; i++) {
+      double g0 = gamma_of_u(u + 3 * i);
+      for (int c = 0; c < 3; c++) {
+        Vp[3 * i + c] = u[3 * i + c] / g0;
+        Wp[3 * i + c] = Wn[3 * i + c] + 0.5 * dt * (u[3 * i + c] / g0);
+      }
+    }
+    T[n + 1] = T[n] + 0.5 * dt;
+    st = orc_self_fields_ex(N, T, W, V, n + 1, D, wts, NULL, 0, variant, Es, Bs, NULL, stats);
+  } else if (self_on) {
+    st = orc_self_fields_ex(N, T, W, V, n, D, wts, NULL, 0, variant, Es, Bs, NULL, stats);
+  }
   memcpy(x, W + n * N * 3, (size_t)N * 3 * sizeof(double));
   if (st == ORC_OK) {
     double* vnew = V + (n + 1) * N * 3;
@@ -458,6 +516,13 @@ int orc_step(int64_t N, double* T, double* W, double* V, double* u, int64_t n, i
   free(Bs);
   free(x);
   return st;
+}
+
+/* the method's own step: present field point, linear reconstruction */
+int orc_step(int64_t N, double* T, double* W, double* V, double* u, int64_t n, int64_t D, double dt,
+             const double* wts, int bkind, const double* bpar, int self_on, double* E, double* B,
+             int64_t* stats) {
+  return orc_step_ex(N, T, W, V, u, n, D, dt, wts, bkind, bpar, self_on, 0, E, B, stats);
 }
 
 /* Interaction scale of the adaptive time step (Sec. 2.4) at step n, from the same retarded solve as the
@@ -482,7 +547,7 @@ int orc_interaction_scale(int64_t N, const double* T, const double* W, const dou
       double w[3], v[3], a[3], tr;
       int br, nt;
       int64_t k1;
-      int st = retarded_state(&h, j, r, t, k0, n, w, v, a, &tr, &br, &k1, &nt);
+      int st = retarded_state(&h, j, r, t, k0, n, 0, w, v, a, &tr, &br, &k1, &nt);
       if (st != ORC_OK) {
         err |= st;
         continue;

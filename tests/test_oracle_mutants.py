@@ -39,6 +39,14 @@ MUTANTS = [
      "if (!node_test(r, t, h->T[n - 1], hist_w(h, n, j))) {"),
     ("half_width_test", "double ct = C_LIGHT * (t - tk);", "double ct = 0.5 * C_LIGHT * (t - tk);"),
     ("special_keeps_accel", "      a[c] = 0.0;\n", "      a[c] = v1[c] * 1e3;\n"),
+    # eq:mid and the half-step field point (comparison variants)
+    ("mid_w_from_w1", "w[c] = (w1[c] + w2[c]) / 2.0;", "w[c] = w1[c];"),
+    ("mid_v_from_v1", "v[c] = (v1[c] + v2[c]) / 2.0;", "v[c] = v1[c];"),
+    ("mid_a_sign", "a[c] = (v2[c] - v1[c]) / span;", "a[c] = (v1[c] - v2[c]) / span;"),
+    ("mid_tr_at_t1", "*tr = (t1 + t2) / 2.0;", "*tr = t1;"),
+    ("half_full_time", "T[n + 1] = T[n] + 0.5 * dt;", "T[n + 1] = T[n] + dt;"),
+    ("half_no_drift", "Wp[3 * i + c] = Wn[3 * i + c] + 0.5 * dt * (u[3 * i + c] / g0);", "Wp[3 * i + c] = Wn[3 * i + c];"),
+    ("half_present_point", "st = orc_self_fields_ex(N, T, W, V, n + 1, D,", "st = orc_self_fields_ex(N, T, W, V, n, D,"),
     # Sec. 2.4 adaptive time step
     ("adapt_target_velocity_old_slot", "const double* vi = hist_v(&h, n, i);", "const double* vi = hist_v(&h, k0, i);"),
     ("adapt_cutoff_ignored", "if (R < eta_allow) continue;", "if (R < 0.0) continue;"),
