@@ -65,8 +65,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--proposal", choices=["bisect", "closed_form", "mlp"], default="closed_form")
-    ap.add_argument("--workload", choices=["bunch", "batch", "paper"], default="bunch",
-                    help="bunch: the N = 65536 bunch (default); batch: 64 bunches, stage 1 then stage 2")
+    ap.add_argument("--workload", choices=["bunch", "batch", "paper", "variants"], default="bunch",
+                    help="bunch: the N = 65536 bunch (default); batch: 64 bunches, stage 1 then stage 2; paper: "
+                         "the paper's own cases; variants: eq:mid and the half-step point on the FP64 path")
     ap.add_argument("--stage2-steps", type=int, default=100000, help="stage-2 steps of the batch workload")
     ap.add_argument("--no-ablation", action="store_true",
                     help="skip the other proposals (node tests per pair and ms/step on the same state)")
@@ -281,7 +282,8 @@ def train_proposal(wl, win, n_hist, samples=65536, epochs=60, seed=3):
                "target": "z = log(c (t - t_r) / |r - w_n|), MSE"}
 
 
-def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True, net=None):
+def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True, net=None,
+             **solver_kw):
     import numpy as np
     import torch
 
@@ -291,7 +293,8 @@ def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, ke
     T, W, V, u = win
     N, D = wl["N"], wl["depth"]
     out = {}
-    with emppp.Solver(N, D, wl["dt"], precision=path, proposal=proposal, stream=stream, timing=True) as s:
+    with emppp.Solver(N, D, wl["dt"], precision=path, proposal=proposal, stream=stream, timing=True,
+                      **solver_kw) as s:
         s.set_history(h.n, T, W, V, u)
         if net is not None:
             s.set_proposal(net)
@@ -640,6 +643,65 @@ def run_paper(args):
         print(json.dumps(line), flush=True)
 
 
+VARIANTS = {"linear_present": {}, "midpoint": {"reconstruction": "midpoint"},
+            "half_step": {"field_point": "half_step"}}
+
+
+def run_variants(args):
+    """The comparison variants of the step on the benchmark workload (FP64 path): the method as built,
+    the midpoint reconstruction of eq:mid and the half-step field point, each timed on the same stored
+    state; the line's value is the midpoint variant's pair rate. The first step's fields of each variant
+    are compared with the method's (relative to each target's |E|): the size of the change the variant
+    makes, not an error (the tests measure errors against exact fields)."""
+    import numpy as np
+    import torch
+
+    from paper_2605_05543_gb300 import emppp
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist_init("nccl")
+    emppp.load(build_if_missing=True)
+    wl, h, win = workload(args.small, rank, args)
+    steps = args.steps if args.steps is not None else 2
+    warmup = max(args.warmup, 1)
+    dev = torch.device("cuda", local)
+    pairs_per_step = wl["N"] * (wl["N"] - 1)
+    res, rows, clocks = {}, {}, None
+    for name, kw in VARIANTS.items():
+        r = run_path(args, "fp64", args.proposal, steps, warmup, wl, h, win, rank, e2e=False, keep_fields=True, **kw)
+        res[name] = r
+        ms = max_over_ranks(r["ms"], dev)
+        st = r["stats"]
+        rows[name] = {"ms_per_step": ms, "pairs_per_s": sum_over_ranks(pairs_per_step, dev) / (ms / 1e3),
+                      "pair_kernel_ms": st["pair_ms"] / max(st["timed_steps"], 1),
+                      "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
+                      "gpu_launches_per_step": r["launches"] / steps}
+        if name == "midpoint":
+            clocks = r["clocks"]
+    if rank == 0:
+        E0 = res["linear_present"]["fields0"][0]
+        n0 = np.maximum(np.linalg.norm(E0, axis=1), 1e-300)
+        for name in ("midpoint", "half_step"):
+            d = np.linalg.norm(res[name]["fields0"][0] - E0, axis=1) / n0
+            rows[name]["first_step_E_change_vs_method"] = {"median": float(np.median(d)), "max": float(np.max(d))}
+    m = rows["midpoint"]
+    line = {
+        "metric": METRIC, "value": m["pairs_per_s"], "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
+        "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded Gaussian bunch and stored history; no dataset)",
+        "config": {"workload": workload_name(wl) + "; comparison variants of the step (eq:mid, half-step point)",
+                   "path": "fp64", "proposal": args.proposal, "N": wl["N"], "history_depth": wl["depth"],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2: 0.79 GB of history window read per step (L2 129 MB)"},
+        "variants": rows,
+        "clocks": clocks,
+        "gpu_launches": res["midpoint"]["launches"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """The CPU oracle as the reference arm: each step is a bounded sample of the workload (the fields
     of a fixed random subset of targets against all N sources)."""
@@ -694,6 +756,8 @@ def main(argv=None):
         run_batch(args)
     elif args.workload == "paper":
         run_paper(args)
+    elif args.workload == "variants":
+        run_variants(args)
     else:
         run_ours(args)
     try:

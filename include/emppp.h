@@ -75,6 +75,22 @@ typedef enum { EMPPP_FP64 = 0, EMPPP_MIXED = 1 } emppp_precision;
  *   MLP:         delay predicted by the 10-64-64-1 network set by emppp_set_proposal. */
 typedef enum { EMPPP_PROPOSAL_BISECT = 0, EMPPP_PROPOSAL_CLOSED_FORM = 1, EMPPP_PROPOSAL_MLP = 2 } emppp_proposal;
 
+/* Reconstruction of the retarded state inside the bracket [t_1, t_2] (Sec. 2.2).
+ *   LINEAR:   the method's own: delta t from the quadratic eq:dt, then eq:linear.
+ *   MIDPOINT: eq:mid, the earlier scheme the paper improves on, kept as an accuracy comparison:
+ *             t_r = (t_1 + t_2) / 2, w = (w_1 + w_2) / 2, v = (v_1 + v_2) / 2, a = (v_2 - v_1) / (t_2 - t_1).
+ *             Pairs older than the history keep eq:linear2. FP64 precision and a fixed dt only. */
+typedef enum { EMPPP_RECON_LINEAR = 0, EMPPP_RECON_MIDPOINT = 1 } emppp_reconstruction;
+
+/* Where a step evaluates the self fields (Sec. 2.3).
+ *   PRESENT:   at the stored present positions x^n and time t_n (the method as built).
+ *   HALF_STEP: at the pusher's half-step positions x^{n+1/2} = x^n + (dt/2) v^n and time t_n + dt/2,
+ *              kept as a comparison. Before the pair evaluation every particle's history gains a
+ *              provisional slot n+1 = (t_n + dt/2, x^{n+1/2}, v^n), which counts in the depth D; the push
+ *              then replaces it with the real slot n+1 at t_n + dt. FP64 precision and a fixed dt only;
+ *              emppp_fields is not affected. */
+typedef enum { EMPPP_FIELD_PRESENT = 0, EMPPP_FIELD_HALF_STEP = 1 } emppp_field_point;
+
 typedef struct {
   int32_t precision;   /* emppp_precision, default FP64 */
   int32_t proposal;    /* emppp_proposal, default BISECT */
@@ -83,7 +99,8 @@ typedef struct {
   int32_t timing;      /* 1: record CUDA events around every pair evaluation and step (see emppp_stats) */
   int32_t graphs;      /* 1 (default): emppp_step with nsteps > 1 replays one captured CUDA graph per step
                           (only on a non-default stream and with timing off) */
-  int32_t reserved[2]; /* must be 0 */
+  int32_t reconstruction; /* emppp_reconstruction, default LINEAR */
+  int32_t field_point;    /* emppp_field_point, default PRESENT */
 } emppp_options;
 
 /* Counters accumulated over the steps since the last emppp_reset_stats (Sec. 2.2 branches). */
@@ -126,7 +143,9 @@ EMPPP_API void emppp_default_options(emppp_options* out);
 /* Creates a solver for n particles with a history of `history_depth` slots (the present slot
  * included; depth >= 2) and fixed step dt > 0. opt may be NULL (defaults). cuda_stream is a
  * cudaStream_t (NULL: the legacy default stream). Allocates all device memory of the solver on the
- * current device. *out is NULL on failure. Sec. 2.2 (history), Sec. 2.3 (time step). */
+ * current device. *out is NULL on failure; EMPPP_ERR_ARG for an unknown option value or for the
+ * MIDPOINT reconstruction or HALF_STEP field point with MIXED precision. Sec. 2.2 (history), Sec. 2.3
+ * (time step). */
 EMPPP_API emppp_status emppp_create(int64_t n, int32_t history_depth, double dt, const emppp_options* opt,
                                     void* cuda_stream, emppp_handle* out);
 
@@ -207,7 +226,8 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
 /* Sets the work split directly (e.g. a tuning found earlier). items_per_block in 1..256. */
 EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning);
 
-/* Replaces the options (precision, proposal, pair_fields, source_split, timing) for later steps. */
+/* Replaces the options for later steps. EMPPP_ERR_STATE for a comparison variant (MIDPOINT, HALF_STEP)
+ * while the adaptive time step is on. */
 EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* opt);
 
 /* Replaces the stream later calls enqueue on (cudaStream_t, NULL: legacy default stream). */
@@ -296,8 +316,9 @@ EMPPP_API emppp_status emppp_mlp_train(float* params, const float* features, con
  * fixed dt of emppp_create. In a batch each bunch's step comes from its own pairs, and the step taken,
  * common to all bunches, is the smallest of them; with
  * pair fields off no pair qualifies and every step is dt_max. Returns EMPPP_ERR_ARG unless c_dt > 0,
- * eta_allow >= 0 and 0 < dt_min <= dt_max, all finite. The setting is kept until changed, across
- * emppp_set_particles and emppp_set_history. */
+ * eta_allow >= 0 and 0 < dt_min <= dt_max, all finite, and EMPPP_ERR_STATE when enabling it on a solver
+ * created with the MIDPOINT reconstruction or the HALF_STEP field point. The setting is kept until
+ * changed, across emppp_set_particles and emppp_set_history. */
 typedef struct {
   int32_t enable;
   int32_t reserved;

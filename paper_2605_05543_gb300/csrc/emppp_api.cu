@@ -75,7 +75,7 @@ struct emppp_ctx {
   unsigned* ord_key = nullptr;
   int* order = nullptr;
   // resident blocks per SM of the pair kernels (queried on first use), per proposal
-  int blocks_fp64[2][3] = {{0, 0, 0}, {0, 0, 0}};   // [adaptive time step][proposal]
+  int blocks_fp64[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // [kernel variant][proposal]
   int blocks_mixed[2][3] = {{0, 0, 0}, {0, 0, 0}};
   // adaptive time step (Sec. 2.4): the rule, and whether the host mirror of t lags the device
   AdaptParams adapt{0, 0.05, 0.0, 1e-15, 1e-12};
@@ -123,6 +123,11 @@ emppp_status dalloc(emppp_ctx* c, T** p, size_t count) {
   return EMPPP_OK;
 }
 
+// a comparison variant of the step (eq:mid or the half-step field point)
+bool is_variant(const emppp_options& o) {
+  return o.reconstruction != EMPPP_RECON_LINEAR || o.field_point != EMPPP_FIELD_PRESENT;
+}
+
 emppp_status validate_options(const emppp_options* o) {
   if (o->precision != EMPPP_FP64 && o->precision != EMPPP_MIXED)
     return fail(EMPPP_ERR_ARG, "unknown precision %d", o->precision);
@@ -133,8 +138,13 @@ emppp_status validate_options(const emppp_options* o) {
   if (o->source_split < 0) return fail(EMPPP_ERR_ARG, "source_split must be >= 0");
   if (o->timing != 0 && o->timing != 1) return fail(EMPPP_ERR_ARG, "timing must be 0 or 1");
   if (o->graphs != 0 && o->graphs != 1) return fail(EMPPP_ERR_ARG, "graphs must be 0 or 1");
-  for (int k = 0; k < 2; k++)
-    if (o->reserved[k] != 0) return fail(EMPPP_ERR_ARG, "reserved option fields must be 0");
+  if (o->reconstruction != EMPPP_RECON_LINEAR && o->reconstruction != EMPPP_RECON_MIDPOINT)
+    return fail(EMPPP_ERR_ARG, "unknown reconstruction %d", o->reconstruction);
+  if (o->field_point != EMPPP_FIELD_PRESENT && o->field_point != EMPPP_FIELD_HALF_STEP)
+    return fail(EMPPP_ERR_ARG, "unknown field point %d", o->field_point);
+  if ((o->reconstruction != EMPPP_RECON_LINEAR || o->field_point != EMPPP_FIELD_PRESENT) &&
+      o->precision != EMPPP_FP64)
+    return fail(EMPPP_ERR_ARG, "the midpoint reconstruction and the half-step field point run on the FP64 path");
   return EMPPP_OK;
 }
 
@@ -156,12 +166,15 @@ constexpr long long kMinChunk = 8;  // fewest sources per chunk
 emppp_status update_schedule(emppp_handle c) {
   const bool mixed = c->opt.precision == EMPPP_MIXED;
   const int ad = c->adapt.on ? 1 : 0;
+  // FP64 kernel variant: the method (0), with the adaptive step's reduction (1), eq:mid (2)
+  const int var64 = c->opt.reconstruction == EMPPP_RECON_MIDPOINT ? 2 : ad;
   const long long key = (mixed ? 1 : 0) | ((long long)(c->opt.proposal & 3) << 1) |
                         ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13) |
-                        ((long long)ad << 40);
+                        ((long long)ad << 40) | ((long long)var64 << 41);
   if (key == c->sched_key) return EMPPP_OK;
-  int& nb = mixed ? c->blocks_mixed[ad][c->opt.proposal % 3] : c->blocks_fp64[ad][c->opt.proposal % 3];
-  if (nb <= 0) nb = mixed ? max_blocks_pair_mixed(c->opt.proposal, ad) : max_blocks_pair_fp64(c->opt.proposal, ad);
+  int& nb = mixed ? c->blocks_mixed[ad][c->opt.proposal % 3] : c->blocks_fp64[var64][c->opt.proposal % 3];
+  if (nb <= 0)
+    nb = mixed ? max_blocks_pair_mixed(c->opt.proposal, ad) : max_blocks_pair_fp64(c->opt.proposal, var64);
   // The source chunking (and with it the order of every target's sum) follows the closed-form
   // variant's residency whatever the proposal, so that all proposals give identical fields; only the
   // number of persistent blocks follows the variant that runs.
@@ -331,6 +344,12 @@ emppp_status convert_bext(const emppp_bext* bext, BextParams* bp) {
 emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev, int* nkernels) {
   int k = 0;
   if (ev) CU(cudaEventRecord(ev[0], h->stream));
+  const bool half = h->opt.pair_fields && h->opt.field_point == EMPPP_FIELD_HALF_STEP;
+  if (half) {
+    // provisional slot n+1 at t_n + dt/2 holding the half-drifted positions; the clock moves there
+    CU(launch_half_slot(h->ds, h->stream));
+    k += 1;
+  }
   // window, slot tables, work counter and (mixed path) per-source segment vectors
   const bool mixed_pairs = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED;
   CU(launch_setup(h->ds, mixed_pairs, h->stream));
@@ -345,7 +364,7 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
     if (h->opt.precision == EMPPP_MIXED)
       CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
     else
-      CU(launch_pair_fp64(h->ds, h->opt.proposal, h->adapt, h->launch, h->stream));
+      CU(launch_pair_fp64(h->ds, h->opt.proposal, h->opt.reconstruction, h->adapt, h->launch, h->stream));
     k += 1;
   } else {
     CU(launch_zero_self(h->ds, h->stream));
@@ -353,7 +372,7 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   }
   if (ev) CU(cudaEventRecord(ev[2], h->stream));
   // partial sums, step size (Sec. 2.4), push and append (Sec. 2.3), clock advance: one launch
-  CU(launch_step_post(h->ds, bp, h->adapt, h->opt.pair_fields && any_chunked(h), h->stream));
+  CU(launch_step_post(h->ds, bp, h->adapt, h->opt.pair_fields && any_chunked(h), half, h->stream));
   k += 1;
   if (h->energy.on) {
     // mean energy of the new state and the switch criterion (Sec. 2.7)
@@ -913,7 +932,7 @@ emppp_status enqueue_fields(emppp_handle h) {
   if (h->opt.precision == EMPPP_MIXED) {
     CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
   } else {
-    CU(launch_pair_fp64(h->ds, h->opt.proposal, h->adapt, h->launch, h->stream));
+    CU(launch_pair_fp64(h->ds, h->opt.proposal, h->opt.reconstruction, h->adapt, h->launch, h->stream));
   }
   if (any_chunked(h)) CU(launch_reduce_partials(h->ds, h->stream));
   h->launches += 2 + (ordered ? 1 : 0) + (any_chunked(h) ? 1 : 0);
@@ -1181,6 +1200,8 @@ EMPPP_API emppp_status emppp_set_adaptive_dt(emppp_handle h, const emppp_adaptiv
   ap.c_dt = 0.05;
   ap.dt_min = 1e-15;
   ap.dt_max = 1e-12;
+  if (cfg && cfg->enable && is_variant(h->opt))
+    return fail(EMPPP_ERR_STATE, "the midpoint reconstruction and the half-step field point run with a fixed dt");
   if (cfg && cfg->enable) {
     const bool ok = cfg->c_dt > 0.0 && cfg->c_dt < 1e300 && cfg->eta_allow >= 0.0 && cfg->eta_allow < 1e300 &&
                     cfg->dt_min > 0.0 && cfg->dt_max >= cfg->dt_min && cfg->dt_max < 1e300;
@@ -1317,6 +1338,8 @@ EMPPP_API emppp_status emppp_set_options(emppp_handle h, const emppp_options* op
   if (st != EMPPP_OK) return st;
   if (!opt) return fail(EMPPP_ERR_ARG, "opt is NULL");
   if ((st = validate_options(opt)) != EMPPP_OK) return st;
+  if (h->adapt.on && is_variant(*opt))
+    return fail(EMPPP_ERR_STATE, "the midpoint reconstruction and the half-step field point run with a fixed dt");
   h->opt = *opt;
   if ((st = ensure_events(h)) != EMPPP_OK) return st;
   return update_schedule(h);

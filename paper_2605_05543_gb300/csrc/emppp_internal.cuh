@@ -214,14 +214,17 @@ cudaError_t launch_setup(const DeviceState& s, bool extrap, cudaStream_t st);
 cudaError_t launch_reset_scale(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_t st);
 // pair_fp64.cu
-int max_blocks_pair_fp64(int proposal, bool adapt);
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptParams& ap, const PairLaunch& pl,
-                             cudaStream_t st);
+// kernel variant of the FP64 pair path: 0 the method, 1 with the adaptive time step's reduction, 2 the
+// midpoint reconstruction eq:mid
+int max_blocks_pair_fp64(int proposal, int variant);
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int reconstruction, const AdaptParams& ap,
+                             const PairLaunch& pl, cudaStream_t st);
 cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
 cudaError_t launch_step_post(const DeviceState& s, const BextParams& b, const AdaptParams& ap, bool chunked,
-                             cudaStream_t st);
+                             bool half, cudaStream_t st);
+cudaError_t launch_half_slot(const DeviceState& s, cudaStream_t st);
 // stage2.cu
 cudaError_t launch_bunch_sums(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_translate(const DeviceState& s, const double* shifts, cudaStream_t st);

@@ -9,7 +9,8 @@
 //      or, with the closed-form proposal, a guarded galloping search started at the slot predicted
 //      by uniform motion from j's present state. Both return the unique sign change of P.
 //   2. linear reconstruction (eq:dt, eq:linear; eq:linear2 out of history): delta t from the
-//      quadratic, w = w1 + v1 dt, v = v1 + (dt / (t2 - t1)) (v2 - v1), a = (v2 - v1) / (t2 - t1).
+//      quadratic, w = w1 + v1 dt, v = v1 + (dt / (t2 - t1)) (v2 - v1), a = (v2 - v1) / (t2 - t1);
+//      or, in the comparison variant MID, the bracket's midpoint values of eq:mid for bracketed pairs.
 //   3. Lienard-Wiechert E (eq:LW_E) and B = eta_hat x E / c (eq:LW_B), summed over j != i in
 //      blocks of kSumBlock sources (blocked summation keeps the FP64 rounding error of a 65536-term
 //      sum near 1e-14 of the sum of magnitudes).
@@ -87,7 +88,7 @@ struct Window {
 
 }  // namespace
 
-template <int PROP, bool ADAPT>
+template <int PROP, bool ADAPT, bool MID>
 __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   __shared__ int s_item;
   __shared__ mlp::InferImage s_net[1];
@@ -270,38 +271,57 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     else
       n_bi++;
 
-    // ---- 2. reconstruction (eq:dt, eq:linear, eq:linear2) -------------------------------------
+    // ---- 2. reconstruction (eq:dt, eq:linear, eq:linear2; eq:mid in the MID variant) -----------
     const int p1 = win.phys(k1);
     const double2* R1 = reinterpret_cast<const double2*>(src + p1 * 6);
     const double2 x01 = __ldg(R1), x23 = __ldg(R1 + 1), x45 = __ldg(R1 + 2);
     const double w10 = x01.x, w11 = x01.y, w12 = x23.x;
     const double v10 = x23.y, v11 = x45.x, v12 = x45.y;
-    const double T1 = t - __ldg(a.slot_t + p1);
-    const double d0 = r0 - w10, d1 = r1 - w11, d2 = r2 - w12;
-    const double C2 = c2 - (v10 * v10 + v11 * v11 + v12 * v12);
-    const double hb = (d0 * v10 + d1 * v11 + d2 * v12) - c2 * T1;  // C1 / 2
-    const double C0 = c2 * T1 * T1 - (d0 * d0 + d1 * d1 + d2 * d2);
-    const double qd = hb * hb - C2 * C0;  // disc / 4
-    if (!(C2 > 0.0) || !(qd >= 0.0)) {
-      errbits |= kErrDisc;
-      continue;
-    }
-    const double sq = qd * rsqrt(fmax(qd, 1e-300));  // sqrt(qd); the reciprocal root costs fewer FP64-pipe operations
-    // smaller root of C2 x^2 + 2 hb x + C0 without cancellation
-    const double dt = (hb <= 0.0) ? C0 * recip_newton(sq - hb) : -(hb + sq) * recip_newton(C2);
-    const double w0 = w10 + v10 * dt, w1 = w11 + v11 * dt, w2 = w12 + v12 * dt;
-    double v0 = v10, v1 = v11, v2 = v12, a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    if (br != 0) {
+    double w0, w1, w2, v0 = v10, v1 = v11, v2 = v12, a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    if (MID && br != 0) {
+      // eq:mid: the midpoint of the bracket stands for the retarded time
       const int p2 = p1 + 1 == D ? 0 : p1 + 1;
       const double2* R2 = reinterpret_cast<const double2*>(src + p2 * 6);
-      const double2 y23 = __ldg(R2 + 1), y45 = __ldg(R2 + 2);
+      const double2 y01 = __ldg(R2), y23 = __ldg(R2 + 1), y45 = __ldg(R2 + 2);
       const double idt = __ldg(a.inv_dtk + p1);
+      w0 = 0.5 * (w10 + y01.x);
+      w1 = 0.5 * (w11 + y01.y);
+      w2 = 0.5 * (w12 + y23.x);
+      v0 = 0.5 * (v10 + y23.y);
+      v1 = 0.5 * (v11 + y45.x);
+      v2 = 0.5 * (v12 + y45.y);
       a0 = (y23.y - v10) * idt;
       a1 = (y45.x - v11) * idt;
       a2 = (y45.y - v12) * idt;
-      v0 = v10 + dt * a0;
-      v1 = v11 + dt * a1;
-      v2 = v12 + dt * a2;
+    } else {
+      const double T1 = t - __ldg(a.slot_t + p1);
+      const double d0 = r0 - w10, d1 = r1 - w11, d2 = r2 - w12;
+      const double C2 = c2 - (v10 * v10 + v11 * v11 + v12 * v12);
+      const double hb = (d0 * v10 + d1 * v11 + d2 * v12) - c2 * T1;  // C1 / 2
+      const double C0 = c2 * T1 * T1 - (d0 * d0 + d1 * d1 + d2 * d2);
+      const double qd = hb * hb - C2 * C0;  // disc / 4
+      if (!(C2 > 0.0) || !(qd >= 0.0)) {
+        errbits |= kErrDisc;
+        continue;
+      }
+      const double sq = qd * rsqrt(fmax(qd, 1e-300));  // sqrt(qd); the reciprocal root costs fewer FP64-pipe operations
+      // smaller root of C2 x^2 + 2 hb x + C0 without cancellation
+      const double dt = (hb <= 0.0) ? C0 * recip_newton(sq - hb) : -(hb + sq) * recip_newton(C2);
+      w0 = w10 + v10 * dt;
+      w1 = w11 + v11 * dt;
+      w2 = w12 + v12 * dt;
+      if (br != 0) {
+        const int p2 = p1 + 1 == D ? 0 : p1 + 1;
+        const double2* R2 = reinterpret_cast<const double2*>(src + p2 * 6);
+        const double2 y23 = __ldg(R2 + 1), y45 = __ldg(R2 + 2);
+        const double idt = __ldg(a.inv_dtk + p1);
+        a0 = (y23.y - v10) * idt;
+        a1 = (y45.x - v11) * idt;
+        a2 = (y45.y - v12) * idt;
+        v0 = v10 + dt * a0;
+        v1 = v11 + dt * a1;
+        v2 = v12 + dt * a2;
+      }
     }
     // ---- 3. Lienard-Wiechert fields ----------------------------------------------------------
     const double e0 = r0 - w0, e1 = r1 - w1, e2 = r2 - w2;
@@ -416,34 +436,35 @@ __global__ void zero_kernel(double* __restrict__ a, double* __restrict__ b, long
   }
 }
 
-template <bool ADAPT>
+template <bool ADAPT, bool MID>
 int max_blocks_fp64(int proposal) {
   int nb = 0;
   if (proposal == kPropClosedForm)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm, ADAPT>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm, ADAPT, MID>, kBlock, 0);
   else if (proposal == kPropMlp)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp, ADAPT>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp, ADAPT, MID>, kBlock, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect, ADAPT>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect, ADAPT, MID>, kBlock, 0);
   return nb > 0 ? nb : 1;
 }
 
-int max_blocks_pair_fp64(int proposal, bool adapt) {
-  return adapt ? max_blocks_fp64<true>(proposal) : max_blocks_fp64<false>(proposal);
+int max_blocks_pair_fp64(int proposal, int variant) {
+  if (variant == 2) return max_blocks_fp64<false, true>(proposal);
+  return variant == 1 ? max_blocks_fp64<true, false>(proposal) : max_blocks_fp64<false, false>(proposal);
 }
 
-template <bool ADAPT>
+template <bool ADAPT, bool MID>
 void launch_fp64(int proposal, const PairLaunch& pl, const PairArgs& a, cudaStream_t st) {
   if (proposal == kPropClosedForm)
-    pair_fp64_kernel<kPropClosedForm, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropClosedForm, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
   else if (proposal == kPropMlp)
-    pair_fp64_kernel<kPropMlp, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropMlp, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
   else
-    pair_fp64_kernel<kPropBisect, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropBisect, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
 }
 
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptParams& ap, const PairLaunch& pl,
-                             cudaStream_t st) {
+cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int reconstruction, const AdaptParams& ap,
+                             const PairLaunch& pl, cudaStream_t st) {
   PairArgs a;
   a.rec64 = s.rec64;
   a.rec32 = s.rec32;
@@ -468,10 +489,13 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, const AdaptPara
   a.scale = s.scale;
   a.eta_allow = ap.eta_allow;
   // the work counter is zeroed by the set-up launch that precedes every pair launch
-  if (ap.on)
-    launch_fp64<true>(proposal, pl, a, st);
+  // the midpoint reconstruction runs with a fixed time step only (the host refuses the combination)
+  if (reconstruction == 1)
+    launch_fp64<false, true>(proposal, pl, a, st);
+  else if (ap.on)
+    launch_fp64<true, false>(proposal, pl, a, st);
   else
-    launch_fp64<false>(proposal, pl, a, st);
+    launch_fp64<false, false>(proposal, pl, a, st);
   return cudaGetLastError();
 }
 

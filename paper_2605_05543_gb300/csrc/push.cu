@@ -39,19 +39,67 @@ __device__ __forceinline__ double adaptive_step(const DeviceState& s, const Adap
   return dt;
 }
 
+// Half-step field point (comparison variant, fixed dt): before the pair evaluation of step n every
+// particle's history gains a provisional slot n+1 holding its half-drifted position
+// x^{n+1/2} = x^n + (dt/2) v^n (the push's own half drift, same operations) and v^n, stamped t_n + dt/2,
+// and the clock moves to (n+1, t_n + dt/2), so that the set-up and pair launches evaluate the fields
+// there. The post-pair launch (half = 1) then pushes from slot n and overwrites slot n+1. The last block
+// to finish moves the clock, as in the post-pair launch.
+__global__ void half_slot_kernel(DeviceState s) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const StepState st = *s.state;
+  const int pn = (int)(st.n % s.D);
+  const int pnext = pn + 1 == s.D ? 0 : pn + 1;
+  if (i == 0) s.slot_t[pnext] = st.t + 0.5 * st.dt;
+  if (i < s.N) {
+    const double* rec = s.rec64 + ((size_t)i * s.D + pn) * 6;
+    const double u0 = s.u[3 * i], u1 = s.u[3 * i + 1], u2 = s.u[3 * i + 2];
+    const double ig0 = rsqrt(1.0 + (u0 * u0 + u1 * u1 + u2 * u2) * (1.0 / (kC * kC)));
+    const double hdt = 0.5 * st.dt;
+    const double v0 = u0 * ig0, v1 = u1 * ig0, v2 = u2 * ig0;
+    const double x0 = rec[0] + hdt * v0, x1 = rec[1] + hdt * v1, x2 = rec[2] + hdt * v2;
+    double* r = s.rec64 + ((size_t)i * s.D + pnext) * 6;
+    reinterpret_cast<double2*>(r)[0] = make_double2(x0, x1);
+    reinterpret_cast<double2*>(r)[1] = make_double2(x2, v0);
+    reinterpret_cast<double2*>(r)[2] = make_double2(v1, v2);
+    float4 q[3];
+    const BunchDesc& bd = s.bunches[s.bunch_of[i]];
+    shadow_record(bd.origin, bd.beta_ref, x0, x1, x2, v0, v1, v2, gamma2_of_u(u0, u1, u2), q);
+    float4* o = reinterpret_cast<float4*>(s.rec32 + ((size_t)i * s.D + pnext) * 12);
+    o[0] = q[0];
+    o[1] = q[1];
+    o[2] = q[2];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(s.done, 1u);
+    if (prev == gridDim.x - 1) {
+      s.state->n = st.n + 1;
+      s.state->t = st.t + 0.5 * st.dt;
+      *s.done = 0u;
+    }
+  }
+}
+
 // The rest of a step after the pair kernel, in one launch: the sum of each target's per-chunk partial
 // fields (fixed chunk order), the adaptive step size, the push of every particle and the append of slot
 // n+1, then (by the last block to finish) the clock advance n -> n+1, t -> t + dt and the reset of the
 // interaction-scale reduction. The last block is found with a counter that every block increments once
-// after its work; nothing waits on it.
-__global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, int chunked) {
+// after its work; nothing waits on it. With half = 1 (half-step field point) the clock already stands at
+// the provisional slot n+1: the push starts from slot n, the provisional slot is overwritten and the
+// clock moves from t_n + dt/2 to t_n + dt (formed from t_n, as without the variant).
+__global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, int chunked, int half) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const StepState st = *s.state;
   double dt = st.dt, eta_rep = 0.0, v_rep = 0.0;
   if (ap.on) dt = adaptive_step(s, ap, eta_rep, v_rep);
-  const int pnext = st.pn + 1 == s.D ? 0 : st.pn + 1;
+  // slot of x^n, the slot the push writes and t_n
+  const int pfrom = half ? (st.pn == 0 ? s.D - 1 : st.pn - 1) : st.pn;
+  const int pnext = half ? st.pn : (st.pn + 1 == s.D ? 0 : st.pn + 1);
+  const double t_n = half ? s.slot_t[pfrom] : st.t;
   if (i == 0) {
-    s.slot_t[pnext] = st.t + dt;
+    s.slot_t[pnext] = t_n + dt;
     if (ap.on) {
       s.adapt_info[0] = dt;
       s.adapt_info[1] = eta_rep;
@@ -75,7 +123,7 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
         }
       }
     }
-    const double* rec = s.rec64 + ((size_t)i * s.D + st.pn) * 6;
+    const double* rec = s.rec64 + ((size_t)i * s.D + pfrom) * 6;
     double x[3] = {rec[0], rec[1], rec[2]};
     double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
     const double E[3] = {s.Eself[3 * i], s.Eself[3 * i + 1], s.Eself[3 * i + 2]};
@@ -107,8 +155,8 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
     __threadfence();
     const unsigned prev = atomicAdd(s.done, 1u);
     if (prev == gridDim.x - 1) {
-      s.state->n = st.n + 1;
-      s.state->t = st.t + dt;
+      s.state->n = half ? st.n : st.n + 1;
+      s.state->t = t_n + dt;
       s.state->dt = dt;
       if (ap.on) {
         for (int b = 0; b < s.nbunch; b++) {
@@ -122,8 +170,13 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
 }
 
 cudaError_t launch_step_post(const DeviceState& s, const BextParams& b, const AdaptParams& ap, bool chunked,
-                             cudaStream_t st) {
-  step_post_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s, b, ap, chunked ? 1 : 0);
+                             bool half, cudaStream_t st) {
+  step_post_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s, b, ap, chunked ? 1 : 0, half ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_half_slot(const DeviceState& s, cudaStream_t st) {
+  half_slot_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s);
   return cudaGetLastError();
 }
 

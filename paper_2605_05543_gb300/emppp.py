@@ -23,6 +23,9 @@ _STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NUMERIC", -4: "ERR_T
 PRECISION = {"fp64": 0, "mixed": 1}
 PROPOSAL = {"bisect": 0, "closed_form": 1, "mlp": 2}
 BEXT = {"none": 0, "uniform": 1, "dipole": 2}
+# comparison variants of the step: eq:mid, and the self fields at the half-step point
+RECONSTRUCTION = {"linear": 0, "midpoint": 1}
+FIELD_POINT = {"present": 0, "half_step": 1}
 
 
 class EmpppError(RuntimeError):
@@ -34,7 +37,7 @@ class EmpppError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("proposal", ctypes.c_int32), ("pair_fields", ctypes.c_int32),
                 ("source_split", ctypes.c_int32), ("timing", ctypes.c_int32), ("graphs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("reconstruction", ctypes.c_int32), ("field_point", ctypes.c_int32)]
 
 
 class Bext(ctypes.Structure):
@@ -226,9 +229,11 @@ def bext_dipole(m0: float, center=(0.0, 0.0, 0.0)) -> Bext:
 
 
 def make_options(precision="fp64", proposal="bisect", pair_fields=True, source_split=0, timing=False,
-                 graphs=True) -> Options:
+                 graphs=True, reconstruction="linear", field_point="present") -> Options:
     o = Options()
     load().emppp_default_options(ctypes.byref(o))
+    o.reconstruction = RECONSTRUCTION[reconstruction] if isinstance(reconstruction, str) else int(reconstruction)
+    o.field_point = FIELD_POINT[field_point] if isinstance(field_point, str) else int(field_point)
     o.graphs = 1 if graphs else 0
     o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     o.proposal = PROPOSAL[proposal] if isinstance(proposal, str) else int(proposal)
@@ -243,12 +248,14 @@ class Solver:
     particles are concatenated in every per-particle array), history depth `depth` and step dt."""
 
     def __init__(self, n: int, depth: int, dt: float, precision="fp64", proposal="bisect", pair_fields=True,
-                 source_split=0, stream=None, timing=False, graphs=True, bunches=None):
+                 source_split=0, stream=None, timing=False, graphs=True, bunches=None, reconstruction="linear",
+                 field_point="present"):
         self.lib = load()
         self.depth = int(depth)
         self.dt = float(dt)
         self._h = _H()
-        self._opt = make_options(precision, proposal, pair_fields, source_split, timing, graphs)
+        self._opt = make_options(precision, proposal, pair_fields, source_split, timing, graphs, reconstruction,
+                                 field_point)
         if bunches is None:
             self.n = int(n)
             self.bunches = [self.n]
@@ -283,8 +290,12 @@ class Solver:
         return self._h
 
     def set_options(self, precision=None, proposal=None, pair_fields=None, source_split=None, timing=None,
-                    graphs=None):
+                    graphs=None, reconstruction=None, field_point=None):
         o = self._opt
+        if reconstruction is not None:
+            o.reconstruction = RECONSTRUCTION[reconstruction] if isinstance(reconstruction, str) else int(reconstruction)
+        if field_point is not None:
+            o.field_point = FIELD_POINT[field_point] if isinstance(field_point, str) else int(field_point)
         if graphs is not None:
             o.graphs = 1 if graphs else 0
         if timing is not None:
