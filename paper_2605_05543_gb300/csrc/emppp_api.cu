@@ -67,7 +67,7 @@ struct emppp_ctx {
   PairLaunch launch{};
   long long sched_key = -1;  // configuration the uploaded schedule belongs to
   int items_per_block = 16;  // work items per resident block of the pair kernel
-  int target_order = 1;      // spatial target order on the mixed path
+  int target_order = 1;      // spatial target order of the pair kernels
   // proposal network image (EMPPP_PROPOSAL_MLP)
   void* mlp_image = nullptr;
   bool has_mlp = false;
@@ -354,7 +354,7 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   const bool mixed_pairs = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED;
   CU(launch_setup(h->ds, mixed_pairs, h->stream));
   k += 1;
-  const bool ordered = mixed_pairs && h->target_order;
+  const bool ordered = h->opt.pair_fields && h->target_order;
   if (ordered) {
     CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
     k += 1;
@@ -364,7 +364,8 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
     if (h->opt.precision == EMPPP_MIXED)
       CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
     else
-      CU(launch_pair_fp64(h->ds, h->opt.proposal, h->opt.reconstruction, h->adapt, h->launch, h->stream));
+      CU(launch_pair_fp64(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->opt.reconstruction, h->adapt,
+                          h->launch, h->stream));
     k += 1;
   } else {
     CU(launch_zero_self(h->ds, h->stream));
@@ -927,12 +928,13 @@ EMPPP_API emppp_status emppp_reset_stats(emppp_handle h) {
 // reduction (no push: the state does not change)
 emppp_status enqueue_fields(emppp_handle h) {
   CU(launch_setup(h->ds, h->opt.precision == EMPPP_MIXED, h->stream));
-  const bool ordered = h->opt.precision == EMPPP_MIXED && h->target_order;
+  const bool ordered = h->target_order != 0;
   if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
   if (h->opt.precision == EMPPP_MIXED) {
     CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
   } else {
-    CU(launch_pair_fp64(h->ds, h->opt.proposal, h->opt.reconstruction, h->adapt, h->launch, h->stream));
+    CU(launch_pair_fp64(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->opt.reconstruction, h->adapt,
+                        h->launch, h->stream));
   }
   if (any_chunked(h)) CU(launch_reduce_partials(h->ds, h->stream));
   h->launches += 2 + (ordered ? 1 : 0) + (any_chunked(h) ? 1 : 0);
@@ -948,7 +950,7 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
     return fail(EMPPP_ERR_STATE, "the MLP proposal needs a network: call emppp_set_proposal first");
   if ((st = read_err(h)) != EMPPP_OK) return st;
   const int ipb[5] = {4, 8, 16, 32, 64};
-  const int norders = h->opt.precision == EMPPP_MIXED ? 2 : 1;
+  const int norders = 2;
   emppp_tuning_report rep;
   memset(&rep, 0, sizeof(rep));
   cudaEvent_t e0, e1;

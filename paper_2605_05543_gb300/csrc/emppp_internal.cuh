@@ -217,8 +217,8 @@ cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_
 // kernel variant of the FP64 pair path: 0 the method, 1 with the adaptive time step's reduction, 2 the
 // midpoint reconstruction eq:mid
 int max_blocks_pair_fp64(int proposal, int variant);
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int reconstruction, const AdaptParams& ap,
-                             const PairLaunch& pl, cudaStream_t st);
+cudaError_t launch_pair_fp64(const DeviceState& s, const int* order, int proposal, int reconstruction,
+                             const AdaptParams& ap, const PairLaunch& pl, cudaStream_t st);
 cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu

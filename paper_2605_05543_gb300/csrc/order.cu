@@ -1,10 +1,10 @@
-// Spatial order of the targets for the mixed-precision pair kernel.
+// Spatial order of the targets for the pair kernels.
 //
 // Each bunch's present positions are binned into a 2^b x 2^b x 2^b grid over the bunch's bounding box
 // (b = 2..5 from the bunch size), the cells are numbered along a Morton (Z-order) curve, and a
 // counting sort lists the bunch's particles cell by cell. Threads then take targets in this order, so
-// the 32 targets of a warp are close in space and their retarded slots of any one source lie within a
-// few cache lines. One block of 1024 threads sorts one bunch entirely in shared memory. The order is a
+// the 32 targets of a warp are close in space: their retarded slots of any one source lie within a
+// few cache lines, and they mostly take the same branch of the retarded-time search. One block of 1024 threads sorts one bunch entirely in shared memory. The order is a
 // permutation of each bunch's index range (each target is evaluated exactly once whatever the order);
 // the order inside a cell comes from shared-memory atomics and may differ run to run, which changes
 // which thread evaluates a target but not its result.

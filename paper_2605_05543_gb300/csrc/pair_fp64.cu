@@ -8,12 +8,18 @@
 //      bit): out-of-history if P(k0), near-field shortcut if not P(n-1), else bisection (Sec. 2.2);
 //      or, with the closed-form proposal, a guarded galloping search started at the slot predicted
 //      by uniform motion from j's present state. Both return the unique sign change of P.
-//   2. linear reconstruction (eq:dt, eq:linear; eq:linear2 out of history): delta t from the
-//      quadratic, w = w1 + v1 dt, v = v1 + (dt / (t2 - t1)) (v2 - v1), a = (v2 - v1) / (t2 - t1);
-//      or, in the comparison variant MID, the bracket's midpoint values of eq:mid for bracketed pairs.
+//   2. linear reconstruction (eq:dt, eq:linear): delta t from the quadratic, w = w1 + v1 dt,
+//      v = v1 + (dt / (t2 - t1)) (v2 - v1), a = (v2 - v1) / (t2 - t1); or, in the comparison variant MID,
+//      the bracket's midpoint values of eq:mid.
 //   3. Lienard-Wiechert E (eq:LW_E) and B = eta_hat x E / c (eq:LW_B), summed over j != i in
 //      blocks of kSumBlock sources (blocked summation keeps the FP64 rounding error of a 65536-term
 //      sum near 1e-14 of the sum of magnitudes).
+//   Out of history (eq:linear2) the source moves uniformly with v1 along the line through w_{k0}, and its
+//   Lienard-Wiechert field is Heaviside's field about the line's point at t_n: with X = r - w_{k0} -
+//   v1 (t_n - t_{k0}), E = kq c (c^2 - v1^2) X / [|X|^2 (c^2 - v1^2) + (X.v1)^2]^{3/2}, B = v1 x E / c^2.
+//   It is the same field, without the quadratic and the retarded reconstruction.
+// Targets are taken in the spatial order of order.cu (when given), so that the pairs of a warp mostly
+// take the same branch; which thread evaluates a target does not change its result.
 // The arithmetic is FP64-pipe bound (GB300: 2 DFMA/clk/SM); everything that is not an FP64 result
 // (the guess, indices, loads) runs on the FP32/INT pipes beside it.
 #include "emppp_internal.cuh"
@@ -65,6 +71,7 @@ struct PairArgs {
   const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
   unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
   double eta_allow;
+  const int* __restrict__ order;  // spatial order of the targets (nullptr: index order)
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -126,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const float3 bref = make_float3((float)bd.beta_ref[0], (float)bd.beta_ref[1], (float)bd.beta_ref[2]);
   const long long i_loc = (long long)tb * kBlock + threadIdx.x;
   const bool active = i_loc < bd.n;
-  const long long i = bd.off + (active ? i_loc : 0);
+  const long long i = a.order ? a.order[bd.off + (active ? i_loc : 0)] : bd.off + (active ? i_loc : 0);
   const long long ic = i;
 
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
@@ -271,12 +278,62 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     else
       n_bi++;
 
-    // ---- 2. reconstruction (eq:dt, eq:linear, eq:linear2; eq:mid in the MID variant) -----------
+    // ---- 2. reconstruction (eq:dt, eq:linear; eq:mid in the MID variant) ----------------------
     const int p1 = win.phys(k1);
     const double2* R1 = reinterpret_cast<const double2*>(src + p1 * 6);
     const double2 x01 = __ldg(R1), x23 = __ldg(R1 + 1), x45 = __ldg(R1 + 2);
     const double w10 = x01.x, w11 = x01.y, w12 = x23.x;
     const double v10 = x23.y, v11 = x45.x, v12 = x45.y;
+    if (br == 0) {
+      // ---- out of history (eq:linear2): Heaviside's field of the uniformly moving source -------
+      const double T1 = t - __ldg(a.slot_t + p1);
+      const double X0 = (r0 - w10) - v10 * T1, X1 = (r1 - w11) - v11 * T1, X2 = (r2 - w12) - v12 * T1;
+      const double c2mv2 = c2 - (v10 * v10 + v11 * v11 + v12 * v12);
+      const double XX = X0 * X0 + X1 * X1 + X2 * X2;
+      const double Xv = X0 * v10 + X1 * v11 + X2 * v12;
+      const double Dh = XX * c2mv2 + Xv * Xv;  // c^2 [|X|^2 (1 - beta^2) + (X.beta)^2]
+      if (!(c2mv2 > 0.0)) {
+        errbits |= kErrDisc;
+        continue;
+      }
+      if (!(Dh > 0.0)) {
+        errbits |= kErrCoincide;
+        continue;
+      }
+      const double iD = rsqrt(Dh);
+      const double q = -kQe * __ldg(a.wts + j);
+      const double pref = (kCoulomb * kC) * q * c2mv2 * (iD * iD * iD);
+      const double E0 = pref * X0, E1 = pref * X1, E2 = pref * X2;
+      if (ADAPT) {
+        // retarded distance R = c (t - t_r), the positive root of R^2 (c^2 - v^2) - 2 R c (X.v) - c^2 |X|^2
+        // = 0, formed without cancellation; v(t_r) = v1
+        const double sD = Dh * iD;
+        const double R = (Xv >= 0.0) ? kC * (Xv + sD) / c2mv2 : kC * XX / (sD - Xv);
+        if (R >= a.eta_allow) {
+          emin = fmin(emin, R);
+          const double dv0 = vi0 - v10, dv1 = vi1 - v11, dv2 = vi2 - v12;
+          vmax2 = fmax(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+        }
+      }
+      const double ic2 = 1.0 / c2;
+      Ep[0] += E0;
+      Ep[1] += E1;
+      Ep[2] += E2;
+      Bp[0] += (v11 * E2 - v12 * E1) * ic2;
+      Bp[1] += (v12 * E0 - v10 * E2) * ic2;
+      Bp[2] += (v10 * E1 - v11 * E0) * ic2;
+      if (++in_block == kSumBlock) {
+        in_block = 0;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          Et[c] += Ep[c];
+          Bt[c] += Bp[c];
+          Ep[c] = 0.0;
+          Bp[c] = 0.0;
+        }
+      }
+      continue;
+    }
     double w0, w1, w2, v0 = v10, v1 = v11, v2 = v12, a0 = 0.0, a1 = 0.0, a2 = 0.0;
     if (MID && br != 0) {
       // eq:mid: the midpoint of the bracket stands for the retarded time
@@ -463,8 +520,8 @@ void launch_fp64(int proposal, const PairLaunch& pl, const PairArgs& a, cudaStre
     pair_fp64_kernel<kPropBisect, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
 }
 
-cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int reconstruction, const AdaptParams& ap,
-                             const PairLaunch& pl, cudaStream_t st) {
+cudaError_t launch_pair_fp64(const DeviceState& s, const int* order, int proposal, int reconstruction,
+                             const AdaptParams& ap, const PairLaunch& pl, cudaStream_t st) {
   PairArgs a;
   a.rec64 = s.rec64;
   a.rec32 = s.rec32;
@@ -488,6 +545,7 @@ cudaError_t launch_pair_fp64(const DeviceState& s, int proposal, int reconstruct
   a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
   a.scale = s.scale;
   a.eta_allow = ap.eta_allow;
+  a.order = order;
   // the work counter is zeroed by the set-up launch that precedes every pair launch
   // the midpoint reconstruction runs with a fixed time step only (the host refuses the combination)
   if (reconstruction == 1)

@@ -206,7 +206,7 @@ def test_autotune_keeps_state_and_results(precision):
         s.set_history(80, T, W, V, u)
         rep = s.autotune()
         _, _, t0, n0 = s.get_state()
-        assert n0 == 80 and len(rep["candidates"]) == (10 if precision == "mixed" else 5)
+        assert n0 == 80 and len(rep["candidates"]) == 10  # 5 splits x both target orders
         assert all(c["ms"] > 0 for c in rep["candidates"])
         s.step(1)
         Ea, Ba = s.get_fields()
