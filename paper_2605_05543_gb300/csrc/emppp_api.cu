@@ -49,6 +49,8 @@ struct emppp_ctx {
   double dt = 0.0;
   emppp_options opt{};
   cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;      // second stream: the target order runs on it beside the set-up launch
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = 0;
   int num_sms = 0;
   bool has_state = false;
@@ -241,6 +243,15 @@ bool any_chunked(const emppp_ctx* c) {
   return false;
 }
 
+// the post-pair launch reads the per-chunk partial sums with a warp per particle when a small system is
+// split into many chunks (a thread per particle would read them one after another)
+bool wide_reduction(const emppp_ctx* c) {
+  if (c->N > 16384) return false;
+  for (int b = 0; b < c->nbunch; b++)
+    if (c->hs[b].nchunk >= 8) return true;
+  return false;
+}
+
 emppp_status read_err(emppp_handle h) {
   int herr = 0;
   CU(cudaMemcpyAsync(&herr, h->ds.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -350,15 +361,20 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
     CU(launch_half_slot(h->ds, h->stream));
     k += 1;
   }
-  // window, slot tables, work counter and (mixed path) per-source segment vectors
+  // window, slot tables, work counter and (mixed path) per-source segment vectors; beside it, on the
+  // second stream, the spatial order of the targets (it reads only the present positions)
   const bool mixed_pairs = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED;
-  CU(launch_setup(h->ds, mixed_pairs, h->stream));
-  k += 1;
   const bool ordered = h->opt.pair_fields && h->target_order;
   if (ordered) {
-    CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
+    CU(cudaEventRecord(h->ev_fork, h->stream));
+    CU(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+    CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->aux));
+    CU(cudaEventRecord(h->ev_join, h->aux));
     k += 1;
   }
+  CU(launch_setup(h->ds, mixed_pairs, h->stream));
+  k += 1;
+  if (ordered) CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
     if (h->opt.precision == EMPPP_MIXED)
@@ -373,9 +389,13 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   }
   if (ev) CU(cudaEventRecord(ev[2], h->stream));
   // partial sums, step size (Sec. 2.4), push and append (Sec. 2.3), clock advance: one launch
-  CU(launch_step_post(h->ds, bp, h->adapt, h->opt.pair_fields && any_chunked(h), half, h->stream));
+  const bool chunked = h->opt.pair_fields && any_chunked(h);
+  // small systems: the energy monitor runs in the post-pair launch's last block
+  const bool fused_energy = h->energy.on && h->N <= 16384;
+  CU(launch_step_post(h->ds, bp, h->adapt, chunked, half, chunked && wide_reduction(h),
+                      fused_energy ? &h->energy : nullptr, h->d_mon, h->stream));
   k += 1;
-  if (h->energy.on) {
+  if (h->energy.on && !fused_energy) {
     // mean energy of the new state and the switch criterion (Sec. 2.7)
     CU(launch_energy(h->ds, h->energy, h->d_mon, false, h->stream));
     k += 1;
@@ -448,7 +468,12 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = prepare_target_order();
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->aux) cudaStreamDestroy(c->aux);
     delete c;
     return fail(EMPPP_ERR_CUDA, "no usable CUDA device: %s", cudaGetErrorString(e));
   }
@@ -593,6 +618,12 @@ EMPPP_API void emppp_destroy(emppp_handle h) {
   invalidate_graph(h);
   for (cudaEvent_t e : h->events)
     if (e) cudaEventDestroy(e);
+  if (h->aux) {
+    cudaStreamSynchronize(h->aux);
+    cudaStreamDestroy(h->aux);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (void* p : h->allocs) cudaFree(p);
   delete h;
 }

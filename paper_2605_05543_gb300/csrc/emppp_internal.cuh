@@ -223,7 +223,7 @@ cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
 cudaError_t launch_step_post(const DeviceState& s, const BextParams& b, const AdaptParams& ap, bool chunked,
-                             bool half, cudaStream_t st);
+                             bool half, bool wide, const EnergyParams* ep, EnergyMon* mon, cudaStream_t st);
 cudaError_t launch_half_slot(const DeviceState& s, cudaStream_t st);
 // stage2.cu
 cudaError_t launch_bunch_sums(const DeviceState& s, cudaStream_t st);
@@ -245,6 +245,7 @@ cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float
                         int step, cudaStream_t st);
 // energy.cu
 cudaError_t launch_energy(const DeviceState& s, const EnergyParams& ep, EnergyMon* mon, bool reset, cudaStream_t st);
+constexpr int kEnergyThreads = 256;  // block size of the energy monitor (and of the post-pair launch)
 // pair_mixed.cu
 int max_blocks_pair_mixed(int proposal, bool adapt);
 cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const AdaptParams& ap,

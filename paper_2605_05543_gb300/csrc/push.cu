@@ -12,6 +12,7 @@
 // per-chunk partial fields, picks the adaptive step and advances the clock, so that a step after the
 // pair kernel is one launch.
 #include "emppp_internal.cuh"
+#include "energy.cuh"
 #include "push_math.cuh"
 #include "shadow.cuh"
 
@@ -89,8 +90,15 @@ __global__ void half_slot_kernel(DeviceState s) {
 // after its work; nothing waits on it. With half = 1 (half-step field point) the clock already stands at
 // the provisional slot n+1: the push starts from slot n, the provisional slot is overwritten and the
 // clock moves from t_n + dt/2 to t_n + dt (formed from t_n, as without the variant).
-__global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, int chunked, int half) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kEnergyThreads) step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap,
+                                                                   int chunked, int half, int wide, EnergyParams ep,
+                                                                   EnergyMon* __restrict__ mon) {
+  // wide = 1: one warp per particle, whose lanes read the per-chunk partial sums in parallel (small
+  // systems, where a bunch is split into many short chunks); else one thread per particle
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long i = wide ? (g >> 5) : g;
+  const int lane = threadIdx.x & 31;
+  const bool owner = !wide || lane == 0;
   const StepState st = *s.state;
   double dt = st.dt, eta_rep = 0.0, v_rep = 0.0;
   if (ap.on) dt = adaptive_step(s, ap, eta_rep, v_rep);
@@ -98,7 +106,7 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
   const int pfrom = half ? (st.pn == 0 ? s.D - 1 : st.pn - 1) : st.pn;
   const int pnext = half ? st.pn : (st.pn + 1 == s.D ? 0 : st.pn + 1);
   const double t_n = half ? s.slot_t[pfrom] : st.t;
-  if (i == 0) {
+  if (g == 0) {
     s.slot_t[pnext] = t_n + dt;
     if (ap.on) {
       s.adapt_info[0] = dt;
@@ -108,21 +116,40 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
   }
   if (i < s.N) {
     if (chunked) {
-      // E_i = sum over the source chunks c of partial[c][i], in chunk order
+      // E_i = sum over the source chunks c of partial[c][i], in a fixed order
       const int S = s.sched[s.bunch_of[i]].nchunk;
       if (S > 1) {
         double acc[6] = {0, 0, 0, 0, 0, 0};
-        for (int c = 0; c < S; c++) {
-          const double* o = s.partial + ((size_t)c * s.N + i) * 6;
+        if (wide) {
+          // lane l adds chunks l, l + 32, ... in order; then a butterfly over the lanes, which leaves the
+          // same sum in every lane (each step adds two equal-order partial sums, a commutative operation)
+          for (int c = lane; c < S; c += 32) {
+            const double* o = s.partial + ((size_t)c * s.N + i) * 6;
 #pragma unroll
-          for (int k = 0; k < 6; k++) acc[k] += o[k];
+            for (int k = 0; k < 6; k++) acc[k] += o[k];
+          }
+#pragma unroll
+          for (int m = 16; m >= 1; m >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; k++) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], m);
+          }
+        } else {
+          for (int c = 0; c < S; c++) {
+            const double* o = s.partial + ((size_t)c * s.N + i) * 6;
+#pragma unroll
+            for (int k = 0; k < 6; k++) acc[k] += o[k];
+          }
         }
-        for (int c = 0; c < 3; c++) {
-          s.Eself[3 * i + c] = acc[c];
-          s.Bself[3 * i + c] = acc[3 + c];
+        if (owner) {
+          for (int c = 0; c < 3; c++) {
+            s.Eself[3 * i + c] = acc[c];
+            s.Bself[3 * i + c] = acc[3 + c];
+          }
         }
       }
     }
+  }
+  if (i < s.N && owner) {
     const double* rec = s.rec64 + ((size_t)i * s.D + pfrom) * 6;
     double x[3] = {rec[0], rec[1], rec[2]};
     double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
@@ -149,12 +176,16 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
     o[1] = q[1];
     o[2] = q[2];
   }
-  // the last block to finish advances the clock and resets the reduction for the next step
+  // the last block to finish advances the clock and resets the reduction for the next step (and, with
+  // ep.on, evaluates the energy monitor of every bunch on the pushed state)
+  __shared__ bool s_last;
+  __shared__ double s_num[kEnergyThreads], s_den[kEnergyThreads];
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned prev = atomicAdd(s.done, 1u);
-    if (prev == gridDim.x - 1) {
+    s_last = (prev == gridDim.x - 1);
+    if (s_last) {
       s.state->n = half ? st.n : st.n + 1;
       s.state->t = t_n + dt;
       s.state->dt = dt;
@@ -167,11 +198,20 @@ __global__ void step_post_kernel(DeviceState s, BextParams bp, AdaptParams ap, i
       *s.done = 0u;
     }
   }
+  __syncthreads();
+  if (ep.on && s_last) {
+    __threadfence();
+    for (int b = 0; b < s.nbunch; b++) energy_block(s, ep, mon, 0, b, half ? st.n : st.n + 1, t_n + dt, s_num, s_den);
+  }
 }
 
 cudaError_t launch_step_post(const DeviceState& s, const BextParams& b, const AdaptParams& ap, bool chunked,
-                             bool half, cudaStream_t st) {
-  step_post_kernel<<<(unsigned)((s.N + 255) / 256), 256, 0, st>>>(s, b, ap, chunked ? 1 : 0, half ? 1 : 0);
+                             bool half, bool wide, const EnergyParams* ep, EnergyMon* mon, cudaStream_t st) {
+  const long long threads = wide ? 32 * s.N : s.N;
+  EnergyParams e{0, 1, 0.0};
+  if (ep) e = *ep;  // the energy monitor in the last block (small systems)
+  step_post_kernel<<<(unsigned)((threads + kEnergyThreads - 1) / kEnergyThreads), kEnergyThreads, 0, st>>>(
+      s, b, ap, chunked ? 1 : 0, half ? 1 : 0, wide ? 1 : 0, e, mon);
   return cudaGetLastError();
 }
 
