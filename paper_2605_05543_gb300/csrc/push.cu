@@ -149,7 +149,17 @@ __global__ void __launch_bounds__(kEnergyThreads) step_post_kernel(DeviceState s
       }
     }
   }
-  if (i < s.N && owner) {
+  // the particle this thread pushes: its own, or (wide) one of the block's particles by the lanes of the
+  // first warp, so that the FP64 push occupies one warp per block rather than one lane of each warp
+  long long ip = i;
+  bool pusher = i < s.N && owner;
+  if (wide) {
+    __syncthreads();  // the block's field sums are written
+    ip = (long long)blockIdx.x * (blockDim.x >> 5) + threadIdx.x;
+    pusher = threadIdx.x < (blockDim.x >> 5) && ip < s.N;
+  }
+  if (pusher) {
+    const long long i = ip;
     const double* rec = s.rec64 + ((size_t)i * s.D + pfrom) * 6;
     double x[3] = {rec[0], rec[1], rec[2]};
     double u[3] = {s.u[3 * i], s.u[3 * i + 1], s.u[3 * i + 2]};
