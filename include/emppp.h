@@ -124,7 +124,8 @@ typedef struct {
 
 /* Work split of the pair kernel: items_per_block work items (bunch, source chunk, target tile) per
  * resident block, which sets the sources per chunk; target_order 1 sorts the targets spatially each
- * step (both paths; the fields do not depend on it). Chosen by emppp_autotune or set with emppp_set_tuning. */
+ * step (both paths; the fields do not depend on it; a step of a system of at most 2048 particles on the
+ * mixed path skips it). Chosen by emppp_autotune or set with emppp_set_tuning. */
 typedef struct {
   int32_t items_per_block; /* default 16 */
   int32_t target_order;    /* default 1 */

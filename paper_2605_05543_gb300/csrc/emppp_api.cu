@@ -362,9 +362,11 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
     k += 1;
   }
   // window, slot tables, work counter and (mixed path) per-source segment vectors; beside it, on the
-  // second stream, the spatial order of the targets (it reads only the present positions)
+  // second stream, the spatial order of the targets (it reads only the present positions). Small systems
+  // on the mixed path skip the order: a few target tiles gain less from it than its launch costs (the
+  // FP64 path keeps it, since it keeps out-of-history and bracketed pairs in separate warps).
   const bool mixed_pairs = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED;
-  const bool ordered = h->opt.pair_fields && h->target_order;
+  const bool ordered = h->opt.pair_fields && h->target_order && !(mixed_pairs && h->N <= 2048);
   if (ordered) {
     CU(cudaEventRecord(h->ev_fork, h->stream));
     CU(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
@@ -523,6 +525,7 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.Eself, N * 3);
   ALLOC(s.Bself, N * 3);
   ALLOC(s.Bout, N * 3);
+  ALLOC(s.ke, N);
   ALLOC(s.partial, (size_t)s.max_split * N * 6);
   ALLOC(s.state, 1);
   ALLOC(s.work, 1);

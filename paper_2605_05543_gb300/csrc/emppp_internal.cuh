@@ -19,6 +19,7 @@
 //                             and w_{k0} + v_{k0} (t_n - t_{k0}) - w_n.
 //   u      [N][3]             present proper velocities (FP64).
 //   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
+//   ke     [N]                kinetic-energy terms of the energy monitor (small systems, formed by the push).
 //   bunches [nbunch]          offsets, sizes, FP32-split origins and reference velocities.
 //   sched   [nbunch]          work split of the pair kernels (target tiles, source chunks, items).
 //   StepState (device)        present step n, t_n, dt and the derived window k0..n; kernels read it
@@ -113,6 +114,7 @@ struct DeviceState {
   double* Eself;
   double* Bself;
   double* Bout;
+  double* ke;       // [N] kinetic-energy terms of the energy monitor, formed by the push (small systems)
   double* partial;  // [C][N][6] per-source-chunk partial sums
   int max_split;    // chunks the partial buffer holds
   int* work;        // work-item counter of the persistent pair kernels (zeroed by the set-up launch)

@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(DeviceState s, E
                                                                 EnergyMon* __restrict__ mon, int reset) {
   __shared__ double s_num[kEnergyThreads];
   __shared__ double s_den[kEnergyThreads];
-  energy_block(s, ep, mon, reset, blockIdx.x, s.state->n, s.state->t, s_num, s_den);
+  energy_block(s, ep, mon, reset, blockIdx.x, s.state->n, s.state->t, nullptr, s_num, s_den);
 }
 
 cudaError_t launch_energy(const DeviceState& s, const EnergyParams& ep, EnergyMon* mon, bool reset, cudaStream_t st) {

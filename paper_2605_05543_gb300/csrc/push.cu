@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(kEnergyThreads) step_post_kernel(DeviceState s
     s.u[3 * i] = u[0];
     s.u[3 * i + 1] = u[1];
     s.u[3 * i + 2] = u[2];
+    if (ep.on) s.ke[i] = kinetic_term(u[0], u[1], u[2], s.wts[i]);  // for the monitor in the last block
     for (int c = 0; c < 3; c++) s.Bout[3 * i + c] = B[c];
     // append slot n+1 (both rings)
     double* r = s.rec64 + ((size_t)i * s.D + pnext) * 6;
@@ -211,7 +212,8 @@ __global__ void __launch_bounds__(kEnergyThreads) step_post_kernel(DeviceState s
   __syncthreads();
   if (ep.on && s_last) {
     __threadfence();
-    for (int b = 0; b < s.nbunch; b++) energy_block(s, ep, mon, 0, b, half ? st.n : st.n + 1, t_n + dt, s_num, s_den);
+    for (int b = 0; b < s.nbunch; b++)
+      energy_block(s, ep, mon, 0, b, half ? st.n : st.n + 1, t_n + dt, s.ke, s_num, s_den);
   }
 }
 
