@@ -163,7 +163,7 @@ void invalidate_graph(emppp_handle h) {
 // cost of the items (the branch mix differs across a bunch) evens out; systems too small for that get
 // one round of items with short chunks instead. At most max_split chunks per bunch. Uploaded when the
 // configuration changes.
-constexpr long long kMinChunk = 8;  // fewest sources per chunk
+constexpr long long kMinChunk = 4;  // fewest sources per chunk
 
 emppp_status update_schedule(emppp_handle c) {
   const bool mixed = c->opt.precision == EMPPP_MIXED;
@@ -190,7 +190,7 @@ emppp_status update_schedule(emppp_handle c) {
   for (int b = 0; b < c->nbunch; b++) total_tiles += (c->hb[b].n + 127) / 128;
   // chunking of one bunch: about items_per_block items per resident block over all bunches, in
   // whole 128-source tiles of at least 256 sources (small == false); or, for a system too small to fill
-  // the resident blocks that way, one round of items with chunks of 8k sources (small == true), since
+  // the resident blocks that way, one round of items with chunks of 4k sources (small == true), since
   // then each block's time is its own chunk length
   auto chunks = [&](long long n, bool small) -> long long {
     long long nchunk;
