@@ -224,7 +224,9 @@ cudaError_t launch_prep(const DeviceState& s, cudaStream_t st) {
 
 cudaError_t launch_setup(const DeviceState& s, bool extrap, cudaStream_t st) {
   const long long n = extrap ? (s.N > s.D ? s.N : s.D) : s.D;
-  setup_kernel<<<blocks_for(n, 256), 256, 0, st>>>(s, extrap ? 1 : 0);
+  // small blocks: the per-slot and per-source FP64 work spreads over more SMs (an FP64 warp instruction
+  // holds an SM's FP64 pipe for 16 cycles)
+  setup_kernel<<<blocks_for(n, 64), 64, 0, st>>>(s, extrap ? 1 : 0);
   return cudaGetLastError();
 }
 
