@@ -186,3 +186,21 @@ def test_monitor_errors():
         with pytest.raises(emppp.EmpppError) as ei:
             s.get_energy()
         assert ei.value.status == emppp.ERR_STATE
+
+
+@pytest.mark.parametrize("N", [300, 20000])
+def test_monitor_on_both_launch_forms(N):
+    """Systems of up to 16384 particles evaluate the monitor in the post-pair launch's last block from
+    terms the pushing threads formed; larger ones in the monitor's own launch. Both against the oracle's
+    mean energy of the GPU's own state after each step."""
+    b = inputs.gaussian_bunch(N, 20e-6, 3.0, seed=5)
+    w = np.linspace(0.5, 2.0, N)
+    with emppp.Solver(N, 8, 1e-15, precision="mixed", proposal="closed_form") as s:
+        s.set_particles(b.x.copy(), b.u.copy(), w.copy())
+        s.set_energy_monitor(1.0)
+        for _ in range(3):
+            s.step(1)
+            x, u, t, n = s.get_state()
+            e = s.get_energy()[0]
+            ref = oracle.mean_kinetic_energy(u, w)
+            assert abs(e["ebar"] - ref) <= 1e-12 * ref, (N, e["ebar"], ref)
