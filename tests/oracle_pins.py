@@ -899,6 +899,72 @@ def pin_half_step_uniform_motion(lib):
             assert np.max(np.abs(run.W[n + 1] - (x_now + dt * v))) <= 1e-9 * dt * beta * C
 
 
+# ---------------------------------------------------------------------------------------------
+# eq:linear's model error against exact fields: analytic trajectories (uniform drift plus a harmonic
+# wiggle, the synthetic history's form), each retarded time solved by Newton on the trajectory itself
+# ---------------------------------------------------------------------------------------------
+def _wiggle_exact_fields(lib, x, v, A, omega, targets):
+    """Exact Lienard-Wiechert fields at the present positions of w_j(s) = x_j + v_j s + (A_j / omega^2)
+    (1 - cos omega s), s = t - t_n; returns (E, sum_j |E_ij|) per target."""
+    N = x.shape[0]
+    E = np.zeros((len(targets), 3))
+    M = np.zeros(len(targets))
+    for ii, i in enumerate(targets):
+        js = np.array([j for j in range(N) if j != i])
+        d = x[i] - x[js]
+        dv = np.sum(d * v[js], axis=1)
+        c2v2 = C * C - np.sum(v[js] ** 2, axis=1)
+        s = -(dv + np.sqrt(dv * dv + c2v2 * np.sum(d * d, axis=1))) / c2v2
+        for _ in range(40):
+            w = x[js] + v[js] * s[:, None] + (A[js] / omega ** 2) * (1.0 - np.cos(omega * s))[:, None]
+            vs = v[js] + (A[js] / omega) * np.sin(omega * s)[:, None]
+            e = x[i] - w
+            s = s - (C * C * s * s - np.sum(e * e, axis=1)) / (2.0 * C * C * s + 2.0 * np.sum(e * vs, axis=1))
+        w = x[js] + v[js] * s[:, None] + (A[js] / omega ** 2) * (1.0 - np.cos(omega * s))[:, None]
+        vs = v[js] + (A[js] / omega) * np.sin(omega * s)[:, None]
+        acc = A[js] * np.cos(omega * s)[:, None]
+        for k in range(len(js)):
+            Ej, _ = oracle.lw_fields(x[i] - w[k], vs[k], acc[k], -QE, lib=lib)
+            E[ii] += Ej
+            M[ii] += np.linalg.norm(Ej)
+    return E, M
+
+
+def pin_linear_reconstruction_model_error(lib):
+    """The linear reconstruction's error against the exact fields of wiggling trajectories (every
+    retarded time inside the history): below 1e-5 of sum_j |E_ij| at dt = 1e-15 s for a 1e-3 c wiggle,
+    proportional to the wiggle (the motion's departure from a straight line; zero for uniform motion),
+    and falling faster than a first-order scheme's when dt halves (median ratio above 2.4; eq:mid, a
+    first-order scheme, gives 2.0). A wrong velocity interpolation or a dropped or misplaced
+    acceleration term breaks one of the three."""
+    from paper_2605_05543_gb300 import inputs
+
+    N, span, period = 48, 150e-15, 160e-15
+    b = inputs.gaussian_bunch(N, 1e-6, 1.5, seed=47)
+    omega = 2.0 * math.pi / period
+    dirs = inputs.normals(48, 3 * N).reshape(N, 3)
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    targets = np.arange(0, N, 3)
+    med = {}
+    for wig in (1e-4, 1e-3):
+        for dt in (2e-15, 1e-15):
+            n = int(round(span / dt))
+            h = inputs.synthetic_history(b.x, b.u, n, dt, wiggle=wig, period_steps=period / dt, seed=48)
+            A = dirs * (wig * C * omega)
+            E_ex, M = _wiggle_exact_fields(lib, h.W[n], h.V[n], A, omega, targets)
+            E, _, st = oracle.self_fields(h.T, h.W, h.V, n, n + 1, targets=targets, lib=lib)
+            assert st["out_of_history"] == 0
+            e = np.max(np.abs(E - E_ex) / M[:, None], axis=1)
+            med[(wig, dt)] = float(np.median(e))
+            if dt == 1e-15:
+                assert float(np.max(e)) <= 1e-5 * (wig / 1e-3), (wig, float(np.max(e)))
+    for dt in (2e-15, 1e-15):
+        ratio = med[(1e-3, dt)] / med[(1e-4, dt)]
+        assert 8.0 <= ratio <= 12.0, (dt, ratio)
+    for wig in (1e-4, 1e-3):
+        assert med[(wig, 2e-15)] / med[(wig, 1e-15)] >= 2.4, (wig, med)
+
+
 PINS = [
     pin_hc_pure_electric,
     pin_hc_pure_magnetic,
@@ -927,4 +993,5 @@ PINS = [
     pin_midpoint_constant_acceleration,
     pin_linear_beats_midpoint,
     pin_half_step_uniform_motion,
+    pin_linear_reconstruction_model_error,
 ]
