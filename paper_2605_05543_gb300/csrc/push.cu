@@ -101,7 +101,17 @@ __global__ void __launch_bounds__(kEnergyThreads) step_post_kernel(DeviceState s
   const bool owner = !wide || lane == 0;
   const StepState st = *s.state;
   double dt = st.dt, eta_rep = 0.0, v_rep = 0.0;
-  if (ap.on) dt = adaptive_step(s, ap, eta_rep, v_rep);
+  if (ap.on) {
+    // the step size, once per block (FP64 root and division) and shared
+    __shared__ double s_step[3];
+    if (threadIdx.x == 0) {
+      s_step[0] = adaptive_step(s, ap, s_step[1], s_step[2]);
+    }
+    __syncthreads();
+    dt = s_step[0];
+    eta_rep = s_step[1];
+    v_rep = s_step[2];
+  }
   // slot of x^n, the slot the push writes and t_n
   const int pfrom = half ? (st.pn == 0 ? s.D - 1 : st.pn - 1) : st.pn;
   const int pnext = half ? st.pn : (st.pn + 1 == s.D ? 0 : st.pn + 1);
