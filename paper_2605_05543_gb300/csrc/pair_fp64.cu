@@ -53,6 +53,7 @@ struct PairArgs {
   const float* __restrict__ rec32;
   const double* __restrict__ slot_t;
   const double* __restrict__ lhs64;
+  const float4* __restrict__ tab32;  // per slot: FP32 guard-band thresholds of (c (t_n - t_k))^2
   const double* __restrict__ inv_dtk;
   const double* __restrict__ wts;
   const StepState* __restrict__ state;
@@ -139,13 +140,12 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
   const double r0 = rr[0], r1 = rr[1], r2 = rr[2];
   const double vi0 = ADAPT ? rr[3] : 0.0, vi1 = ADAPT ? rr[4] : 0.0, vi2 = ADAPT ? rr[5] : 0.0;  // v_i(t_n)
-  float rh0 = 0.f, rh1 = 0.f, rh2 = 0.f;
-  if (PROP != kPropBisect) {
-    const float* q = a.rec32 + ((size_t)ic * D + pn) * 12;
-    rh0 = q[0];
-    rh1 = q[1];
-    rh2 = q[2];
-  }
+  // FP32 hi/lo split of the target's position: node tests run in FP32 against the guard-band thresholds
+  // of the slot tables and fall back to the FP64 test between them (the decision is the FP64 one)
+  const float* tq = a.rec32 + ((size_t)ic * D + pn) * 12;
+  const float rh0 = tq[0], rh1 = tq[1], rh2 = tq[2];
+  const float rl0 = tq[4], rl1 = tq[5], rl2 = tq[6];
+  const bool far_target = fmaxf(fabsf(rh0), fmaxf(fabsf(rh1), fabsf(rh2))) > 0.5f;
 
   const long long j_begin = bd.off + (long long)chunk_id * bs.chunk;
   const long long j_end = min(bd.off + bd.n, j_begin + bs.chunk);
@@ -174,18 +174,31 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
     if (!active) continue;  // and stay in the loop for the next source's evaluation
     if (j == i) continue;
     const double* src = a.rec64 + (size_t)j * D * 6;
+    const float4* src32 = reinterpret_cast<const float4*>(a.rec32 + (size_t)j * D * 12);
+    // P(k) at physical slot p: FP32 on the hi/lo split outside the guard band, else the FP64 test
+    auto ntest = [&](int p) -> bool {
+      const float4 q0 = __ldg(src32 + 3 * p), q1 = __ldg(src32 + 3 * p + 1);
+      const float d0 = (rh0 - q0.x) + (rl0 - q1.x), d1 = (rh1 - q0.y) + (rl1 - q1.y), d2 = (rh2 - q0.z) + (rl2 - q1.z);
+      const float D2 = d0 * d0 + d1 * d1 + d2 * d2;
+      const float4 tb = __ldg(a.tab32 + p);
+      if (!far_target) {
+        if (D2 > tb.x) return true;
+        if (D2 < tb.y) return false;
+      }
+      return node_test(r0, r1, r2, src + p * 6, __ldg(a.lhs64 + p));
+    };
     // ---- 1. bracket ------------------------------------------------------------------------
     long long k1;
     int br;
     if (PROP == kPropBisect) {
       n_tests += 1;
-      if (node_test(r0, r1, r2, src + win.p0 * 6, __ldg(a.lhs64 + win.p0))) {
+      if (ntest(win.p0)) {
         k1 = win.k0;
         br = 0;
       } else {
         n_tests += 1;
         const int pm1 = win.phys(win.n - 1);
-        if (!node_test(r0, r1, r2, src + pm1 * 6, __ldg(a.lhs64 + pm1))) {
+        if (!ntest(pm1)) {
           k1 = win.n - 1;
           br = 1;
         } else {
@@ -194,7 +207,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
             const long long m = (lo + hi) >> 1;
             const int pm = win.phys(m);
             n_tests += 1;
-            if (node_test(r0, r1, r2, src + pm * 6, __ldg(a.lhs64 + pm)))
+            if (ntest(pm))
               hi = m;
             else
               lo = m;
@@ -221,7 +234,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
         bool ooh = false;
         n_tests += 1;
         int pg = win.phys(kg);
-        if (node_test(r0, r1, r2, src + pg * 6, __ldg(a.lhs64 + pg))) {
+        if (ntest(pg)) {
           hi = kg;
           long long s = 1;
           for (;;) {
@@ -233,7 +246,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
             if (lo < win.k0) lo = win.k0;
             const int pl = win.phys(lo);
             n_tests += 1;
-            if (!node_test(r0, r1, r2, src + pl * 6, __ldg(a.lhs64 + pl))) break;
+            if (!ntest(pl)) break;
             hi = lo;
             s <<= 1;
           }
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
             }
             const int ph = win.phys(hi);
             n_tests += 1;
-            if (node_test(r0, r1, r2, src + ph * 6, __ldg(a.lhs64 + ph))) break;
+            if (ntest(ph)) break;
             lo = hi;
             s <<= 1;
           }
@@ -261,7 +274,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
             const long long m = (lo + hi) >> 1;
             const int pm = win.phys(m);
             n_tests += 1;
-            if (node_test(r0, r1, r2, src + pm * 6, __ldg(a.lhs64 + pm)))
+            if (ntest(pm))
               hi = m;
             else
               lo = m;
@@ -527,6 +540,7 @@ cudaError_t launch_pair_fp64(const DeviceState& s, const int* order, int proposa
   a.rec32 = s.rec32;
   a.slot_t = s.slot_t;
   a.lhs64 = s.tab.lhs64;
+  a.tab32 = s.tab.tab32;
   a.inv_dtk = s.tab.inv_dtk;
   a.wts = s.wts;
   a.state = s.state;
