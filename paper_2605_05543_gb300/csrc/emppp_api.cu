@@ -197,7 +197,9 @@ emppp_status update_schedule(emppp_handle c) {
     if (c->opt.source_split > 0) {
       nchunk = c->opt.source_split;
     } else if (!small) {
-      nchunk = ((long long)c->items_per_block * Rsched + total_tiles - 1) / total_tiles;
+      // the FP64 path gathers both rings, so its chunks are cut 4x shorter to keep a chunk's window in L2
+      const long long ipb = mixed ? c->items_per_block : 4LL * c->items_per_block;
+      nchunk = (ipb * Rsched + total_tiles - 1) / total_tiles;
       const long long by_size = (n + 255) / 256;
       if (nchunk > by_size) nchunk = by_size;
     } else {
