@@ -198,7 +198,7 @@ emppp_status update_schedule(emppp_handle c) {
       nchunk = c->opt.source_split;
     } else if (!small) {
       // the FP64 path gathers both rings, so its chunks are cut 4x shorter to keep a chunk's window in L2
-      const long long ipb = mixed ? c->items_per_block : 4LL * c->items_per_block;
+      const long long ipb = mixed ? 2LL * c->items_per_block : 4LL * c->items_per_block;
       nchunk = (ipb * Rsched + total_tiles - 1) / total_tiles;
       const long long by_size = (n + 255) / 256;
       if (nchunk > by_size) nchunk = by_size;
