@@ -206,7 +206,8 @@ def workload_name(wl):
 
 def kernel_traffic_record(path_name, proposal):
     """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it was taken on the
-    same kernel instance and on the kernel source as it is now (else None)."""
+    same kernel instance and on the sources as they are now (the kernel and the work split, which sets
+    the source chunks), else None."""
     rec = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     if not os.path.exists(rec):
         return None
@@ -215,9 +216,10 @@ def kernel_traffic_record(path_name, proposal):
         ent = d.get(path_name)
         if not ent or ent.get("proposal") != proposal:
             return None
-        src = os.path.join(ROOT, "paper_2605_05543_gb300", "csrc", ent["source"])
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return ent["dram_bytes_per_launch"] if digest == ent["source_sha256_16"] else None
+        h = hashlib.sha256()
+        for name in ent["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2605_05543_gb300", "csrc", name), "rb").read())
+        return ent["dram_bytes_per_launch"] if h.hexdigest()[:16] == ent["sources_sha256_16"] else None
     except Exception:
         return None
 
