@@ -63,7 +63,7 @@
    permeability. */
 static const double C_LIGHT = 299792458.0;
 static const double Q_E = 1.602176634e-19;
-static const double M_E = 9.1093837015e-31;
+static const double M_ELEC = 9.1093837015e-31;
 static const double EPS0 = 8.8541878128e-12;
 static const double MU0 = 1.25663706212e-6;
 static const double PI = 3.14159265358979323846;
@@ -301,7 +301,7 @@ static double gamma_of_u(const double u[3]) { return sqrt(1.0 + dot3(u, u) / (C_
 void orc_constants(double out[5]) {
   out[0] = C_LIGHT;
   out[1] = Q_E;
-  out[2] = M_E;
+  out[2] = M_ELEC;
   out[3] = EPS0;
   out[4] = MU0;
 }
@@ -443,7 +443,7 @@ int orc_self_fields(int64_t N, const double* T, const double* W, const double* V
 int orc_push(int64_t N, double dt, double* x, double* u, const double* Eself, const double* Bself, int bkind,
              const double* bpar, double* v, double* Btot) {
   if (N < 0) return ORC_ERR_ARG;
-  double h = -Q_E * dt / (2.0 * M_E);
+  double h = -Q_E * dt / (2.0 * M_ELEC);
   for (int64_t i = 0; i < N; i++) {
     double* xi = x + 3 * i;
     double* ui = u + 3 * i;
@@ -600,7 +600,7 @@ double orc_mean_kinetic_energy(int64_t N, const double* u, const double* w) {
   for (int64_t i = 0; i < N; i++) {
     double wi = w ? w[i] : 1.0;
     double uu = dot3(u + 3 * i, u + 3 * i) / (C_LIGHT * C_LIGHT);
-    double Ei = uu / (gamma_of_u(u + 3 * i) + 1.0) * M_E * C_LIGHT * C_LIGHT;
+    double Ei = uu / (gamma_of_u(u + 3 * i) + 1.0) * M_ELEC * C_LIGHT * C_LIGHT;
     csum_add(&num, wi * Ei);
     csum_add(&den, wi);
   }

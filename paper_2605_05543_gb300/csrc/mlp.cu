@@ -119,10 +119,8 @@ __global__ void sample_kernel(DeviceState s, const int* __restrict__ pairs, long
   };
   // the paper's search (Sec. 2.2)
   long long k1;
-  bool ooh = false;
   if (node_test64(r0, r1, r2, src + 6 * st.p0, s.tab.lhs64[st.p0])) {
-    k1 = st.k0;
-    ooh = true;
+    k1 = st.k0;  // out of history: eq:linear2 from the oldest slot
   } else if (!node_test64(r0, r1, r2, src + 6 * phys(st.n - 1), s.tab.lhs64[phys(st.n - 1)])) {
     k1 = st.n - 1;
   } else {
@@ -136,7 +134,6 @@ __global__ void sample_kernel(DeviceState s, const int* __restrict__ pairs, long
     }
     k1 = lo;
   }
-  (void)ooh;
   const int p1 = phys(k1);
   const double* w1 = src + 6 * p1;
   const double T1 = t - s.slot_t[p1];

@@ -12,7 +12,7 @@ MUTANTS = [
     ("hc_sigma_sign", "double sigma = gm * gm - tau2;", "double sigma = gm * gm + tau2;"),
     ("hc_half_kick", "for (int c = 0; c < 3; c++) unew[c] = up[c] + h * E[c] + up_x_t[c];",
      "for (int c = 0; c < 3; c++) unew[c] = up[c] + up_x_t[c];"),
-    ("push_charge_sign", "double h = -Q_E * dt / (2.0 * M_E);", "double h = Q_E * dt / (2.0 * M_E);"),
+    ("push_charge_sign", "double h = -Q_E * dt / (2.0 * M_ELEC);", "double h = Q_E * dt / (2.0 * M_ELEC);"),
     ("push_full_drift", "xi[c] = xh[c] + 0.5 * dt * v[3 * i + c];", "xi[c] = xh[c] + dt * v[3 * i + c];"),
     # eq:LW_E / eq:LW_B
     ("lw_drop_accel", "E[c] = pref * (c2mv2 * vp[c] + acc[c]);", "E[c] = pref * (c2mv2 * vp[c]);"),
@@ -56,8 +56,8 @@ MUTANTS = [
     ("adapt_present_separation", "double eta[3] = {r[0] - w[0], r[1] - w[1], r[2] - w[2]};\n      double R",
      "double eta[3] = {r[0] - hist_w(&h, n, j)[0], r[1] - hist_w(&h, n, j)[1], r[2] - hist_w(&h, n, j)[2]};\n      double R"),
     # Sec. 2.7 stage switch
-    ("energy_includes_rest_mass", "double Ei = uu / (gamma_of_u(u + 3 * i) + 1.0) * M_E * C_LIGHT * C_LIGHT;",
-     "double Ei = (uu / (gamma_of_u(u + 3 * i) + 1.0) + 1.0) * M_E * C_LIGHT * C_LIGHT;"),
+    ("energy_includes_rest_mass", "double Ei = uu / (gamma_of_u(u + 3 * i) + 1.0) * M_ELEC * C_LIGHT * C_LIGHT;",
+     "double Ei = (uu / (gamma_of_u(u + 3 * i) + 1.0) + 1.0) * M_ELEC * C_LIGHT * C_LIGHT;"),
     ("energy_weight_squared", "csum_add(&num, wi * Ei);", "csum_add(&num, wi * wi * Ei);"),
     ("switch_not_armed", "run = (armed && fabs(r) < eps) ? run + 1 : 0;", "run = (fabs(r) < eps) ? run + 1 : 0;"),
     ("switch_signed_rate", "run = (armed && fabs(r) < eps) ? run + 1 : 0;", "run = (armed && r < eps) ? run + 1 : 0;"),
