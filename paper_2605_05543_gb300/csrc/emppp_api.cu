@@ -394,8 +394,9 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   if (ev) CU(cudaEventRecord(ev[2], h->stream));
   // partial sums, step size (Sec. 2.4), push and append (Sec. 2.3), clock advance: one launch
   const bool chunked = h->opt.pair_fields && any_chunked(h);
-  // small systems: the energy monitor runs in the post-pair launch's last block
-  const bool fused_energy = h->energy.on && h->N <= 16384;
+  // small systems of few bunches: the energy monitor runs in the post-pair launch's last block (its own
+  // launch evaluates the bunches in parallel, one block each)
+  const bool fused_energy = h->energy.on && h->N <= 16384 && h->nbunch <= 8;
   CU(launch_step_post(h->ds, bp, h->adapt, chunked, half, chunked && wide_reduction(h),
                       fused_energy ? &h->energy : nullptr, h->d_mon, h->stream));
   k += 1;
