@@ -258,6 +258,7 @@ emppp_status read_err(emppp_handle h) {
   int herr = 0;
   CU(cudaMemcpyAsync(&herr, h->ds.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
+  if (herr & kErrTimeout) return fail(EMPPP_ERR_TIMEOUT, "a bounded device wait gave up (bits 0x%x)", herr);
   if (herr) {
     return fail(EMPPP_ERR_NUMERIC,
                 "device numeric fault (bits 0x%x: 1 = negative discriminant or |v| >= c, 2 = coincident pair, "
