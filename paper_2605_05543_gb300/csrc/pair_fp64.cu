@@ -4,7 +4,8 @@
 // its slice. Per pair:
 //   1. bracket the retarded time in j's history with the node test
 //        P(k):  (c (t - t_k))^2 <= |r - w_{j,k}|^2       (true: t_r at or before t_k)
-//      evaluated in FP64 in the same operation order as the reference (so decisions agree bit for
+//      evaluated in FP32 on the shadow ring's hi/lo split against guard-band thresholds of the slot
+//      tables, and in FP64 in the reference operation order between them (so decisions agree bit for
 //      bit): out-of-history if P(k0), near-field shortcut if not P(n-1), else bisection (Sec. 2.2);
 //      or, with the closed-form proposal, a guarded galloping search started at the slot predicted
 //      by uniform motion from j's present state. Both return the unique sign change of P.
@@ -21,7 +22,7 @@
 // Targets are taken in the spatial order of order.cu (when given), so that the pairs of a warp mostly
 // take the same branch; which thread evaluates a target does not change its result.
 // The arithmetic is FP64-pipe bound (GB300: 2 DFMA/clk/SM); everything that is not an FP64 result
-// (the guess, indices, loads) runs on the FP32/INT pipes beside it.
+// (the guess, the node tests outside the guard band, indices, loads) runs on the FP32/INT pipes beside it.
 #include "emppp_internal.cuh"
 #include "mlp.cuh"
 #include "shadow.cuh"
