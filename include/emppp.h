@@ -62,7 +62,8 @@ typedef struct {
 } emppp_bext;
 
 /* Precision of the pair-field path.
- *   FP64:  every step of the pair path in FP64; agrees with the FP64 oracle to ~1e-14.
+ *   FP64:  every result of the pair path in FP64 (node tests decided in FP32 outside a guard band and
+ *          in FP64 inside it, so the brackets are the FP64 ones); agrees with the FP64 oracle to ~1e-14.
  *   MIXED: pair geometry and fields in FP32 on hi/lo-split coordinates with compensated FP32
  *          sums; time stamps, the bracket decision and the push stay FP64. */
 typedef enum { EMPPP_FP64 = 0, EMPPP_MIXED = 1 } emppp_precision;
