@@ -90,3 +90,58 @@ def test_mixed_path_far_from_the_split_origin():
     for k in ("out_of_history", "shortcut", "bisection"):
         assert st[k] == st_ref[k]
     assert st["guard_fallbacks"] > 0  # the far cluster's tests ran in FP64
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("proposal", ["bisect", "closed_form"])
+def test_node_tests_at_the_light_sphere(precision, proposal):
+    """Targets placed on the light sphere of one stored slot of their source, to within 1e-16 to 1e-12 of
+    its radius (64 two-particle bunches in one batch): every such node test falls inside the FP32 guard
+    band, the FP64 test decides it, and the brackets must be the oracle's (branch counts equal) with
+    fields within each path's bar."""
+    rng = np.random.default_rng(70)
+    C = oracle.constants()["c"]
+    n, D, nb = 40, 64, 64
+    T = np.array([k * DT for k in range(n + 1)])
+    W = np.zeros((n + 1, 2 * nb, 3))
+    V = np.zeros((n + 1, 2 * nb, 3))
+    eps = [0.0, 1e-16, -1e-16, 1e-15, -1e-15, 1e-14, -1e-14, 1e-12, -1e-12]
+    for b in range(nb):
+        beta = rng.uniform(0.3, 0.9)
+        vdir = rng.normal(size=3)
+        v0 = beta * C * vdir / np.linalg.norm(vdir)
+        acc = rng.normal(size=3) * 1e18
+        w00 = rng.normal(size=3) * 1e-6
+        k = int(rng.integers(1, n - 1))
+        nhat = rng.normal(size=3)
+        nhat /= np.linalg.norm(nhat)
+        wk = w00 + v0 * T[k] + 0.5 * acc * T[k] ** 2
+        r = wk + C * (T[n] - T[k]) * (1.0 + eps[b % len(eps)]) * nhat
+        W[:, 2 * b] = r  # the target rests on the sphere
+        W[:, 2 * b + 1] = w00 + v0[None] * T[:, None] + 0.5 * acc[None] * T[:, None] ** 2
+        V[:, 2 * b + 1] = v0[None] + acc[None] * T[:, None]
+    u = np.zeros((2 * nb, 3))
+    g = 1.0 / np.sqrt(1.0 - np.sum(V[n, 1::2] ** 2, axis=1) / C ** 2)
+    u[1::2] = V[n, 1::2] * g[:, None]
+    with emppp.Solver(0, D, DT, precision=precision, proposal=proposal, bunches=[2] * nb) as s:
+        s.set_history(n, T, W, V, u)
+        s.step(1)
+        E, B = s.get_fields()
+        st = s.stats()
+    counts = dict(out_of_history=0, shortcut=0, bisection=0)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for b in range(nb):
+        sl = slice(2 * b, 2 * b + 2)
+        E_ref, B_ref, st_ref, M = oracle.self_fields(T, W[:, sl], V[:, sl], n, D, mags=True)
+        # the resting target's own B at the source is zero up to rounding: B is measured against the
+        # E scale (over c) where sum_j |B_ij| is only that rounding
+        M = M.copy()
+        M[:, 1] = np.maximum(M[:, 1], M[:, 0] / C)
+        eE, eB = field_errors(E[sl], B[sl], E_ref, B_ref, M)
+        assert eE <= tol and eB <= tol, (b, eE, eB)
+        for key in counts:
+            counts[key] += st_ref[key]
+    for key in counts:
+        assert st[key] == counts[key], (key, st, counts)
+    if precision == "mixed":
+        assert st["guard_fallbacks"] >= nb // 2  # the band was exercised (the FP64 path does not count them)
