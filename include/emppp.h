@@ -112,7 +112,7 @@ typedef struct {
   int64_t shortcut;        /* pairs bracketed by the near-field shortcut */
   int64_t bisection;       /* pairs bracketed by the search */
   int64_t node_tests;      /* evaluations of c (t - t_k) <= |r - w_k| over all pairs */
-  int64_t guard_fallbacks; /* node tests decided in FP64 after an inconclusive FP32 test (mixed path) */
+  int64_t guard_fallbacks; /* node tests decided in FP64 after an inconclusive FP32 test */
   int64_t kernel_launches; /* kernels launched by the library (cumulative since emppp_create) */
   double pair_ms;          /* device time of the pair evaluations (timing option on, else 0) */
   double step_ms;          /* device time of whole steps (timing option on, else 0) */

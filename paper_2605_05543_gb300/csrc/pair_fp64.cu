@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const float invL = (float)(1.0 / (kC * a.state->dt * D));
   const int pprev = win.n > win.k0 ? win.phys(win.n - 1) : pn;  // slot n - 1 (or n)
 
-  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0;
+  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   double emin = __longlong_as_double(0x7ff0000000000000LL), vmax2 = 0.0;  // adaptive time step (Sec. 2.4)
   int errbits = 0;
 
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
         if (D2 > tb.x) return true;
         if (D2 < tb.y) return false;
       }
+      n_fb += 1;
       return node_test(r0, r1, r2, src + p * 6, __ldg(a.lhs64 + p));
     };
     // ---- 1. bracket ------------------------------------------------------------------------
@@ -469,12 +470,14 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
   n_bi = __reduce_add_sync(0xffffffffu, n_bi);
   n_tests = __reduce_add_sync(0xffffffffu, n_tests);
+  n_fb = __reduce_add_sync(0xffffffffu, n_fb);
   errbits = __reduce_or_sync(0xffffffffu, errbits);
   if ((threadIdx.x & 31) == 0) {
     if (n_ooh) atomicAdd(a.stats + kStatOOH, (unsigned long long)n_ooh);
     if (n_sc) atomicAdd(a.stats + kStatShortcut, (unsigned long long)n_sc);
     if (n_bi) atomicAdd(a.stats + kStatBisect, (unsigned long long)n_bi);
     if (n_tests) atomicAdd(a.stats + kStatNodeTests, (unsigned long long)n_tests);
+    if (n_fb) atomicAdd(a.stats + kStatGuard, (unsigned long long)n_fb);
     if (errbits) atomicOr(a.err, errbits);
   }
 }
