@@ -102,3 +102,16 @@ def test_paper_bunch_recipe():
     assert np.allclose(R @ R.T, np.eye(3), atol=1e-15) and abs(np.linalg.det(R) - 1) < 1e-15
     w = inputs.paper_bunch(10, 1.0, weight=2.5e6).weights
     assert w.shape == (10,) and np.all(w == 2.5e6)
+
+
+def test_printed_baseline_states_move_at_the_beam_speed():
+    """The paper's printed states of the baseline run (tests/golden/paper_centroid_steps.txt) against
+    the 1 MeV beam kinematics: zbar / t is the beam speed beta c to within the printed digits (t to 3
+    significant figures, zbar to 4)."""
+    gamma0, beta0 = inputs.beam_kinematics(1.0e6 * inputs.Q_E)
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_centroid_steps.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) == 2
+    for Np, step, t, z in rows:
+        t, z = float(t), float(z)
+        assert abs(z / (t * inputs.C_LIGHT) / beta0 - 1.0) <= 1e-3, (Np, z / (t * inputs.C_LIGHT), beta0)
