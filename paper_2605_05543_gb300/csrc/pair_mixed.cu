@@ -202,6 +202,8 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
   const int pprev = win.nw > 1 ? win.phys(win.nw - 2) : pn;  // slot n - 1 (or n)
   const float invL = (float)(1.0 / (kC * a.state->dt * D));
+  // light distance across the window, (nw - 1) c dt (learned proposal only)
+  const float mlp_lh = PROP == kPropMlp ? (float)((win.nw - 1) * (kC * a.state->dt)) : 0.f;
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
@@ -282,13 +284,22 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
         const int j = tile + jj;
         float steps_mlp = 0.f;
         if (PROP == kPropMlp) {
-          // every lane of the warp takes part in the tensor-core evaluation, then idle lanes skip the pair
+          // every lane of the warp takes part in the tensor-core evaluation, then idle lanes skip the pair;
+          // a warp whose lanes uniform motion places all beyond the history (c tau >= Lh, recognised
+          // without a root: |d|^2 + 2 Lh (d.beta) > Lh^2 / gamma^2) skips the network, and its search
+          // starts at the oldest slot, the one test such a pair needs
           const float4 g0 = s_q0[jj], g2 = s_q2[jj], gd = s_db[jj];
           const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
-          float f[mlp::kIn];
-          mlp::features(x0, x1, x2, g2.x, g2.y, g2.z, gd.x, gd.y, gd.z, invL, (float)D, f);
-          const float z = mlp::infer_warp(s_net[0], f, s_stage[threadIdx.x >> 5]);
-          steps_mlp = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 2.0e9f);
+          const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z, dd = x0 * x0 + x1 * x1 + x2 * x2;
+          const bool beyond = !active || fmaf(2.f * mlp_lh, db, dd) > mlp_lh * mlp_lh * g0.w;
+          if (__all_sync(0xffffffffu, beyond)) {
+            steps_mlp = 2.0e9f;
+          } else {
+            float f[mlp::kIn];
+            mlp::features(x0, x1, x2, g2.x, g2.y, g2.z, gd.x, gd.y, gd.z, invL, (float)D, f);
+            const float z = mlp::infer_warp(s_net[0], f, s_stage[threadIdx.x >> 5]);
+            steps_mlp = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 2.0e9f);
+          }
         }
         if (!active) continue;  // and stay in the loop for the next source's evaluation
         if (j == i) continue;
