@@ -74,6 +74,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-run-leg", action="store_true",
+                    help="skip the stated run of the bunch from t = 0 (500 steps of its own dynamics)")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path (FP64 + bisection) on the same state")
     ap.add_argument("--small", action="store_true", help="tiny workload for smoke tests of this script")
@@ -253,35 +255,71 @@ def cpu_baseline(h, wl, seconds, E_gpu=None, B_gpu=None, seed=1):
     return base, parity
 
 
-def train_proposal(wl, win, n_hist, samples=65536, epochs=60, seed=3):
-    """Trains the proposal network on (feature, delay) samples of random pairs of the workload's stored
-    state, drawn with the library's exact retarded-time search; returns (params, report)."""
+def _random_pairs(N, m, rng):
+    import numpy as np
+
+    i = rng.integers(0, N, m)
+    j = rng.integers(0, N - 1, m)
+    j = np.where(j >= i, j + 1, j)
+    return np.stack([i, j], axis=1).astype(np.int32)
+
+
+# training data of the proposal network: the N = 4096 uniform-field workload (sigma = 10 um, gamma0 = 3,
+# B = 5e-5 T along x, dt = 1e-15 s, depth 512) run from t = 0, sampled at these steps
+TRAIN_WL = dict(N=4096, sigma=10e-6, gamma0=3.0, dt=1e-15, depth=512, B=(5e-5, 0.0, 0.0), seed=0,
+                states=(64, 128, 256, 384, 511, 640, 800, 1000, 1250, 1500))
+
+
+def train_proposal(wl, win, n_hist, per_state=1 << 20, epochs=3, seed=3, small=False):
+    """Trains the proposal network out of sample: (feature, delay) pairs of random particle pairs drawn with
+    the library's exact retarded-time search from states of the N = 4096 uniform-field workload as it runs
+    from t = 0 (about 1e7 samples), then measures its loss on pairs of the benchmark's own state (held out)
+    beside the loss of z = 0, which is the closed-form guess itself; returns (params, report)."""
     import numpy as np
     import torch
 
     from paper_2605_05543_gb300 import emppp, inputs
 
-    N, D = wl["N"], wl["depth"]
+    tw = dict(TRAIN_WL)
+    if small:
+        tw.update(N=1024, states=(64, 128, 256), depth=128)
+        per_state = 1 << 16
     rng = np.random.default_rng(seed)
-    i = rng.integers(0, N, samples)
-    j = rng.integers(0, N - 1, samples)
-    j = np.where(j >= i, j + 1, j)
-    pairs = np.stack([i, j], axis=1).astype(np.int32)
-    T, W, V, u = win
     t0 = time.perf_counter()
-    with emppp.Solver(N, D, wl["dt"]) as s:
+    b = inputs.gaussian_bunch(tw["N"], tw["sigma"], tw["gamma0"], seed=tw["seed"])
+    feats, zs = [], []
+    stream = torch.cuda.Stream()
+    with emppp.Solver(tw["N"], tw["depth"], tw["dt"], precision="mixed", proposal="closed_form", stream=stream) as s:
+        s.set_particles(b.x.copy(), b.u.copy())
+        n = 0
+        for k in tw["states"]:
+            s.step(k - n, emppp.bext_uniform(tw["B"]))
+            n = k
+            f, _, z = s.sample_delays(_random_pairs(tw["N"], per_state, rng))
+            feats.append(f)
+            zs.append(z)
+    X, Z = np.concatenate(feats), np.concatenate(zs)
+    # held-out pairs: the benchmark's own state
+    T, W, V, u = win
+    with emppp.Solver(wl["N"], wl["depth"], wl["dt"]) as s:
         s.set_history(n_hist, T, W, V, u)
-        feat, delay, z = s.sample_delays(pairs)
+        Xh, _, Zh = s.sample_delays(_random_pairs(wl["N"], 1 << 16, rng))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     p0 = inputs.mlp_init_params(seed)
-    loss0, _ = emppp.mlp_gradient(p0, feat, z)
-    p, losses = emppp.mlp_train(p0, feat, z, epochs=epochs, batch=512, lr=3e-3, lr_final=1e-5)
-    loss1, _ = emppp.mlp_gradient(p, feat, z)
+    loss0, _ = emppp.mlp_gradient(p0, X[:1 << 18], Z[:1 << 18])
+    p, losses = emppp.mlp_train(p0, X, Z, epochs=epochs, batch=4096, lr=2e-3, lr_final=1e-5)
     t2 = time.perf_counter()
-    return p, {"samples": samples, "epochs": epochs, "batch": 512, "lr": "3e-3 -> 1e-5 (cosine)", "loss_initial": loss0,
-               "loss_final": loss1, "sample_seconds": t1 - t0, "train_seconds": t2 - t1,
-               "target": "z = log(c (t - t_r) / |r - w_n|), MSE"}
+    loss1, _ = emppp.mlp_gradient(p, X[:1 << 18], Z[:1 << 18])
+    held, _ = emppp.mlp_gradient(p, Xh, Zh)
+    return p, {"train_workload": (f"N={tw['N']} sigma=10um gamma0=3 B=5e-5T along x dt=1e-15s depth={tw['depth']}, "
+                                  f"run from t=0, sampled at steps {list(tw['states'])}"),
+               "samples": int(X.shape[0]), "epochs": epochs, "batch": 4096, "lr": "2e-3 -> 1e-5 (cosine)",
+               "loss_initial": loss0, "loss_final_train": loss1, "loss_per_epoch": [float(x) for x in losses],
+               "held_out": {"pairs": int(Xh.shape[0]), "state": "the benchmark's state (not in the training data)",
+                            "loss": held, "loss_of_closed_form_guess": float(np.mean(Zh.astype(np.float64) ** 2))},
+               "sample_seconds": t1 - t0, "train_seconds": t2 - t1,
+               "target": "z = log((t - t_r) / tau_u), tau_u the uniform-motion delay of the source's present record; MSE"}
 
 
 def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True, net=None,
@@ -350,6 +388,33 @@ def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, ke
     return out
 
 
+def run_from_t0(wl, path, proposal, steps, rank):
+    """The workload's bunch run from t = 0 for `steps` steps with its own dynamics (steps replayed from a
+    CUDA graph), timed as a whole with CUDA events: the stated run of the configuration, whose history
+    grows from one slot."""
+    import torch
+
+    from paper_2605_05543_gb300 import emppp, inputs
+
+    N = wl["N"]
+    b = inputs.gaussian_bunch(N, wl["sigma"], wl["gamma0"], seed=wl["seed"] + rank)
+    stream = torch.cuda.Stream()
+    with emppp.Solver(N, wl["depth"], wl["dt"], precision=path, proposal=proposal, stream=stream) as s:
+        s.set_particles(b.x.copy(), b.u.copy())
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        st = s.stats()
+    return {"steps": steps, "path": path, "proposal": proposal, "ms_per_step": ms / steps,
+            "pairs_per_s": N * (N - 1) * steps / (ms / 1e3),
+            "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
+            "branch_mix": {k: st[k] / max(st["pairs"], 1) for k in ("out_of_history", "shortcut", "bisection")}}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -366,7 +431,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     net, net_report = None, None
     if args.proposal == "mlp" or not args.no_ablation:
-        net, net_report = train_proposal(wl, win, h.n)
+        net, net_report = train_proposal(wl, win, h.n, small=args.small)
+    peaks = emppp.measure_peaks()
     res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e,
                    net=net if args.proposal == "mlp" else None)
     ms = max_over_ranks(res["ms"], dev)
@@ -378,6 +444,7 @@ def run_ours(args):
     pair_ms_avg = st["pair_ms"] / max(st["timed_steps"], 1)
     achieved = flops / max(st["timed_steps"], 1) / (pair_ms_avg / 1e3) / 1e12
     peak = PEAK_FP64_TFLOPS if args.path == "fp64" else PEAK_FP32_TFLOPS
+    peak_meas = (peaks["fp64_flops"] if args.path == "fp64" else peaks["fp32_flops"]) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -390,8 +457,14 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "pair_fp64_kernel" if args.path == "fp64" else "pair_mixed_kernel",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": kernel_traffic_record(args.path, args.proposal),
-                     "peak_note": ("FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz" if args.path == "fp64"
-                                   else "FP32: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+                     "peak_note": ("nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz" if args.path == "fp64"
+                                   else "nominal FP32: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
+                     "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas,
+                     "peak_measured_source": ("emppp_measure_peaks in this run: dependent FMA chains on every SM "
+                                              f"({'FP64' if args.path == 'fp64' else 'FP32'}), best of 3 "
+                                              "event-timed launches, at the clock the GPU ran"),
+                     "probe": {"fp32_tflops": peaks["fp32_flops"] / 1e12, "fp64_tflops": peaks["fp64_flops"] / 1e12,
+                               "mufu_tera_ops": peaks["mufu_ops"] / 1e12},
                      "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1)},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
@@ -434,6 +507,8 @@ def run_ours(args):
         line["speedup_vs_fp64_plain"] = ref_ms / ms
         for v in line.get("proposal_ablation", {}).values():
             v["speedup_vs_fp64_plain"] = ref_ms / v["ms_per_step"]
+    if not args.no_run_leg:
+        line["run_from_t0"] = run_from_t0(wl, args.path, args.proposal, 50 if args.small else 500, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         E0, B0 = res.get("fields0", (None, None))
         line["cpu_baseline"], parity = cpu_baseline(h, wl, args.cpu_seconds, E0, B0)

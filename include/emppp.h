@@ -43,7 +43,8 @@ typedef enum {
   EMPPP_ERR_ARG = -1,     /* bad handle, size, pointer or option */
   EMPPP_ERR_CUDA = -2,    /* a CUDA runtime call failed (text in emppp_last_error) */
   EMPPP_ERR_NUMERIC = -3, /* device-side numeric fault in a previous step */
-  EMPPP_ERR_TIMEOUT = -4, /* a bounded device wait gave up */
+  EMPPP_ERR_TIMEOUT = -4, /* reserved for a bounded device wait that gives up; no kernel of this version
+                             waits on another, so no call returns it */
   EMPPP_ERR_STATE = -5,   /* call out of order (e.g. step before set_particles) */
   EMPPP_ERR_OOM = -6      /* device allocation failed */
 } emppp_status;
@@ -123,20 +124,28 @@ typedef struct {
   double v_max;            /* adaptive step: max |v_i - v_j(t_r)| over the same pairs (m/s), else 0 */
 } emppp_stats;
 
-/* Work split of the pair kernel: items_per_block work items (bunch, source chunk, target tile) per
- * resident block, which sets the sources per chunk; target_order 1 sorts the targets spatially each
- * step (both paths; the fields do not depend on it; a step of a system of at most 2048 particles on the
- * mixed path skips it). Chosen by emppp_autotune or set with emppp_set_tuning. */
+/* Work split and tile shape of the pair kernel: items_per_block work items (bunch, source chunk, target
+ * tile) per resident block of 128 threads, which sets the sources per chunk; target_order 1 sorts the
+ * targets spatially each step (both paths; the fields do not depend on it; a step of a system of at most
+ * 2048 particles on the mixed path skips it). The tile shape: targets_per_block targets per work item and
+ * thread block (64, 128 or 256; on the mixed path also the sources a block stages per tile) and, on the
+ * mixed path, sources_per_sum sources per FP32 partial sum before the compensated addition (8 or 16; with
+ * 16 only at 128 targets per block). The FP64 path ignores sources_per_sum. The shape changes the order
+ * of each target's sum, so fields of different shapes agree within rounding, not bit for bit; the
+ * adaptive time step and the comparison variants run the default shape (128, 8). Chosen by emppp_autotune
+ * or set with emppp_set_tuning. */
 typedef struct {
-  int32_t items_per_block; /* default 16 */
-  int32_t target_order;    /* default 1 */
-  double ms;               /* measured time of one field evaluation (emppp_autotune), else 0 */
+  int32_t items_per_block;   /* default 16 */
+  int32_t target_order;      /* default 1 */
+  double ms;                 /* measured time of one field evaluation (emppp_autotune), else 0 */
+  int32_t targets_per_block; /* default 128 (0 in emppp_set_tuning: 128) */
+  int32_t sources_per_sum;   /* default 8 (0 in emppp_set_tuning: 8) */
 } emppp_tuning;
 
 typedef struct {
   int32_t ncand;           /* candidates timed */
   int32_t best;            /* index of the chosen one */
-  emppp_tuning cand[16];
+  emppp_tuning cand[32];
 } emppp_tuning_report;
 
 /* Fills *out with the defaults listed above. */
@@ -220,12 +229,31 @@ EMPPP_API emppp_status emppp_get_stats(emppp_handle h, emppp_stats* out);
 EMPPP_API emppp_status emppp_reset_stats(emppp_handle h);
 
 /* Times the pair-field evaluation of the present state (slot tables, target order, pair kernel and
- * partial-sum reduction; the state is not advanced) for items_per_block in {4, 8, 16, 32, 64} and,
- * on the mixed path, with and without the spatial target order; keeps the fastest for later steps of
- * the current precision and proposal. report may be NULL. Synchronises the stream; resets the stats. */
+ * partial-sum reduction; the state is not advanced; one warm-up, best of two) for items_per_block in
+ * {4, 8, 16, 32, 64}, with and without the spatial target order, at the default tile shape; then, with
+ * the fastest of those and unless the adaptive time step is on, for the other tile shapes (targets per
+ * block 64 and 256; on the mixed path also 16 sources per partial sum). Keeps the fastest candidate for
+ * later steps of the current precision and proposal. report may be NULL. Synchronises the stream; resets
+ * the stats; afterwards emppp_get_fields reports the fields of the last evaluation. */
 EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* report);
 
-/* Sets the work split directly (e.g. a tuning found earlier). items_per_block in 1..256. */
+/* Bracket of the retarded-time search of every ordered pair of the present state (Sec. 2.2), for
+ * checking the search pair by pair: one evaluation of the present state's self fields with the handle's
+ * precision and proposal (the state does not advance; emppp_get_fields then reports this evaluation's
+ * fields), whose pair kernel also writes, for target i and source j != i of one bunch,
+ *   brackets[i * n + j] = 4 (k1 - k0) + branch   (branch 0 out of history, 1 near-field shortcut,
+ *                                                 2 bisection; k1 the older node of the bracket),
+ * and -1 for i == j and for pairs of different bunches. brackets: DEVICE array of n * n int32 (n the
+ * particles of all bunches, at most 65536), owned by the caller. *k0 (host, may be NULL) receives the
+ * absolute index of the earliest usable slot. Synchronises the stream and resets the stats; the library
+ * allocates nothing.
+ * EMPPP_ERR_STATE with pair fields off, with the half-step field point, or with the MLP proposal and no
+ * network. */
+EMPPP_API emppp_status emppp_bracket_dump(emppp_handle h, int32_t* brackets, int64_t* k0);
+
+/* Sets the work split and tile shape directly (e.g. a tuning found earlier). items_per_block in 1..256,
+ * targets_per_block in {0 (= 128), 64, 128, 256}, sources_per_sum in {0 (= 8), 8, 16}, 16 only with 128
+ * targets per block; EMPPP_ERR_ARG otherwise. */
 EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning);
 
 /* Replaces the options for later steps. EMPPP_ERR_STATE for a comparison variant (MIDPOINT, HALF_STEP)
@@ -252,8 +280,11 @@ EMPPP_API emppp_status emppp_synchronize(emppp_handle h);
  * library until the process exits), which limits n to 348160 and nslots to 4096: larger sizes are
  * rejected with EMPPP_ERR_ARG. All calls share that array, so calls whose work overlaps on the GPU
  * race with each other: serialise them. The first call on a device looks up the array's device
- * address (with that device current); make that first call before any stream capture. A numeric
- * fault of a pair (|v| >= c, coincident particles) makes that target's E and B NaN. */
+ * address (with that device current) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not reset the device (cudaDeviceReset) between calls. The work runs
+ * on the current device: T, W, V, w, E and B must be allocations of that device, and cuda_stream a stream
+ * of it. A numeric fault of a pair (|v| >= c, coincident particles, a non-finite input) is not reported
+ * through the status: that target's E and B come out NaN and the call returns EMPPP_OK. */
 EMPPP_API emppp_status emppp_fields_noalloc(int64_t n, int32_t nslots, const double* T, const double* W,
                                             const double* V, const double* w, double* E, double* B,
                                             void* cuda_stream);
@@ -402,6 +433,30 @@ EMPPP_API emppp_status emppp_two_stage(emppp_handle h, const double* x0, const d
 
 /* Sets the network used by EMPPP_PROPOSAL_MLP (params host or device, EMPPP_MLP_NUM_PARAMS values). */
 EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, int32_t is_device_ptr);
+
+/* ---- diagnostics ------------------------------------------------------------------------------------
+ * Measured throughput of the plain ALU pipes that bound the pair kernels, at the clock the GPU runs at
+ * during the call: every SM runs independent dependent chains of FP32 FMAs, FP64 FMAs and FP32 reciprocal
+ * square roots (the multi-function unit); each rate is the operation count of one launch over its
+ * event-timed duration (best of three after a warm-up). These are the measured denominators of the
+ * benchmark's roofline fractions (no counterpart in the paper). Allocates and frees one scratch buffer
+ * of 8 bytes per thread of the probe grid; synchronous on cuda_stream (NULL: legacy default stream). */
+typedef struct {
+  double fp32_flops; /* FP32 FMA: 2 flop per FMA, per second */
+  double fp64_flops; /* FP64 FMA: 2 flop per FMA, per second */
+  double mufu_ops;   /* FP32 reciprocal square roots per second */
+  int32_t sms;       /* streaming multiprocessors of the device */
+  int32_t launches;  /* kernels launched by the call */
+} emppp_peaks;
+
+EMPPP_API emppp_status emppp_measure_peaks(emppp_peaks* out, void* cuda_stream);
+
+/* The FP64 pair kernel's reciprocal, y[k] = 1 / x[k] for n values (device pointers; synchronous on
+ * cuda_stream): the hardware's approximate reciprocal refined by two Newton-Raphson steps, which the
+ * kernel uses for 1 / (eta . v') and in the root of eq:dt. Exposed so that its error can be measured
+ * against the correctly rounded quotient (within 2 units in the last place for finite x > 0 with
+ * 2^-1022 < x < 2^1022; no counterpart in the paper). */
+EMPPP_API emppp_status emppp_reciprocal_probe(const double* x, double* y, int64_t n, void* cuda_stream);
 
 /* Text of the last failing call on this thread ("" if none). Valid until the next call. */
 EMPPP_API const char* emppp_last_error(void);

@@ -67,6 +67,9 @@ def _bind(lib):
     lib.orc_retarded_ex.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                     _d, ctypes.c_int, _d, _d, _i64]
     lib.orc_retarded_ex.restype = ctypes.c_int
+    lib.orc_bracket_table.argtypes = [ctypes.c_int64, _d, _d, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.POINTER(ctypes.c_int32)]
+    lib.orc_bracket_table.restype = ctypes.c_int
     lib.orc_self_fields.argtypes = [ctypes.c_int64, _d, _d, _d, ctypes.c_int64, ctypes.c_int64, _d, _i64,
                                     ctypes.c_int64, _d, _d, _d, _i64]
     lib.orc_self_fields.restype = ctypes.c_int
@@ -203,6 +206,18 @@ def retarded(T, W, V, n, D, j, r, lib=None, variant=0):
                 branch=int(info[0]), k1=int(info[1]), ntest=int(info[2]))
 
 
+def bracket_table(T, W, n, D, lib=None):
+    """Brackets of all ordered pairs at step n (Sec. 2.2 search): int32 [N, N] with 4 (k1 - k0) + branch
+    for j != i (k0 = max(0, n - D + 1)) and -1 on the diagonal."""
+    lib = lib or load()
+    T, W = _f64(T), _f64(W)
+    N = W.shape[1]
+    out = np.zeros((N, N), dtype=np.int32)
+    _check(lib.orc_bracket_table(N, _p(T), _p(W), int(n), int(D), out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "bracket_table")
+    return out
+
+
 def self_fields(T, W, V, n, D, weights=None, targets=None, lib=None, mags=False, variant=0):
     """Self fields on targets (all if None) at step n. Returns (E, B, stats), or (E, B, stats, M) with
     mags=True where M[:, 0] = sum_j |E_ij| and M[:, 1] = sum_j |B_ij| per target. variant = MIDPOINT
@@ -266,6 +281,19 @@ def energy_switch(T, E, eps, hold=1, lib=None):
     rate = np.zeros(T.shape[0])
     n = int(lib.orc_energy_switch(T.shape[0], _p(T), _p(E), float(eps), int(hold), _p(rate)))
     return n, rate
+
+
+def push(x, u, E, B, dt, bkind=0, bpar=None, lib=None):
+    """The push of Sec. 2.3 for the given particles with the given self fields (drift dt/2, background
+    field at the half-step position, Higuera-Cary kick, drift dt/2). Returns (x_new, u_new, B_total)."""
+    lib = lib or load()
+    x, u, E, B = (_f64(a).reshape(-1, 3).copy() for a in (x, u, E, B))
+    bpar = bext_params() if bpar is None else _f64(bpar, 7)
+    v = np.zeros_like(x)
+    Bt = np.zeros_like(x)
+    _check(lib.orc_push(x.shape[0], float(dt), _p(x), _p(u), _p(E), _p(B), int(bkind), _p(bpar), _p(v), _p(Bt)),
+           "push")
+    return x, u, Bt
 
 
 def velocity(u):

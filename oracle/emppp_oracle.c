@@ -358,6 +358,30 @@ int orc_retarded_ex(int64_t N, const double* T, const double* W, const double* V
   return st;
 }
 
+/* Bracket of every ordered pair at step n with depth D (the search of Sec. 2.2 alone): for target i at
+   (W[n][i], T[n]) and source j != i, out[i * N + j] = 4 (k1 - k0) + branch with k1 the older node of the
+   bracket and k0 = max(0, n - D + 1); out[i * N + i] = -1. */
+int orc_bracket_table(int64_t N, const double* T, const double* W, int64_t n, int64_t D, int32_t* out) {
+  if (N < 1 || n < 0 || D < 1) return ORC_ERR_ARG;
+  history h = {N, T, W, NULL};
+  int64_t k0 = n - D + 1 > 0 ? n - D + 1 : 0;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t i = 0; i < N; i++) {
+    const double* r = hist_w(&h, n, i);
+    for (int64_t j = 0; j < N; j++) {
+      if (j == i) {
+        out[i * N + j] = -1;
+        continue;
+      }
+      int64_t k1;
+      int nt;
+      int br = bracket(&h, j, r, T[n], k0, n, &k1, &nt);
+      out[i * N + j] = (int32_t)(4 * (k1 - k0) + br);
+    }
+  }
+  return ORC_OK;
+}
+
 /* the same with the method's own reconstruction */
 int orc_retarded(int64_t N, const double* T, const double* W, const double* V, int64_t n, int64_t D, int64_t j,
                  const double* r, double* out9, double* tr, int64_t* info) {

@@ -77,8 +77,10 @@ struct emppp_ctx {
   unsigned* ord_key = nullptr;
   int* order = nullptr;
   // resident blocks per SM of the pair kernels (queried on first use), per proposal
-  int blocks_fp64[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // [kernel variant][proposal]
-  int blocks_mixed[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  int blocks_fp64[3][3][kNumShapes] = {};  // [kernel variant][proposal][tile shape]
+  int blocks_mixed[2][3][kNumShapes] = {};
+  int shape = 0;          // tile shape of the fixed-step pair kernels (emppp_tuning)
+  bool dumping = false;   // the bracket dump runs the default shape
   // adaptive time step (Sec. 2.4): the rule, and whether the host mirror of t lags the device
   AdaptParams adapt{0, 0.05, 0.0, 1e-15, 1e-12};
   bool t_stale = false;
@@ -170,28 +172,41 @@ emppp_status update_schedule(emppp_handle c) {
   const int ad = c->adapt.on ? 1 : 0;
   // FP64 kernel variant: the method (0), with the adaptive step's reduction (1), eq:mid (2)
   const int var64 = c->opt.reconstruction == EMPPP_RECON_MIDPOINT ? 2 : ad;
+  // tile shape: the tuned one for the fixed-step kernels; the adaptive-step and eq:mid variants and the
+  // bracket dump run the default shape, and the FP64 path runs shape 3 as the default
+  int shp = (ad || var64 != 0 || c->dumping) ? 0 : c->shape;
+  if (!mixed && shp == 3) shp = 0;
+  const long long TB = shape_block(shp);  // targets per work item (and sources per staged tile)
   const long long key = (mixed ? 1 : 0) | ((long long)(c->opt.proposal & 3) << 1) |
                         ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13) |
-                        ((long long)ad << 40) | ((long long)var64 << 41);
+                        ((long long)ad << 40) | ((long long)var64 << 41) | ((long long)shp << 44);
   if (key == c->sched_key) return EMPPP_OK;
-  int& nb = mixed ? c->blocks_mixed[ad][c->opt.proposal % 3] : c->blocks_fp64[var64][c->opt.proposal % 3];
+  int& nb = mixed ? c->blocks_mixed[ad][c->opt.proposal % 3][shp] : c->blocks_fp64[var64][c->opt.proposal % 3][shp];
   if (nb <= 0)
-    nb = mixed ? max_blocks_pair_mixed(c->opt.proposal, ad) : max_blocks_pair_fp64(c->opt.proposal, var64);
+    nb = mixed ? max_blocks_pair_mixed(c->opt.proposal, ad, shp) : max_blocks_pair_fp64(c->opt.proposal, var64, shp);
   // The source chunking (and with it the order of every target's sum) follows the closed-form
   // variant's residency whatever the proposal, so that all proposals give identical fields; only the
   // number of persistent blocks follows the variant that runs.
-  int& nref = mixed ? c->blocks_mixed[ad][EMPPP_PROPOSAL_CLOSED_FORM] : c->blocks_fp64[ad][EMPPP_PROPOSAL_CLOSED_FORM];
+  int& nref = mixed ? c->blocks_mixed[ad][EMPPP_PROPOSAL_CLOSED_FORM][shp]
+                    : c->blocks_fp64[ad][EMPPP_PROPOSAL_CLOSED_FORM][shp];
   if (nref <= 0)
-    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM, ad)
-                 : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM, ad);
+    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM, ad, shp)
+                 : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM, ad, shp);
+  // resident blocks in units of 128 threads, so that the item count per SM does not depend on the shape
   const long long R = (long long)nb * c->num_sms;
-  const long long Rsched = (long long)nref * c->num_sms;
+  const long long Rsched = (long long)nref * c->num_sms * TB / 128;
+  const long long Rreal = (long long)nref * c->num_sms;  // resident blocks of the shape
   long long total_tiles = 0;
-  for (int b = 0; b < c->nbunch; b++) total_tiles += (c->hb[b].n + 127) / 128;
-  // chunking of one bunch: about items_per_block items per resident block over all bunches, in
-  // whole 128-source tiles of at least 256 sources (small == false); or, for a system too small to fill
-  // the resident blocks that way, one round of items with chunks of 4k sources (small == true), since
-  // then each block's time is its own chunk length
+  for (int b = 0; b < c->nbunch; b++) total_tiles += (c->hb[b].n + TB - 1) / TB;
+  const long long tiles128 = [&] {
+    long long t = 0;
+    for (int b = 0; b < c->nbunch; b++) t += (c->hb[b].n + 127) / 128;
+    return t;
+  }();
+  // chunking of one bunch: about items_per_block items per resident block over all bunches (counted in
+  // 128-target tiles), in whole tiles of TB sources and at least 256 sources (small == false); or, for a
+  // system too small to fill the resident blocks that way, one round of items with chunks of 4k sources
+  // (small == true), since then each block's time is its own chunk length
   auto chunks = [&](long long n, bool small) -> long long {
     long long nchunk;
     if (c->opt.source_split > 0) {
@@ -199,31 +214,31 @@ emppp_status update_schedule(emppp_handle c) {
     } else if (!small) {
       // the FP64 path gathers both rings, so its chunks are cut 4x shorter to keep a chunk's window in L2
       const long long ipb = mixed ? 2LL * c->items_per_block : 4LL * c->items_per_block;
-      nchunk = (ipb * Rsched + total_tiles - 1) / total_tiles;
+      nchunk = (ipb * Rsched + tiles128 - 1) / tiles128;
       const long long by_size = (n + 255) / 256;
       if (nchunk > by_size) nchunk = by_size;
     } else {
-      nchunk = Rsched / total_tiles > 1 ? Rsched / total_tiles : 1;
+      nchunk = Rreal / total_tiles > 1 ? Rreal / total_tiles : 1;
       const long long by_size = (n + kMinChunk - 1) / kMinChunk;
       if (nchunk > by_size) nchunk = by_size;
     }
     if (nchunk > c->ds.max_split) nchunk = c->ds.max_split;
     if (nchunk < 1) nchunk = 1;
     long long chunk = (n + nchunk - 1) / nchunk;
-    return chunk >= 128 ? (chunk + 127) / 128 * 128 : (chunk + kMinChunk - 1) / kMinChunk * kMinChunk;
+    return chunk >= TB ? (chunk + TB - 1) / TB * TB : (chunk + kMinChunk - 1) / kMinChunk * kMinChunk;
   };
   long long items_large = 0;
   for (int b = 0; b < c->nbunch; b++) {
     const long long n = c->hb[b].n;
     const long long chunk = chunks(n, false);
-    items_large += ((n + 127) / 128) * ((n + chunk - 1) / chunk);
+    items_large += ((n + TB - 1) / TB) * ((n + chunk - 1) / chunk);
   }
-  const bool small = items_large < Rsched;
+  const bool small = items_large < Rreal;
   int item = 0;
   for (int b = 0; b < c->nbunch; b++) {
     BunchSched& s = c->hs[b];
     const long long n = c->hb[b].n;
-    s.ntb = (int)((n + 127) / 128);
+    s.ntb = (int)((n + TB - 1) / TB);
     const long long chunk = chunks(n, small);
     s.chunk = (int)chunk;
     s.nchunk = (int)((n + chunk - 1) / chunk);
@@ -232,6 +247,7 @@ emppp_status update_schedule(emppp_handle c) {
   }
   c->launch.nitems = item;
   c->launch.grid = (int)(R < item ? R : item);
+  c->launch.shape = shp;
   CU(cudaMemcpyAsync(c->d_sched, c->hs.data(), sizeof(BunchSched) * c->nbunch, cudaMemcpyHostToDevice, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   c->sched_key = key;
@@ -258,7 +274,6 @@ emppp_status read_err(emppp_handle h) {
   int herr = 0;
   CU(cudaMemcpyAsync(&herr, h->ds.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
-  if (herr & kErrTimeout) return fail(EMPPP_ERR_TIMEOUT, "a bounded device wait gave up (bits 0x%x)", herr);
   if (herr) {
     return fail(EMPPP_ERR_NUMERIC,
                 "device numeric fault (bits 0x%x: 1 = negative discriminant or |v| >= c, 2 = coincident pair, "
@@ -964,19 +979,29 @@ EMPPP_API emppp_status emppp_reset_stats(emppp_handle h) {
 
 // one evaluation of the self fields of the present state: slot tables, target order, pair kernel,
 // reduction (no push: the state does not change)
-emppp_status enqueue_fields(emppp_handle h) {
+emppp_status enqueue_fields(emppp_handle h, int* dump = nullptr) {
   CU(launch_setup(h->ds, h->opt.precision == EMPPP_MIXED, h->stream));
   const bool ordered = h->target_order != 0;
   if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
   if (h->opt.precision == EMPPP_MIXED) {
-    CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
+    CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream,
+                         dump));
   } else {
     CU(launch_pair_fp64(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->opt.reconstruction, h->adapt,
-                        h->launch, h->stream));
+                        h->launch, h->stream, dump));
   }
   if (any_chunked(h)) CU(launch_reduce_partials(h->ds, h->stream));
   h->launches += 2 + (ordered ? 1 : 0) + (any_chunked(h) ? 1 : 0);
   return EMPPP_OK;
+}
+
+// tile shape of (targets per block, sources per partial sum), -1 if it is none
+static int shape_of(int targets_per_block, int sources_per_sum) {
+  const int tb = targets_per_block == 0 ? 128 : targets_per_block;
+  const int ss = sources_per_sum == 0 ? 8 : sources_per_sum;
+  for (int k = 0; k < kNumShapes; k++)
+    if (shape_block(k) == tb && shape_sub(k) == ss) return k;
+  return -1;
 }
 
 EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* report) {
@@ -988,47 +1013,59 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
     return fail(EMPPP_ERR_STATE, "the MLP proposal needs a network: call emppp_set_proposal first");
   if ((st = read_err(h)) != EMPPP_OK) return st;
   const int ipb[5] = {4, 8, 16, 32, 64};
-  const int norders = 2;
   emppp_tuning_report rep;
   memset(&rep, 0, sizeof(rep));
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
   double best_ms = 1e300;
-  for (int o = 0; o < norders; o++) {
-    for (int k = 0; k < 5; k++) {
-      h->items_per_block = ipb[k];
-      h->target_order = 1 - o;
-      if ((st = update_schedule(h)) != EMPPP_OK) break;
-      if ((st = enqueue_fields(h)) != EMPPP_OK) break;  // warm-up
-      float best = 3.4e38f;
-      for (int rpt = 0; rpt < 2 && st == EMPPP_OK; rpt++) {
-        cudaEventRecord(e0, h->stream);
-        st = enqueue_fields(h);
-        cudaEventRecord(e1, h->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) best = ms;
-      }
-      if (st != EMPPP_OK) break;
-      emppp_tuning& c = rep.cand[rep.ncand];
-      c.items_per_block = ipb[k];
-      c.target_order = 1 - o;
-      c.ms = best;
-      if (best < best_ms) {
-        best_ms = best;
-        rep.best = rep.ncand;
-      }
-      rep.ncand++;
+  // one candidate: warm-up, then the best of two timed evaluations
+  auto time_candidate = [&](int items, int order, int shape) -> emppp_status {
+    h->items_per_block = items;
+    h->target_order = order;
+    h->shape = shape;
+    emppp_status s2 = update_schedule(h);
+    if (s2 == EMPPP_OK) s2 = enqueue_fields(h);
+    float best = 3.4e38f;
+    for (int rpt = 0; rpt < 2 && s2 == EMPPP_OK; rpt++) {
+      cudaEventRecord(e0, h->stream);
+      s2 = enqueue_fields(h);
+      cudaEventRecord(e1, h->stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) best = ms;
     }
-    if (st != EMPPP_OK) break;
+    if (s2 != EMPPP_OK) return s2;
+    emppp_tuning& c = rep.cand[rep.ncand];
+    c.items_per_block = items;
+    c.target_order = order;
+    c.targets_per_block = shape_block(shape);
+    c.sources_per_sum = shape_sub(shape);
+    c.ms = best;
+    if (best < best_ms) {
+      best_ms = best;
+      rep.best = rep.ncand;
+    }
+    rep.ncand++;
+    return EMPPP_OK;
+  };
+  // work split and target order at the default shape
+  for (int o = 0; o < 2 && st == EMPPP_OK; o++)
+    for (int k = 0; k < 5 && st == EMPPP_OK; k++) st = time_candidate(ipb[k], 1 - o, 0);
+  // the other tile shapes with the fastest split and order (the adaptive step runs the default shape)
+  if (st == EMPPP_OK && !h->adapt.on) {
+    const int items = rep.cand[rep.best].items_per_block, order = rep.cand[rep.best].target_order;
+    const int nshapes = h->opt.precision == EMPPP_MIXED ? kNumShapes : 3;
+    for (int shp = 1; shp < nshapes && st == EMPPP_OK; shp++) st = time_candidate(items, order, shp);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != EMPPP_OK) return st;
-  h->items_per_block = rep.cand[rep.best].items_per_block;
-  h->target_order = rep.cand[rep.best].target_order;
+  const emppp_tuning& b = rep.cand[rep.best];
+  h->items_per_block = b.items_per_block;
+  h->target_order = b.target_order;
+  h->shape = shape_of(b.targets_per_block, b.sources_per_sum);
   invalidate_graph(h);
   if ((st = update_schedule(h)) != EMPPP_OK) return st;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
@@ -1038,14 +1075,50 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
   return EMPPP_OK;
 }
 
+EMPPP_API emppp_status emppp_bracket_dump(emppp_handle h, int32_t* brackets, int64_t* k0) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (!brackets) return fail(EMPPP_ERR_ARG, "brackets is NULL");
+  if (h->N > 65536) return fail(EMPPP_ERR_ARG, "the bracket dump is for systems of at most 65536 particles");
+  if (!h->has_state) return fail(EMPPP_ERR_STATE, "no state: call emppp_set_particles first");
+  if (!h->opt.pair_fields) return fail(EMPPP_ERR_STATE, "pair fields are off: there are no brackets");
+  if (h->opt.field_point != EMPPP_FIELD_PRESENT)
+    return fail(EMPPP_ERR_STATE, "the bracket dump evaluates the present field point only");
+  if (h->opt.proposal == EMPPP_PROPOSAL_MLP && !h->has_mlp)
+    return fail(EMPPP_ERR_STATE, "the MLP proposal needs a network: call emppp_set_proposal first");
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  h->dumping = true;  // the dump instances run the default tile shape
+  st = update_schedule(h);
+  if (st == EMPPP_OK) {
+    cudaError_t e = cudaMemsetAsync(brackets, 0xff, sizeof(int32_t) * (size_t)h->N * (size_t)h->N, h->stream);
+    st = e == cudaSuccess ? enqueue_fields(h, brackets) : fail(EMPPP_ERR_CUDA, "memset: %s", cudaGetErrorString(e));
+  }
+  h->dumping = false;
+  if (st != EMPPP_OK) return st;
+  CU(cudaStreamSynchronize(h->stream));
+  if ((st = read_err(h)) != EMPPP_OK) return st;
+  if ((st = reset_counters(h)) != EMPPP_OK) return st;
+  if (k0) {
+    StepState ss;
+    CU(cudaMemcpy(&ss, h->ds.state, sizeof(StepState), cudaMemcpyDeviceToHost));
+    *k0 = ss.k0;
+  }
+  return EMPPP_OK;
+}
+
 EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning) {
   emppp_status st = check_handle(h);
   if (st != EMPPP_OK) return st;
   if (!tuning || tuning->items_per_block < 1 || tuning->items_per_block > 256 ||
       (tuning->target_order != 0 && tuning->target_order != 1))
     return fail(EMPPP_ERR_ARG, "items_per_block must be in 1..256 and target_order 0 or 1");
+  const int shp = shape_of(tuning->targets_per_block, tuning->sources_per_sum);
+  if (shp < 0)
+    return fail(EMPPP_ERR_ARG, "tile shape (%d targets per block, %d sources per sum) is not one of (128, 8), "
+                "(64, 8), (256, 8), (128, 16)", tuning->targets_per_block, tuning->sources_per_sum);
   h->items_per_block = tuning->items_per_block;
   h->target_order = tuning->target_order;
+  h->shape = shp;
   invalidate_graph(h);
   return update_schedule(h);
 }

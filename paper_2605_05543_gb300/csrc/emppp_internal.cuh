@@ -44,7 +44,6 @@ enum : int {
   kErrDisc = 1,      // negative discriminant or C2 <= 0 in eq:dt (|v| >= c)
   kErrCoincide = 2,  // eta = 0 or eta . v' <= 0
   kErrNonFinite = 4, // non-finite field or state
-  kErrTimeout = 8,   // a bounded wait gave up
 };
 
 struct StepState {
@@ -87,7 +86,8 @@ struct BunchDesc {
   double beta_ref[3];  // reference velocity / c of the FP32 velocities
 };
 
-// Work split of the persistent pair kernels, per bunch: items are (source chunk, target tile of 128)
+// Work split of the persistent pair kernels, per bunch: items are (source chunk, target tile of the
+// tile shape's targets per block)
 // pairs taken chunk-major from an atomic counter by resident blocks; per-chunk partial sums are
 // reduced in a fixed order afterwards (nchunk > 1).
 struct BunchSched {
@@ -180,10 +180,18 @@ struct BextParams {
   double center[3];
 };
 
+// Tile shapes of the pair kernels (emppp_tuning): targets per block, which is also the number of sources
+// a mixed-path block stages per tile, and the mixed path's sources per FP32 partial sum. Shape 0 is the
+// default; the FP64 path runs shape 3 as shape 0 (its sums are blocked by 64 sources).
+constexpr int kNumShapes = 4;
+__host__ __device__ constexpr int shape_block(int shape) { return shape == 1 ? 64 : (shape == 2 ? 256 : 128); }
+__host__ __device__ constexpr int shape_sub(int shape) { return shape == 3 ? 16 : 8; }
+
 // launch configuration of a persistent pair kernel
 struct PairLaunch {
   int nitems;  // work items of all bunches
   int grid;    // blocks launched
+  int shape;   // tile shape (shape_block(shape) threads per block, targets per work item)
 };
 
 // item -> (bunch, chunk, target tile): bunches are searched by their first item
@@ -218,9 +226,11 @@ cudaError_t launch_gather_positions(const DeviceState& s, double* x, cudaStream_
 // pair_fp64.cu
 // kernel variant of the FP64 pair path: 0 the method, 1 with the adaptive time step's reduction, 2 the
 // midpoint reconstruction eq:mid
-int max_blocks_pair_fp64(int proposal, int variant);
+int max_blocks_pair_fp64(int proposal, int variant, int shape);
+// dump (nullptr in the step): [N][N] device array that receives the bracket of every evaluated pair,
+// 4 (k1 - k0) + branch (emppp_bracket_dump)
 cudaError_t launch_pair_fp64(const DeviceState& s, const int* order, int proposal, int reconstruction,
-                             const AdaptParams& ap, const PairLaunch& pl, cudaStream_t st);
+                             const AdaptParams& ap, const PairLaunch& pl, cudaStream_t st, int* dump = nullptr);
 cudaError_t launch_reduce_partials(const DeviceState& s, cudaStream_t st);
 cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st);
 // push.cu
@@ -249,8 +259,8 @@ cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float
 cudaError_t launch_energy(const DeviceState& s, const EnergyParams& ep, EnergyMon* mon, bool reset, cudaStream_t st);
 constexpr int kEnergyThreads = 256;  // block size of the energy monitor (and of the post-pair launch)
 // pair_mixed.cu
-int max_blocks_pair_mixed(int proposal, bool adapt);
+int max_blocks_pair_mixed(int proposal, bool adapt, int shape);
 cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const AdaptParams& ap,
-                              const PairLaunch& pl, cudaStream_t st);
+                              const PairLaunch& pl, cudaStream_t st, int* dump = nullptr);
 
 }  // namespace emppp

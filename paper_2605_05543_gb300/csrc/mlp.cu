@@ -3,7 +3,8 @@
 //   sample_kernel  for given (target, source) pairs at the present state: the 10 features (mlp.cuh)
 //                  and the exact retarded delay t - t_r from the FP64 bracket of Sec. 2.2 (the paper's
 //                  search) and the smaller root of eq:dt; the training target is
-//                  z = log(c (t - t_r) / |d|).
+//                  z = log((t - t_r) / tau_u), tau_u the delay of the source's uniform motion from its
+//                  present record.
 //   train_kernel   one pass over a batch: forward on the tensor cores (BF16 operands, FP32 accumulate),
 //                  the mean squared error of z, the input gradients of layer 2 on the tensor cores
 //                  (dA1 = dH2 W2^T), the weight gradients reduced in FP32 per warp and summed into a
@@ -161,8 +162,14 @@ __global__ void sample_kernel(DeviceState s, const int* __restrict__ pairs, long
            (float)D, f);
   for (int k = 0; k < kIn; k++) feat[q * kIn + k] = f[k];
   delay[q] = tau;
-  const double dn = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
-  zt[q] = (float)log(kC * tau / dn);
+  // uniform-motion delay from the present record: c tau_u = [d.beta + sqrt((d.beta)^2 + (1 - beta^2) |d|^2)] /
+  // (1 - beta^2), d = r - w_n, formed as |d|^2 / (sqrt(...) - d.beta) when d.beta < 0 (no cancellation)
+  const double b0 = wn[3] * ic, b1 = wn[4] * ic, b2 = wn[5] * ic;
+  const double ig2 = 1.0 - (b0 * b0 + b1 * b1 + b2 * b2);
+  const double db = e0 * b0 + e1 * b1 + e2 * b2, dd = e0 * e0 + e1 * e1 + e2 * e2;
+  const double sq = sqrt(db * db + ig2 * dd);
+  const double ctau_u = db >= 0.0 ? (db + sq) / ig2 : dd / (sq - db);
+  zt[q] = (float)log(kC * tau / ctau_u);
 }
 
 // ---------------------------------------------------------------------------------------------

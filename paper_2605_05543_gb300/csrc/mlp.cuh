@@ -1,8 +1,12 @@
 // Learned retarded-time proposal: a 10-64-64-1 perceptron with SiLU activations that predicts, for a
-// target and a source, z = log(c (t - t_r) / |d|) with d = r - w_n the present separation. The
-// retarded-time search then starts from the slot the predicted delay points at and finishes with the
-// same guarded search as the closed-form proposal, so the bracket (and every field) is the one of the
-// paper's search whatever the network predicts.
+// target and a source, the correction z = log(tau / tau_u) of the delay tau = t - t_r over the delay
+// tau_u that the source's uniform motion from its present record gives (the closed-form guess; the
+// network learns what the source's acceleration history does to it). The pair kernels evaluate the
+// network once per (warp, source), at the mean position of the warp's targets (a warp's targets lie close
+// together in the spatial target order), and every lane scales its own uniform-motion delay by e^z; the
+// retarded-time search then starts from the slot that delay points at and finishes with the same guarded
+// search as the closed-form proposal, so the bracket (and every field) is the one of the paper's search
+// whatever the network predicts.
 //
 // Tensor-core arithmetic: mma.sync m16n8k16 with BF16 operands and FP32 accumulation, one warp per 16
 // (or 32) rows. Hidden layers are chained from the accumulator layout of one GEMM to the operand
@@ -255,6 +259,41 @@ __device__ __forceinline__ float infer_warp(const InferImage& net, const float f
   const float v00 = __shfl_sync(0xffffffffu, zo[0][0], src), v01 = __shfl_sync(0xffffffffu, zo[0][2], src);
   const float v10 = __shfl_sync(0xffffffffu, zo[1][0], src), v11 = __shfl_sync(0xffffffffu, zo[1][2], src);
   return m == 0 ? (local < 8 ? v00 : v01) : (local < 8 ? v10 : v11);
+}
+
+// Mean of (x0, x1, x2) over the active lanes of the warp (the origin if none is active). Every lane of
+// the warp must call it.
+__device__ __forceinline__ float3 warp_mean(bool active, float x0, float x1, float x2) {
+  float s0 = active ? x0 : 0.f, s1 = active ? x1 : 0.f, s2 = active ? x2 : 0.f;
+  float cnt = active ? 1.f : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  const float ic = cnt > 0.f ? 1.f / cnt : 0.f;
+  return make_float3(s0 * ic, s1 * ic, s2 * ic);
+}
+
+// Delay factor e^z of one source per lane (the warp evaluates up to 32 sources at once): d = r_c - w_n
+// from the warp's mean target position r_c to the source's present position, beta_n and
+// beta_n - beta_{n-1} of the source. Lanes without a source (valid false) take part in the tensor-core
+// pass with zero features and return 1. z is clamped to [-20, 20] (a factor the search absorbs anyway).
+// Every lane of the warp must call it (converged).
+__device__ __forceinline__ float warp_delay_factor(const InferImage& net, bool valid, float d0, float d1, float d2,
+                                                   float b0, float b1, float b2, float db0, float db1, float db2,
+                                                   float invL, float Df, uint32_t (*stage)[8]) {
+  float f[kIn];
+  if (valid) {
+    features(d0, d1, d2, b0, b1, b2, db0, db1, db2, invL, Df, f);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kIn; k++) f[k] = 0.f;
+  }
+  const float z = infer_warp(net, f, stage);
+  return valid ? __expf(fminf(fmaxf(z, -20.f), 20.f)) : 1.f;
 }
 
 }  // namespace mlp

@@ -15,7 +15,12 @@
 // overwrites every scratch word it reads before reading it, so nothing is left to clear between
 // calls. The device address of g_scratch is looked up with cudaGetSymbolAddress the first time the
 // entry point runs on a device (with that device current); that first call should come before any
-// stream capture on the device.
+// stream capture on the device. The looked-up address is kept for the life of the process, so the
+// entry point does not support cudaDeviceReset (or any other replacement of the device's primary
+// context) between its calls.
+//
+// A numeric fault of a pair (|v| >= c in the history, coincident particles, non-finite input) is not
+// reported through a status: the affected target's E and B come out NaN and the call returns EMPPP_OK.
 //
 // The evaluation is the FP64 path with the paper's own search (out-of-history test, near-field
 // shortcut, bisection), reading the caller's history in the slot-major layout of emppp_set_history.
@@ -87,7 +92,9 @@ __global__ void __launch_bounds__(kBlock)
     const double* vj = V + (size_t)j * 3;
     int k1;
     bool ooh = false;
-    if (na_node_test(r0, r1, r2, wj, lhs[0])) {
+    // with a single slot (kn = 0) every pair is out of history; otherwise a test that is false at slot 0
+    // (including a NaN separation) leads to slots kn - 1 >= 0 and, by bisection, 1..kn - 1 only
+    if (kn == 0 || na_node_test(r0, r1, r2, wj, lhs[0])) {
       k1 = 0;
       ooh = true;
     } else if (!na_node_test(r0, r1, r2, wj + (size_t)(kn - 1) * sstride, lhs[kn - 1])) {

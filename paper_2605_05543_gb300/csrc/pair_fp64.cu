@@ -23,6 +23,7 @@
 // take the same branch; which thread evaluates a target does not change its result.
 // The arithmetic is FP64-pipe bound (GB300: 2 DFMA/clk/SM); everything that is not an FP64 result
 // (the guess, the node tests outside the guard band, indices, loads) runs on the FP32/INT pipes beside it.
+#include "../../include/emppp.h"
 #include "emppp_internal.cuh"
 #include "mlp.cuh"
 #include "shadow.cuh"
@@ -31,7 +32,6 @@ namespace emppp {
 
 namespace {
 
-constexpr int kBlock = 128;
 constexpr int kSumBlock = 64;
 constexpr double kCoulomb = 1.0 / (4.0 * kPi * kEps0);
 
@@ -74,6 +74,7 @@ struct PairArgs {
   unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
   double eta_allow;
   const int* __restrict__ order;  // spatial order of the targets (nullptr: index order)
+  int* __restrict__ dump;  // [N][N] bracket of every evaluated pair, 4 (k1 - k0) + branch (DUMP instances only)
 };
 
 // node test P(k) with the reference operation order (no contraction)
@@ -97,12 +98,14 @@ struct Window {
 
 }  // namespace
 
-template <int PROP, bool ADAPT, bool MID>
-__global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
+// SHAPE: targets per block (kBlock = shape_block(SHAPE); shape 3 runs as shape 0)
+template <int PROP, bool ADAPT, bool MID, bool DUMP, int SHAPE>
+__global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs a) {
+  constexpr int kBlock = shape_block(SHAPE);
   __shared__ int s_item;
-  __shared__ mlp::InferImage s_net[1];
+  // staging buffer of the learned proposal's network (its weights are read from global memory: it runs
+  // once per 32 sources per warp)
   __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
-  if (PROP == kPropMlp) mlp::load_image(s_net[0], a.net);
   const long long N = a.N;
   const int D = a.D;
 
@@ -147,6 +150,10 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
   const float rh0 = tq[0], rh1 = tq[1], rh2 = tq[2];
   const float rl0 = tq[4], rl1 = tq[5], rl2 = tq[6];
   const bool far_target = fmaxf(fabsf(rh0), fmaxf(fabsf(rh1), fabsf(rh2))) > 0.5f;
+  // learned proposal: the mean position of the warp's targets, where the network is evaluated
+  float3 rc = make_float3(0.f, 0.f, 0.f);
+  if (PROP == kPropMlp) rc = mlp::warp_mean(active, rh0, rh1, rh2);
+  float fac_lane = 1.f;  // delay factor of source j0 + lane of the current group of 32
 
   const long long j_begin = bd.off + (long long)chunk_id * bs.chunk;
   const long long j_end = min(bd.off + bd.n, j_begin + bs.chunk);
@@ -157,22 +164,26 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
 
   const double c2 = kC * kC;
   for (long long j = j_begin; (PROP == kPropMlp || active) && j < j_end; ++j) {
-    long long kg_mlp = 0;
+    float fac = 1.f;
     if (PROP == kPropMlp) {
-      // every lane of the warp takes part in the tensor-core evaluation, then idle lanes skip the pair
-      const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
-      const float4 q0n = __ldg(qn), q2n = __ldg(qn + 2);
-      const float4 q2p = __ldg(reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pprev) * 12) + 2);
-      const float x0 = rh0 - q0n.x, x1 = rh1 - q0n.y, x2 = rh2 - q0n.z;
-      float f[mlp::kIn];
-      mlp::features(x0, x1, x2, bref.x + q2n.x, bref.y + q2n.y, bref.z + q2n.z, q2n.x - q2p.x, q2n.y - q2p.y,
-                    q2n.z - q2p.z, invL, (float)D, f);
-      const float z = mlp::infer_warp(s_net[0], f, s_stage[threadIdx.x >> 5]);
-      const float steps = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 1e9f);
-      long long k = win.n - 1 - (long long)steps;
-      kg_mlp = k < win.k0 ? win.k0 : (k > win.n - 1 ? win.n - 1 : k);
+      // every 32 sources, the warp evaluates the network for the next 32 (one per lane) at its mean target
+      // position; each pair then scales its uniform-motion delay by its source's factor
+      const int l = (int)((j - j_begin) & 31);
+      if (l == 0) {
+        __syncwarp();
+        const long long js = j + (threadIdx.x & 31);
+        const bool v = js < j_end;
+        const long long jr = v ? js : j;
+        const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)jr * D + pn) * 12);
+        const float4 q0n = __ldg(qn), q2n = __ldg(qn + 2);
+        const float4 q2p = __ldg(reinterpret_cast<const float4*>(a.rec32 + ((size_t)jr * D + pprev) * 12) + 2);
+        fac_lane = mlp::warp_delay_factor(*a.net, v, rc.x - q0n.x, rc.y - q0n.y, rc.z - q0n.z, bref.x + q2n.x,
+                                          bref.y + q2n.y, bref.z + q2n.z, q2n.x - q2p.x, q2n.y - q2p.y,
+                                          q2n.z - q2p.z, invL, (float)D, s_stage[threadIdx.x >> 5]);
+      }
+      fac = __shfl_sync(0xffffffffu, fac_lane, l);
     }
-    if (!active) continue;  // and stay in the loop for the next source's evaluation
+    if (!active) continue;  // and stay in the loop for the next group's evaluation
     if (j == i) continue;
     const double* src = a.rec64 + (size_t)j * D * 6;
     const float4* src32 = reinterpret_cast<const float4*>(a.rec32 + (size_t)j * D * 12);
@@ -225,13 +236,10 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
         br = 0;
         n_tests += 1;
       } else {
-        long long kg;
-        if (PROP == kPropMlp) {
-          kg = kg_mlp;
-        } else {
-          const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
-          kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), bref, inv_cdt, win.k0, win.n);
-        }
+        // the uniform-motion delay (scaled by the network's factor with the learned proposal)
+        const float4* qn = reinterpret_cast<const float4*>(a.rec32 + ((size_t)j * D + pn) * 12);
+        const long long kg = uniform_motion_guess(rh0, rh1, rh2, __ldg(qn), __ldg(qn + 2), bref,
+                                                  PROP == kPropMlp ? inv_cdt * fac : inv_cdt, win.k0, win.n);
         long long lo, hi;
         bool ooh = false;
         n_tests += 1;
@@ -292,6 +300,7 @@ __global__ void __launch_bounds__(kBlock) pair_fp64_kernel(PairArgs a) {
       n_sc++;
     else
       n_bi++;
+    if (DUMP) a.dump[(size_t)i * N + j] = 4 * (int)(k1 - win.k0) + br;
 
     // ---- 2. reconstruction (eq:dt, eq:linear; eq:mid in the MID variant) ----------------------
     const int p1 = win.phys(k1);
@@ -510,35 +519,41 @@ __global__ void zero_kernel(double* __restrict__ a, double* __restrict__ b, long
   }
 }
 
-template <bool ADAPT, bool MID>
+template <bool ADAPT, bool MID, int SHAPE>
 int max_blocks_fp64(int proposal) {
   int nb = 0;
+  constexpr int B = shape_block(SHAPE);
   if (proposal == kPropClosedForm)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm, ADAPT, MID>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropClosedForm, ADAPT, MID, false, SHAPE>, B, 0);
   else if (proposal == kPropMlp)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp, ADAPT, MID>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropMlp, ADAPT, MID, false, SHAPE>, B, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect, ADAPT, MID>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_fp64_kernel<kPropBisect, ADAPT, MID, false, SHAPE>, B, 0);
   return nb > 0 ? nb : 1;
 }
 
-int max_blocks_pair_fp64(int proposal, int variant) {
-  if (variant == 2) return max_blocks_fp64<false, true>(proposal);
-  return variant == 1 ? max_blocks_fp64<true, false>(proposal) : max_blocks_fp64<false, false>(proposal);
+// the adaptive-step and eq:mid instances and the bracket dump run the default shape only
+int max_blocks_pair_fp64(int proposal, int variant, int shape) {
+  if (variant == 2) return max_blocks_fp64<false, true, 0>(proposal);
+  if (variant == 1) return max_blocks_fp64<true, false, 0>(proposal);
+  if (shape == 1) return max_blocks_fp64<false, false, 1>(proposal);
+  if (shape == 2) return max_blocks_fp64<false, false, 2>(proposal);
+  return max_blocks_fp64<false, false, 0>(proposal);
 }
 
-template <bool ADAPT, bool MID>
+template <bool ADAPT, bool MID, bool DUMP, int SHAPE>
 void launch_fp64(int proposal, const PairLaunch& pl, const PairArgs& a, cudaStream_t st) {
+  constexpr int B = shape_block(SHAPE);
   if (proposal == kPropClosedForm)
-    pair_fp64_kernel<kPropClosedForm, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropClosedForm, ADAPT, MID, DUMP, SHAPE><<<pl.grid, B, 0, st>>>(a);
   else if (proposal == kPropMlp)
-    pair_fp64_kernel<kPropMlp, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropMlp, ADAPT, MID, DUMP, SHAPE><<<pl.grid, B, 0, st>>>(a);
   else
-    pair_fp64_kernel<kPropBisect, ADAPT, MID><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_fp64_kernel<kPropBisect, ADAPT, MID, DUMP, SHAPE><<<pl.grid, B, 0, st>>>(a);
 }
 
 cudaError_t launch_pair_fp64(const DeviceState& s, const int* order, int proposal, int reconstruction,
-                             const AdaptParams& ap, const PairLaunch& pl, cudaStream_t st) {
+                             const AdaptParams& ap, const PairLaunch& pl, cudaStream_t st, int* dump) {
   PairArgs a;
   a.rec64 = s.rec64;
   a.rec32 = s.rec32;
@@ -564,14 +579,22 @@ cudaError_t launch_pair_fp64(const DeviceState& s, const int* order, int proposa
   a.scale = s.scale;
   a.eta_allow = ap.eta_allow;
   a.order = order;
+  a.dump = dump;
   // the work counter is zeroed by the set-up launch that precedes every pair launch
-  // the midpoint reconstruction runs with a fixed time step only (the host refuses the combination)
-  if (reconstruction == 1)
-    launch_fp64<false, true>(proposal, pl, a, st);
+  // the midpoint reconstruction runs with a fixed time step only (the host refuses the combination);
+  // the bracket dump runs the method's instance (the brackets depend on neither variant)
+  if (dump)
+    launch_fp64<false, false, true, 0>(proposal, pl, a, st);
+  else if (reconstruction == 1)
+    launch_fp64<false, true, false, 0>(proposal, pl, a, st);
   else if (ap.on)
-    launch_fp64<true, false>(proposal, pl, a, st);
+    launch_fp64<true, false, false, 0>(proposal, pl, a, st);
+  else if (pl.shape == 1)
+    launch_fp64<false, false, false, 1>(proposal, pl, a, st);
+  else if (pl.shape == 2)
+    launch_fp64<false, false, false, 2>(proposal, pl, a, st);
   else
-    launch_fp64<false, false>(proposal, pl, a, st);
+    launch_fp64<false, false, false, 0>(proposal, pl, a, st);
   return cudaGetLastError();
 }
 
@@ -586,4 +609,30 @@ cudaError_t launch_zero_self(const DeviceState& s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+__global__ void recip_probe_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) y[k] = recip_newton(x[k]);
+}
+}  // namespace
+
+void set_error_text(const char* msg);
+
 }  // namespace emppp
+
+extern "C" EMPPP_API emppp_status emppp_reciprocal_probe(const double* x, double* y, int64_t n, void* cuda_stream) {
+  if (n < 0 || (n > 0 && (!x || !y))) {
+    emppp::set_error_text("emppp_reciprocal_probe: n >= 0 and device arrays x, y are required");
+    return EMPPP_ERR_ARG;
+  }
+  if (n == 0) return EMPPP_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  emppp::recip_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, y, (long long)n);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    emppp::set_error_text(cudaGetErrorString(e));
+    return EMPPP_ERR_CUDA;
+  }
+  return EMPPP_OK;
+}

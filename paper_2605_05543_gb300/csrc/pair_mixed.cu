@@ -40,9 +40,6 @@ namespace {
 #define EMPPP_MIXED_MIN_BLOCKS 8  // resident blocks per SM the register budget is fitted to (64 registers)
 #endif
 
-constexpr int kBlock = 128;
-constexpr int kTile = 128;
-constexpr int kSub = 8;  // sources per FP32 partial sum
 // FP64 recomputation of C0 when u L1^2 |s| / (C0 (L1 - s)) exceeds 2e-6: kC0Guard = 2e-6 / u
 constexpr float kC0Guard = 2.0e-6f / 5.9604644775390625e-08f;
 // FP64 recomputation of X.beta (out-of-history pairs) when 2 u |X| |X.beta| / denominator exceeds 1.3e-6
@@ -73,6 +70,7 @@ struct MixedArgs {
   unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
   float eta_allow;
   const float4* __restrict__ ext32;  // [N][3] per source: segment end hi/lo, out-of-history line offset
+  int* __restrict__ dump;  // [N][N] bracket of every evaluated pair, 4 (k1 - k0) + branch (DUMP instances only)
 };
 
 struct Target {
@@ -175,18 +173,25 @@ __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict_
 
 }  // namespace
 
-template <int PROP, bool ADAPT>
-__global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN_BLOCKS) pair_mixed_kernel(MixedArgs a) {
+// SHAPE: targets per block = sources per staged tile (kBlock), sources per FP32 partial sum (kSub); the
+// register budget stays at 64 per thread for every block size
+template <int PROP, bool ADAPT, bool DUMP, int SHAPE>
+__global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 128 / shape_block(SHAPE))
+    pair_mixed_kernel(MixedArgs a) {
+  constexpr int kBlock = shape_block(SHAPE);
+  constexpr int kTile = kBlock;
+  constexpr int kSub = shape_sub(SHAPE);
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
   __shared__ float4 s_q1[kTile];  // present record (lo, 0) of the tile's sources
   __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position (ext32)
   __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
-  __shared__ float4 s_db[PROP == kPropMlp ? kTile : 1];  // beta_n - beta_{n-1} of the tile's sources
-  __shared__ mlp::InferImage s_net[1];
+  // learned proposal: the network's staging buffer per warp, which afterwards holds the delay factor e^z of
+  // each of the tile's sources (the network's weights are read from global memory: it runs once per 32
+  // sources per warp)
+  static_assert(kTile <= 32 * 8, "the factors of a tile must fit the staging buffer of a warp");
   __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
-  if (PROP == kPropMlp) mlp::load_image(s_net[0], a.net);
 
   __shared__ int s_item;
   const int N = a.N;
@@ -202,8 +207,6 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
   const int pprev = win.nw > 1 ? win.phys(win.nw - 2) : pn;  // slot n - 1 (or n)
   const float invL = (float)(1.0 / (kC * a.state->dt * D));
-  // light distance across the window, (nw - 1) c dt (learned proposal only)
-  const float mlp_lh = PROP == kPropMlp ? (float)((win.nw - 1) * (kC * a.state->dt)) : 0.f;
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
@@ -240,6 +243,9 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
     r.rr = a.rec64 + ((size_t)i * D + pn) * 6;
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
+  // learned proposal: the mean position of the warp's targets, where the network is evaluated
+  float3 rc = make_float3(0.f, 0.f, 0.f);
+  if (PROP == kPropMlp) rc = mlp::warp_mean(active, r.h0, r.h1, r.h2);
   // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
   // so relative velocities are formed from these small differences at full FP32 relative precision)
   float bi0 = 0.f, bi1 = 0.f, bi2 = 0.f;
@@ -271,37 +277,37 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
       s_kq[threadIdx.x] = a.kq32[j];
       s_q1[threadIdx.x] = q[1];
       s_x[threadIdx.x] = __ldg(a.ext32 + 3 * j + 2);
-      if (PROP == kPropMlp) {
-        const float4 q2p = a.rec32[((size_t)j * D + pprev) * 3 + 2];
-        s_db[threadIdx.x] = make_float4(q2.x - q2p.x, q2.y - q2p.y, q2.z - q2p.z, 0.f);
-      }
     }
     __syncthreads();
+    if (PROP == kPropMlp) {
+      // the network for the tile's sources, 32 at a time, at the warp's mean target position; the factors
+      // then replace the staging buffer of the warp
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      float fac[kTile / 32];
+#pragma unroll
+      for (int g = 0; g < kTile / 32; g++) {
+        const int jj = 32 * g + lane;
+        const bool v = jj < tn;
+        const int jr = tile + (v ? jj : 0);
+        const float4 g0 = s_q0[v ? jj : 0], g2 = s_q2[v ? jj : 0];
+        const float4 q2n = __ldg(a.rec32 + ((size_t)jr * D + pn) * 3 + 2);
+        const float4 q2p = __ldg(a.rec32 + ((size_t)jr * D + pprev) * 3 + 2);
+        fac[g] = 32 * g < tn ? mlp::warp_delay_factor(*a.net, v, rc.x - g0.x, rc.y - g0.y, rc.z - g0.z, g2.x, g2.y,
+                                                       g2.z, q2n.x - q2p.x, q2n.y - q2p.y, q2n.z - q2p.z, invL,
+                                                       (float)D, s_stage[w])
+                             : 1.f;
+      }
+      __syncwarp();
+      float* s_fac = reinterpret_cast<float*>(s_stage[w]);
+#pragma unroll
+      for (int g = 0; g < kTile / 32; g++) s_fac[32 * g + lane] = fac[g];
+      __syncwarp();
+    }
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
-      for (int jj = jj0; (PROP == kPropMlp || active) && jj < jend; ++jj) {
+      for (int jj = jj0; active && jj < jend; ++jj) {
         const int j = tile + jj;
-        float steps_mlp = 0.f;
-        if (PROP == kPropMlp) {
-          // every lane of the warp takes part in the tensor-core evaluation, then idle lanes skip the pair;
-          // a warp whose lanes uniform motion places all beyond the history (c tau >= Lh, recognised
-          // without a root: |d|^2 + 2 Lh (d.beta) > Lh^2 / gamma^2) skips the network, and its search
-          // starts at the oldest slot, the one test such a pair needs
-          const float4 g0 = s_q0[jj], g2 = s_q2[jj], gd = s_db[jj];
-          const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
-          const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z, dd = x0 * x0 + x1 * x1 + x2 * x2;
-          const bool beyond = !active || fmaf(2.f * mlp_lh, db, dd) > mlp_lh * mlp_lh * g0.w;
-          if (__all_sync(0xffffffffu, beyond)) {
-            steps_mlp = 2.0e9f;
-          } else {
-            float f[mlp::kIn];
-            mlp::features(x0, x1, x2, g2.x, g2.y, g2.z, gd.x, gd.y, gd.z, invL, (float)D, f);
-            const float z = mlp::infer_warp(s_net[0], f, s_stage[threadIdx.x >> 5]);
-            steps_mlp = fminf(fmaxf(floorf(__expf(fminf(z, 80.f)) * (f[3] / invL) * inv_cdt), 0.f), 2.0e9f);
-          }
-        }
-        if (!active) continue;  // and stay in the loop for the next source's evaluation
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
@@ -345,11 +351,11 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
             fast = (l1 == 0);
           }
         } else {
-          float steps;
-          if (PROP == kPropMlp)
-            steps = steps_mlp;
-          else
-            steps = closed_form_steps(r, s_q0[jj], s_q2[jj], inv_cdt);
+          // the uniform-motion delay, scaled by the network's factor for this warp and source (learned
+          // proposal)
+          const float steps = closed_form_steps(
+              r, s_q0[jj], s_q2[jj],
+              PROP == kPropMlp ? inv_cdt * reinterpret_cast<const float*>(s_stage[threadIdx.x >> 5])[jj] : inv_cdt);
           const int lraw = guessed_offset(steps, win.nw);
           const int lg = max(lraw, 0);
           pA = win.phys(lg);
@@ -451,6 +457,7 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
           tabA = __ldg(a.tab32 + pA);
         }
         brc += 1u << (10 * br);  // branch counts of this tile, 10 bits each
+        if (DUMP) a.dump[(size_t)i * N + j] = 4 * l1 + br;
 
         if (br == 0) {
           // ---- out of history (eq:linear2): the source moves uniformly with beta1 along the line through
@@ -687,34 +694,43 @@ __global__ void __launch_bounds__(kBlock, PROP == kPropMlp ? 4 : EMPPP_MIXED_MIN
   }
 }
 
-template <bool ADAPT>
+template <bool ADAPT, int SHAPE>
 int max_blocks_mixed(int proposal) {
   int nb = 0;
+  constexpr int B = shape_block(SHAPE);
   if (proposal == kPropClosedForm)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropClosedForm, ADAPT>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropClosedForm, ADAPT, false, SHAPE>, B, 0);
   else if (proposal == kPropMlp)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropMlp, ADAPT>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropMlp, ADAPT, false, SHAPE>, B, 0);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropBisect, ADAPT>, kBlock, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pair_mixed_kernel<kPropBisect, ADAPT, false, SHAPE>, B, 0);
   return nb > 0 ? nb : 1;
 }
 
-int max_blocks_pair_mixed(int proposal, bool adapt) {
-  return adapt ? max_blocks_mixed<true>(proposal) : max_blocks_mixed<false>(proposal);
+// the adaptive-step instances and the bracket dump run the default shape only
+int max_blocks_pair_mixed(int proposal, bool adapt, int shape) {
+  if (adapt) return max_blocks_mixed<true, 0>(proposal);
+  switch (shape) {
+    case 1: return max_blocks_mixed<false, 1>(proposal);
+    case 2: return max_blocks_mixed<false, 2>(proposal);
+    case 3: return max_blocks_mixed<false, 3>(proposal);
+    default: return max_blocks_mixed<false, 0>(proposal);
+  }
 }
 
-template <bool ADAPT>
+template <bool ADAPT, bool DUMP, int SHAPE>
 void launch_mixed(int proposal, const PairLaunch& pl, const MixedArgs& a, cudaStream_t st) {
+  constexpr int B = shape_block(SHAPE);
   if (proposal == kPropClosedForm)
-    pair_mixed_kernel<kPropClosedForm, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropClosedForm, ADAPT, DUMP, SHAPE><<<pl.grid, B, 0, st>>>(a);
   else if (proposal == kPropMlp)
-    pair_mixed_kernel<kPropMlp, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropMlp, ADAPT, DUMP, SHAPE><<<pl.grid, B, 0, st>>>(a);
   else
-    pair_mixed_kernel<kPropBisect, ADAPT><<<pl.grid, kBlock, 0, st>>>(a);
+    pair_mixed_kernel<kPropBisect, ADAPT, DUMP, SHAPE><<<pl.grid, B, 0, st>>>(a);
 }
 
 cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int proposal, const AdaptParams& ap,
-                              const PairLaunch& pl, cudaStream_t st) {
+                              const PairLaunch& pl, cudaStream_t st, int* dump) {
   MixedArgs a;
   a.rec32 = reinterpret_cast<const float4*>(s.rec32);
   a.rec64 = s.rec64;
@@ -740,11 +756,21 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.scale = s.scale;
   a.eta_allow = (float)ap.eta_allow;
   a.ext32 = s.ext32;
-  // the work counter is zeroed by the set-up launch that precedes every pair launch
-  if (ap.on)
-    launch_mixed<true>(proposal, pl, a, st);
+  a.dump = dump;
+  // the work counter is zeroed by the set-up launch that precedes every pair launch; the bracket dump
+  // runs the instance without the adaptive step's reduction (the brackets do not depend on it)
+  if (dump)
+    launch_mixed<false, true, 0>(proposal, pl, a, st);
+  else if (ap.on)
+    launch_mixed<true, false, 0>(proposal, pl, a, st);
+  else if (pl.shape == 1)
+    launch_mixed<false, false, 1>(proposal, pl, a, st);
+  else if (pl.shape == 2)
+    launch_mixed<false, false, 2>(proposal, pl, a, st);
+  else if (pl.shape == 3)
+    launch_mixed<false, false, 3>(proposal, pl, a, st);
   else
-    launch_mixed<false>(proposal, pl, a, st);
+    launch_mixed<false, false, 0>(proposal, pl, a, st);
   return cudaGetLastError();
 }
 

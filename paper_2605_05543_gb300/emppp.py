@@ -46,11 +46,12 @@ class Bext(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("items_per_block", ctypes.c_int32), ("target_order", ctypes.c_int32), ("ms", ctypes.c_double)]
+    _fields_ = [("items_per_block", ctypes.c_int32), ("target_order", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("targets_per_block", ctypes.c_int32), ("sources_per_sum", ctypes.c_int32)]
 
 
 class TuningReport(ctypes.Structure):
-    _fields_ = [("ncand", ctypes.c_int32), ("best", ctypes.c_int32), ("cand", Tuning * 16)]
+    _fields_ = [("ncand", ctypes.c_int32), ("best", ctypes.c_int32), ("cand", Tuning * 32)]
 
 
 class MlpConfig(ctypes.Structure):
@@ -68,6 +69,11 @@ class Stats(ctypes.Structure):
                 ("guard_fallbacks", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("pair_ms", ctypes.c_double),
                 ("step_ms", ctypes.c_double), ("timed_steps", ctypes.c_int64), ("dt_last", ctypes.c_double),
                 ("eta_min", ctypes.c_double), ("v_max", ctypes.c_double)]
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_flops", ctypes.c_double), ("fp64_flops", ctypes.c_double), ("mufu_ops", ctypes.c_double),
+                ("sms", ctypes.c_int32), ("launches", ctypes.c_int32)]
 
 
 class AdaptiveDt(ctypes.Structure):
@@ -126,6 +132,7 @@ SIGNATURES = {
     "emppp_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
     "emppp_autotune": (ctypes.c_int, [_H, ctypes.POINTER(TuningReport)]),
     "emppp_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
+    "emppp_bracket_dump": (ctypes.c_int, [_H, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "emppp_set_stream": (ctypes.c_int, [_H, _vp]),
     "emppp_synchronize": (ctypes.c_int, [_H]),
     "emppp_fields_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -139,6 +146,8 @@ SIGNATURES = {
     "emppp_get_energy": (ctypes.c_int, [_H, ctypes.POINTER(EnergyState)]),
     "emppp_two_stage": (ctypes.c_int, [_H, _vp, _vp, _vp, ctypes.c_int32, ctypes.POINTER(TwoStageConfig),
                                        ctypes.POINTER(TwoStageReport)]),
+    "emppp_measure_peaks": (ctypes.c_int, [ctypes.POINTER(Peaks), _vp]),
+    "emppp_reciprocal_probe": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
     "emppp_last_error": (ctypes.c_char_p, []),
     "emppp_version": (ctypes.c_char_p, []),
 }
@@ -424,15 +433,25 @@ class Solver:
         _check(self.lib.emppp_reset_stats(self._h))
 
     def autotune(self) -> dict:
-        """Time the candidate work splits on the present state and keep the fastest."""
+        """Time the candidate work splits and tile shapes on the present state and keep the fastest."""
         r = TuningReport()
         _check(self.lib.emppp_autotune(self._h, ctypes.byref(r)))
-        cands = [dict(items_per_block=r.cand[k].items_per_block, target_order=r.cand[k].target_order,
-                      ms=r.cand[k].ms) for k in range(r.ncand)]
+        cands = [{k: getattr(r.cand[q], k) for k, _ in Tuning._fields_} for q in range(r.ncand)]
         return dict(best=cands[r.best], candidates=cands)
 
-    def set_tuning(self, items_per_block=16, target_order=1):
-        t = Tuning(items_per_block=int(items_per_block), target_order=int(target_order), ms=0.0)
+    def bracket_dump(self):
+        """(brackets [n, n] int32 numpy array, k0): the bracket 4 (k1 - k0) + branch of every ordered pair of
+        the present state (emppp_bracket_dump); -1 on the diagonal and between bunches."""
+        import torch
+
+        out = torch.empty((self.n, self.n), dtype=torch.int32, device="cuda")
+        k0 = ctypes.c_int64()
+        _check(self.lib.emppp_bracket_dump(self._h, out.data_ptr(), ctypes.byref(k0)))
+        return out.cpu().numpy(), k0.value
+
+    def set_tuning(self, items_per_block=16, target_order=1, targets_per_block=128, sources_per_sum=8):
+        t = Tuning(items_per_block=int(items_per_block), target_order=int(target_order), ms=0.0,
+                   targets_per_block=int(targets_per_block), sources_per_sum=int(sources_per_sum))
         _check(self.lib.emppp_set_tuning(self._h, ctypes.byref(t)))
 
     def synchronize(self):
@@ -461,14 +480,24 @@ def fields_noalloc(T, W, V, E, B, w=None, stream=None):
     """Self fields at the present (last) slot of a caller-held device history, computed by the
     library without allocating device memory (see emppp_fields_noalloc in include/emppp.h).
     T [nslots], W, V [nslots, n, 3], E, B [n, 3]: float64 CUDA tensors; w [n] optional."""
-    nslots = int(T.numel()) if _is_torch(T) else int(np.size(T))
-    n = (int(W.numel()) if _is_torch(W) else int(np.size(W))) // (3 * max(nslots, 1))
+    import torch
+
+    tensors = [a for a in (T, W, V, w, E, B) if a is not None]
+    if not all(_is_torch(a) and a.is_cuda for a in tensors):
+        raise ValueError("fields_noalloc takes device (CUDA tensor) arrays only")
+    devices = {a.device for a in tensors}
+    if len(devices) != 1:
+        raise ValueError(f"fields_noalloc: all arrays must be on one device, got {sorted(map(str, devices))}")
+    device = devices.pop()
+    if isinstance(stream, torch.cuda.Stream) and stream.device != device:
+        raise ValueError(f"fields_noalloc: stream of {stream.device}, arrays on {device}")
+    nslots = int(T.numel())
+    n = int(W.numel()) // (3 * max(nslots, 1))
     ptrs = [_ptr(T, nslots, "T"), _ptr(W, nslots * 3 * n, "W"), _ptr(V, nslots * 3 * n, "V"),
             _ptr(w, n, "w"), _ptr(E, 3 * n, "E"), _ptr(B, 3 * n, "B")]
-    if _same_kind(*ptrs) != 1:
-        raise ValueError("fields_noalloc takes device (CUDA tensor) arrays only")
     pT, pW, pV, pw, pE, pB = (p for p, _ in ptrs)
-    _check(load().emppp_fields_noalloc(n, nslots, pT, pW, pV, pw, pE, pB, _stream_handle(stream)))
+    with torch.cuda.device(device):
+        _check(load().emppp_fields_noalloc(n, nslots, pT, pW, pV, pw, pE, pB, _stream_handle(stream)))
 
 
 def _dev_f32(a):
@@ -518,6 +547,27 @@ def mlp_train(params, features, targets, epochs=4, batch=4096, lr=1e-3, beta1=0.
     _check(load().emppp_mlp_train(p.data_ptr(), X.data_ptr(), T.data_ptr(), X.shape[0], ctypes.byref(cfg),
                                   losses.ctypes.data, torch.cuda.current_stream().cuda_stream))
     return p.cpu().numpy(), losses[:int(epochs)]
+
+
+def measure_peaks(stream=None) -> dict:
+    """Measured FP32 / FP64 FMA and reciprocal-square-root throughput of the current device
+    (emppp_measure_peaks): flop/s, flop/s, operations/s."""
+    p = Peaks()
+    _check(load().emppp_measure_peaks(ctypes.byref(p), _stream_handle(stream)))
+    return {k: getattr(p, k) for k, _ in Peaks._fields_}
+
+
+def reciprocal_probe(x):
+    """1 / x by the FP64 pair kernel's reciprocal, for a float64 CUDA tensor x; returns a CUDA tensor."""
+    import torch
+
+    if not (_is_torch(x) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ValueError("x: need a contiguous float64 CUDA tensor")
+    y = torch.empty_like(x)
+    with torch.cuda.device(x.device):
+        _check(load().emppp_reciprocal_probe(x.data_ptr(), y.data_ptr(), x.numel(),
+                                             torch.cuda.current_stream().cuda_stream))
+    return y
 
 
 def version() -> str:

@@ -202,20 +202,32 @@ def test_autotune_keeps_state_and_results(precision):
 
     h = history_case(3000, 80, sigma=10e-6, seed=21)
     T, W, V, u = window(h, 128)
+    shapes = [(128, 8), (64, 8), (256, 8)] + ([(128, 16)] if precision == "mixed" else [])
+    fields = []
     with emppp.Solver(3000, 128, DT, precision=precision, proposal="closed_form") as s:
         s.set_history(80, T, W, V, u)
         rep = s.autotune()
         _, _, t0, n0 = s.get_state()
-        assert n0 == 80 and len(rep["candidates"]) == 10  # 5 splits x both target orders
+        # 5 splits x both target orders at the default shape, then the other tile shapes
+        assert n0 == 80 and len(rep["candidates"]) == 10 + len(shapes) - 1
         assert all(c["ms"] > 0 for c in rep["candidates"])
+        assert {(c["targets_per_block"], c["sources_per_sum"]) for c in rep["candidates"]} == set(shapes)
         s.step(1)
-        Ea, Ba = s.get_fields()
-        s.set_history(80, T, W, V, u)
-        s.set_tuning(items_per_block=4, target_order=0)
-        s.step(1)
-        Eb, Bb = s.get_fields()
+        fields.append(s.get_fields())
+        for tpb, sps in shapes:
+            for ipb, order in ((4, 0), (16, 1)):
+                s.set_history(80, T, W, V, u)
+                s.set_tuning(items_per_block=ipb, target_order=order, targets_per_block=tpb, sources_per_sum=sps)
+                s.step(1)
+                fields.append(s.get_fields())
+                st = s.stats()
+                assert st["pairs"] == 3000 * 2999
+        with pytest.raises(emppp.EmpppError):
+            s.set_tuning(targets_per_block=96)
+        with pytest.raises(emppp.EmpppError):
+            s.set_tuning(targets_per_block=64, sources_per_sum=16)
     E_ref, B_ref, _, M = oracle.self_fields(h.T, h.W, h.V, 80, 128, mags=True)
     tol = 1e-12 if precision == "fp64" else 1e-5
-    for E, B in ((Ea, Ba), (Eb, Bb)):
+    for E, B in fields:
         eE, eB = field_errors(E, B, E_ref, B_ref, M)
         assert eE <= tol and eB <= tol

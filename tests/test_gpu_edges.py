@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import DT, field_errors, history_case, window
+from gpu_helpers import DT, field_errors, history_case, light_sphere_case, window
 
 pytestmark = pytest.mark.gpu
 
@@ -99,30 +99,9 @@ def test_node_tests_at_the_light_sphere(precision, proposal):
     its radius (64 two-particle bunches in one batch): every such node test falls inside the FP32 guard
     band, the FP64 test decides it, and the brackets must be the oracle's (branch counts equal) with
     fields within each path's bar."""
-    rng = np.random.default_rng(70)
     C = oracle.constants()["c"]
     n, D, nb = 40, 64, 64
-    T = np.array([k * DT for k in range(n + 1)])
-    W = np.zeros((n + 1, 2 * nb, 3))
-    V = np.zeros((n + 1, 2 * nb, 3))
-    eps = [0.0, 1e-16, -1e-16, 1e-15, -1e-15, 1e-14, -1e-14, 1e-12, -1e-12]
-    for b in range(nb):
-        beta = rng.uniform(0.3, 0.9)
-        vdir = rng.normal(size=3)
-        v0 = beta * C * vdir / np.linalg.norm(vdir)
-        acc = rng.normal(size=3) * 1e18
-        w00 = rng.normal(size=3) * 1e-6
-        k = int(rng.integers(1, n - 1))
-        nhat = rng.normal(size=3)
-        nhat /= np.linalg.norm(nhat)
-        wk = w00 + v0 * T[k] + 0.5 * acc * T[k] ** 2
-        r = wk + C * (T[n] - T[k]) * (1.0 + eps[b % len(eps)]) * nhat
-        W[:, 2 * b] = r  # the target rests on the sphere
-        W[:, 2 * b + 1] = w00 + v0[None] * T[:, None] + 0.5 * acc[None] * T[:, None] ** 2
-        V[:, 2 * b + 1] = v0[None] + acc[None] * T[:, None]
-    u = np.zeros((2 * nb, 3))
-    g = 1.0 / np.sqrt(1.0 - np.sum(V[n, 1::2] ** 2, axis=1) / C ** 2)
-    u[1::2] = V[n, 1::2] * g[:, None]
+    T, W, V, u = light_sphere_case(nb, n)
     with emppp.Solver(0, D, DT, precision=precision, proposal=proposal, bunches=[2] * nb) as s:
         s.set_history(n, T, W, V, u)
         s.step(1)
