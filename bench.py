@@ -74,6 +74,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample size (seconds of work)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default work split and tile shape (no emppp_autotune before the timed steps)")
     ap.add_argument("--no-run-leg", action="store_true",
                     help="skip the stated run of the bunch from t = 0 (500 steps of its own dynamics)")
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -322,8 +324,26 @@ def train_proposal(wl, win, n_hist, per_state=1 << 20, epochs=3, seed=3, small=F
                "target": "z = log((t - t_r) / tau_u), tau_u the uniform-motion delay of the source's present record; MSE"}
 
 
+def autotune_state(path, proposal, wl, h, win, net=None):
+    """Runs emppp_autotune on the workload's state; returns the chosen tuning (work split, target order, tile
+    shape) and the number of candidates timed."""
+    import torch
+
+    from paper_2605_05543_gb300 import emppp
+
+    T, W, V, u = win
+    with emppp.Solver(wl["N"], wl["depth"], wl["dt"], precision=path, proposal=proposal,
+                      stream=torch.cuda.current_stream()) as s:
+        s.set_history(h.n, T, W, V, u)
+        if net is not None:
+            s.set_proposal(net)
+        rep = s.autotune()
+    best = {k: rep["best"][k] for k in ("items_per_block", "target_order", "targets_per_block", "sources_per_sum")}
+    return best, len(rep["candidates"])
+
+
 def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, keep_fields=True, net=None,
-             **solver_kw):
+             tuning=None, **solver_kw):
     import numpy as np
     import torch
 
@@ -338,6 +358,8 @@ def run_path(args, path, proposal, steps, warmup, wl, h, win, rank, e2e=True, ke
         s.set_history(h.n, T, W, V, u)
         if net is not None:
             s.set_proposal(net)
+        if tuning is not None:
+            s.set_tuning(**tuning)
         # warm-up; the first step's fields are those of the stored state
         s.step(1)
         if keep_fields and rank == 0:
@@ -433,8 +455,11 @@ def run_ours(args):
     if args.proposal == "mlp" or not args.no_ablation:
         net, net_report = train_proposal(wl, win, h.n, small=args.small)
     peaks = emppp.measure_peaks()
+    # the work split and tile shape for this state and path, chosen once (closed-form instance) and used by
+    # every proposal, so that their fields stay comparable bit for bit
+    tuning, ncand = (None, 0) if args.no_tune else autotune_state(args.path, "closed_form", wl, h, win)
     res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e,
-                   net=net if args.proposal == "mlp" else None)
+                   net=net if args.proposal == "mlp" else None, tuning=tuning)
     ms = max_over_ranks(res["ms"], dev)
     pairs_per_step = wl["N"] * (wl["N"] - 1)
     total_pairs = sum_over_ranks(pairs_per_step * steps, dev)
@@ -468,6 +493,9 @@ def run_ours(args):
                      "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1)},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
+        "tuning": ({**tuning, "candidates_timed": ncand, "by": "emppp_autotune on this state, before the timed steps"}
+                   if tuning else "default (items_per_block 16, spatial target order, 128 targets per block, "
+                                  "8 sources per partial sum)"),
         "branch_mix": {k: st[k] / max(st["pairs"], 1) for k in ("out_of_history", "shortcut", "bisection")},
         "node_tests_per_pair": st["node_tests"] / max(st["pairs"], 1),
     }
@@ -483,7 +511,7 @@ def run_ours(args):
                 continue
             else:
                 r = run_path(args, args.path, prop, 2 if args.path == "fp64" else 5, 1, wl, h, win, rank, e2e=False,
-                             keep_fields=True, net=net if prop == "mlp" else None)
+                             keep_fields=True, net=net if prop == "mlp" else None, tuning=tuning)
             abl[prop] = {"node_tests_per_pair": r["stats"]["node_tests"] / max(r["stats"]["pairs"], 1),
                          "ms_per_step": r["ms"], "pairs_per_s": pairs_per_step / (r["ms"] / 1e3)}
             if rank == 0 and "fields0" in r and "fields0" in res:

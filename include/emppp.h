@@ -129,8 +129,8 @@ typedef struct {
  * targets spatially each step (both paths; the fields do not depend on it; a step of a system of at most
  * 2048 particles on the mixed path skips it). The tile shape: targets_per_block targets per work item and
  * thread block (64, 128 or 256; on the mixed path also the sources a block stages per tile) and, on the
- * mixed path, sources_per_sum sources per FP32 partial sum before the compensated addition (8 or 16; with
- * 16 only at 128 targets per block). The FP64 path ignores sources_per_sum. The shape changes the order
+ * mixed path, sources_per_sum sources per FP32 partial sum before the compensated addition (8, 16 or 32;
+ * 16 and 32 only at 128 targets per block). The FP64 path ignores sources_per_sum. The shape changes the order
  * of each target's sum, so fields of different shapes agree within rounding, not bit for bit; the
  * adaptive time step and the comparison variants run the default shape (128, 8). Chosen by emppp_autotune
  * or set with emppp_set_tuning. */
@@ -232,7 +232,7 @@ EMPPP_API emppp_status emppp_reset_stats(emppp_handle h);
  * partial-sum reduction; the state is not advanced; one warm-up, best of two) for items_per_block in
  * {4, 8, 16, 32, 64}, with and without the spatial target order, at the default tile shape; then, with
  * the fastest of those and unless the adaptive time step is on, for the other tile shapes (targets per
- * block 64 and 256; on the mixed path also 16 sources per partial sum). Keeps the fastest candidate for
+ * block 64 and 256; on the mixed path also 16 and 32 sources per partial sum). Keeps the fastest candidate for
  * later steps of the current precision and proposal. report may be NULL. Synchronises the stream; resets
  * the stats; afterwards emppp_get_fields reports the fields of the last evaluation. */
 EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* report);
@@ -252,8 +252,8 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
 EMPPP_API emppp_status emppp_bracket_dump(emppp_handle h, int32_t* brackets, int64_t* k0);
 
 /* Sets the work split and tile shape directly (e.g. a tuning found earlier). items_per_block in 1..256,
- * targets_per_block in {0 (= 128), 64, 128, 256}, sources_per_sum in {0 (= 8), 8, 16}, 16 only with 128
- * targets per block; EMPPP_ERR_ARG otherwise. */
+ * targets_per_block in {0 (= 128), 64, 128, 256}, sources_per_sum in {0 (= 8), 8, 16, 32}, 16 and 32 only
+ * with 128 targets per block; EMPPP_ERR_ARG otherwise. */
 EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning);
 
 /* Replaces the options for later steps. EMPPP_ERR_STATE for a comparison variant (MIDPOINT, HALF_STEP)

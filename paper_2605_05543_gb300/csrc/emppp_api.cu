@@ -175,7 +175,7 @@ emppp_status update_schedule(emppp_handle c) {
   // tile shape: the tuned one for the fixed-step kernels; the adaptive-step and eq:mid variants and the
   // bracket dump run the default shape, and the FP64 path runs shape 3 as the default
   int shp = (ad || var64 != 0 || c->dumping) ? 0 : c->shape;
-  if (!mixed && shp == 3) shp = 0;
+  if (!mixed && shp >= 3) shp = 0;
   const long long TB = shape_block(shp);  // targets per work item (and sources per staged tile)
   const long long key = (mixed ? 1 : 0) | ((long long)(c->opt.proposal & 3) << 1) |
                         ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13) |
@@ -1115,7 +1115,7 @@ EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuni
   const int shp = shape_of(tuning->targets_per_block, tuning->sources_per_sum);
   if (shp < 0)
     return fail(EMPPP_ERR_ARG, "tile shape (%d targets per block, %d sources per sum) is not one of (128, 8), "
-                "(64, 8), (256, 8), (128, 16)", tuning->targets_per_block, tuning->sources_per_sum);
+                "(64, 8), (256, 8), (128, 16), (128, 32)", tuning->targets_per_block, tuning->sources_per_sum);
   h->items_per_block = tuning->items_per_block;
   h->target_order = tuning->target_order;
   h->shape = shp;

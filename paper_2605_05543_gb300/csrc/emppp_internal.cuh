@@ -182,10 +182,10 @@ struct BextParams {
 
 // Tile shapes of the pair kernels (emppp_tuning): targets per block, which is also the number of sources
 // a mixed-path block stages per tile, and the mixed path's sources per FP32 partial sum. Shape 0 is the
-// default; the FP64 path runs shape 3 as shape 0 (its sums are blocked by 64 sources).
-constexpr int kNumShapes = 4;
+// default; the FP64 path runs shapes 3 and 4 as shape 0 (its sums are blocked by 64 sources).
+constexpr int kNumShapes = 5;
 __host__ __device__ constexpr int shape_block(int shape) { return shape == 1 ? 64 : (shape == 2 ? 256 : 128); }
-__host__ __device__ constexpr int shape_sub(int shape) { return shape == 3 ? 16 : 8; }
+__host__ __device__ constexpr int shape_sub(int shape) { return shape == 3 ? 16 : (shape == 4 ? 32 : 8); }
 
 // launch configuration of a persistent pair kernel
 struct PairLaunch {

@@ -98,7 +98,7 @@ struct Window {
 
 }  // namespace
 
-// SHAPE: targets per block (kBlock = shape_block(SHAPE); shape 3 runs as shape 0)
+// SHAPE: targets per block (kBlock = shape_block(SHAPE); shapes 3 and 4 run as shape 0)
 template <int PROP, bool ADAPT, bool MID, bool DUMP, int SHAPE>
 __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs a) {
   constexpr int kBlock = shape_block(SHAPE);

@@ -75,8 +75,8 @@ struct MixedArgs {
 
 struct Target {
   float h0, h1, h2, l0, l1, l2;
-  const double* rr;  // FP64 present position, read only by the rare FP64 node tests
-  bool exact_only;   // coordinates too far from the split origin for the FP32 band: FP64 tests only
+  int idx;          // particle index (its FP64 present record is formed only for the rare FP64 node tests)
+  bool exact_only;  // coordinates too far from the split origin for the FP32 band: FP64 tests only
 };
 
 // slots of the usable window k0..n are addressed by their offset l = k - k0 (0..nw-1)
@@ -100,10 +100,10 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ src32, int p)
   return r;
 }
 
-__device__ __forceinline__ bool exact_test(const Target& r, const double* __restrict__ w, double lhs) {
-  const double d0 = __dsub_rn(__ldg(r.rr + 0), __ldg(w + 0));
-  const double d1 = __dsub_rn(__ldg(r.rr + 1), __ldg(w + 1));
-  const double d2 = __dsub_rn(__ldg(r.rr + 2), __ldg(w + 2));
+__device__ __forceinline__ bool exact_test(const double* __restrict__ rr, const double* __restrict__ w, double lhs) {
+  const double d0 = __dsub_rn(__ldg(rr + 0), __ldg(w + 0));
+  const double d1 = __dsub_rn(__ldg(rr + 1), __ldg(w + 1));
+  const double d2 = __dsub_rn(__ldg(rr + 2), __ldg(w + 2));
   const double rhs = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
   return lhs <= rhs;
 }
@@ -130,7 +130,7 @@ __device__ __forceinline__ bool node_test_d(const Target& r, float3 d, float4 ta
     if (D2 < tab.y) return false;
   }
   n_fb++;
-  return exact_test(r, src64 + 6 * p, __ldg(a.lhs64 + p));
+  return exact_test(a.rec64 + ((size_t)r.idx * a.D + a.state->pn) * 6, src64 + 6 * p, __ldg(a.lhs64 + p));
 }
 
 __device__ __forceinline__ bool node_test(const Target& r, const float4* __restrict__ src32,
@@ -140,20 +140,21 @@ __device__ __forceinline__ bool node_test(const Target& r, const float4* __restr
                      a, n_fb);
 }
 
-// uniform-motion guess of the retarded delay in steps, from the staged present record of the source:
+// uniform-motion guess of the retarded delay, from the staged present record of the source:
 // c tau = gamma^2 [d.beta + sqrt((d.beta)^2 + |d|^2 / gamma^2)] with d from the hi parts only
-__device__ __forceinline__ float closed_form_steps(const Target& r, float4 g0, float4 g2, float inv_cdt) {
+__device__ __forceinline__ float closed_form_ctau(const Target& r, float4 g0, float4 g2) {
   const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
   const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
   const float dd = x0 * x0 + x1 * x1 + x2 * x2;
   const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
-  const float ctau = (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
-  return fminf(fmaxf(floorf(ctau * inv_cdt), 0.f), 2.0e9f);
+  return (db + x * rsqrtf(fmaxf(x, 1e-37f))) * g2.w;
 }
 
-// offset of the guessed older node: (nw - 2) - steps; below 0 means "older than the history"
-__device__ __forceinline__ int guessed_offset(float steps, int nw) {
-  return (steps > (float)(nw - 2)) ? -1 : (nw - 2) - (int)steps;
+// offset of the guessed older node for a delay of sc steps: (nw - 2) - floor(sc); -1 ("older than the
+// history") when floor(sc) > nw - 2, i.e. sc >= nw - 1, decided before any rounding; a negative or NaN
+// delay guesses the newest bracket
+__device__ __forceinline__ int guessed_offset(float sc, int nw, float nw1) {
+  return (sc >= nw1) ? -1 : (nw - 2) - (int)fmaxf(sc, 0.f);
 }
 
 // bisection between offsets lo (P false) and hi (P true); returns lo
@@ -207,6 +208,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
   const int pprev = win.nw > 1 ? win.phys(win.nw - 2) : pn;  // slot n - 1 (or n)
   const float invL = (float)(1.0 / (kC * a.state->dt * D));
+  const float nw1 = (float)(win.nw - 1);  // a guessed delay of at least nw - 1 steps is out of history
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
     r.l0 = q1.x;
     r.l1 = q1.y;
     r.l2 = q1.z;
-    r.rr = a.rec64 + ((size_t)i * D + pn) * 6;
+    r.idx = i;
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
   // learned proposal: the mean position of the warp's targets, where the network is evaluated
@@ -353,10 +355,10 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         } else {
           // the uniform-motion delay, scaled by the network's factor for this warp and source (learned
           // proposal)
-          const float steps = closed_form_steps(
-              r, s_q0[jj], s_q2[jj],
-              PROP == kPropMlp ? inv_cdt * reinterpret_cast<const float*>(s_stage[threadIdx.x >> 5])[jj] : inv_cdt);
-          const int lraw = guessed_offset(steps, win.nw);
+          const float sc =
+              closed_form_ctau(r, s_q0[jj], s_q2[jj]) *
+              (PROP == kPropMlp ? inv_cdt * reinterpret_cast<const float*>(s_stage[threadIdx.x >> 5])[jj] : inv_cdt);
+          const int lraw = guessed_offset(sc, win.nw, nw1);
           const int lg = max(lraw, 0);
           pA = win.phys(lg);
           A = load_rec(src32, pA);
@@ -480,9 +482,10 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             const double* w0 = src64 + 6 * pA;  // FP64 record of slot k0: X = r - w_k0 - v_k0 (t_n - t_k0)
             const double ct = kC * (a.state->t - __ldg(a.slot_t + pA));  // c (t_n - t_k0)
             const double ic = 1.0 / kC;
-            const double y0 = (__ldg(r.rr + 0) - __ldg(w0 + 0)) - __ldg(w0 + 3) * ic * ct;
-            const double y1 = (__ldg(r.rr + 1) - __ldg(w0 + 1)) - __ldg(w0 + 4) * ic * ct;
-            const double y2 = (__ldg(r.rr + 2) - __ldg(w0 + 2)) - __ldg(w0 + 5) * ic * ct;
+            const double* rr = a.rec64 + ((size_t)i * D + pn) * 6;
+            const double y0 = (__ldg(rr + 0) - __ldg(w0 + 0)) - __ldg(w0 + 3) * ic * ct;
+            const double y1 = (__ldg(rr + 1) - __ldg(w0 + 1)) - __ldg(w0 + 4) * ic * ct;
+            const double y2 = (__ldg(rr + 2) - __ldg(w0 + 2)) - __ldg(w0 + 5) * ic * ct;
             X0 = (float)y0;
             X1 = (float)y1;
             X2 = (float)y2;
@@ -555,9 +558,10 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           if (br == 2 && ig2 < 0.0625f &&
               __fmul_rn(__fmul_rn(L1, L1), fabsf(s)) > __fmul_rn(kC0Guard, __fmul_rn(C0, __fsub_rn(L1, s)))) {
             const double* w64 = src64 + 6 * pA;
-            const double x0 = __dsub_rn(__ldg(r.rr + 0), __ldg(w64 + 0));
-            const double x1 = __dsub_rn(__ldg(r.rr + 1), __ldg(w64 + 1));
-            const double x2 = __dsub_rn(__ldg(r.rr + 2), __ldg(w64 + 2));
+            const double* rr = a.rec64 + ((size_t)i * D + pn) * 6;
+            const double x0 = __dsub_rn(__ldg(rr + 0), __ldg(w64 + 0));
+            const double x1 = __dsub_rn(__ldg(rr + 1), __ldg(w64 + 1));
+            const double x2 = __dsub_rn(__ldg(rr + 2), __ldg(w64 + 2));
             C0 = (float)(__ldg(a.lhs64 + pA) - (x0 * x0 + x1 * x1 + x2 * x2));
             qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
             sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
@@ -714,6 +718,7 @@ int max_blocks_pair_mixed(int proposal, bool adapt, int shape) {
     case 1: return max_blocks_mixed<false, 1>(proposal);
     case 2: return max_blocks_mixed<false, 2>(proposal);
     case 3: return max_blocks_mixed<false, 3>(proposal);
+    case 4: return max_blocks_mixed<false, 4>(proposal);
     default: return max_blocks_mixed<false, 0>(proposal);
   }
 }
@@ -769,6 +774,8 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
     launch_mixed<false, false, 2>(proposal, pl, a, st);
   else if (pl.shape == 3)
     launch_mixed<false, false, 3>(proposal, pl, a, st);
+  else if (pl.shape == 4)
+    launch_mixed<false, false, 4>(proposal, pl, a, st);
   else
     launch_mixed<false, false, 0>(proposal, pl, a, st);
   return cudaGetLastError();

@@ -202,7 +202,7 @@ def test_autotune_keeps_state_and_results(precision):
 
     h = history_case(3000, 80, sigma=10e-6, seed=21)
     T, W, V, u = window(h, 128)
-    shapes = [(128, 8), (64, 8), (256, 8)] + ([(128, 16)] if precision == "mixed" else [])
+    shapes = [(128, 8), (64, 8), (256, 8)] + ([(128, 16), (128, 32)] if precision == "mixed" else [])
     fields = []
     with emppp.Solver(3000, 128, DT, precision=precision, proposal="closed_form") as s:
         s.set_history(80, T, W, V, u)
@@ -226,6 +226,8 @@ def test_autotune_keeps_state_and_results(precision):
             s.set_tuning(targets_per_block=96)
         with pytest.raises(emppp.EmpppError):
             s.set_tuning(targets_per_block=64, sources_per_sum=16)
+        with pytest.raises(emppp.EmpppError):
+            s.set_tuning(targets_per_block=128, sources_per_sum=64)
     E_ref, B_ref, _, M = oracle.self_fields(h.T, h.W, h.V, 80, 128, mags=True)
     tol = 1e-12 if precision == "fp64" else 1e-5
     for E, B in fields:
