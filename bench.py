@@ -76,6 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default work split and tile shape (no emppp_autotune before the timed steps)")
+    ap.add_argument("--shape", default=None,
+                    help="targets per block and sources per partial sum, e.g. 128,32 (no emppp_autotune)")
     ap.add_argument("--no-run-leg", action="store_true",
                     help="skip the stated run of the bunch from t = 0 (500 steps of its own dynamics)")
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -208,10 +210,10 @@ def workload_name(wl):
     return f"reduced case N={wl['N']} depth={wl['depth']} history slots={wl['n0'] + 1}"
 
 
-def kernel_traffic_record(path_name, proposal):
+def kernel_traffic_record(path_name, proposal, shape=None):
     """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it was taken on the
-    same kernel instance and on the sources as they are now (the kernel and the work split, which sets
-    the source chunks), else None."""
+    same kernel instance (proposal and tile shape) and on the sources as they are now (the kernel, the tile
+    shapes and the work split, which sets the source chunks), else None."""
     rec = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     if not os.path.exists(rec):
         return None
@@ -219,6 +221,8 @@ def kernel_traffic_record(path_name, proposal):
         d = json.load(open(rec))
         ent = d.get(path_name)
         if not ent or ent.get("proposal") != proposal:
+            return None
+        if list(ent.get("shape", [128, 8])) != list(shape or (128, 8)):
             return None
         h = hashlib.sha256()
         for name in ent["sources"]:
@@ -457,7 +461,11 @@ def run_ours(args):
     peaks = emppp.measure_peaks()
     # the work split and tile shape for this state and path, chosen once (closed-form instance) and used by
     # every proposal, so that their fields stay comparable bit for bit
-    tuning, ncand = (None, 0) if args.no_tune else autotune_state(args.path, "closed_form", wl, h, win)
+    if args.shape:
+        tpb, sps = (int(v) for v in args.shape.split(","))
+        tuning, ncand = dict(items_per_block=16, target_order=1, targets_per_block=tpb, sources_per_sum=sps), 0
+    else:
+        tuning, ncand = (None, 0) if args.no_tune else autotune_state(args.path, "closed_form", wl, h, win)
     res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e,
                    net=net if args.proposal == "mlp" else None, tuning=tuning)
     ms = max_over_ranks(res["ms"], dev)
@@ -481,7 +489,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2: 0.79 GB of history window read per step (L2 129 MB)"},
         "roofline": {"bound": "alu", "kernel": "pair_fp64_kernel" if args.path == "fp64" else "pair_mixed_kernel",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic_record(args.path, args.proposal),
+                     "traffic": kernel_traffic_record(
+                         args.path, args.proposal,
+                         (tuning["targets_per_block"], tuning["sources_per_sum"]) if tuning else None),
                      "peak_note": ("nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz" if args.path == "fp64"
                                    else "nominal FP32: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
                      "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas,
@@ -493,7 +503,8 @@ def run_ours(args):
                      "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1)},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
-        "tuning": ({**tuning, "candidates_timed": ncand, "by": "emppp_autotune on this state, before the timed steps"}
+        "tuning": ({**tuning, "candidates_timed": ncand,
+                    "by": ("emppp_autotune on this state, before the timed steps" if ncand else "--shape")}
                    if tuning else "default (items_per_block 16, spatial target order, 128 targets per block, "
                                   "8 sources per partial sum)"),
         "branch_mix": {k: st[k] / max(st["pairs"], 1) for k in ("out_of_history", "shortcut", "bisection")},

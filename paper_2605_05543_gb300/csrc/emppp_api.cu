@@ -10,6 +10,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/emppp.h"
 #include "emppp_internal.cuh"
 
@@ -41,6 +43,15 @@ namespace emppp {
 // lets other translation units of the library report an error text through emppp_last_error
 void set_error_text(const char* msg) { g_last_error = msg ? msg : ""; }
 }  // namespace emppp
+
+namespace {
+// NVTX range over a scope of the host code (tracing: the ranges name each step's launches in a timeline
+// tool; without one attached they cost a few nanoseconds)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct emppp_ctx {
   DeviceState ds{};
@@ -385,18 +396,22 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   // FP64 path keeps it, since it keeps out-of-history and bracketed pairs in separate warps).
   const bool mixed_pairs = h->opt.pair_fields && h->opt.precision == EMPPP_MIXED;
   const bool ordered = h->opt.pair_fields && h->target_order && !(mixed_pairs && h->N <= 2048);
-  if (ordered) {
-    CU(cudaEventRecord(h->ev_fork, h->stream));
-    CU(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
-    CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->aux));
-    CU(cudaEventRecord(h->ev_join, h->aux));
+  {
+    NvtxRange r("emppp:setup");
+    if (ordered) {
+      CU(cudaEventRecord(h->ev_fork, h->stream));
+      CU(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+      CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->aux));
+      CU(cudaEventRecord(h->ev_join, h->aux));
+      k += 1;
+    }
+    CU(launch_setup(h->ds, mixed_pairs, h->stream));
     k += 1;
   }
-  CU(launch_setup(h->ds, mixed_pairs, h->stream));
-  k += 1;
   if (ordered) CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
+    NvtxRange r("emppp:pair_fields");
     if (h->opt.precision == EMPPP_MIXED)
       CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
     else
@@ -413,6 +428,7 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   // small systems of few bunches: the energy monitor runs in the post-pair launch's last block (its own
   // launch evaluates the bunches in parallel, one block each)
   const bool fused_energy = h->energy.on && h->N <= 16384 && h->nbunch <= 8;
+  NvtxRange r_post("emppp:push_append");
   CU(launch_step_post(h->ds, bp, h->adapt, chunked, half, chunked && wide_reduction(h),
                       fused_energy ? &h->energy : nullptr, h->d_mon, h->stream));
   k += 1;
@@ -817,6 +833,7 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
     return fail(EMPPP_ERR_STATE, "the MLP proposal needs a network: call emppp_set_proposal first");
   if ((st = update_schedule(h)) != EMPPP_OK) return st;
   const bool use_graph = h->opt.graphs && !h->opt.timing && h->stream != nullptr && nsteps > 1;
+  NvtxRange r_step(use_graph ? "emppp_step (graph replay)" : "emppp_step");
   if (use_graph && (st = capture_step(h, bp)) != EMPPP_OK) return st;
   long long pairs_per_step = 0;
   if (h->opt.pair_fields)

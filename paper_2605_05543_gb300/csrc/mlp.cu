@@ -202,9 +202,8 @@ __global__ void forward_kernel(const NetImage* __restrict__ img, const float* __
 __global__ void forward_infer_kernel(const InferImage* __restrict__ img, const float* __restrict__ X, long long m,
                                      float* __restrict__ z) {
   __shared__ InferImage net;
-  __shared__ uint32_t stage[4][32][8];
   load_image(net, img);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long base = warp * 32; base < m; base += nwarps * 32) {
@@ -212,7 +211,7 @@ __global__ void forward_infer_kernel(const InferImage* __restrict__ img, const f
     float f[kIn];
 #pragma unroll
     for (int k = 0; k < kIn; k++) f[k] = r < m ? X[r * kIn + k] : 0.f;
-    const float zr = infer_warp(net, f, stage[w]);
+    const float zr = infer_warp(net, f);
     if (r < m) z[r] = zr;
   }
 }

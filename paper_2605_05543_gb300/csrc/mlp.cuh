@@ -2,8 +2,9 @@
 // target and a source, the correction z = log(tau / tau_u) of the delay tau = t - t_r over the delay
 // tau_u that the source's uniform motion from its present record gives (the closed-form guess; the
 // network learns what the source's acceleration history does to it). The pair kernels evaluate the
-// network once per (warp, source), at the mean position of the warp's targets (a warp's targets lie close
-// together in the spatial target order), and every lane scales its own uniform-motion delay by e^z; the
+// network once per (block, source) on the mixed path and once per (warp, source) on the FP64 path, at the
+// mean position of the block's or warp's targets (which lie close together in the spatial target order),
+// and every pair scales its own uniform-motion delay by e^z; the
 // retarded-time search then starts from the slot that delay points at and finishes with the same guarded
 // search as the closed-form proposal, so the bracket (and every field) is the one of the paper's search
 // whatever the network predicts.
@@ -188,29 +189,32 @@ __device__ __forceinline__ void load_image(Image& dst, const Image* __restrict__
   __syncthreads();
 }
 
-// Inference form of the forward pass for the 32 rows held one per lane: f are this lane's features,
-// stage is a per-warp shared buffer of 32 x 8 uint32; returns z of this lane's row. Every lane of the
-// warp must call it (converged). Both 16-row tiles share each B-fragment load.
-__device__ __forceinline__ float infer_warp(const InferImage& net, const float f[kIn], uint32_t (*stage)[8]) {
+// Inference form of the forward pass for the 32 rows held one per lane: f are this lane's features;
+// returns z of this lane's row. The A fragments of the two 16-row input tiles are gathered from the
+// lanes that hold the rows by warp shuffles (no shared memory): lane (g, t) takes feature pair t of rows
+// g and g + 8 (words 0..3 of those lanes) and pair 4 + t (word 4 for t = 0; the padding is zero). Every
+// lane of the warp must call it (converged). Both 16-row tiles share each B-fragment load.
+__device__ __forceinline__ float infer_warp(const InferImage& net, const float f[kIn]) {
   const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  stage[lane][0] = pack_bf16x2(f[0], f[1]);
-  stage[lane][1] = pack_bf16x2(f[2], f[3]);
-  stage[lane][2] = pack_bf16x2(f[4], f[5]);
-  stage[lane][3] = pack_bf16x2(f[6], f[7]);
-  stage[lane][4] = pack_bf16x2(f[8], f[9]);
-  stage[lane][5] = 0u;
-  stage[lane][6] = 0u;
-  stage[lane][7] = 0u;
-  __syncwarp();
+  const uint32_t w[5] = {pack_bf16x2(f[0], f[1]), pack_bf16x2(f[2], f[3]), pack_bf16x2(f[4], f[5]),
+                         pack_bf16x2(f[6], f[7]), pack_bf16x2(f[8], f[9])};
   uint32_t a_in[2][4];
 #pragma unroll
   for (int m = 0; m < 2; m++) {
-    a_in[m][0] = stage[16 * m + g][t];
-    a_in[m][1] = stage[16 * m + g + 8][t];
-    a_in[m][2] = stage[16 * m + g][4 + t];
-    a_in[m][3] = stage[16 * m + g + 8][4 + t];
+    const int r0 = 16 * m + g, r1 = r0 + 8;
+    uint32_t lo0 = 0u, lo1 = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t v0 = __shfl_sync(0xffffffffu, w[q], r0), v1 = __shfl_sync(0xffffffffu, w[q], r1);
+      lo0 = (t == q) ? v0 : lo0;
+      lo1 = (t == q) ? v1 : lo1;
+    }
+    const uint32_t h0 = __shfl_sync(0xffffffffu, w[4], r0), h1 = __shfl_sync(0xffffffffu, w[4], r1);
+    a_in[m][0] = lo0;
+    a_in[m][1] = lo1;
+    a_in[m][2] = t == 0 ? h0 : 0u;
+    a_in[m][3] = t == 0 ? h1 : 0u;
   }
-  __syncwarp();
   // layer 1: accumulators start at b1 / 2, activations packed straight into layer 2's A fragments
   uint32_t a1[2][4][4];
 #pragma unroll
@@ -284,7 +288,7 @@ __device__ __forceinline__ float3 warp_mean(bool active, float x0, float x1, flo
 // Every lane of the warp must call it (converged).
 __device__ __forceinline__ float warp_delay_factor(const InferImage& net, bool valid, float d0, float d1, float d2,
                                                    float b0, float b1, float b2, float db0, float db1, float db2,
-                                                   float invL, float Df, uint32_t (*stage)[8]) {
+                                                   float invL, float Df) {
   float f[kIn];
   if (valid) {
     features(d0, d1, d2, b0, b1, b2, db0, db1, db2, invL, Df, f);
@@ -292,7 +296,7 @@ __device__ __forceinline__ float warp_delay_factor(const InferImage& net, bool v
 #pragma unroll
     for (int k = 0; k < kIn; k++) f[k] = 0.f;
   }
-  const float z = infer_warp(net, f, stage);
+  const float z = infer_warp(net, f);
   return valid ? __expf(fminf(fmaxf(z, -20.f), 20.f)) : 1.f;
 }
 

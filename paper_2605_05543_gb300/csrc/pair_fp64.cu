@@ -103,9 +103,6 @@ template <int PROP, bool ADAPT, bool MID, bool DUMP, int SHAPE>
 __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs a) {
   constexpr int kBlock = shape_block(SHAPE);
   __shared__ int s_item;
-  // staging buffer of the learned proposal's network (its weights are read from global memory: it runs
-  // once per 32 sources per warp)
-  __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
   const long long N = a.N;
   const int D = a.D;
 
@@ -179,7 +176,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
         const float4 q2p = __ldg(reinterpret_cast<const float4*>(a.rec32 + ((size_t)jr * D + pprev) * 12) + 2);
         fac_lane = mlp::warp_delay_factor(*a.net, v, rc.x - q0n.x, rc.y - q0n.y, rc.z - q0n.z, bref.x + q2n.x,
                                           bref.y + q2n.y, bref.z + q2n.z, q2n.x - q2p.x, q2n.y - q2p.y,
-                                          q2n.z - q2p.z, invL, (float)D, s_stage[threadIdx.x >> 5]);
+                                          q2n.z - q2p.z, invL, (float)D);
       }
       fac = __shfl_sync(0xffffffffu, fac_lane, l);
     }

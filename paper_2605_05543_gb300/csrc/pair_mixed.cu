@@ -188,11 +188,10 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   __shared__ float4 s_q1[kTile];  // present record (lo, 0) of the tile's sources
   __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position (ext32)
   __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
-  // learned proposal: the network's staging buffer per warp, which afterwards holds the delay factor e^z of
-  // each of the tile's sources (the network's weights are read from global memory: it runs once per 32
-  // sources per warp)
-  static_assert(kTile <= 32 * 8, "the factors of a tile must fit the staging buffer of a warp");
-  __shared__ uint32_t s_stage[PROP == kPropMlp ? kBlock / 32 : 1][32][8];
+  // learned proposal: the delay factor e^z of each of the tile's sources at the block's mean target position
+  // (each warp evaluates the network for 32 of them; its weights are read from global memory)
+  __shared__ float s_fac[PROP == kPropMlp ? kTile : 1];
+  __shared__ float4 s_rc[PROP == kPropMlp ? kBlock / 32 : 1];
 
   __shared__ int s_item;
   const int N = a.N;
@@ -245,9 +244,22 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
     r.idx = i;
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
-  // learned proposal: the mean position of the warp's targets, where the network is evaluated
+  // learned proposal: the mean position of the block's targets, where the network is evaluated
   float3 rc = make_float3(0.f, 0.f, 0.f);
-  if (PROP == kPropMlp) rc = mlp::warp_mean(active, r.h0, r.h1, r.h2);
+  if (PROP == kPropMlp) {
+    const float3 wm = mlp::warp_mean(active, r.h0, r.h1, r.h2);
+    const unsigned na = __popc(__ballot_sync(0xffffffffu, active));
+    if ((threadIdx.x & 31) == 0) s_rc[threadIdx.x >> 5] = make_float4(wm.x * na, wm.y * na, wm.z * na, (float)na);
+    __syncthreads();
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; w++) {
+      const float4 q = s_rc[w];
+      sum = make_float4(sum.x + q.x, sum.y + q.y, sum.z + q.z, sum.w + q.w);
+    }
+    const float ic = sum.w > 0.f ? 1.f / sum.w : 0.f;
+    rc = make_float3(sum.x * ic, sum.y * ic, sum.z * ic);
+  }
   // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
   // so relative velocities are formed from these small differences at full FP32 relative precision)
   float bi0 = 0.f, bi1 = 0.f, bi2 = 0.f;
@@ -282,28 +294,20 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
     }
     __syncthreads();
     if (PROP == kPropMlp) {
-      // the network for the tile's sources, 32 at a time, at the warp's mean target position; the factors
-      // then replace the staging buffer of the warp
-      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      float fac[kTile / 32];
-#pragma unroll
-      for (int g = 0; g < kTile / 32; g++) {
-        const int jj = 32 * g + lane;
-        const bool v = jj < tn;
-        const int jr = tile + (v ? jj : 0);
-        const float4 g0 = s_q0[v ? jj : 0], g2 = s_q2[v ? jj : 0];
+      // the network for the tile's sources at the block's mean target position: warp w takes sources
+      // 32 w .. 32 w + 31, one per lane (tiles hold 32 sources per warp of the block)
+      const int jl = 32 * (threadIdx.x >> 5) + (threadIdx.x & 31);
+      if (32 * (threadIdx.x >> 5) < tn) {
+        const bool v = jl < tn;
+        const int jr = tile + (v ? jl : 0);
+        const float4 g0 = s_q0[v ? jl : 0], g2 = s_q2[v ? jl : 0];
         const float4 q2n = __ldg(a.rec32 + ((size_t)jr * D + pn) * 3 + 2);
         const float4 q2p = __ldg(a.rec32 + ((size_t)jr * D + pprev) * 3 + 2);
-        fac[g] = 32 * g < tn ? mlp::warp_delay_factor(*a.net, v, rc.x - g0.x, rc.y - g0.y, rc.z - g0.z, g2.x, g2.y,
-                                                       g2.z, q2n.x - q2p.x, q2n.y - q2p.y, q2n.z - q2p.z, invL,
-                                                       (float)D, s_stage[w])
-                             : 1.f;
+        const float fac = mlp::warp_delay_factor(*a.net, v, rc.x - g0.x, rc.y - g0.y, rc.z - g0.z, g2.x, g2.y, g2.z,
+                                                 q2n.x - q2p.x, q2n.y - q2p.y, q2n.z - q2p.z, invL, (float)D);
+        if (v) s_fac[jl] = fac;
       }
-      __syncwarp();
-      float* s_fac = reinterpret_cast<float*>(s_stage[w]);
-#pragma unroll
-      for (int g = 0; g < kTile / 32; g++) s_fac[32 * g + lane] = fac[g];
-      __syncwarp();
+      __syncthreads();
     }
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -355,9 +359,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         } else {
           // the uniform-motion delay, scaled by the network's factor for this warp and source (learned
           // proposal)
-          const float sc =
-              closed_form_ctau(r, s_q0[jj], s_q2[jj]) *
-              (PROP == kPropMlp ? inv_cdt * reinterpret_cast<const float*>(s_stage[threadIdx.x >> 5])[jj] : inv_cdt);
+          const float sc = closed_form_ctau(r, s_q0[jj], s_q2[jj]) * (PROP == kPropMlp ? inv_cdt * s_fac[jj] : inv_cdt);
           const int lraw = guessed_offset(sc, win.nw, nw1);
           const int lg = max(lraw, 0);
           pA = win.phys(lg);
