@@ -84,6 +84,7 @@ struct emppp_ctx {
   // proposal network image (EMPPP_PROPOSAL_MLP)
   void* mlp_image = nullptr;
   bool has_mlp = false;
+  long long fac_count = 0;  // delay factors of the learned proposal (mixed path), all bunches
   // spatial target order of the mixed path
   unsigned* ord_key = nullptr;
   int* order = nullptr;
@@ -412,6 +413,11 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
     NvtxRange r("emppp:pair_fields");
+    if (h->opt.precision == EMPPP_MIXED && h->opt.proposal == EMPPP_PROPOSAL_MLP) {
+      // the learned proposal's delay factors of every (target group, source) pair
+      CU(launch_mlp_factors(h->ds, ordered ? h->order : nullptr, h->stream));
+      k += 1;
+    }
     if (h->opt.precision == EMPPP_MIXED)
       CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream));
     else
@@ -517,11 +523,18 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   c->hb.resize(nbunch);
   c->hs.resize(nbunch);
   std::vector<int> bunch_of((size_t)n);
-  long long off = 0;
+  long long off = 0, fac_off = 0;
+  int grp_off = 0;
   for (int b = 0; b < nbunch; b++) {
     memset(&c->hb[b], 0, sizeof(BunchDesc));
     c->hb[b].off = off;
     c->hb[b].n = (int)nper[b];
+    // learned proposal: target groups of the bunch and its delay factors [groups][n]
+    const int groups = (int)((nper[b] + kFacGroup - 1) / kFacGroup);
+    c->hb[b].grp_off = grp_off;
+    c->hb[b].fac_off = fac_off;
+    grp_off += groups;
+    fac_off += (long long)groups * nper[b];
     if (nper[b] > c->max_bunch) c->max_bunch = nper[b];
     for (long long k = 0; k < nper[b]; k++) bunch_of[(size_t)(off + k)] = b;
     off += nper[b];
@@ -530,6 +543,9 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   s.N = n;
   s.D = history_depth;
   s.nbunch = nbunch;
+  s.ngroups = grp_off;
+  s.mlp_fac = nullptr;  // allocated by the first emppp_set_proposal
+  c->fac_count = fac_off;
   const size_t N = (size_t)n, D = (size_t)history_depth;
   {
     // partial sums of up to 64 source chunks within 1 GiB, or up to 256 chunks for small systems, whose
@@ -1001,6 +1017,10 @@ emppp_status enqueue_fields(emppp_handle h, int* dump = nullptr) {
   const bool ordered = h->target_order != 0;
   if (ordered) CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->stream));
   if (h->opt.precision == EMPPP_MIXED) {
+    if (h->opt.proposal == EMPPP_PROPOSAL_MLP) {
+      CU(launch_mlp_factors(h->ds, ordered ? h->order : nullptr, h->stream));
+      h->launches += 1;
+    }
     CU(launch_pair_mixed(h->ds, ordered ? h->order : nullptr, h->opt.proposal, h->adapt, h->launch, h->stream,
                          dump));
   } else {
@@ -1206,6 +1226,11 @@ EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, i
   emppp_status st = check_handle(h);
   if (st != EMPPP_OK) return st;
   if (!params) return fail(EMPPP_ERR_ARG, "params is NULL");
+  if (!h->ds.mlp_fac && h->fac_count > 0) {
+    // the delay factors of the mixed path's learned proposal: one per (target group, source) pair
+    if ((st = dalloc(h, &h->ds.mlp_fac, (size_t)h->fac_count)) != EMPPP_OK) return st;
+    invalidate_graph(h);
+  }
   float* dparams = nullptr;
   if (cudaMalloc(&dparams, sizeof(float) * EMPPP_MLP_NUM_PARAMS) != cudaSuccess) {
     cudaGetLastError();

@@ -81,10 +81,15 @@ struct SlotTables {
 struct BunchDesc {
   long long off;       // first particle
   int n;               // particles
-  int pad_;
+  int grp_off;         // learned proposal: first target group of the bunch (groups of kFacGroup targets)
+  long long fac_off;   // learned proposal: first delay factor of the bunch ([groups][n] per bunch)
   double origin[3];    // origin of the FP32 hi/lo position split
   double beta_ref[3];  // reference velocity / c of the FP32 velocities
 };
+
+// learned proposal, mixed path: targets per group that share one delay factor per source (a multiple of
+// every tile shape's targets per block)
+constexpr int kFacGroup = 512;
 
 // Work split of the persistent pair kernels, per bunch: items are (source chunk, target tile of the
 // tile shape's targets per block)
@@ -124,6 +129,10 @@ struct DeviceState {
   int* err;
   double* bsum;     // [nbunch][4] per-bunch reductions (weighted position sums and weight)
   const void* mlp_image;  // BF16 image of the proposal network (EMPPP_PROPOSAL_MLP), or null
+  // learned proposal, mixed path: the delay factor e^z of each (target group, source) pair of each bunch,
+  // [groups_b][n_b] from BunchDesc::fac_off, written by the factor kernel before each pair evaluation
+  float* mlp_fac;
+  int ngroups;  // target groups of all bunches
   // [N][3] FP32 hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) relative to the bunch origin (the end of the
   // last history segment of eq:linear, from which the mixed path forms near-field retarded points), and
   // w_{k0} + v_{k0} (t_n - t_{k0}) - w_n (where the out-of-history line of eq:linear2 is at t_n)
@@ -251,6 +260,8 @@ cudaError_t launch_build_image(const float* params, void* image, cudaStream_t st
 cudaError_t launch_sample(const DeviceState& s, const int* pairs, long long m, float* feat, double* delay, float* zt,
                           cudaStream_t st);
 cudaError_t launch_mlp_forward(const void* image, const float* X, long long m, float* z, int mode, cudaStream_t st);
+// delay factors of the learned proposal (mixed path) for the present state, targets in `order` (or index order)
+cudaError_t launch_mlp_factors(const DeviceState& s, const int* order, cudaStream_t st);
 cudaError_t launch_mlp_train_pass(const void* image, const float* X, const float* T, long long row0, long long rows,
                                   float norm, float* grad, float* loss, int num_sms, cudaStream_t st);
 cudaError_t launch_adam(float* p, const float* grad, float* m1, float* m2, float lr, float b1, float b2, float eps,

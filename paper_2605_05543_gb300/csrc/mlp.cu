@@ -416,6 +416,70 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gra
   p[k] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
 }
 
+// ---------------------------------------------------------------------------------------------
+// delay factors of the mixed path's learned proposal
+// ---------------------------------------------------------------------------------------------
+// One block per target group (kFacGroup targets in the order the pair kernel takes them): the group's mean
+// present position r_c, then e^z of the network for every source j of the bunch at r_c (features from the
+// source's present record and its velocity one slot earlier, in the FP32 shadow ring), one source per lane.
+constexpr int kFacThreads = 256;
+
+__global__ void __launch_bounds__(kFacThreads) factor_kernel(DeviceState s, const int* __restrict__ order) {
+  __shared__ float4 s_part[kFacThreads / 32];
+  const int gall = blockIdx.x;
+  int b = 0;
+  while (b + 1 < s.nbunch && s.bunches[b + 1].grp_off <= gall) b++;
+  const BunchDesc& bd = s.bunches[b];
+  const int g = gall - bd.grp_off;
+  const int t0 = g * kFacGroup, t1 = min(bd.n, t0 + kFacGroup);
+  const StepState st = *s.state;
+  const int D = s.D, pn = st.pn;
+  const int pprev = st.n > st.k0 ? (pn == 0 ? D - 1 : pn - 1) : pn;  // slot n - 1 (or n)
+  const float invL = (float)(1.0 / (kC * st.dt * D));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // mean present position of the group (hi parts, relative to the bunch's split origin)
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  for (int t = t0 + threadIdx.x; t < t1; t += kFacThreads) {
+    const long long i = order ? order[bd.off + t] : bd.off + t;
+    const float4 q = __ldg(reinterpret_cast<const float4*>(s.rec32) + ((size_t)i * D + pn) * 3);
+    sx += q.x;
+    sy += q.y;
+    sz += q.z;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    sz += __shfl_xor_sync(0xffffffffu, sz, o);
+  }
+  if (lane == 0) s_part[w] = make_float4(sx, sy, sz, 0.f);
+  __syncthreads();
+  float3 rc = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < kFacThreads / 32; k++) {
+    rc.x += s_part[k].x;
+    rc.y += s_part[k].y;
+    rc.z += s_part[k].z;
+  }
+  const float inv = 1.f / (float)max(t1 - t0, 1);
+  rc = make_float3(rc.x * inv, rc.y * inv, rc.z * inv);
+  const float b0 = (float)bd.beta_ref[0], b1 = (float)bd.beta_ref[1], b2 = (float)bd.beta_ref[2];
+  const InferImage& net = *infer_image(s.mlp_image);
+  float* __restrict__ fac = s.mlp_fac + bd.fac_off + (size_t)g * bd.n;
+  // warp w takes sources 32 w, 32 w + 256, ...: the loop bounds are the same for every lane (converged)
+  for (int j0 = 32 * w; j0 < bd.n; j0 += kFacThreads) {
+    const int jl = j0 + lane;
+    const bool v = jl < bd.n;
+    const size_t j = (size_t)bd.off + (v ? jl : j0);
+    const float4* q = reinterpret_cast<const float4*>(s.rec32) + (j * D + pn) * 3;
+    const float4 q0n = __ldg(q), q2n = __ldg(q + 2);
+    const float4 q2p = __ldg(reinterpret_cast<const float4*>(s.rec32) + (j * D + pprev) * 3 + 2);
+    const float f = warp_delay_factor(net, v, rc.x - q0n.x, rc.y - q0n.y, rc.z - q0n.z, b0 + q2n.x, b1 + q2n.y,
+                                      b2 + q2n.z, q2n.x - q2p.x, q2n.y - q2p.y, q2n.z - q2p.z, invL, (float)D);
+    if (v) fac[jl] = f;
+  }
+}
+
 }  // namespace
 
 namespace emppp {
@@ -432,6 +496,12 @@ cudaError_t launch_sample(const DeviceState& s, const int* pairs, long long m, f
                           cudaStream_t st) {
   if (m <= 0) return cudaSuccess;
   sample_kernel<<<(unsigned)((m + 127) / 128), 128, 0, st>>>(s, pairs, m, feat, delay, zt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_factors(const DeviceState& s, const int* order, cudaStream_t st) {
+  if (s.ngroups <= 0 || !s.mlp_fac) return cudaSuccess;
+  factor_kernel<<<s.ngroups, kFacThreads, 0, st>>>(s, order);
   return cudaGetLastError();
 }
 

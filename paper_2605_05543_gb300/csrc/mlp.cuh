@@ -1,10 +1,11 @@
 // Learned retarded-time proposal: a 10-64-64-1 perceptron with SiLU activations that predicts, for a
 // target and a source, the correction z = log(tau / tau_u) of the delay tau = t - t_r over the delay
 // tau_u that the source's uniform motion from its present record gives (the closed-form guess; the
-// network learns what the source's acceleration history does to it). The pair kernels evaluate the
-// network once per (block, source) on the mixed path and once per (warp, source) on the FP64 path, at the
-// mean position of the block's or warp's targets (which lie close together in the spatial target order),
-// and every pair scales its own uniform-motion delay by e^z; the
+// network learns what the source's acceleration history does to it). The network is evaluated once per
+// (group of 512 targets, source) and step on the mixed path (a kernel of its own, before the pair kernel)
+// and once per (warp, source) on the FP64 path, at the mean position of the group's or warp's targets
+// (which lie close together in the spatial target order), and every pair scales its own uniform-motion
+// delay by e^z; the
 // retarded-time search then starts from the slot that delay points at and finishes with the same guarded
 // search as the closed-form proposal, so the bracket (and every field) is the one of the paper's search
 // whatever the network predicts.

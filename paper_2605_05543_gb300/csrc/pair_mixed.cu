@@ -29,7 +29,6 @@
 // memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
 // source are close together in the source-major FP32 shadow ring.
 #include "emppp_internal.cuh"
-#include "mlp.cuh"
 #include "shadow.cuh"
 
 namespace emppp {
@@ -66,7 +65,7 @@ struct MixedArgs {
   const BunchSched* __restrict__ sched;
   int nitems;  // work items of all bunches
   int* work;   // work-item counter (zero at launch)
-  const mlp::InferImage* __restrict__ net;  // proposal network, inference form (EMPPP_PROPOSAL_MLP)
+  const float* __restrict__ fac;  // learned proposal: delay factors [groups][n] per bunch (factor kernel)
   unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
   float eta_allow;
   const float4* __restrict__ ext32;  // [N][3] per source: segment end hi/lo, out-of-history line offset
@@ -188,10 +187,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   __shared__ float4 s_q1[kTile];  // present record (lo, 0) of the tile's sources
   __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position (ext32)
   __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
-  // learned proposal: the delay factor e^z of each of the tile's sources at the block's mean target position
-  // (each warp evaluates the network for 32 of them; its weights are read from global memory)
+  // learned proposal: the delay factor e^z of each of the tile's sources for the block's target group
   __shared__ float s_fac[PROP == kPropMlp ? kTile : 1];
-  __shared__ float4 s_rc[PROP == kPropMlp ? kBlock / 32 : 1];
 
   __shared__ int s_item;
   const int N = a.N;
@@ -205,8 +202,6 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   win.nw = (int)(n_abs - k0_abs) + 1;
   const int pn = a.state->pn;
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
-  const int pprev = win.nw > 1 ? win.phys(win.nw - 2) : pn;  // slot n - 1 (or n)
-  const float invL = (float)(1.0 / (kC * a.state->dt * D));
   const float nw1 = (float)(win.nw - 1);  // a guessed delay of at least nw - 1 steps is out of history
 
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
@@ -244,22 +239,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
     r.idx = i;
     r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
   }
-  // learned proposal: the mean position of the block's targets, where the network is evaluated
-  float3 rc = make_float3(0.f, 0.f, 0.f);
-  if (PROP == kPropMlp) {
-    const float3 wm = mlp::warp_mean(active, r.h0, r.h1, r.h2);
-    const unsigned na = __popc(__ballot_sync(0xffffffffu, active));
-    if ((threadIdx.x & 31) == 0) s_rc[threadIdx.x >> 5] = make_float4(wm.x * na, wm.y * na, wm.z * na, (float)na);
-    __syncthreads();
-    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int w = 0; w < kBlock / 32; w++) {
-      const float4 q = s_rc[w];
-      sum = make_float4(sum.x + q.x, sum.y + q.y, sum.z + q.z, sum.w + q.w);
-    }
-    const float ic = sum.w > 0.f ? 1.f / sum.w : 0.f;
-    rc = make_float3(sum.x * ic, sum.y * ic, sum.z * ic);
-  }
+  // learned proposal: the delay factors of this target tile's group (kFacGroup targets, a multiple of the
+  // tile), one per source of the bunch
+  const float* fac_row = PROP == kPropMlp ? a.fac + bd.fac_off + (size_t)((tb * kBlock) / kFacGroup) * bd.n : nullptr;
   // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
   // so relative velocities are formed from these small differences at full FP32 relative precision)
   float bi0 = 0.f, bi1 = 0.f, bi2 = 0.f;
@@ -291,24 +273,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       s_kq[threadIdx.x] = a.kq32[j];
       s_q1[threadIdx.x] = q[1];
       s_x[threadIdx.x] = __ldg(a.ext32 + 3 * j + 2);
+      if (PROP == kPropMlp) s_fac[threadIdx.x] = __ldg(fac_row + (j - boff));
     }
     __syncthreads();
-    if (PROP == kPropMlp) {
-      // the network for the tile's sources at the block's mean target position: warp w takes sources
-      // 32 w .. 32 w + 31, one per lane (tiles hold 32 sources per warp of the block)
-      const int jl = 32 * (threadIdx.x >> 5) + (threadIdx.x & 31);
-      if (32 * (threadIdx.x >> 5) < tn) {
-        const bool v = jl < tn;
-        const int jr = tile + (v ? jl : 0);
-        const float4 g0 = s_q0[v ? jl : 0], g2 = s_q2[v ? jl : 0];
-        const float4 q2n = __ldg(a.rec32 + ((size_t)jr * D + pn) * 3 + 2);
-        const float4 q2p = __ldg(a.rec32 + ((size_t)jr * D + pprev) * 3 + 2);
-        const float fac = mlp::warp_delay_factor(*a.net, v, rc.x - g0.x, rc.y - g0.y, rc.z - g0.z, g2.x, g2.y, g2.z,
-                                                 q2n.x - q2p.x, q2n.y - q2p.y, q2n.z - q2p.z, invL, (float)D);
-        if (v) s_fac[jl] = fac;
-      }
-      __syncthreads();
-    }
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
@@ -759,7 +726,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.sched = s.sched;
   a.nitems = pl.nitems;
   a.work = s.work;
-  a.net = s.mlp_image ? mlp::infer_image(s.mlp_image) : nullptr;
+  a.fac = s.mlp_fac;
   a.scale = s.scale;
   a.eta_allow = (float)ap.eta_allow;
   a.ext32 = s.ext32;

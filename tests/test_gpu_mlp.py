@@ -234,3 +234,47 @@ def test_mlp_proposal_needs_a_network():
             s.set_proposal(np.zeros(10, dtype=np.float32))
         with pytest.raises(emppp.EmpppError):
             s.sample_delays(np.array([[3, 3]], dtype=np.int32))
+
+
+def test_network_trained_out_of_sample_gains_over_bisection():
+    """What the trained network gains over the method without it, out of sample: trained on (feature, delay)
+    samples of the N = 4096 uniform-field run (sigma = 10 um, B = 5e-5 T along x, depth 512, from t = 0), then
+    used on another bunch (N = 8192, sigma = 20 um, seeded step-200 history, depth 1024). Over the same step
+    from the same state: fields identical to the paper's bisection (the brackets are the bisection's), node
+    tests per pair far below bisection's and within 1 % of the closed-form guess (which sits at the floor of
+    one test beyond the history and two for a bracket)."""
+    rng = np.random.default_rng(60)
+    N2, D2 = 4096, 512
+    b = inputs.gaussian_bunch(N2, 10e-6, 3.0, seed=0)
+    feats, zs = [], []
+    with emppp.Solver(N2, D2, DT, precision="mixed", proposal="closed_form") as s:
+        s.set_particles(b.x.copy(), b.u.copy())
+        n = 0
+        for k in (64, 256, 511):
+            s.step(k - n, emppp.bext_uniform((5e-5, 0.0, 0.0)))
+            n = k
+            f, _, z = s.sample_delays(_pairs(N2, 1 << 17, int(rng.integers(1 << 30))))
+            feats.append(f)
+            zs.append(z)
+    X, Z = np.concatenate(feats), np.concatenate(zs)
+    p, losses = emppp.mlp_train(inputs.mlp_init_params(1), X, Z, epochs=3, batch=4096, lr=2e-3, lr_final=1e-5)
+    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0]
+    N, n0, D = 8192, 200, 1024
+    h = history_case(N, n0, sigma=20e-6, seed=61)
+    T, W, V, u = window(h, D)
+    out = {}
+    for prop in ("bisect", "closed_form", "mlp"):
+        with emppp.Solver(N, D, DT, precision="mixed", proposal=prop) as s:
+            s.set_history(h.n, T, W, V, u)
+            if prop == "mlp":
+                s.set_proposal(p)
+            s.step(1)
+            E, B = s.get_fields()
+            st = s.stats()
+        out[prop] = (E, B, st["node_tests"] / st["pairs"])
+    for prop in ("closed_form", "mlp"):
+        assert np.array_equal(out[prop][0], out["bisect"][0]) and np.array_equal(out[prop][1], out["bisect"][1])
+    tb, tc, tm = out["bisect"][2], out["closed_form"][2], out["mlp"][2]
+    print(f"out of sample: node tests per pair bisection {tb:.4f}, closed form {tc:.4f}, network {tm:.4f}")
+    assert tm < 0.5 * tb
+    assert tm <= 1.01 * tc
