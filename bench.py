@@ -77,7 +77,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default work split and tile shape (no emppp_autotune before the timed steps)")
     ap.add_argument("--shape", default=None,
-                    help="targets per block and sources per partial sum, e.g. 128,32 (no emppp_autotune)")
+                    help="targets per block, sources per partial sum and optionally 1 for the staged history window, e.g. 128,32 or 128,32,1 (no emppp_autotune)")
     ap.add_argument("--no-run-leg", action="store_true",
                     help="skip the stated run of the bunch from t = 0 (500 steps of its own dynamics)")
     ap.add_argument("--no-fp64-compare", action="store_true",
@@ -208,6 +208,14 @@ def workload_name(wl):
     if wl["N"] == WL["N"] and wl["n0"] == WL["n0"] and wl["depth"] == WL["depth"]:
         return WORKLOAD_NAME
     return f"reduced case N={wl['N']} depth={wl['depth']} history slots={wl['n0'] + 1}"
+
+
+def shape_key(tuning):
+    """(targets per block, sources per sum[, window slots]) of a tuning, None for the default shape."""
+    if not tuning:
+        return None
+    k = (tuning["targets_per_block"], tuning["sources_per_sum"])
+    return k + (tuning["history_window"],) if tuning.get("history_window") else k
 
 
 def kernel_traffic_record(path_name, proposal, shape=None):
@@ -342,7 +350,8 @@ def autotune_state(path, proposal, wl, h, win, net=None):
         if net is not None:
             s.set_proposal(net)
         rep = s.autotune()
-    best = {k: rep["best"][k] for k in ("items_per_block", "target_order", "targets_per_block", "sources_per_sum")}
+    best = {k: rep["best"][k] for k in ("items_per_block", "target_order", "targets_per_block", "sources_per_sum",
+                                        "history_window")}
     return best, len(rep["candidates"])
 
 
@@ -462,8 +471,9 @@ def run_ours(args):
     # the work split and tile shape for this state and path, chosen once (closed-form instance) and used by
     # every proposal, so that their fields stay comparable bit for bit
     if args.shape:
-        tpb, sps = (int(v) for v in args.shape.split(","))
-        tuning, ncand = dict(items_per_block=16, target_order=1, targets_per_block=tpb, sources_per_sum=sps), 0
+        tpb, sps, *hw = (int(v) for v in args.shape.split(","))
+        tuning, ncand = dict(items_per_block=16, target_order=1, targets_per_block=tpb, sources_per_sum=sps,
+                             history_window=hw[0] if hw else 0), 0
     else:
         tuning, ncand = (None, 0) if args.no_tune else autotune_state(args.path, "closed_form", wl, h, win)
     res = run_path(args, args.path, args.proposal, steps, warmup, wl, h, win, rank, e2e=not args.no_e2e,
@@ -489,9 +499,7 @@ def run_ours(args):
                    "l2": "inputs larger than L2: 0.79 GB of history window read per step (L2 129 MB)"},
         "roofline": {"bound": "alu", "kernel": "pair_fp64_kernel" if args.path == "fp64" else "pair_mixed_kernel",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": kernel_traffic_record(
-                         args.path, args.proposal,
-                         (tuning["targets_per_block"], tuning["sources_per_sum"]) if tuning else None),
+                     "traffic": kernel_traffic_record(args.path, args.proposal, shape_key(tuning)),
                      "peak_note": ("nominal FP64: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz" if args.path == "fp64"
                                    else "nominal FP32: 152 SM x 128 FFMA/clk x 2 flop x 2.07 GHz"),
                      "peak_measured": peak_meas, "frac_of_measured": achieved / peak_meas,
@@ -601,7 +609,7 @@ def run_batch(args):
         # the tuner runs on the first steps' state, where every pair is older than the history and the
         # target order makes no difference; the spatial order is kept for the deep histories that follow
         b = tune["best"]
-        s.set_tuning(b["items_per_block"], 1, b["targets_per_block"], b["sources_per_sum"])
+        s.set_tuning(b["items_per_block"], 1, b["targets_per_block"], b["sources_per_sum"], b["history_window"])
         s.synchronize()
         s.reset_stats()
         barrier()

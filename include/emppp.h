@@ -43,8 +43,8 @@ typedef enum {
   EMPPP_ERR_ARG = -1,     /* bad handle, size, pointer or option */
   EMPPP_ERR_CUDA = -2,    /* a CUDA runtime call failed (text in emppp_last_error) */
   EMPPP_ERR_NUMERIC = -3, /* device-side numeric fault in a previous step */
-  EMPPP_ERR_TIMEOUT = -4, /* reserved for a bounded device wait that gives up; no kernel of this version
-                             waits on another, so no call returns it */
+  EMPPP_ERR_TIMEOUT = -4, /* a bounded device wait gave up: a warp's wait on its staged history window
+                             (emppp_set_wait_limit); the fields of that step are still exact */
   EMPPP_ERR_STATE = -5,   /* call out of order (e.g. step before set_particles) */
   EMPPP_ERR_OOM = -6      /* device allocation failed */
 } emppp_status;
@@ -132,14 +132,19 @@ typedef struct {
  * mixed path, sources_per_sum sources per FP32 partial sum before the compensated addition (8, 16 or 32;
  * 16 and 32 only at 128 targets per block). The FP64 path ignores sources_per_sum. The shape changes the order
  * of each target's sum, so fields of different shapes agree within rounding, not bit for bit; the
- * adaptive time step and the comparison variants run the default shape (128, 8). Chosen by emppp_autotune
- * or set with emppp_set_tuning. */
+ * adaptive time step and the comparison variants run the default shape (128, 8). history_window nonzero
+ * (mixed path, shape (128, 32), closed-form or MLP proposal) has each warp copy, one source ahead, the
+ * run of history slots its 32 targets' guessed brackets of the next source fall in (at most 32 slots) from
+ * the FP32 ring into shared memory by bulk copy, and read those brackets' records there; it changes where
+ * records are read, not the arithmetic or the work split, so its fields equal those of (128, 32) without
+ * it bit for bit. Chosen by emppp_autotune or set with emppp_set_tuning. */
 typedef struct {
   int32_t items_per_block;   /* default 16 */
   int32_t target_order;      /* default 1 */
   double ms;                 /* measured time of one field evaluation (emppp_autotune), else 0 */
   int32_t targets_per_block; /* default 128 (0 in emppp_set_tuning: 128) */
   int32_t sources_per_sum;   /* default 8 (0 in emppp_set_tuning: 8) */
+  int32_t history_window;    /* default 0; slots of the staged window per warp and source when on */
 } emppp_tuning;
 
 typedef struct {
@@ -253,8 +258,16 @@ EMPPP_API emppp_status emppp_bracket_dump(emppp_handle h, int32_t* brackets, int
 
 /* Sets the work split and tile shape directly (e.g. a tuning found earlier). items_per_block in 1..256,
  * targets_per_block in {0 (= 128), 64, 128, 256}, sources_per_sum in {0 (= 8), 8, 16, 32}, 16 and 32 only
- * with 128 targets per block; EMPPP_ERR_ARG otherwise. */
+ * with 128 targets per block, history_window nonzero only with (128, 32); EMPPP_ERR_ARG otherwise.
+ * history_window on the FP64 path or with the bisection proposal reads the ring directly (no window). */
 EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning);
+
+/* Probes of the bounded wait of a warp on its staged history window (history_window on; default 65536, each
+ * probe may suspend the thread for a short hardware-defined time). A wait that gives up leaves that warp
+ * gathering the records from the ring for the rest of the launch, so the fields are unchanged, and the
+ * device error word records it: the next call that reads it returns EMPPP_ERR_TIMEOUT. probes = 0 makes
+ * every such wait give up at once (a test of that path). EMPPP_ERR_ARG for probes < 0. */
+EMPPP_API emppp_status emppp_set_wait_limit(emppp_handle h, int32_t probes);
 
 /* Replaces the options for later steps. EMPPP_ERR_STATE for a comparison variant (MIDPOINT, HALF_STEP)
  * while the adaptive time step is on. */

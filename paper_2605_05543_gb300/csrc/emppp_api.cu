@@ -199,11 +199,14 @@ emppp_status update_schedule(emppp_handle c) {
   // The source chunking (and with it the order of every target's sum) follows the closed-form
   // variant's residency whatever the proposal, so that all proposals give identical fields; only the
   // number of persistent blocks follows the variant that runs.
-  int& nref = mixed ? c->blocks_mixed[ad][EMPPP_PROPOSAL_CLOSED_FORM][shp]
-                    : c->blocks_fp64[ad][EMPPP_PROPOSAL_CLOSED_FORM][shp];
+  // The history-window shape splits the work like the same shape without the window, so that their fields
+  // are identical.
+  const int shp_ref = shape_win(shp) > 0 ? 4 : shp;
+  int& nref = mixed ? c->blocks_mixed[ad][EMPPP_PROPOSAL_CLOSED_FORM][shp_ref]
+                    : c->blocks_fp64[ad][EMPPP_PROPOSAL_CLOSED_FORM][shp_ref];
   if (nref <= 0)
-    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM, ad, shp)
-                 : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM, ad, shp);
+    nref = mixed ? max_blocks_pair_mixed(EMPPP_PROPOSAL_CLOSED_FORM, ad, shp_ref)
+                 : max_blocks_pair_fp64(EMPPP_PROPOSAL_CLOSED_FORM, ad, shp_ref);
   // resident blocks in units of 128 threads, so that the item count per SM does not depend on the shape
   const long long R = (long long)nb * c->num_sms;
   const long long Rsched = (long long)nref * c->num_sms * TB / 128;
@@ -286,6 +289,12 @@ emppp_status read_err(emppp_handle h) {
   int herr = 0;
   CU(cudaMemcpyAsync(&herr, h->ds.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CU(cudaStreamSynchronize(h->stream));
+  if (herr == kErrTimeout) {
+    CU(cudaMemsetAsync(h->ds.err, 0, sizeof(int), h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return fail(EMPPP_ERR_TIMEOUT, "a warp's wait on its staged history window gave up (the records were "
+                "gathered from the ring instead; the fields are exact)");
+  }
   if (herr) {
     return fail(EMPPP_ERR_NUMERIC,
                 "device numeric fault (bits 0x%x: 1 = negative discriminant or |v| >= c, 2 = coincident pair, "
@@ -1032,12 +1041,12 @@ emppp_status enqueue_fields(emppp_handle h, int* dump = nullptr) {
   return EMPPP_OK;
 }
 
-// tile shape of (targets per block, sources per partial sum), -1 if it is none
-static int shape_of(int targets_per_block, int sources_per_sum) {
+// tile shape of (targets per block, sources per partial sum, history window on), -1 if it is none
+static int shape_of(int targets_per_block, int sources_per_sum, int history_window) {
   const int tb = targets_per_block == 0 ? 128 : targets_per_block;
   const int ss = sources_per_sum == 0 ? 8 : sources_per_sum;
   for (int k = 0; k < kNumShapes; k++)
-    if (shape_block(k) == tb && shape_sub(k) == ss) return k;
+    if (shape_block(k) == tb && shape_sub(k) == ss && (shape_win(k) > 0) == (history_window != 0)) return k;
   return -1;
 }
 
@@ -1079,6 +1088,7 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
     c.target_order = order;
     c.targets_per_block = shape_block(shape);
     c.sources_per_sum = shape_sub(shape);
+    c.history_window = shape_win(shape);
     c.ms = best;
     if (best < best_ms) {
       best_ms = best;
@@ -1102,7 +1112,7 @@ EMPPP_API emppp_status emppp_autotune(emppp_handle h, emppp_tuning_report* repor
   const emppp_tuning& b = rep.cand[rep.best];
   h->items_per_block = b.items_per_block;
   h->target_order = b.target_order;
-  h->shape = shape_of(b.targets_per_block, b.sources_per_sum);
+  h->shape = shape_of(b.targets_per_block, b.sources_per_sum, b.history_window);
   invalidate_graph(h);
   if ((st = update_schedule(h)) != EMPPP_OK) return st;
   if ((st = reset_counters(h)) != EMPPP_OK) return st;
@@ -1149,15 +1159,25 @@ EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuni
   if (!tuning || tuning->items_per_block < 1 || tuning->items_per_block > 256 ||
       (tuning->target_order != 0 && tuning->target_order != 1))
     return fail(EMPPP_ERR_ARG, "items_per_block must be in 1..256 and target_order 0 or 1");
-  const int shp = shape_of(tuning->targets_per_block, tuning->sources_per_sum);
+  const int shp = shape_of(tuning->targets_per_block, tuning->sources_per_sum, tuning->history_window);
   if (shp < 0)
-    return fail(EMPPP_ERR_ARG, "tile shape (%d targets per block, %d sources per sum) is not one of (128, 8), "
-                "(64, 8), (256, 8), (128, 16), (128, 32)", tuning->targets_per_block, tuning->sources_per_sum);
+    return fail(EMPPP_ERR_ARG, "tile shape (%d targets per block, %d sources per sum, history window %d) is not one "
+                "of (128, 8), (64, 8), (256, 8), (128, 16), (128, 32) or (128, 32) with the window",
+                tuning->targets_per_block, tuning->sources_per_sum, tuning->history_window);
   h->items_per_block = tuning->items_per_block;
   h->target_order = tuning->target_order;
   h->shape = shp;
   invalidate_graph(h);
   return update_schedule(h);
+}
+
+EMPPP_API emppp_status emppp_set_wait_limit(emppp_handle h, int32_t probes) {
+  emppp_status st = check_handle(h);
+  if (st != EMPPP_OK) return st;
+  if (probes < 0) return fail(EMPPP_ERR_ARG, "probes must be >= 0");
+  h->launch.wait_limit = probes;
+  invalidate_graph(h);
+  return EMPPP_OK;
 }
 
 // ---- learned proposal ------------------------------------------------------------------------

@@ -44,6 +44,7 @@ enum : int {
   kErrDisc = 1,      // negative discriminant or C2 <= 0 in eq:dt (|v| >= c)
   kErrCoincide = 2,  // eta = 0 or eta . v' <= 0
   kErrNonFinite = 4, // non-finite field or state
+  kErrTimeout = 8,   // a bounded wait of a pair kernel on its bulk copies gave up
 };
 
 struct StepState {
@@ -190,17 +191,23 @@ struct BextParams {
 };
 
 // Tile shapes of the pair kernels (emppp_tuning): targets per block, which is also the number of sources
-// a mixed-path block stages per tile, and the mixed path's sources per FP32 partial sum. Shape 0 is the
-// default; the FP64 path runs shapes 3 and 4 as shape 0 (its sums are blocked by 64 sources).
-constexpr int kNumShapes = 5;
+// a mixed-path block stages per tile, the mixed path's sources per FP32 partial sum, and the slots of the
+// history window each warp of a mixed-path block stages per source by bulk copy (0: none). Shape 0 is the
+// default; the FP64 path runs shapes 3 to 5 as shape 0 (its sums are blocked by 64 sources).
+#ifndef EMPPP_WIN_SLOTS
+#define EMPPP_WIN_SLOTS 16
+#endif
+constexpr int kNumShapes = 6;
 __host__ __device__ constexpr int shape_block(int shape) { return shape == 1 ? 64 : (shape == 2 ? 256 : 128); }
-__host__ __device__ constexpr int shape_sub(int shape) { return shape == 3 ? 16 : (shape == 4 ? 32 : 8); }
+__host__ __device__ constexpr int shape_sub(int shape) { return shape == 3 ? 16 : (shape >= 4 ? 32 : 8); }
+__host__ __device__ constexpr int shape_win(int shape) { return shape == 5 ? EMPPP_WIN_SLOTS : 0; }
 
 // launch configuration of a persistent pair kernel
 struct PairLaunch {
   int nitems;  // work items of all bunches
   int grid;    // blocks launched
   int shape;   // tile shape (shape_block(shape) threads per block, targets per work item)
+  int wait_limit = 1 << 16;  // probes of a bounded wait on a staged history window (window shapes)
 };
 
 // item -> (bunch, chunk, target tile): bunches are searched by their first item

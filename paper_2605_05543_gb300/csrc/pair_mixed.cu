@@ -27,7 +27,11 @@
 //             of 128 threads per SM), converted to FP64 at the end.
 // Sources are walked in tiles of kTile whose present records and FP32 charges are staged in shared
 // memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
-// source are close together in the source-major FP32 shadow ring.
+// source are close together in the source-major FP32 shadow ring. The window instance (shape_win)
+// also copies, per warp and one source ahead, the ring slots its lanes' guessed brackets fall in to
+// shared memory by bulk copy (bulk.cuh) and reads the predicted brackets' records there; the search,
+// the arithmetic and the work split are those of the same shape without it, so the fields are too.
+#include "bulk.cuh"
 #include "emppp_internal.cuh"
 #include "shadow.cuh"
 
@@ -70,7 +74,11 @@ struct MixedArgs {
   float eta_allow;
   const float4* __restrict__ ext32;  // [N][3] per source: segment end hi/lo, out-of-history line offset
   int* __restrict__ dump;  // [N][N] bracket of every evaluated pair, 4 (k1 - k0) + branch (DUMP instances only)
+  int wait_limit;          // probes of a bounded wait on a staged history window (window shapes)
 };
+
+// probes of the wait, before a block exits, on a window copy whose own wait gave up
+constexpr int kDrainLimit = 1 << 20;
 
 struct Target {
   float h0, h1, h2, l0, l1, l2;
@@ -181,6 +189,16 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   constexpr int kBlock = shape_block(SHAPE);
   constexpr int kTile = kBlock;
   constexpr int kSub = shape_sub(SHAPE);
+  // history windows (shape_win): one elected lane per warp copies, one source ahead, the slots its lanes'
+  // guessed brackets of the next source fall in from the FP32 shadow ring to shared memory (bulk copy,
+  // two buffers per warp); the lanes whose predicted bracket lies in the window read its two records
+  // there instead of gathering them
+  constexpr bool WIN = shape_win(SHAPE) > 0 && PROP != kPropBisect;
+  constexpr int kWin = WIN ? shape_win(SHAPE) : 1;
+  constexpr int kWarps = kBlock / 32;
+  __shared__ __align__(128) float4 s_win[WIN ? kWarps * 2 * kWin * 3 : 1];
+  __shared__ __align__(8) unsigned long long s_bar[WIN ? kWarps * 2 : 1];
+  __shared__ int2 s_wd[WIN ? kWarps * 2 : 1];  // (first offset, slots) of each staged window
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
   __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
   __shared__ float s_kq[kTile];
@@ -207,6 +225,17 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
   float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
   int errbits = 0;
+  // history windows: phase parity and pending copy of each of the warp's two buffers (warp-uniform), and
+  // whether the warp still stages (a wait that gave up stops it; the pairs then gather from the ring)
+  unsigned wph = 0, wpend = 0;
+  bool wok = true;
+  int g_nxt = -1;  // the lane's guessed offset for the next source (-1: out of history)
+  if (WIN) {
+    if (threadIdx.x < kWarps * 2) {
+      mbar_init(smem_u32(&s_bar[threadIdx.x]), 1);
+      fence_mbar_init();
+    }
+  }
 
   // persistent blocks pull (source chunk, target tile) items, chunk-major, until none is left
   for (;;) {
@@ -242,6 +271,11 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   // learned proposal: the delay factors of this target tile's group (kFacGroup targets, a multiple of the
   // tile), one per source of the bunch
   const float* fac_row = PROP == kPropMlp ? a.fac + bd.fac_off + (size_t)((tb * kBlock) / kFacGroup) * bd.n : nullptr;
+  // the lane's guessed older-node offset for staged source jj of the tile (-1: predicted out of history)
+  auto guess_of = [&](int jj) -> int {
+    const float sc = closed_form_ctau(r, s_q0[jj], s_q2[jj]) * (PROP == kPropMlp ? inv_cdt * s_fac[jj] : inv_cdt);
+    return guessed_offset(sc, win.nw, nw1);
+  };
   // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
   // so relative velocities are formed from these small differences at full FP32 relative precision)
   float bi0 = 0.f, bi1 = 0.f, bi2 = 0.f;
@@ -276,11 +310,65 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       if (PROP == kPropMlp) s_fac[threadIdx.x] = __ldg(fac_row + (j - boff));
     }
     __syncthreads();
+    // window of staged source jn into buffer sb: the offsets lo .. hi + 1 of the guessed brackets [lg, lg + 1]
+    // of the warp's lanes that predict one in history, at most kWin slots from lo (one or two contiguous
+    // runs of the ring)
+    auto win_issue = [&](int jn, int g, int sb) {
+      const bool want = wok && active && (tile + jn != i) && g >= 0;
+      const int lo = __reduce_min_sync(0xffffffffu, want ? g : 0x7fffffff);
+      const int hi = __reduce_max_sync(0xffffffffu, want ? g : -1);
+      if (lo > hi) return;
+      const int nsl = min(hi + 2 - lo, kWin);
+      if ((threadIdx.x & 31) == 0) {
+        const int wb = (threadIdx.x >> 5) * 2 + sb;
+        s_wd[wb] = make_int2(lo, nsl);
+        const uint32_t bar = smem_u32(&s_bar[wb]);
+        mbar_arrive_expect_tx(bar, (uint32_t)nsl * 48u);
+        const int p = win.phys(lo);
+        const int n1 = min(nsl, D - p);
+        const size_t base = (size_t)(tile + jn) * D;
+        float4* dst = s_win + (size_t)wb * kWin * 3;
+        bulk_copy_g2s(smem_u32(dst), a.rec32 + (base + p) * 3, (uint32_t)n1 * 48u, bar);
+        if (nsl > n1) bulk_copy_g2s(smem_u32(dst + 3 * n1), a.rec32 + base * 3, (uint32_t)(nsl - n1) * 48u, bar);
+      }
+      wpend |= 1u << sb;
+    };
+    if (WIN && win.nw > 1) {
+      g_nxt = guess_of(0);
+      win_issue(0, g_nxt, 0);
+    }
     for (int jj0 = 0; jj0 < tn; jj0 += kSub) {
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
-      for (int jj = jj0; active && jj < jend; ++jj) {
+      for (int jj = jj0; (WIN || active) && jj < jend; ++jj) {
         const int j = tile + jj;
+        // history window of this source (WIN): guessed offset, first offset and slots of the staged run
+        int g_cur = -1, w_lo = 0, w_n = 1;
+        const int sb = jj & 1;
+        if (WIN && win.nw > 1) {
+          g_cur = g_nxt;
+          __syncwarp();  // every lane is done with the buffer the next copy overwrites
+          if (jj + 1 < tn) {
+            g_nxt = guess_of(jj + 1);
+            win_issue(jj + 1, g_nxt, sb ^ 1);
+          }
+          if (wpend & (1u << sb)) {
+            const uint32_t bar = smem_u32(&s_bar[(threadIdx.x >> 5) * 2 + sb]);
+            const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(bar, (wph >> sb) & 1u, a.wait_limit));
+            if (ok) {
+              wph ^= 1u << sb;
+              wpend &= ~(1u << sb);
+              const int2 wd = s_wd[(threadIdx.x >> 5) * 2 + sb];
+              w_lo = wd.x;
+              w_n = wd.y;
+            } else {
+              // the copy stays pending (drained before the block exits); no further windows
+              errbits |= kErrTimeout;
+              wok = false;
+            }
+          }
+        }
+        if (WIN && !active) continue;
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
@@ -326,11 +414,20 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         } else {
           // the uniform-motion delay, scaled by the network's factor for this warp and source (learned
           // proposal)
-          const float sc = closed_form_ctau(r, s_q0[jj], s_q2[jj]) * (PROP == kPropMlp ? inv_cdt * s_fac[jj] : inv_cdt);
-          const int lraw = guessed_offset(sc, win.nw, nw1);
+          const int lraw = WIN ? g_cur : guess_of(jj);
           const int lg = max(lraw, 0);
           pA = win.phys(lg);
-          A = load_rec(src32, pA);
+          // records of the guessed bracket: from the staged window when both lie in it
+          const float4* ra = src32 + 3 * pA;
+          const bool inw = WIN && (unsigned)(lraw - w_lo) < (unsigned)(w_n - 1);
+          if (WIN) {
+            if (inw) ra = s_win + ((size_t)(threadIdx.x >> 5) * 2 + sb) * kWin * 3 + 3 * (lraw - w_lo);
+            A.q0 = ra[0];
+            A.q1 = ra[1];
+            A.q2 = ra[2];
+          } else {
+            A = load_rec(src32, pA);
+          }
           dA = separation(r, A.q0, A.q1);
           tabA = __ldg(a.tab32 + pA);
           if (lraw < 0) {
@@ -360,7 +457,15 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           } else {
             // predicted bracket [lg, lg + 1]: both records are loaded at once
             const int pg1 = pA + 1 == D ? 0 : pA + 1;  // slot of offset lg + 1
-            const Rec Bn = load_rec(src32, pg1);
+            Rec Bn;
+            if (WIN) {
+              const float4* rb = inw ? ra + 3 : src32 + 3 * pg1;
+              Bn.q0 = rb[0];
+              Bn.q1 = rb[1];
+              Bn.q2 = rb[2];
+            } else {
+              Bn = load_rec(src32, pg1);
+            }
             n_tests += 1;
             const bool tA = node_test_d(r, dA, tabA, src64, pA, a, n_fb);
             if (!tA) {
@@ -651,6 +756,12 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
     vmax2 = 0.f;
   }
   }  // work items
+  if (WIN) {
+    // a window whose wait gave up: its copy completes before the block's shared memory is released
+    for (int sb = 0; sb < 2; sb++)
+      if (wpend & (1u << sb))
+        mbar_wait_bounded(smem_u32(&s_bar[(threadIdx.x >> 5) * 2 + sb]), (wph >> sb) & 1u, kDrainLimit);
+  }
   n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
   n_sc = __reduce_add_sync(0xffffffffu, n_sc);
   n_bi = __reduce_add_sync(0xffffffffu, n_bi);
@@ -688,6 +799,7 @@ int max_blocks_pair_mixed(int proposal, bool adapt, int shape) {
     case 2: return max_blocks_mixed<false, 2>(proposal);
     case 3: return max_blocks_mixed<false, 3>(proposal);
     case 4: return max_blocks_mixed<false, 4>(proposal);
+    case 5: return max_blocks_mixed<false, 5>(proposal);
     default: return max_blocks_mixed<false, 0>(proposal);
   }
 }
@@ -731,6 +843,7 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
   a.eta_allow = (float)ap.eta_allow;
   a.ext32 = s.ext32;
   a.dump = dump;
+  a.wait_limit = pl.wait_limit;
   // the work counter is zeroed by the set-up launch that precedes every pair launch; the bracket dump
   // runs the instance without the adaptive step's reduction (the brackets do not depend on it)
   if (dump)
@@ -745,6 +858,8 @@ cudaError_t launch_pair_mixed(const DeviceState& s, const int* order, int propos
     launch_mixed<false, false, 3>(proposal, pl, a, st);
   else if (pl.shape == 4)
     launch_mixed<false, false, 4>(proposal, pl, a, st);
+  else if (pl.shape == 5)
+    launch_mixed<false, false, 5>(proposal, pl, a, st);
   else
     launch_mixed<false, false, 0>(proposal, pl, a, st);
   return cudaGetLastError();

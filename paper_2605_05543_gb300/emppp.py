@@ -47,7 +47,8 @@ class Bext(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     _fields_ = [("items_per_block", ctypes.c_int32), ("target_order", ctypes.c_int32), ("ms", ctypes.c_double),
-                ("targets_per_block", ctypes.c_int32), ("sources_per_sum", ctypes.c_int32)]
+                ("targets_per_block", ctypes.c_int32), ("sources_per_sum", ctypes.c_int32),
+                ("history_window", ctypes.c_int32)]
 
 
 class TuningReport(ctypes.Structure):
@@ -132,6 +133,7 @@ SIGNATURES = {
     "emppp_set_options": (ctypes.c_int, [_H, ctypes.POINTER(Options)]),
     "emppp_autotune": (ctypes.c_int, [_H, ctypes.POINTER(TuningReport)]),
     "emppp_set_tuning": (ctypes.c_int, [_H, ctypes.POINTER(Tuning)]),
+    "emppp_set_wait_limit": (ctypes.c_int, [_H, ctypes.c_int32]),
     "emppp_bracket_dump": (ctypes.c_int, [_H, _vp, ctypes.POINTER(ctypes.c_int64)]),
     "emppp_set_stream": (ctypes.c_int, [_H, _vp]),
     "emppp_synchronize": (ctypes.c_int, [_H]),
@@ -449,10 +451,16 @@ class Solver:
         _check(self.lib.emppp_bracket_dump(self._h, out.data_ptr(), ctypes.byref(k0)))
         return out.cpu().numpy(), k0.value
 
-    def set_tuning(self, items_per_block=16, target_order=1, targets_per_block=128, sources_per_sum=8):
+    def set_tuning(self, items_per_block=16, target_order=1, targets_per_block=128, sources_per_sum=8,
+                   history_window=0):
         t = Tuning(items_per_block=int(items_per_block), target_order=int(target_order), ms=0.0,
-                   targets_per_block=int(targets_per_block), sources_per_sum=int(sources_per_sum))
+                   targets_per_block=int(targets_per_block), sources_per_sum=int(sources_per_sum),
+                   history_window=int(history_window))
         _check(self.lib.emppp_set_tuning(self._h, ctypes.byref(t)))
+
+    def set_wait_limit(self, probes):
+        """Probes of a warp's bounded wait on its staged history window (emppp_set_wait_limit)."""
+        _check(self.lib.emppp_set_wait_limit(self._h, int(probes)))
 
     def synchronize(self):
         _check(self.lib.emppp_synchronize(self._h))

@@ -202,7 +202,9 @@ def test_autotune_keeps_state_and_results(precision):
 
     h = history_case(3000, 80, sigma=10e-6, seed=21)
     T, W, V, u = window(h, 128)
-    shapes = [(128, 8), (64, 8), (256, 8)] + ([(128, 16), (128, 32)] if precision == "mixed" else [])
+    # (targets per block, sources per sum, staged history window)
+    shapes = [(128, 8, 0), (64, 8, 0), (256, 8, 0)] + ([(128, 16, 0), (128, 32, 0), (128, 32, 1)]
+                                                       if precision == "mixed" else [])
     fields = []
     with emppp.Solver(3000, 128, DT, precision=precision, proposal="closed_form") as s:
         s.set_history(80, T, W, V, u)
@@ -211,13 +213,15 @@ def test_autotune_keeps_state_and_results(precision):
         # 5 splits x both target orders at the default shape, then the other tile shapes
         assert n0 == 80 and len(rep["candidates"]) == 10 + len(shapes) - 1
         assert all(c["ms"] > 0 for c in rep["candidates"])
-        assert {(c["targets_per_block"], c["sources_per_sum"]) for c in rep["candidates"]} == set(shapes)
+        assert {(c["targets_per_block"], c["sources_per_sum"], int(c["history_window"] > 0))
+                for c in rep["candidates"]} == set(shapes)
         s.step(1)
         fields.append(s.get_fields())
-        for tpb, sps in shapes:
+        for tpb, sps, hw in shapes:
             for ipb, order in ((4, 0), (16, 1)):
                 s.set_history(80, T, W, V, u)
-                s.set_tuning(items_per_block=ipb, target_order=order, targets_per_block=tpb, sources_per_sum=sps)
+                s.set_tuning(items_per_block=ipb, target_order=order, targets_per_block=tpb, sources_per_sum=sps,
+                             history_window=hw)
                 s.step(1)
                 fields.append(s.get_fields())
                 st = s.stats()
