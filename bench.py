@@ -13,10 +13,13 @@ push and the ring append. pairs/step = N (N - 1).
 
 Prints one JSON line (rank 0). With N > 1 ranks (torchrun), every rank runs an independent replica
 of the workload (no data-path collective: this path is single-GPU) and value = all pairs / max time.
+On one GPU the line also carries, under other_workloads, the lines of the paper's own cases, the FP64
+comparison variants and the 64-bunch two-stage batch (--no-legs skips them).
 """
 from __future__ import annotations
 
 import argparse
+import copy
 import hashlib
 import json
 import math
@@ -80,6 +83,8 @@ def parse_args(argv=None):
                     help="targets per block, sources per partial sum and optionally 1 for the staged history window, e.g. 128,32 or 128,32,1 (no emppp_autotune)")
     ap.add_argument("--no-run-leg", action="store_true",
                     help="skip the stated run of the bunch from t = 0 (500 steps of its own dynamics)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the other workloads (batch, paper, variants) that a one-GPU run of the bunch adds")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the plain FP64 path (FP64 + bisection) on the same state")
     ap.add_argument("--small", action="store_true", help="tiny workload for smoke tests of this script")
@@ -560,8 +565,25 @@ def run_ours(args):
         line["cpu_baseline"], parity = cpu_baseline(h, wl, args.cpu_seconds, E0, B0)
         if parity:
             line["rel_field_err_vs_fp64_oracle"] = parity
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    if world == 1 and not args.no_legs and args.workload == "bunch":
+        line["other_workloads"] = other_workloads(args, (wl, h, win))
+    return line if rank == 0 else None
+
+
+def other_workloads(args, state):
+    """The other workloads at their own default sizes (one GPU only): the paper's own cases, the FP64
+    comparison variants on the bunch's state, and the 64-bunch two-stage batch, each as its own line
+    (value, clocks, config), as `--workload paper|variants|batch` prints it."""
+    sub = copy.copy(args)
+    sub.steps, sub.warmup = None, 3
+    out = {}
+    sub.workload = "paper"
+    out["paper"] = run_paper(sub)
+    sub.workload = "variants"
+    out["variants"] = run_variants(sub, state)
+    sub.workload = "batch"
+    out["batch"] = run_batch(sub)
+    return out
 
 
 BATCH_NAME = ("batched two-stage transport: 64 bunches, N ~ U[512, 16384], sigma ~ U[5, 50] um, gamma0 ~ U[2, 20]; "
@@ -675,8 +697,7 @@ def run_batch(args):
         "stage2": {"particle_steps_per_s": npart * s2_steps * world / (s2_ms / 1e3), "steps": s2_steps,
                    "ms": s2_ms, "particles": npart, "gpu_launches": s2_launches, "dt": 1e-9},
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
 
 
 PAPER_NAME = ("the paper's own runs (Sec. 2.5, Sec. 3.1): 2 mm Gaussian bunches of N_p macroparticles "
@@ -770,15 +791,14 @@ def run_paper(args):
         "clocks": clocks,
         "gpu_launches": launches,
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
 
 
 VARIANTS = {"linear_present": {}, "midpoint": {"reconstruction": "midpoint"},
             "half_step": {"field_point": "half_step"}}
 
 
-def run_variants(args):
+def run_variants(args, state=None):
     """The comparison variants of the step on the benchmark workload (FP64 path): the method as built,
     the midpoint reconstruction of eq:mid and the half-step field point, each timed on the same stored
     state; the line's value is the midpoint variant's pair rate. The first step's fields of each variant
@@ -793,7 +813,7 @@ def run_variants(args):
     torch.cuda.set_device(local)
     dist_init("nccl")
     emppp.load(build_if_missing=True)
-    wl, h, win = workload(args.small, rank, args)
+    wl, h, win = state if state is not None else workload(args.small, rank, args)
     steps = args.steps if args.steps is not None else 2
     warmup = max(args.warmup, 1)
     dev = torch.device("cuda", local)
@@ -829,8 +849,7 @@ def run_variants(args):
         "clocks": clocks,
         "gpu_launches": res["midpoint"]["launches"],
     }
-    if rank == 0:
-        print(json.dumps(line), flush=True)
+    return line if rank == 0 else None
 
 
 def run_reference(args):
@@ -883,14 +902,11 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "batch":
-        run_batch(args)
-    elif args.workload == "paper":
-        run_paper(args)
-    elif args.workload == "variants":
-        run_variants(args)
     else:
-        run_ours(args)
+        run = {"batch": run_batch, "paper": run_paper, "variants": run_variants}.get(args.workload, run_ours)
+        line = run(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
     try:
         import torch.distributed as dist
 

@@ -14,6 +14,7 @@
 // Rounding points (also followed by the CPU reference in oracle/mlp.py): the GEMM operands X, W1, A1 =
 // silu(H1), W2 (forward) and dH2, W2 (input gradient) are rounded to BF16; products accumulate in FP32;
 // biases, activations, w3 and every weight gradient are FP32.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -466,8 +467,9 @@ __global__ void __launch_bounds__(kFacThreads) factor_kernel(DeviceState s, cons
   const float b0 = (float)bd.beta_ref[0], b1 = (float)bd.beta_ref[1], b2 = (float)bd.beta_ref[2];
   const InferImage& net = *infer_image(s.mlp_image);
   float* __restrict__ fac = s.mlp_fac + bd.fac_off + (size_t)g * bd.n;
-  // warp w takes sources 32 w, 32 w + 256, ...: the loop bounds are the same for every lane (converged)
-  for (int j0 = 32 * w; j0 < bd.n; j0 += kFacThreads) {
+  // block y of the group's gridDim.y blocks, warp w: sources 32 (w + 8 y), then every 256 gridDim.y; the
+  // loop bounds are the same for every lane (converged)
+  for (int j0 = 32 * (w + (kFacThreads / 32) * (int)blockIdx.y); j0 < bd.n; j0 += kFacThreads * (int)gridDim.y) {
     const int jl = j0 + lane;
     const bool v = jl < bd.n;
     const size_t j = (size_t)bd.off + (v ? jl : j0);
@@ -501,7 +503,14 @@ cudaError_t launch_sample(const DeviceState& s, const int* pairs, long long m, f
 
 cudaError_t launch_mlp_factors(const DeviceState& s, const int* order, cudaStream_t st) {
   if (s.ngroups <= 0 || !s.mlp_fac) return cudaSuccess;
-  factor_kernel<<<s.ngroups, kFacThreads, 0, st>>>(s, order);
+  // the sources of each group split over enough blocks for about 8 resident blocks per SM (each block
+  // forms the group's centroid again: 2 loads per thread)
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int split = std::min(64, std::max(1, (8 * sms + s.ngroups - 1) / s.ngroups));
+  factor_kernel<<<dim3(s.ngroups, split), kFacThreads, 0, st>>>(s, order);
   return cudaGetLastError();
 }
 

@@ -148,7 +148,8 @@ __device__ __forceinline__ bool node_test(const Target& r, const float4* __restr
 }
 
 // uniform-motion guess of the retarded delay, from the staged present record of the source:
-// c tau = gamma^2 [d.beta + sqrt((d.beta)^2 + |d|^2 / gamma^2)] with d from the hi parts only
+// c tau = gamma^2 [d.beta + sqrt((d.beta)^2 + |d|^2 / gamma^2)] with d from the hi parts only (g2.w is
+// gamma^2, times the learned delay factor with that proposal)
 __device__ __forceinline__ float closed_form_ctau(const Target& r, float4 g0, float4 g2) {
   const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
   const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
@@ -200,13 +201,13 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   __shared__ __align__(8) unsigned long long s_bar[WIN ? kWarps * 2 : 1];
   __shared__ int2 s_wd[WIN ? kWarps * 2 : 1];  // (first offset, slots) of each staged window
   __shared__ float4 s_q0[kTile];  // present record (hi, 1/gamma^2) of the tile's sources
-  __shared__ float4 s_q2[kTile];  // (beta, gamma^2) of the same records
+  // (beta, gamma^2) of the same records; with the learned proposal the w component carries gamma^2 times the
+  // network's delay factor for the block's target group, which only the delay guess reads
+  __shared__ float4 s_q2[kTile];
   __shared__ float s_kq[kTile];
   __shared__ float4 s_q1[kTile];  // present record (lo, 0) of the tile's sources
   __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position (ext32)
   __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
-  // learned proposal: the delay factor e^z of each of the tile's sources for the block's target group
-  __shared__ float s_fac[PROP == kPropMlp ? kTile : 1];
 
   __shared__ int s_item;
   const int N = a.N;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   const float* fac_row = PROP == kPropMlp ? a.fac + bd.fac_off + (size_t)((tb * kBlock) / kFacGroup) * bd.n : nullptr;
   // the lane's guessed older-node offset for staged source jj of the tile (-1: predicted out of history)
   auto guess_of = [&](int jj) -> int {
-    const float sc = closed_form_ctau(r, s_q0[jj], s_q2[jj]) * (PROP == kPropMlp ? inv_cdt * s_fac[jj] : inv_cdt);
+    const float sc = closed_form_ctau(r, s_q0[jj], s_q2[jj]) * inv_cdt;
     return guessed_offset(sc, win.nw, nw1);
   };
   // beta_i(t_n) - beta_ref of the target (adaptive time step; target and sources share the bunch's beta_ref,
@@ -303,11 +304,11 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       const float4* q = a.rec32 + ((size_t)j * D + pn) * 3;
       s_q0[threadIdx.x] = q[0];
       const float4 q2 = q[2];
-      s_q2[threadIdx.x] = make_float4(bref0 + q2.x, bref1 + q2.y, bref2 + q2.z, q2.w);
+      s_q2[threadIdx.x] = make_float4(bref0 + q2.x, bref1 + q2.y, bref2 + q2.z,
+                                      PROP == kPropMlp ? q2.w * __ldg(fac_row + (j - boff)) : q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
       s_q1[threadIdx.x] = q[1];
       s_x[threadIdx.x] = __ldg(a.ext32 + 3 * j + 2);
-      if (PROP == kPropMlp) s_fac[threadIdx.x] = __ldg(fac_row + (j - boff));
     }
     __syncthreads();
     // window of staged source jn into buffer sb: the offsets lo .. hi + 1 of the guessed brackets [lg, lg + 1]
@@ -412,8 +413,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             fast = (l1 == 0);
           }
         } else {
-          // the uniform-motion delay, scaled by the network's factor for this warp and source (learned
-          // proposal)
+          // the uniform-motion delay (with the learned proposal scaled by the network's factor for the
+          // block's target group and this source, staged in s_q2)
           const int lraw = WIN ? g_cur : guess_of(jj);
           const int lg = max(lraw, 0);
           pA = win.phys(lg);
