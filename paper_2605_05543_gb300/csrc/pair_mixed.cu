@@ -22,9 +22,11 @@
 //             (eq:LW_E with v' = c u', a = c^2 alpha), B = eta_hat x E / c (eq:LW_B). eta.u' = R - eta.beta
 //             cancels for a source moving towards the target; there it is formed as
 //             [R^2 (1 - beta^2) + |eta x beta|^2] / (R + eta.beta), a sum of non-negative terms.
-//   sums      FP32 partial sums over 8 sources, added with Kahan compensation into FP32 running totals
-//             (kept in shared memory, which leaves the registers to the pair loop: 64 registers, 8 blocks
-//             of 128 threads per SM), converted to FP64 at the end.
+//   sums      FP32 partial sums over kSub sources (8, 16 or 32 by tile shape), added with Kahan
+//             compensation into FP32 running totals (kept in shared memory, which leaves the registers to
+//             the pair loop: 64 registers, 8 blocks of 128 threads per SM), converted to FP64 at the end.
+// Vector arithmetic takes x and y in one packed FP32x2 instruction where both operands come as pairs
+// (separations, velocity differences, the retarded point, u', F, the sums) and z as a scalar.
 // Sources are walked in tiles of kTile whose present records and FP32 charges are staged in shared
 // memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
 // source are close together in the source-major FP32 shadow ring. The window instance (shape_win)
@@ -81,7 +83,8 @@ struct MixedArgs {
 constexpr int kDrainLimit = 1 << 20;
 
 struct Target {
-  float h0, h1, h2, l0, l1, l2;
+  float2 h01, l01;  // x and y of the hi and lo parts (packed FP32x2 operands)
+  float h2, l2;
   int idx;          // particle index (its FP64 present record is formed only for the rare FP64 node tests)
   bool exact_only;  // coordinates too far from the split origin for the FP32 band: FP64 tests only
 };
@@ -123,9 +126,13 @@ __device__ __forceinline__ float cross1(float a0, float a1, float b0, float b1) 
   return __fmaf_rn(a0, b1, -__fmul_rn(a1, b0));
 }
 
-// r - w of a record, from the hi and lo parts (each component exact to two roundings)
+// a - (b.x, b.y) by one packed FP32x2 addition of the negation (the same rounding as two subtractions)
+__device__ __forceinline__ float2 sub2(float2 a, float4 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// r - w of a record, from the hi and lo parts (each component exact to two roundings); x and y packed
 __device__ __forceinline__ float3 separation(const Target& r, float4 q0, float4 q1) {
-  return make_float3((r.h0 - q0.x) + (r.l0 - q1.x), (r.h1 - q0.y) + (r.l1 - q1.y), (r.h2 - q0.z) + (r.l2 - q1.z));
+  const float2 d = __fadd2_rn(sub2(r.h01, q0), sub2(r.l01, q1));
+  return make_float3(d.x, d.y, (r.h2 - q0.z) + (r.l2 - q1.z));
 }
 
 // P(k) from a separation d already formed at physical slot p, with that slot's table entry tab
@@ -151,7 +158,8 @@ __device__ __forceinline__ bool node_test(const Target& r, const float4* __restr
 // c tau = gamma^2 [d.beta + sqrt((d.beta)^2 + |d|^2 / gamma^2)] with d from the hi parts only (g2.w is
 // gamma^2, times the learned delay factor with that proposal)
 __device__ __forceinline__ float closed_form_ctau(const Target& r, float4 g0, float4 g2) {
-  const float x0 = r.h0 - g0.x, x1 = r.h1 - g0.y, x2 = r.h2 - g0.z;
+  const float2 x01 = sub2(r.h01, g0);
+  const float x0 = x01.x, x1 = x01.y, x2 = r.h2 - g0.z;
   const float db = x0 * g2.x + x1 * g2.y + x2 * g2.z;
   const float dd = x0 * x0 + x1 * x1 + x2 * x2;
   const float x = fmaxf(fmaf(db, db, g0.w * dd), 0.f);
@@ -250,7 +258,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   const BunchDesc& bd = a.bunches[b];
   const BunchSched& bs = a.sched[b];
   const int boff = (int)bd.off;
-  const float bref0 = (float)bd.beta_ref[0], bref1 = (float)bd.beta_ref[1], bref2 = (float)bd.beta_ref[2];
+  const float2 bref01 = make_float2((float)bd.beta_ref[0], (float)bd.beta_ref[1]);
+  const float bref2 = (float)bd.beta_ref[2];
   const int t_loc = tb * kBlock + threadIdx.x;
   const bool active = t_loc < bd.n;
   const int t = boff + (active ? t_loc : 0);
@@ -260,14 +269,12 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   {
     const float4 q0 = a.rec32[((size_t)i * D + pn) * 3];
     const float4 q1 = a.rec32[((size_t)i * D + pn) * 3 + 1];
-    r.h0 = q0.x;
-    r.h1 = q0.y;
+    r.h01 = make_float2(q0.x, q0.y);
     r.h2 = q0.z;
-    r.l0 = q1.x;
-    r.l1 = q1.y;
+    r.l01 = make_float2(q1.x, q1.y);
     r.l2 = q1.z;
     r.idx = i;
-    r.exact_only = fmaxf(fabsf(r.h0), fmaxf(fabsf(r.h1), fabsf(r.h2))) > 0.5f;
+    r.exact_only = fmaxf(fabsf(r.h01.x), fmaxf(fabsf(r.h01.y), fabsf(r.h2))) > 0.5f;
   }
   // learned proposal: the delay factors of this target tile's group (kFacGroup targets, a multiple of the
   // tile), one per source of the bunch
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       const float4* q = a.rec32 + ((size_t)j * D + pn) * 3;
       s_q0[threadIdx.x] = q[0];
       const float4 q2 = q[2];
-      s_q2[threadIdx.x] = make_float4(bref0 + q2.x, bref1 + q2.y, bref2 + q2.z,
+      s_q2[threadIdx.x] = make_float4(bref01.x + q2.x, bref01.y + q2.y, bref2 + q2.z,
                                       PROP == kPropMlp ? q2.w * __ldg(fac_row + (j - boff)) : q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
       s_q1[threadIdx.x] = q[1];
@@ -542,10 +549,11 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           //   E = kq (1 - beta^2) X / [X^2 (1 - beta^2) + (X.beta)^2]^{3/2},  c B = beta x E,
           // with X = (r - w_n) - (line at t_n - w_n) from the staged present record and line offset.
           const float4 g0 = s_q0[jj], g1 = s_q1[jj], gx = s_x[jj];
-          float X0 = __fsub_rn(__fadd_rn(__fsub_rn(r.h0, g0.x), __fsub_rn(r.l0, g1.x)), gx.x);
-          float X1 = __fsub_rn(__fadd_rn(__fsub_rn(r.h1, g0.y), __fsub_rn(r.l1, g1.y)), gx.y);
+          const float2 X01 = sub2(__fadd2_rn(sub2(r.h01, g0), sub2(r.l01, g1)), gx);
+          float X0 = X01.x, X1 = X01.y;
           float X2 = __fsub_rn(__fadd_rn(__fsub_rn(r.h2, g0.z), __fsub_rn(r.l2, g1.z)), gx.z);
-          const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
+          const float2 b101 = __fadd2_rn(bref01, make_float2(A.q2.x, A.q2.y));
+          const float b10 = b101.x, b11 = b101.y, b12 = __fadd_rn(bref2, A.q2.z);
           const float ig2 = A.q0.w;
           float Xb = dot3(X0, X1, X2, b10, b11, b12);
           float XX = dot3(X0, X1, X2, X0, X1, X2);
@@ -575,7 +583,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             continue;
           }
           const float pref = __fmul_rn(__fmul_rn(s_kq[jj], ig2), __fmul_rn(__fmul_rn(iD, iD), iD));
-          const float E0 = __fmul_rn(pref, X0), E1 = __fmul_rn(pref, X1), E2 = __fmul_rn(pref, X2);
+          const float2 E01 = __fmul2_rn(make_float2(pref, pref), make_float2(X0, X1));
+          const float E0 = E01.x, E1 = E01.y, E2 = __fmul_rn(pref, X2);
           if (ADAPT) {
             // retarded distance c (t - t_r) = gamma^2 [X.beta + sqrt(Dh)], and v(t_r) = v1
             const float sD = __fmul_rn(Dh, iD);
@@ -587,21 +596,28 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
               vmax2 = fmaxf(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
             }
           }
-          P[0] = __fadd_rn(P[0], E0);
-          P[1] = __fadd_rn(P[1], E1);
-          P[2] = __fadd_rn(P[2], E2);
-          P[3] = __fadd_rn(P[3], cross1(b11, b12, E1, E2));
-          P[4] = __fadd_rn(P[4], cross1(b12, b10, E2, E0));
+          const float2 p01 = __ffma2_rn(make_float2(pref, pref), make_float2(X0, X1), make_float2(P[0], P[1]));
+          P[0] = p01.x;
+          P[1] = p01.y;
+          P[2] = __fmaf_rn(pref, X2, P[2]);
+          const float2 p34 = __fadd2_rn(make_float2(P[3], P[4]),
+                                        make_float2(cross1(b11, b12, E1, E2), cross1(b12, b10, E2, E0)));
+          P[3] = p34.x;
+          P[4] = p34.y;
           P[5] = __fadd_rn(P[5], cross1(b10, b11, E0, E1));
           continue;
         }
         // ---- retarded state (light units) --------------------------------------------------------
         // Written with explicit round-to-nearest intrinsics: the compiler may not fuse or regroup any
         // of it, so every search variant (whose own arithmetic shares subexpressions with this code
-        // in different ways) computes the same fields from the same bracket, bit for bit.
+        // in different ways) computes the same fields from the same bracket, bit for bit. The packed
+        // FP32x2 forms (x and y in one instruction) round per component like the scalar ones, but the
+        // compiler fuses a packed product that feeds a packed sum; so no packed product feeds a packed
+        // sum here, and every multiply-add is written as one fused operation (__ffma2_rn, __fmaf_rn).
         const float d0 = dA.x, d1 = dA.y, d2 = dA.z;
         const float L1 = tabA.z;
-        const float b10 = __fadd_rn(bref0, A.q2.x), b11 = __fadd_rn(bref1, A.q2.y), b12 = __fadd_rn(bref2, A.q2.z);
+        const float2 b101 = __fadd2_rn(bref01, make_float2(A.q2.x, A.q2.y));
+        const float b10 = b101.x, b11 = b101.y, b12 = __fadd_rn(bref2, A.q2.z);
         const float ig2 = A.q0.w, g2 = A.q2.w;
         float e0, e1, e2, qd, df;  // eta, the discriminant, and (t_r - t1) / (t2 - t1)
         if (br == 1) {
@@ -615,8 +631,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           qd = __fmaf_rn(pb, pb, __fmul_rn(ig2, pp));
           const float sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
           const float tau = (pb <= 0.f) ? __fdividef(pp, __fsub_rn(sq, pb)) : __fmul_rn(__fadd_rn(pb, sq), g2);
-          e0 = __fmaf_rn(b10, tau, dp.x);
-          e1 = __fmaf_rn(b11, tau, dp.y);
+          const float2 e01 = __ffma2_rn(b101, make_float2(tau, tau), make_float2(dp.x, dp.y));
+          e0 = e01.x;
+          e1 = e01.y;
           e2 = __fmaf_rn(b12, tau, dp.z);
           df = __fmaf_rn(-tau, tabA.w, 1.f);
         } else {
@@ -643,8 +660,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
             n_fb++;
           }
-          e0 = __fmaf_rn(-b10, s, d0);
-          e1 = __fmaf_rn(-b11, s, d1);
+          const float2 e01 = __ffma2_rn(make_float2(-b10, -b11), make_float2(s, s), make_float2(d0, d1));
+          e0 = e01.x;
+          e1 = e01.y;
           e2 = __fmaf_rn(-b12, s, d2);
           df = __fmul_rn(s, tabA.w);
         }
@@ -653,19 +671,23 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         if (br != 0) {
           if (!have_b) q2b = __ldg(src32 + 3 * (pA + 1 == D ? 0 : pA + 1) + 2);
           const float icdt = tabA.w;
-          const float db0 = __fsub_rn(q2b.x, A.q2.x), db1 = __fsub_rn(q2b.y, A.q2.y), db2 = __fsub_rn(q2b.z, A.q2.z);
-          al0 = __fmul_rn(db0, icdt);
-          al1 = __fmul_rn(db1, icdt);
+          const float2 db01 = sub2(make_float2(q2b.x, q2b.y), A.q2);
+          const float db2 = __fsub_rn(q2b.z, A.q2.z);
+          const float2 al01 = __fmul2_rn(db01, make_float2(icdt, icdt));
+          al0 = al01.x;
+          al1 = al01.y;
           al2 = __fmul_rn(db2, icdt);
-          const float x0 = __fmul_rn(db0, df), x1 = __fmul_rn(db1, df), x2 = __fmul_rn(db2, df);
+          const float2 x01 = __fmul2_rn(db01, make_float2(df, df));
+          const float x0 = x01.x, x1 = x01.y, x2 = __fmul_rn(db2, df);
           if (ADAPT) {
             xs0 = x0;
             xs1 = x1;
             xs2 = x2;
           }
-          be0 = __fadd_rn(b10, x0);
-          be1 = __fadd_rn(b11, x1);
-          be2 = __fadd_rn(b12, x2);
+          const float2 be01 = __ffma2_rn(db01, make_float2(df, df), b101);
+          be0 = be01.x;
+          be1 = be01.y;
+          be2 = __fmaf_rn(db2, df, b12);
           // 1 - beta^2 = (1 - beta1^2) - x.(2 beta1 + x)
           ug = __fsub_rn(ig2, dot3(x0, x1, x2, __fmaf_rn(2.f, b10, x0), __fmaf_rn(2.f, b11, x1),
                                    __fmaf_rn(2.f, b12, x2)));
@@ -675,7 +697,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         const float invR = rsqrtf(R2);
         const float R = __fmul_rn(R2, invR);
         // u' = eta / R - beta
-        const float u0 = __fmaf_rn(e0, invR, -be0), u1 = __fmaf_rn(e1, invR, -be1), u2 = __fmaf_rn(e2, invR, -be2);
+        const float2 u01 = __ffma2_rn(make_float2(e0, e1), make_float2(invR, invR), make_float2(-be0, -be1));
+        const float u0 = u01.x, u1 = u01.y, u2 = __fmaf_rn(e2, invR, -be2);
         const float eb = dot3(e0, e1, e2, be0, be1, be2);
         // 1 / (eta . u'): R - eta.beta directly when eta.beta <= 0, else the rationalised form
         const float xb0 = cross1(e1, e2, be1, be2), xb1 = cross1(e2, e0, be2, be0), xb2 = cross1(e0, e1, be0, be1);
@@ -688,14 +711,18 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           continue;
         }
         const float pref = __fmul_rn(__fmul_rn(__fmul_rn(s_kq[jj], __fmul_rn(R, ieu)), ieu), ieu);
-        float F0 = __fmul_rn(ug, u0), F1 = __fmul_rn(ug, u1), F2 = __fmul_rn(ug, u2);
+        float2 F01;
+        float F2;
         if (br != 0) {
-          // eta x (u' x alpha)
+          // (1 - beta^2) u' + eta x (u' x alpha)
           const float c0 = cross1(u1, u2, al1, al2), c1 = cross1(u2, u0, al2, al0), c2 = cross1(u0, u1, al0, al1);
-          F0 = __fadd_rn(F0, cross1(e1, e2, c1, c2));
-          F1 = __fadd_rn(F1, cross1(e2, e0, c2, c0));
-          F2 = __fadd_rn(F2, cross1(e0, e1, c0, c1));
+          F01 = __ffma2_rn(make_float2(ug, ug), u01, make_float2(cross1(e1, e2, c1, c2), cross1(e2, e0, c2, c0)));
+          F2 = __fmaf_rn(ug, u2, cross1(e0, e1, c0, c1));
+        } else {
+          F01 = __fmul2_rn(make_float2(ug, ug), u01);
+          F2 = __fmul_rn(ug, u2);
         }
+        const float F0 = F01.x, F1 = F01.y;
         // E = pref F; c B = eta_hat x E = (pref / R) (eta x F), with 1 / c applied once per target
         if (ADAPT && R >= a.eta_allow) {
           // interaction scale of the adaptive step: |eta_ij| and |beta_i(t_n) - beta_j(t_r)|, with
@@ -704,12 +731,15 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           const float dv0 = (bi0 - A.q2.x) - xs0, dv1 = (bi1 - A.q2.y) - xs1, dv2 = (bi2 - A.q2.z) - xs2;
           vmax2 = fmaxf(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
         }
-        P[0] = __fmaf_rn(pref, F0, P[0]);
-        P[1] = __fmaf_rn(pref, F1, P[1]);
+        const float2 p01 = __ffma2_rn(make_float2(pref, pref), F01, make_float2(P[0], P[1]));
+        P[0] = p01.x;
+        P[1] = p01.y;
         P[2] = __fmaf_rn(pref, F2, P[2]);
         const float pb = __fmul_rn(pref, invR);
-        P[3] = __fmaf_rn(pb, cross1(e1, e2, F1, F2), P[3]);
-        P[4] = __fmaf_rn(pb, cross1(e2, e0, F2, F0), P[4]);
+        const float2 p34 = __ffma2_rn(make_float2(pb, pb), make_float2(cross1(e1, e2, F1, F2), cross1(e2, e0, F2, F0)),
+                                      make_float2(P[3], P[4]));
+        P[3] = p34.x;
+        P[4] = p34.y;
         P[5] = __fmaf_rn(pb, cross1(e0, e1, F0, F1), P[5]);
       }
       // Kahan-add the partial sums of these kSub sources
