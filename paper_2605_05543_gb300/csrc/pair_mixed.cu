@@ -583,8 +583,6 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             continue;
           }
           const float pref = __fmul_rn(__fmul_rn(s_kq[jj], ig2), __fmul_rn(__fmul_rn(iD, iD), iD));
-          const float2 E01 = __fmul2_rn(make_float2(pref, pref), make_float2(X0, X1));
-          const float E0 = E01.x, E1 = E01.y, E2 = __fmul_rn(pref, X2);
           if (ADAPT) {
             // retarded distance c (t - t_r) = gamma^2 [X.beta + sqrt(Dh)], and v(t_r) = v1
             const float sD = __fmul_rn(Dh, iD);
@@ -600,11 +598,13 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           P[0] = p01.x;
           P[1] = p01.y;
           P[2] = __fmaf_rn(pref, X2, P[2]);
-          const float2 p34 = __fadd2_rn(make_float2(P[3], P[4]),
-                                        make_float2(cross1(b11, b12, E1, E2), cross1(b12, b10, E2, E0)));
+          // c B = beta x E = pref (beta x X)
+          const float2 p34 = __ffma2_rn(make_float2(pref, pref),
+                                        make_float2(cross1(b11, b12, X1, X2), cross1(b12, b10, X2, X0)),
+                                        make_float2(P[3], P[4]));
           P[3] = p34.x;
           P[4] = p34.y;
-          P[5] = __fadd_rn(P[5], cross1(b10, b11, E0, E1));
+          P[5] = __fmaf_rn(pref, cross1(b10, b11, X0, X1), P[5]);
           continue;
         }
         // ---- retarded state (light units) --------------------------------------------------------
@@ -689,8 +689,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           be1 = be01.y;
           be2 = __fmaf_rn(db2, df, b12);
           // 1 - beta^2 = (1 - beta1^2) - x.(2 beta1 + x)
-          ug = __fsub_rn(ig2, dot3(x0, x1, x2, __fmaf_rn(2.f, b10, x0), __fmaf_rn(2.f, b11, x1),
-                                   __fmaf_rn(2.f, b12, x2)));
+          const float2 t01 = __ffma2_rn(make_float2(2.f, 2.f), b101, x01);  // 2 beta1 + x
+          ug = __fsub_rn(ig2, dot3(x0, x1, x2, t01.x, t01.y, __fmaf_rn(2.f, b12, x2)));
         }
         // ---- Lienard-Wiechert fields ---------------------------------------------------------------
         const float R2 = dot3(e0, e1, e2, e0, e1, e2);
