@@ -223,10 +223,10 @@ def shape_key(tuning):
     return k + (tuning["history_window"],) if tuning.get("history_window") else k
 
 
-def kernel_traffic_record(path_name, proposal, shape=None):
-    """DRAM bytes per launch of the pair kernel from the committed ncu summary, if it was taken on the
-    same kernel instance (proposal and tile shape) and on the sources as they are now (the kernel, the tile
-    shapes and the work split, which sets the source chunks), else None."""
+def kernel_record(path_name, proposal, shape=None):
+    """The committed one-pass ncu record of a full-size pair-kernel launch (DRAM bytes, warp instructions),
+    if it was taken on the same kernel instance (proposal and tile shape) and on the sources as they are
+    now (the kernel, the tile shapes and the work split, which sets the source chunks), else None."""
     rec = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     if not os.path.exists(rec):
         return None
@@ -240,9 +240,31 @@ def kernel_traffic_record(path_name, proposal, shape=None):
         h = hashlib.sha256()
         for name in ent["sources"]:
             h.update(open(os.path.join(ROOT, "paper_2605_05543_gb300", "csrc", name), "rb").read())
-        return ent["dram_bytes_per_launch"] if h.hexdigest()[:16] == ent["sources_sha256_16"] else None
+        return ent if h.hexdigest()[:16] == ent["sources_sha256_16"] else None
     except Exception:
         return None
+
+
+def kernel_traffic_record(path_name, proposal, shape=None):
+    """DRAM bytes per launch of the pair kernel from the committed record (kernel_record), else None."""
+    ent = kernel_record(path_name, proposal, shape)
+    return ent["dram_bytes_per_launch"] if ent else None
+
+
+def issue_roofline(path_name, proposal, shape, pair_ms, clocks, sms):
+    """Instruction issue of the pair kernel against its ceiling: the committed warp-instruction count of
+    one full-size launch (kernel_record) over the launch's event-timed duration, against every SM's four
+    schedulers issuing one warp instruction per clock at the SM clock sampled in the timed region."""
+    ent = kernel_record(path_name, proposal, shape)
+    if not ent or not ent.get("warp_instructions_per_launch") or not pair_ms:
+        return None
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    achieved = ent["warp_instructions_per_launch"] / (pair_ms / 1e3)
+    peak = sms * 4 * mhz * 1e6
+    return {"achieved": achieved, "peak": peak, "unit": "warp instructions/s", "frac": achieved / peak,
+            "warp_instructions_per_launch": ent["warp_instructions_per_launch"],
+            "note": "smsp__inst_executed.sum of the committed one-pass capture of this instance and sources; "
+                    f"peak = {sms} SMs x 4 schedulers x 1 warp instruction per clock at {mhz:.0f} MHz"}
 
 
 def cpu_baseline(h, wl, seconds, E_gpu=None, B_gpu=None, seed=1):
@@ -513,7 +535,9 @@ def run_ours(args):
                                               "event-timed launches, at the clock the GPU ran"),
                      "probe": {"fp32_tflops": peaks["fp32_flops"] / 1e12, "fp64_tflops": peaks["fp64_flops"] / 1e12,
                                "mufu_tera_ops": peaks["mufu_ops"] / 1e12},
-                     "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1)},
+                     "pair_kernel_ms": pair_ms_avg, "flops_per_pair": flops / max(st["pairs"], 1),
+                     "issue": issue_roofline(args.path, args.proposal, shape_key(tuning), pair_ms_avg, res["clocks"],
+                                             torch.cuda.get_device_properties(dev).multi_processor_count)},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
         "tuning": ({**tuning, "candidates_timed": ncand,
