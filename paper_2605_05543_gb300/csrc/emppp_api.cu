@@ -108,14 +108,23 @@ struct emppp_ctx {
   static constexpr int kTimedSteps = 1024;
   std::vector<cudaEvent_t> events;
   int ev_used = 0;
-  // one captured step, replayed by emppp_step
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  int graph_launches = 0;        // kernels per replayed step
+  // one step captured in two variants, replayed by emppp_step: [1] recomputes the spatial target order,
+  // [0] reuses the last one
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph_exec[2] = {nullptr, nullptr};
+  int graph_launches[2] = {0, 0};  // kernels per replayed step
   unsigned char graph_key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams) +
-                          sizeof(EnergyParams)];  // configuration of the graph
-  bool graph_valid = false;
+                          sizeof(EnergyParams)];  // configuration of both variants
+  bool graph_valid[2] = {false, false};
+  // Steps since the target order was computed (-1: not for the present state). The order is a
+  // permutation of each bunch whatever its age, and a target's sum runs over the sources in a fixed
+  // order whichever thread evaluates it, so an older order changes no result; it is recomputed every
+  // kOrderEvery steps, since a bunch's particles move far less than their spacing in that time.
+  int order_age = -1;
 };
+
+// steps between two computations of the spatial target order
+constexpr int kOrderEvery = 16;
 
 namespace {
 
@@ -165,11 +174,14 @@ emppp_status validate_options(const emppp_options* o) {
 }
 
 void invalidate_graph(emppp_handle h) {
-  if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
-  if (h->graph) cudaGraphDestroy(h->graph);
-  h->graph_exec = nullptr;
-  h->graph = nullptr;
-  h->graph_valid = false;
+  for (int v = 0; v < 2; v++) {
+    if (h->graph_exec[v]) cudaGraphExecDestroy(h->graph_exec[v]);
+    if (h->graph[v]) cudaGraphDestroy(h->graph[v]);
+    h->graph_exec[v] = nullptr;
+    h->graph[v] = nullptr;
+    h->graph_valid[v] = false;
+  }
+  h->order_age = -1;  // every change of state or configuration recomputes the order at the next step
 }
 
 // Work split of the persistent pair kernel, per bunch: one block per resident slot of the kernel that
@@ -390,8 +402,9 @@ emppp_status convert_bext(const emppp_bext* bext, BextParams* bp) {
   return EMPPP_OK;
 }
 
-// enqueues the kernels of one step and reports how many kernels it launched
-emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev, int* nkernels) {
+// enqueues the kernels of one step and reports how many kernels it launched; refresh_order recomputes the
+// spatial target order first (else the last one is used)
+emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev, int* nkernels, bool refresh_order) {
   int k = 0;
   if (ev) CU(cudaEventRecord(ev[0], h->stream));
   const bool half = h->opt.pair_fields && h->opt.field_point == EMPPP_FIELD_HALF_STEP;
@@ -408,7 +421,7 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   const bool ordered = h->opt.pair_fields && h->target_order && !(mixed_pairs && h->N <= 2048);
   {
     NvtxRange r("emppp:setup");
-    if (ordered) {
+    if (ordered && refresh_order) {
       CU(cudaEventRecord(h->ev_fork, h->stream));
       CU(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
       CU(launch_target_order(h->ds, h->ord_key, h->order, h->max_bunch, h->aux));
@@ -418,7 +431,7 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
     CU(launch_setup(h->ds, mixed_pairs, h->stream));
     k += 1;
   }
-  if (ordered) CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  if (ordered && refresh_order) CU(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
   if (ev) CU(cudaEventRecord(ev[1], h->stream));
   if (h->opt.pair_fields) {
     NvtxRange r("emppp:pair_fields");
@@ -457,19 +470,26 @@ emppp_status enqueue_step(emppp_handle h, const BextParams& bp, cudaEvent_t* ev,
   return EMPPP_OK;
 }
 
-// captures one step into a CUDA graph for the current configuration (options and background field)
-emppp_status capture_step(emppp_handle h, const BextParams& bp) {
+// captures one step into a CUDA graph for the current configuration (options and background field), in the
+// variant that recomputes the target order (refresh_order) or the one that reuses it
+emppp_status capture_step(emppp_handle h, const BextParams& bp, bool refresh_order) {
+  const int v = refresh_order ? 1 : 0;
   unsigned char key[sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams) + sizeof(EnergyParams)];
   memset(key, 0, sizeof(key));
   memcpy(key, &h->opt, sizeof(emppp_options));
   memcpy(key + sizeof(emppp_options), &bp, sizeof(BextParams));
   memcpy(key + sizeof(emppp_options) + sizeof(BextParams), &h->adapt, sizeof(AdaptParams));
   memcpy(key + sizeof(emppp_options) + sizeof(BextParams) + sizeof(AdaptParams), &h->energy, sizeof(EnergyParams));
-  if (h->graph_valid && memcmp(key, h->graph_key, sizeof(key)) == 0) return EMPPP_OK;
-  invalidate_graph(h);
+  if (memcmp(key, h->graph_key, sizeof(key)) != 0) {
+    const int age = h->order_age;
+    invalidate_graph(h);
+    h->order_age = age;  // a new field or option does not move the particles
+    memcpy(h->graph_key, key, sizeof(key));
+  }
+  if (h->graph_valid[v]) return EMPPP_OK;
   CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   int k = 0;
-  emppp_status st = enqueue_step(h, bp, nullptr, &k);
+  emppp_status st = enqueue_step(h, bp, nullptr, &k, refresh_order);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->stream, &g);
   if (st != EMPPP_OK) {
@@ -477,15 +497,14 @@ emppp_status capture_step(emppp_handle h, const BextParams& bp) {
     return st;
   }
   if (e != cudaSuccess) return fail(EMPPP_ERR_CUDA, "stream capture: %s", cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->graph_exec, g, 0);
+  e = cudaGraphInstantiate(&h->graph_exec[v], g, 0);
   if (e != cudaSuccess) {
     cudaGraphDestroy(g);
     return fail(EMPPP_ERR_CUDA, "graph instantiation: %s", cudaGetErrorString(e));
   }
-  h->graph = g;
-  h->graph_launches = k;
-  memcpy(h->graph_key, key, sizeof(key));
-  h->graph_valid = true;
+  h->graph[v] = g;
+  h->graph_launches[v] = k;
+  h->graph_valid[v] = true;
   return EMPPP_OK;
 }
 
@@ -729,6 +748,7 @@ EMPPP_API emppp_status emppp_set_particles(emppp_handle h, const double* x, cons
   h->t = 0.0;
   h->hist_start = 0;
   h->has_state = true;
+  h->order_age = -1;  // a new state: the next step recomputes the target order
   return EMPPP_OK;
 }
 
@@ -801,6 +821,7 @@ EMPPP_API emppp_status emppp_set_history(emppp_handle h, int64_t n, int32_t nslo
   h->t = hT[nslots - 1];
   h->hist_start = hs;
   h->has_state = true;
+  h->order_age = -1;  // a new state: the next step recomputes the target order
   return EMPPP_OK;
 }
 
@@ -859,20 +880,23 @@ EMPPP_API emppp_status emppp_step(emppp_handle h, int64_t nsteps, const emppp_be
   if ((st = update_schedule(h)) != EMPPP_OK) return st;
   const bool use_graph = h->opt.graphs && !h->opt.timing && h->stream != nullptr && nsteps > 1;
   NvtxRange r_step(use_graph ? "emppp_step (graph replay)" : "emppp_step");
-  if (use_graph && (st = capture_step(h, bp)) != EMPPP_OK) return st;
   long long pairs_per_step = 0;
   if (h->opt.pair_fields)
     for (int b = 0; b < h->nbunch; b++) pairs_per_step += (long long)h->hb[b].n * (h->hb[b].n - 1);
   for (int64_t k = 0; k < nsteps; k++) {
     int nk = 0;
+    const bool refresh = h->order_age < 0 || h->order_age >= kOrderEvery - 1;
     if (use_graph) {
-      CU(cudaGraphLaunch(h->graph_exec, h->stream));
-      nk = h->graph_launches;
+      if ((st = capture_step(h, bp, refresh)) != EMPPP_OK) return st;
+      const int v = refresh ? 1 : 0;
+      CU(cudaGraphLaunch(h->graph_exec[v], h->stream));
+      nk = h->graph_launches[v];
     } else {
       cudaEvent_t* ev = nullptr;
       if (h->opt.timing && h->ev_used < emppp_ctx::kTimedSteps) ev = &h->events[4 * h->ev_used++];
-      if ((st = enqueue_step(h, bp, ev, &nk)) != EMPPP_OK) return st;
+      if ((st = enqueue_step(h, bp, ev, &nk, refresh)) != EMPPP_OK) return st;
     }
+    h->order_age = refresh ? 0 : h->order_age + 1;
     h->launches += nk;
     h->pairs_acc += pairs_per_step;
     h->steps_acc += 1;

@@ -16,6 +16,7 @@ namespace {
 
 constexpr int kThreads = 1024;
 constexpr int kMaxBits = 5;
+constexpr int kUnroll = 4;  // particles whose positions a thread loads before it uses any of them
 
 __device__ __forceinline__ unsigned spread3(unsigned v, int bits) {  // bit k -> bit 3k
   unsigned r = 0;
@@ -43,15 +44,29 @@ __global__ void __launch_bounds__(kThreads) order_kernel(DeviceState s, unsigned
   const int pn = (int)(s.state->n % s.D);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
 
+  // present FP32 position (hi part) of particle k of the bunch: one record per particle's ring run, so
+  // every particle is its own cache line; kUnroll of them are loaded before any is used
+  const float4* __restrict__ rec = reinterpret_cast<const float4*>(s.rec32);
+  auto position = [&](int k) { return __ldg(rec + ((size_t)(off + k) * s.D + pn) * 3); };
   // bounding box of the present FP32 positions
   float lo[3] = {3.0e38f, 3.0e38f, 3.0e38f}, hi[3] = {-3.0e38f, -3.0e38f, -3.0e38f};
-  for (int k = tid; k < n; k += kThreads) {
-    const float* q = s.rec32 + ((size_t)(off + k) * s.D + pn) * 12;
-    for (int c = 0; c < 3; c++) {
-      const float x = q[c];
-      if (x == x) {
-        lo[c] = fminf(lo[c], x);
-        hi[c] = fmaxf(hi[c], x);
+  for (int k0 = tid; k0 < n; k0 += kUnroll * kThreads) {
+    float4 q[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      const int k = k0 + u * kThreads;
+      const float nan = __int_as_float(0x7fc00000);  // skipped by the box below
+      q[u] = k < n ? position(k) : make_float4(nan, nan, nan, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      const float x3[3] = {q[u].x, q[u].y, q[u].z};
+      for (int c = 0; c < 3; c++) {
+        const float x = x3[c];
+        if (x == x) {
+          lo[c] = fminf(lo[c], x);
+          hi[c] = fmaxf(hi[c], x);
+        }
       }
     }
   }
@@ -79,18 +94,29 @@ __global__ void __launch_bounds__(kThreads) order_kernel(DeviceState s, unsigned
   }
   // cell keys and histogram
   const float side = (float)(1 << bits);
-  for (int k = tid; k < n; k += kThreads) {
-    const float* q = s.rec32 + ((size_t)(off + k) * s.D + pn) * 12;
-    unsigned cc[3];
-    for (int c = 0; c < 3; c++) {
-      float f = bw[c] > 0.f ? (q[c] - blo[c]) / bw[c] : 0.f;
-      f = (f == f) ? fminf(fmaxf(f, 0.f), 1.f) : 0.f;
-      const int m = (int)(f * side);
-      cc[c] = (unsigned)(m >= (1 << bits) ? (1 << bits) - 1 : m);
+  for (int k0 = tid; k0 < n; k0 += kUnroll * kThreads) {
+    float4 q[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      const int k = k0 + u * kThreads;
+      q[u] = k < n ? position(k) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const unsigned m = spread3(cc[0], bits) | (spread3(cc[1], bits) << 1) | (spread3(cc[2], bits) << 2);
-    key[off + k] = m;
-    atomicAdd(hist + m, 1);
+#pragma unroll
+    for (int u = 0; u < kUnroll; u++) {
+      const int k = k0 + u * kThreads;
+      if (k >= n) break;
+      const float x3[3] = {q[u].x, q[u].y, q[u].z};
+      unsigned cc[3];
+      for (int c = 0; c < 3; c++) {
+        float f = bw[c] > 0.f ? (x3[c] - blo[c]) / bw[c] : 0.f;
+        f = (f == f) ? fminf(fmaxf(f, 0.f), 1.f) : 0.f;
+        const int m = (int)(f * side);
+        cc[c] = (unsigned)(m >= (1 << bits) ? (1 << bits) - 1 : m);
+      }
+      const unsigned m = spread3(cc[0], bits) | (spread3(cc[1], bits) << 1) | (spread3(cc[2], bits) << 2);
+      key[off + k] = m;
+      atomicAdd(hist + m, 1);
+    }
   }
   __syncthreads();
   // exclusive scan of the cell counts: each thread owns a contiguous run of cells

@@ -168,6 +168,30 @@ def test_graph_replay_equals_eager(precision):
     assert res[0][3] == res[1][3]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_target_order_refresh_changes_no_result(precision):
+    """The spatial target order is recomputed every 16 steps: an older order is still a permutation of the
+    bunch, and each target's sum runs over the sources in a fixed order, so 40 replayed steps with the order
+    equal 40 with the identity order bit for bit; the ordered run launches the order kernel at steps 0, 16
+    and 32 only."""
+    b = inputs.gaussian_bunch(3000, 8e-6, 3.0, seed=9)
+    stream = torch.cuda.Stream()
+    res = []
+    for order in (0, 1):
+        with emppp.Solver(3000, 64, DT, precision=precision, proposal="closed_form", stream=stream,
+                          graphs=True) as s:
+            s.set_particles(b.x.copy(), b.u.copy())
+            s.set_tuning(items_per_block=16, target_order=order)
+            s.reset_stats()
+            s.step(40)
+            x, u, _, n = s.get_state()
+            E, B = s.get_fields()
+            res.append((x, u, E, B, s.stats()["kernel_launches"]))
+    for k in range(4):
+        assert np.array_equal(res[0][k], res[1][k])
+    assert res[1][4] - res[0][4] == 3
+
+
 def test_two_stage_pipeline_batched_equals_single():
     """Stage 1 (mixed, 20 steps) -> handoff to 4 Earth radii -> stage 2 (dipole, 2000 steps) for a small
     batch of bunches, against the same pipeline run bunch by bunch."""
