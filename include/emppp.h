@@ -447,7 +447,8 @@ EMPPP_API emppp_status emppp_two_stage(emppp_handle h, const double* x0, const d
 /* Sets the network used by EMPPP_PROPOSAL_MLP (params host or device, EMPPP_MLP_NUM_PARAMS values). On the
  * mixed path the network runs once per step in a kernel of its own, for every (group of 512 targets in the
  * spatial order, source) pair of each bunch, at the group's mean position; the first call allocates that
- * buffer of delay factors (sum over bunches of ceil(n / 512) n floats: 33.5 MB at n = 65536). On the FP64
+ * buffer of delay factors (sum over bunches of ceil(n / 512) n floats: 33.5 MB at n = 65536; EMPPP_ERR_ARG
+ * if that sum exceeds 2^31 - 1, i.e. for bunches of more than about a million particles). On the FP64
  * path each warp evaluates it for 32 sources at a time at its own targets' mean position. */
 EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, int32_t is_device_ptr);
 

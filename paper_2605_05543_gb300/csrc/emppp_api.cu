@@ -1270,6 +1270,9 @@ EMPPP_API emppp_status emppp_set_proposal(emppp_handle h, const float* params, i
   emppp_status st = check_handle(h);
   if (st != EMPPP_OK) return st;
   if (!params) return fail(EMPPP_ERR_ARG, "params is NULL");
+  if (h->fac_count > 2147483647LL)
+    return fail(EMPPP_ERR_ARG, "the learned proposal's table of delay factors would hold %lld entries, more than "
+                "2^31 - 1 (bunches of more than about a million particles)", h->fac_count);
   if (!h->ds.mlp_fac && h->fac_count > 0) {
     // the delay factors of the mixed path's learned proposal: one per (target group, source) pair
     if ((st = dalloc(h, &h->ds.mlp_fac, (size_t)h->fac_count)) != EMPPP_OK) return st;

@@ -425,7 +425,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ gra
 // source's present record and its velocity one slot earlier, in the FP32 shadow ring), one source per lane.
 constexpr int kFacThreads = 256;
 
-__global__ void __launch_bounds__(kFacThreads) factor_kernel(DeviceState s, const int* __restrict__ order) {
+__global__ void __launch_bounds__(kFacThreads, 3) factor_kernel(DeviceState s, const int* __restrict__ order) {
   __shared__ float4 s_part[kFacThreads / 32];
   const int gall = blockIdx.x;
   int b = 0;

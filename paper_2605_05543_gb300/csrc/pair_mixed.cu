@@ -278,7 +278,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   }
   // learned proposal: the delay factors of this target tile's group (kFacGroup targets, a multiple of the
   // tile), one per source of the bunch
-  const float* fac_row = PROP == kPropMlp ? a.fac + bd.fac_off + (size_t)((tb * kBlock) / kFacGroup) * bd.n : nullptr;
+  // (as an index of a.fac relative to the bunch's first particle: the table has fewer than 2^31 entries)
+  const int fac_row = PROP == kPropMlp ? (int)(bd.fac_off + (long long)((tb * kBlock) / kFacGroup) * bd.n) - boff : 0;
   // the lane's guessed older-node offset for staged source jj of the tile (-1: predicted out of history)
   auto guess_of = [&](int jj) -> int {
     const float sc = closed_form_ctau(r, s_q0[jj], s_q2[jj]) * inv_cdt;
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       s_q0[threadIdx.x] = q[0];
       const float4 q2 = q[2];
       s_q2[threadIdx.x] = make_float4(bref01.x + q2.x, bref01.y + q2.y, bref2 + q2.z,
-                                      PROP == kPropMlp ? q2.w * __ldg(fac_row + (j - boff)) : q2.w);
+                                      PROP == kPropMlp ? q2.w * __ldg(a.fac + (fac_row + j)) : q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
       s_q1[threadIdx.x] = q[1];
       s_x[threadIdx.x] = __ldg(a.ext32 + 3 * j + 2);
