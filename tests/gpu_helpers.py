@@ -28,11 +28,14 @@ def field_errors(E, B, E_ref, B_ref, M):
     return float(np.max(np.abs(E - E_ref) / sE)), float(np.max(np.abs(B - B_ref) / sB))
 
 
-def gpu_fields_from_history(Solver, h, D, dt=DT, **kw):
-    """Fields and stats of one GPU step evaluated on history h (and the state after the step)."""
+def gpu_fields_from_history(Solver, h, D, dt=DT, tuning=None, **kw):
+    """Fields and stats of one GPU step evaluated on history h (and the state after the step); tuning:
+    keyword arguments of Solver.set_tuning (work split and tile shape), else the defaults."""
     T, W, V, u = window(h, D)
     with Solver(W.shape[1], D, dt, **kw) as s:
         s.set_history(h.n, T, W, V, u)
+        if tuning:
+            s.set_tuning(**tuning)
         s.step(1)
         E, B = s.get_fields()
         st = s.stats()

@@ -121,12 +121,15 @@ def test_dipole_transport_without_pair_fields():
     assert np.max(np.abs(B - run.B)) <= 1e-12 * np.max(np.abs(run.B))
 
 
-def test_full_size_sampled_targets():
-    """N = 65536, sigma = 20 um, gamma0 = 3, depth 1024, history of 251 slots: the launch the
-    benchmark times. The oracle evaluates 48 sampled targets against all sources."""
+@pytest.mark.parametrize("shape", [(128, 8), (64, 8)])
+def test_full_size_sampled_targets(shape):
+    """N = 65536, sigma = 20 um, gamma0 = 3, depth 1024, history of 251 slots: the benchmark's workload,
+    at the default tile shape and at (64, 8), which the autotuner can choose on the FP64 path. The oracle
+    evaluates 48 sampled targets against all sources."""
     N, n, D = 65536, 250, 1024
     h = history_case(N, n, sigma=20e-6, seed=0)
-    E, B, st, x, u = gpu_fields_from_history(emppp.Solver, h, D, proposal="closed_form")
+    tuning = dict(items_per_block=16, target_order=1, targets_per_block=shape[0], sources_per_sum=shape[1])
+    E, B, st, x, u = gpu_fields_from_history(emppp.Solver, h, D, tuning=tuning, proposal="closed_form")
     rng = np.random.default_rng(0)
     tg = np.unique(np.concatenate([[0, 1, N - 1], rng.choice(N, 45, replace=False)]))
     E_ref, B_ref, st_ref, M = oracle.self_fields(h.T, h.W, h.V, n, D, targets=tg, mags=True)

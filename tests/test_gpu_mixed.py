@@ -49,11 +49,16 @@ def test_mixed_fields_match_fp64_oracle(N, n, D, sigma, seed, proposal):
         assert st["node_tests"] == st_ref["node_tests"]
 
 
-def test_mixed_full_size_sampled_targets():
-    """N = 65536, sigma = 20 um, depth 1024, 251-slot history: the benchmark launch."""
+@pytest.mark.parametrize("shape", [(128, 8), (128, 32)])
+def test_mixed_full_size_sampled_targets(shape):
+    """N = 65536, sigma = 20 um, depth 1024, 251-slot history: the benchmark's workload, at the default
+    tile shape and at the one the benchmark's autotuner chooses (128 targets per block, 32 sources per
+    FP32 partial sum)."""
     N, n, D = 65536, 250, 1024
     h = history_case(N, n, sigma=20e-6, seed=0)
-    E, B, st, x, u = gpu_fields_from_history(emppp.Solver, h, D, precision="mixed", proposal="closed_form")
+    tuning = dict(items_per_block=16, target_order=1, targets_per_block=shape[0], sources_per_sum=shape[1])
+    E, B, st, x, u = gpu_fields_from_history(emppp.Solver, h, D, tuning=tuning, precision="mixed",
+                                             proposal="closed_form")
     rng = np.random.default_rng(1)
     tg = np.unique(np.concatenate([[0, N - 1], rng.choice(N, 62, replace=False)]))
     E_ref, B_ref, _, M = oracle.self_fields(h.T, h.W, h.V, n, D, targets=tg, mags=True)
