@@ -278,3 +278,16 @@ def test_network_trained_out_of_sample_gains_over_bisection():
     print(f"out of sample: node tests per pair bisection {tb:.4f}, closed form {tc:.4f}, network {tm:.4f}")
     assert tm < 0.5 * tb
     assert tm <= 1.01 * tc
+
+
+def test_factor_table_beyond_int32_is_refused():
+    """The mixed path's table of delay factors holds sum_b ceil(n_b / 512) n_b entries, addressed with 32-bit
+    offsets: a bunch of 2^20 + 1 particles needs more than 2^31 - 1 of them, and emppp_set_proposal refuses it
+    (a short history keeps the handle's own memory small); 2^20 - 512 particles fit."""
+    params = inputs.mlp_init_params(3)
+    with emppp.Solver((1 << 20) + 1, 2, DT, precision="mixed") as s:
+        with pytest.raises(emppp.EmpppError) as e:
+            s.set_proposal(params)
+        assert e.value.status == emppp.ERR_ARG
+    with emppp.Solver((1 << 20) - 512, 2, DT, precision="mixed") as s:
+        s.set_proposal(params)
