@@ -599,7 +599,8 @@ def other_workloads(args, state):
     comparison variants on the bunch's state, and the 64-bunch two-stage batch, each as its own line
     (value, clocks, config), as `--workload paper|variants|batch` prints it."""
     sub = copy.copy(args)
-    sub.steps, sub.warmup = None, 3
+    # each at its own defaults: the mixed path with the closed-form guess (the variants run the FP64 path)
+    sub.steps, sub.warmup, sub.path, sub.proposal = None, 3, "mixed", "closed_form"
     out = {}
     sub.workload = "paper"
     out["paper"] = run_paper(sub)
