@@ -263,7 +263,7 @@ EMPPP_API emppp_status emppp_bracket_dump(emppp_handle h, int32_t* brackets, int
 EMPPP_API emppp_status emppp_set_tuning(emppp_handle h, const emppp_tuning* tuning);
 
 /* Probes of the bounded wait of a warp on its staged history window (history_window on; default 65536, each
- * probe may suspend the thread for a short hardware-defined time). A wait that gives up leaves that warp
+ * probe suspending the thread for at most 1 us, so a wait gives up after at most about 65 ms). A wait that gives up leaves that warp
  * gathering the records from the ring for the rest of the launch, so the fields are unchanged, and the
  * device error word records it: the next call that reads it returns EMPPP_ERR_TIMEOUT. probes = 0 makes
  * every such wait give up at once (a test of that path). EMPPP_ERR_ARG for probes < 0. */

@@ -33,21 +33,23 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uin
                : "memory");
 }
 
+// suspend-time hint of one probe (ns): the longest a probe keeps the thread waiting for the phase
+constexpr uint32_t kProbeNs = 1000;
+
 // one probe of the phase with the given parity; true once that phase has completed
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kProbeNs)
       : "memory");
   return ok != 0;
 }
 
-// at most `limit` probes (each may suspend the thread for a short, hardware-defined time); false if the
-// phase has not completed by then
+// at most `limit` probes of at most kProbeNs each; false if the phase has not completed by then
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int limit) {
   for (int it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
