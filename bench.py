@@ -602,12 +602,13 @@ def other_workloads(args, state):
     # each at its own defaults: the mixed path with the closed-form guess (the variants run the FP64 path)
     sub.steps, sub.warmup, sub.path, sub.proposal = None, 3, "mixed", "closed_form"
     out = {}
-    sub.workload = "paper"
-    out["paper"] = run_paper(sub)
-    sub.workload = "variants"
-    out["variants"] = run_variants(sub, state)
-    sub.workload = "batch"
-    out["batch"] = run_batch(sub)
+    for name, run in (("paper", lambda: run_paper(sub)), ("variants", lambda: run_variants(sub, state)),
+                      ("batch", lambda: run_batch(sub))):
+        sub.workload = name
+        try:
+            out[name] = run()
+        except Exception as e:  # one workload's failure is reported in the line, not lost with it
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 
