@@ -34,6 +34,9 @@ namespace {
 
 constexpr int kSumBlock = 64;
 constexpr double kCoulomb = 1.0 / (4.0 * kPi * kEps0);
+// the sums run over w_j-weighted fields without the electron's charge constant -e / (4 pi eps0), and over
+// c^2 B; both are scaled once per target
+constexpr double kFieldScale = -kQe * kCoulomb;
 
 // 1 / x for finite x > 0: the hardware's approximate reciprocal refined by two Newton-Raphson steps
 // y <- y + y (1 - x y). Each step squares the relative error, so the approximation's error falls below
@@ -322,8 +325,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
         continue;
       }
       const double iD = rsqrt(Dh);
-      const double q = -kQe * __ldg(a.wts + j);
-      const double pref = (kCoulomb * kC) * q * c2mv2 * (iD * iD * iD);
+      // E / (-e / (4 pi eps0)): the source's charge constant is applied once per target (kFieldScale)
+      const double pref = (kC * __ldg(a.wts + j)) * c2mv2 * (iD * iD * iD);
       const double E0 = pref * X0, E1 = pref * X1, E2 = pref * X2;
       if (ADAPT) {
         // retarded distance R = c (t - t_r), the positive root of R^2 (c^2 - v^2) - 2 R c (X.v) - c^2 |X|^2
@@ -336,13 +339,13 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
           vmax2 = fmax(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
         }
       }
-      const double ic2 = 1.0 / c2;
+      // c^2 B = v x E (the 1 / c^2 is applied once per target)
       Ep[0] += E0;
       Ep[1] += E1;
       Ep[2] += E2;
-      Bp[0] += (v11 * E2 - v12 * E1) * ic2;
-      Bp[1] += (v12 * E0 - v10 * E2) * ic2;
-      Bp[2] += (v10 * E1 - v11 * E0) * ic2;
+      Bp[0] += v11 * E2 - v12 * E1;
+      Bp[1] += v12 * E0 - v10 * E2;
+      Bp[2] += v10 * E1 - v11 * E0;
       if (++in_block == kSumBlock) {
         in_block = 0;
 #pragma unroll
@@ -418,10 +421,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
     const double xa0 = vp1 * a2 - vp2 * a1, xa1 = vp2 * a0 - vp0 * a2, xa2 = vp0 * a1 - vp1 * a0;
     const double ac0 = e1 * xa2 - e2 * xa1, ac1 = e2 * xa0 - e0 * xa2, ac2 = e0 * xa1 - e1 * xa0;
     const double ievp = recip_newton(evp);
-    const double q = -kQe * __ldg(a.wts + j);
-    const double pref = kCoulomb * q * R * (ievp * ievp * ievp);
+    const double pref = (__ldg(a.wts + j) * R) * (ievp * ievp * ievp);  // charge constant once per target
     const double E0 = pref * (c2mv2 * vp0 + ac0), E1 = pref * (c2mv2 * vp1 + ac1), E2 = pref * (c2mv2 * vp2 + ac2);
-    const double bs = invR * (1.0 / kC);
+    const double bs = invR * kC;  // c^2 B = c eta_hat x E
     if (ADAPT && R >= a.eta_allow) {
       // interaction scale of the adaptive step: |eta_ij| and |v_i(t_n) - v_j(t_r)|
       emin = fmin(emin, R);
@@ -447,8 +449,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
   }
 #pragma unroll
   for (int c = 0; c < 3; c++) {
-    Et[c] += Ep[c];
-    Bt[c] += Bp[c];
+    Et[c] = (Et[c] + Ep[c]) * kFieldScale;
+    Bt[c] = (Bt[c] + Bp[c]) * (kFieldScale / (kC * kC));
   }
   if (active) {
     if (bs.nchunk == 1) {
