@@ -9,7 +9,8 @@ same state:
   - both agree with the FP64 oracle within the mixed path's 1e-5 of sum_j |F_ij|.
 Cases: several target tiles with a ragged tail, a ring window that has wrapped (copies in two runs), an
 untrained learned proposal (guesses all over the history, windows cut at their slot limit), targets on the
-light sphere of a stored slot, and a single-slot history (nothing to stage).
+light sphere of a stored slot, a single-slot history (nothing to stage), and the benchmark's N = 65536
+workload.
 A wait limit of zero makes every warp's first wait give up: the kernel then gathers from the ring, the
 fields stay identical and the next status read is EMPPP_ERR_TIMEOUT.
 """
@@ -128,3 +129,15 @@ def test_window_requires_its_shape():
             with pytest.raises(emppp.EmpppError):
                 s.set_tuning(targets_per_block=tpb, sources_per_sum=sps, history_window=1)
         s.set_tuning(targets_per_block=128, sources_per_sum=32, history_window=1)
+
+
+def test_window_full_size_identical():
+    """N = 65536, depth 1024, 251-slot history (the benchmark's workload, where the autotuner times the window
+    instance): fields and counts equal to (128, 32) without the window, bit for bit."""
+    N, n, D = 65536, 250, 1024
+    h = history_case(N, n, sigma=20e-6, seed=0)
+    T, W, V, u = window(h, D)
+    E0, B0, s0, st0 = _fields(T, W, V, u, n, D, "closed_form", False)
+    E1, B1, s1, st1 = _fields(T, W, V, u, n, D, "closed_form", True)
+    assert st0 == emppp.OK and st1 == emppp.OK
+    assert np.array_equal(E0, E1) and np.array_equal(B0, B1) and s0 == s1
