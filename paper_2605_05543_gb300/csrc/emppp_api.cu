@@ -310,7 +310,7 @@ emppp_status read_err(emppp_handle h) {
   if (herr) {
     return fail(EMPPP_ERR_NUMERIC,
                 "device numeric fault (bits 0x%x: 1 = negative discriminant or |v| >= c, 2 = coincident pair, "
-                "4 = non-finite state, 8 = wait limit)",
+                "4 = non-finite state, 8 = wait limit, 16 = index outside its range in the debug build)",
                 herr);
   }
   return EMPPP_OK;

@@ -45,7 +45,28 @@ enum : int {
   kErrCoincide = 2,  // eta = 0 or eta . v' <= 0
   kErrNonFinite = 4, // non-finite field or state
   kErrTimeout = 8,   // a bounded wait of a pair kernel on its bulk copies gave up
+  kErrBounds = 16,   // debug build: an index outside its range (kDebug)
 };
+
+// Debug build (-DEMPPP_DEBUG, library libemppp_debug.so): the pair kernels check every history-window
+// offset they turn into a ring slot, and every source and target index, against its range. A failed
+// check records kErrBounds in the device error word and goes on with a safe index instead of trapping.
+// The release build compiles the checks away.
+#ifdef EMPPP_DEBUG
+constexpr bool kDebug = true;
+#else
+constexpr bool kDebug = false;
+#endif
+
+// v if lo <= v < hi; otherwise (debug build) the error bit and lo
+template <typename I>
+__device__ __forceinline__ I debug_index(I v, I lo, I hi, int* err) {
+  if (kDebug && (v < lo || v >= hi)) {
+    atomicOr(err, kErrBounds);
+    return lo;
+  }
+  return v;
+}
 
 struct StepState {
   long long n;           // present (absolute) step index

@@ -93,8 +93,9 @@ __device__ __forceinline__ bool node_test(double r0, double r1, double r2, const
 struct Window {
   long long k0, n;
   int p0, D;
+  int* err;  // device error word (the debug build's range checks)
   __device__ __forceinline__ int phys(long long k) const {
-    int p = p0 + (int)(k - k0);
+    int p = p0 + (int)(debug_index(k, k0, n + 1, err) - k0);
     return p >= D ? p - D : p;
   }
 };
@@ -114,6 +115,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
   win.k0 = a.state->k0;
   win.p0 = a.state->p0;
   win.D = D;
+  win.err = a.err;
   const int pn = a.state->pn;
   const double t = a.state->t;
   const float inv_cdt = PROP != kPropBisect ? (float)(1.0 / (kC * a.state->dt)) : 0.f;
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
   const float3 bref = make_float3((float)bd.beta_ref[0], (float)bd.beta_ref[1], (float)bd.beta_ref[2]);
   const long long i_loc = (long long)tb * kBlock + threadIdx.x;
   const bool active = i_loc < bd.n;
-  const long long i = a.order ? a.order[bd.off + (active ? i_loc : 0)] : bd.off + (active ? i_loc : 0);
+  const long long i = debug_index<long long>(a.order ? a.order[bd.off + (active ? i_loc : 0)] : bd.off + (active ? i_loc : 0),
+                                            bd.off, bd.off + bd.n, a.err);
   const long long ic = i;
 
   const double* rr = a.rec64 + ((size_t)ic * D + pn) * 6;
@@ -185,8 +188,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE)) pair_fp64_kernel(PairArgs 
     }
     if (!active) continue;  // and stay in the loop for the next group's evaluation
     if (j == i) continue;
-    const double* src = a.rec64 + (size_t)j * D * 6;
-    const float4* src32 = reinterpret_cast<const float4*>(a.rec32 + (size_t)j * D * 12);
+    const long long jc = debug_index(j, bd.off, bd.off + bd.n, a.err);  // j itself in a release build
+    const double* src = a.rec64 + (size_t)jc * D * 6;
+    const float4* src32 = reinterpret_cast<const float4*>(a.rec32 + (size_t)jc * D * 12);
     // P(k) at physical slot p: FP32 on the hi/lo split outside the guard band, else the FP64 test
     auto ntest = [&](int p) -> bool {
       const float4 q0 = __ldg(src32 + 3 * p), q1 = __ldg(src32 + 3 * p + 1);

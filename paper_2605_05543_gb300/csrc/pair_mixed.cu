@@ -92,8 +92,9 @@ struct Target {
 // slots of the usable window k0..n are addressed by their offset l = k - k0 (0..nw-1)
 struct Window {
   int p0, D, nw;
+  int* err;  // device error word (the debug build's range checks)
   __device__ __forceinline__ int phys(int l) const {
-    const int p = p0 + l;
+    const int p = p0 + debug_index(l, 0, nw, err);
     return p >= D ? p - D : p;
   }
 };
@@ -226,6 +227,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   const long long k0_abs = a.state->k0;
   win.p0 = a.state->p0;
   win.D = D;
+  win.err = a.err;
   win.nw = (int)(n_abs - k0_abs) + 1;
   const int pn = a.state->pn;
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   const int t_loc = tb * kBlock + threadIdx.x;
   const bool active = t_loc < bd.n;
   const int t = boff + (active ? t_loc : 0);
-  const int i = a.order ? a.order[t] : t;
+  const int i = debug_index(a.order ? a.order[t] : t, boff, boff + bd.n, a.err);
 
   Target r;
   {
@@ -308,7 +310,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
     unsigned brc = 0;  // out-of-history, shortcut and bisection counts of this tile (at most kTile each)
     __syncthreads();
     if (threadIdx.x < tn) {
-      const int j = tile + threadIdx.x;
+      const int j = debug_index<int>(tile + (int)threadIdx.x, boff, boff + bd.n, a.err);
       const float4* q = a.rec32 + ((size_t)j * D + pn) * 3;
       s_q0[threadIdx.x] = q[0];
       const float4 q2 = q[2];
@@ -328,6 +330,10 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       const int hi = __reduce_max_sync(0xffffffffu, want ? g : -1);
       if (lo > hi) return;
       const int nsl = min(hi + 2 - lo, kWin);
+      if (kDebug && (lo < 0 || lo + nsl > win.nw)) {  // the staged run lies inside the usable window
+        if ((threadIdx.x & 31) == 0) atomicOr(a.err, kErrBounds);
+        return;
+      }
       if ((threadIdx.x & 31) == 0) {
         const int wb = (threadIdx.x >> 5) * 2 + sb;
         s_wd[wb] = make_int2(lo, nsl);
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       const int jend = min(jj0 + kSub, tn);
       for (int jj = jj0; (WIN || active) && jj < jend; ++jj) {
-        const int j = tile + jj;
+        const int j = debug_index(tile + jj, boff, boff + bd.n, a.err);
         // history window of this source (WIN): guessed offset, first offset and slots of the staged run
         int g_cur = -1, w_lo = 0, w_n = 1;
         const int sb = jj & 1;

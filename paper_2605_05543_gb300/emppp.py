@@ -156,7 +156,8 @@ SIGNATURES = {
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library load() uses: the debug build when the environment sets EMPPP_DEBUG_LIB=1."""
+    return _build.DEBUG_LIB if os.environ.get("EMPPP_DEBUG_LIB") == "1" else _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -164,11 +165,12 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    debug = os.environ.get("EMPPP_DEBUG_LIB") == "1"  # the build with the kernels' index range checks
+    path = library_path()
     if not os.path.exists(path):
         if not build_if_missing:
             raise RuntimeError(f"EM-PP CUDA library not built ({path}); run __graft_entry__.build()")
-        _build.build_library()
+        _build.build_library(debug=debug)
     lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
