@@ -618,7 +618,7 @@ emppp_status create_impl(int32_t nbunch, const int64_t* nper, int32_t history_de
   ALLOC(s.bsum, (size_t)nbunch * 4);
   ALLOC(s.scale, (size_t)nbunch * 2);
   ALLOC(s.adapt_info, 3);
-  ALLOC(s.ext32, N * 3);
+  ALLOC(s.ext32, N * kExtCount);
   ALLOC(c->d_mon, (size_t)nbunch);
   ALLOC(c->staging, N * 7);
   ALLOC(c->ord_key, N);

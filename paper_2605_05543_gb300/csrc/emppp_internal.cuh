@@ -15,8 +15,10 @@
 //   slot_t [D]                time stamp of each physical slot.
 //   slot tables [D]           per step: (c (t_n - t_k))^2 in FP64 and FP32, c (t_n - t_k),
 //                             1 / (t_{k+1} - t_k) in FP64 and 1 / (c (t_{k+1} - t_k)) in FP32.
-//   ext32  [N][3] float4      per step (mixed path): hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) - origin,
-//                             and w_{k0} + v_{k0} (t_n - t_{k0}) - w_n.
+//   ext32  [N][5] float4      per step (mixed path): hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) - origin,
+//                             w_{k0} + v_{k0} (t_n - t_{k0}) - w_n, the chord w_n - w_{k0} with the
+//                             threshold of the oldest-slot bound, and the FP32 record's beta - beta_ref,
+//                             1/gamma^2 and gamma^2 of slot k0 (kExt* below).
 //   u      [N][3]             present proper velocities (FP64).
 //   Eself/Bself [N][3]        self fields of the current step; Bout [N][3] = Bself + B_ext.
 //   ke     [N]                kinetic-energy terms of the energy monitor (small systems, formed by the push).
@@ -92,6 +94,28 @@ enum { kStatOOH = 0, kStatShortcut = 1, kStatBisect = 2, kStatNodeTests = 3, kSt
 // rounding, so the FP32 decision is the FP64 one; between the thresholds the FP64 test decides.
 constexpr double kGuardBand = 32.0 * 5.9604644775390625e-08;
 
+// Oldest-slot bound of the mixed path. For a pair whose uniform-motion guess lies beyond the history, the
+// node test of slot k0 is |r - w_k0|^2 = |d|^2 + 2 d.c + |c|^2 with d = r - w_n (formed from the staged
+// present records) and the source's chord c = w_n - w_k0. In FP32, |d|^2 carries a relative error below
+// 7u and d.c (with c rounded to FP32) an absolute one below 3u (|d|^2 + |c|^2). So if
+//   2 d.c + |d|^2 (1 - 32u)  >  T (1 + 32u) - |c|^2 (1 - 32u),
+// both sides as computed, with T the FP32 upper threshold of slot k0, then the exact |r - w_k0|^2 exceeds
+// T (1 + 32u), and the FP32 value the node test forms exceeds T: the test is true by its first
+// comparison, with no record of slot k0 loaded. The right-hand side is formed per source in FP64 and
+// rounded up (setup_kernel); kChordLo is 1 - 32u.
+constexpr double kChordMargin = 32.0 * 5.9604644775390625e-08;
+constexpr float kChordLo = 1.0f - 32.0f * 5.9604644775390625e-08f;
+
+// per-source float4s of ext32 (mixed path)
+enum {
+  kExtSegHi = 0,   // hi of w_{n-1} + v_{n-1} (t_n - t_{n-1}) - origin
+  kExtSegLo = 1,   // lo of the same
+  kExtLine = 2,    // w_{k0} + v_{k0} (t_n - t_{k0}) - w_n; w: gamma^2 of slot k0 (FP32 record)
+  kExtChord = 3,   // FP32 w_n - w_{k0}; w: right-hand side of the oldest-slot bound (+inf without one)
+  kExtOldest = 4,  // FP32 record of slot k0: beta - beta_ref, 1/gamma^2
+  kExtCount = 5
+};
+
 struct SlotTables {
   double* lhs64;    // [D] (c (t_n - t_k))^2, formed as c*(t_n - t_k) then squared (no FMA)
   double* inv_dtk;  // [D] 1 / (t_{k+1} - t_k) for k < n
@@ -155,9 +179,10 @@ struct DeviceState {
   // [groups_b][n_b] from BunchDesc::fac_off, written by the factor kernel before each pair evaluation
   float* mlp_fac;
   int ngroups;  // target groups of all bunches
-  // [N][3] FP32 hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) relative to the bunch origin (the end of the
-  // last history segment of eq:linear, from which the mixed path forms near-field retarded points), and
-  // w_{k0} + v_{k0} (t_n - t_{k0}) - w_n (where the out-of-history line of eq:linear2 is at t_n)
+  // [N][kExtCount] FP32 hi/lo of w_{n-1} + v_{n-1} (t_n - t_{n-1}) relative to the bunch origin (the end
+  // of the last history segment of eq:linear, from which the mixed path forms near-field retarded points),
+  // w_{k0} + v_{k0} (t_n - t_{k0}) - w_n (where the out-of-history line of eq:linear2 is at t_n), and the
+  // oldest slot's chord, bound and velocity (the out-of-history pairs' node test and line)
   float4* ext32;
   // adaptive time step (Sec. 2.4)
   unsigned long long* scale;  // [nbunch][2] bit patterns of eta_min (m, by min) and v_max^2 ((m/s)^2, by max)

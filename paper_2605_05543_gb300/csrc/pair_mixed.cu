@@ -74,7 +74,7 @@ struct MixedArgs {
   const float* __restrict__ fac;  // learned proposal: delay factors [groups][n] per bunch (factor kernel)
   unsigned long long* scale;  // adaptive time step: eta_min / v_max^2 reduction
   float eta_allow;
-  const float4* __restrict__ ext32;  // [N][3] per source: segment end hi/lo, out-of-history line offset
+  const float4* __restrict__ ext32;  // [N][kExtCount] per source: segment end hi/lo, out-of-history line, oldest slot
   int* __restrict__ dump;  // [N][N] bracket of every evaluated pair, 4 (k1 - k0) + branch (DUMP instances only)
   int wait_limit;          // probes of a bounded wait on a staged history window (window shapes)
 };
@@ -191,13 +191,15 @@ __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict_
 
 }  // namespace
 
-// SHAPE: targets per block = sources per staged tile (kBlock), sources per FP32 partial sum (kSub); the
+// SHAPE: targets per block (kBlock), sources per FP32 partial sum (kSub); the
 // register budget stays at 64 per thread for every block size
 template <int PROP, bool ADAPT, bool DUMP, int SHAPE>
 __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 128 / shape_block(SHAPE))
     pair_mixed_kernel(MixedArgs a) {
   constexpr int kBlock = shape_block(SHAPE);
-  constexpr int kTile = kBlock;
+  // sources per staged tile: half a block's targets, which keeps 8 blocks of the (128, *) shapes within the
+  // 132 KB shared-memory carveout (the rest of the SM's 256 KB is the L1 of the pair gathers)
+  constexpr int kTile = kBlock / 2;
   constexpr int kSub = shape_sub(SHAPE);
   // history windows (shape_win): one elected lane per warp copies, one source ahead, the slots its lanes'
   // guessed brackets of the next source fall in from the FP32 shadow ring to shared memory (bulk copy,
@@ -215,7 +217,12 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   __shared__ float4 s_q2[kTile];
   __shared__ float s_kq[kTile];
   __shared__ float4 s_q1[kTile];  // present record (lo, 0) of the tile's sources
-  __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position (ext32)
+  __shared__ float4 s_x[kTile];   // out-of-history line at t_n, relative to the present position; gamma^2 of slot k0
+  // with the uniform-motion guess: the chord w_n - w_k0 and the oldest-slot bound's threshold, and slot k0's
+  // (beta - beta_ref, 1/gamma^2) (ext32)
+  constexpr int kTileG = PROP != kPropBisect ? kTile : 1;
+  __shared__ float4 s_ck[kTileG];
+  __shared__ float4 s_k0[kTileG];
   __shared__ float s_acc[12][kBlock];  // per-thread compensated sums
 
   __shared__ int s_item;
@@ -318,7 +325,12 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
                                       PROP == kPropMlp ? q2.w * __ldg(a.fac + (fac_row + j)) : q2.w);
       s_kq[threadIdx.x] = a.kq32[j];
       s_q1[threadIdx.x] = q[1];
-      s_x[threadIdx.x] = __ldg(a.ext32 + 3 * j + 2);
+      const float4* e = a.ext32 + (size_t)j * kExtCount;
+      s_x[threadIdx.x] = __ldg(e + kExtLine);
+      if (PROP != kPropBisect) {
+        s_ck[threadIdx.x] = __ldg(e + kExtChord);
+        s_k0[threadIdx.x] = __ldg(e + kExtOldest);
+      }
     }
     __syncthreads();
     // window of staged source jn into buffer sb: the offsets lo .. hi + 1 of the guessed brackets [lg, lg + 1]
@@ -387,6 +399,69 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         if (j == i) continue;
         const float4* src32 = a.rec32 + (size_t)j * D * 3;
         const double* src64 = a.rec64 + (size_t)j * D * 6;
+        auto heaviside = [&](float2 dn01, float dn2, float4 o, float g2, int pk) {
+          // ---- out of history (eq:linear2): the source moves uniformly with beta1 along the line through
+          // w1; its Lienard-Wiechert field is Heaviside's field about the line's point at t_n,
+          //   E = kq (1 - beta^2) X / [X^2 (1 - beta^2) + (X.beta)^2]^{3/2},  c B = beta x E,
+          // with X = (r - w_n) - (line at t_n - w_n) from the staged present record and line offset.
+          const float4 gx = s_x[jj];
+          const float2 X01 = sub2(dn01, gx);
+          float X0 = X01.x, X1 = X01.y;
+          float X2 = __fsub_rn(dn2, gx.z);
+          const float2 b101 = __fadd2_rn(bref01, make_float2(o.x, o.y));
+          const float b10 = b101.x, b11 = b101.y, b12 = __fadd_rn(bref2, o.z);
+          const float ig2 = o.w;
+          float Xb = dot3(X0, X1, X2, b10, b11, b12);
+          float XX = dot3(X0, X1, X2, X0, X1, X2);
+          // The FP32 rounding of X.beta (absolute about u |X|) moves the denominator by 2 u |X| |X.beta| /
+          // denominator relative, at most u gamma. Above 1.3e-6 (only for gamma above ~20, at directions
+          // near perpendicular to beta) X and X.beta are formed in FP64 from the FP64 records instead.
+          // (as the shift is at most u gamma, sources with gamma^2 < 100 never need it)
+          if (ig2 < 0.01f && __fmul_rn(kXbGuard, __fmul_rn(sqrtf(XX), fabsf(Xb))) > __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb))) {
+            const double* w0 = src64 + 6 * pk;  // FP64 record of slot k0: X = r - w_k0 - v_k0 (t_n - t_k0)
+            const double ct = kC * (a.state->t - __ldg(a.slot_t + pk));  // c (t_n - t_k0)
+            const double ic = 1.0 / kC;
+            const double* rr = a.rec64 + ((size_t)i * D + pn) * 6;
+            const double y0 = (__ldg(rr + 0) - __ldg(w0 + 0)) - __ldg(w0 + 3) * ic * ct;
+            const double y1 = (__ldg(rr + 1) - __ldg(w0 + 1)) - __ldg(w0 + 4) * ic * ct;
+            const double y2 = (__ldg(rr + 2) - __ldg(w0 + 2)) - __ldg(w0 + 5) * ic * ct;
+            X0 = (float)y0;
+            X1 = (float)y1;
+            X2 = (float)y2;
+            Xb = (float)((y0 * __ldg(w0 + 3) + y1 * __ldg(w0 + 4) + y2 * __ldg(w0 + 5)) * ic);
+            XX = dot3(X0, X1, X2, X0, X1, X2);
+            n_fb++;
+          }
+          const float Dh = __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb));
+          const float iD = rsqrtf(Dh);
+          if (!(Dh > 0.f) || !(ig2 > 0.f)) {
+            errbits |= (ig2 > 0.f) ? kErrCoincide : kErrDisc;
+            return;
+          }
+          const float pref = __fmul_rn(__fmul_rn(s_kq[jj], ig2), __fmul_rn(__fmul_rn(iD, iD), iD));
+          if (ADAPT) {
+            // retarded distance c (t - t_r) = gamma^2 [X.beta + sqrt(Dh)], and v(t_r) = v1
+            const float sD = __fmul_rn(Dh, iD);
+            const float R = (Xb >= 0.f) ? __fmul_rn(__fadd_rn(Xb, sD), g2)
+                                        : __fdividef(dot3(X0, X1, X2, X0, X1, X2), __fsub_rn(sD, Xb));
+            if (R >= a.eta_allow) {
+              emin = fminf(emin, R);
+              const float dv0 = bi0 - o.x, dv1 = bi1 - o.y, dv2 = bi2 - o.z;
+              vmax2 = fmaxf(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
+            }
+          }
+          const float2 p01 = __ffma2_rn(make_float2(pref, pref), make_float2(X0, X1), make_float2(P[0], P[1]));
+          P[0] = p01.x;
+          P[1] = p01.y;
+          P[2] = __fmaf_rn(pref, X2, P[2]);
+          // c B = beta x E = pref (beta x X)
+          const float2 p34 = __ffma2_rn(make_float2(pref, pref),
+                                        make_float2(cross1(b11, b12, X1, X2), cross1(b12, b10, X2, X0)),
+                                        make_float2(P[3], P[4]));
+          P[3] = p34.x;
+          P[4] = p34.y;
+          P[5] = __fmaf_rn(pref, cross1(b10, b11, X0, X1), P[5]);
+        };
         // ---- bracket: offset l1 of the older node, its slot pA, record A, separation dA and table -------
         int l1;
         int br;
@@ -430,6 +505,21 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           // the uniform-motion delay (with the learned proposal scaled by the network's factor for the
           // block's target group and this source, staged in s_q2)
           const int lraw = WIN ? g_cur : guess_of(jj);
+          // predicted out of history: the oldest-slot bound (kChordMargin) from the present separation and
+          // the staged chord; where it holds, slot k0's node test is true without its record
+          if (lraw < 0 && !r.exact_only) {
+            const float4 ck = s_ck[jj];
+            const float3 dn = separation(r, s_q0[jj], s_q1[jj]);
+            const float dd = dn.x * dn.x + dn.y * dn.y + dn.z * dn.z;
+            const float dc = dn.x * ck.x + dn.y * ck.y + dn.z * ck.z;
+            if (fmaf(2.f, dc, dd * kChordLo) > ck.w) {
+              n_tests += 1;
+              brc += 1u;
+              if (DUMP) a.dump[(size_t)i * N + j] = 0;
+              heaviside(make_float2(dn.x, dn.y), dn.z, s_k0[jj], s_x[jj].w, win.phys(0));
+              continue;
+            }
+          }
           const int lg = max(lraw, 0);
           pA = win.phys(lg);
           // records of the guessed bracket: from the staged window when both lie in it
@@ -551,67 +641,9 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         if (DUMP) a.dump[(size_t)i * N + j] = 4 * l1 + br;
 
         if (br == 0) {
-          // ---- out of history (eq:linear2): the source moves uniformly with beta1 along the line through
-          // w1; its Lienard-Wiechert field is Heaviside's field about the line's point at t_n,
-          //   E = kq (1 - beta^2) X / [X^2 (1 - beta^2) + (X.beta)^2]^{3/2},  c B = beta x E,
-          // with X = (r - w_n) - (line at t_n - w_n) from the staged present record and line offset.
-          const float4 g0 = s_q0[jj], g1 = s_q1[jj], gx = s_x[jj];
-          const float2 X01 = sub2(__fadd2_rn(sub2(r.h01, g0), sub2(r.l01, g1)), gx);
-          float X0 = X01.x, X1 = X01.y;
-          float X2 = __fsub_rn(__fadd_rn(__fsub_rn(r.h2, g0.z), __fsub_rn(r.l2, g1.z)), gx.z);
-          const float2 b101 = __fadd2_rn(bref01, make_float2(A.q2.x, A.q2.y));
-          const float b10 = b101.x, b11 = b101.y, b12 = __fadd_rn(bref2, A.q2.z);
-          const float ig2 = A.q0.w;
-          float Xb = dot3(X0, X1, X2, b10, b11, b12);
-          float XX = dot3(X0, X1, X2, X0, X1, X2);
-          // The FP32 rounding of X.beta (absolute about u |X|) moves the denominator by 2 u |X| |X.beta| /
-          // denominator relative, at most u gamma. Above 1.3e-6 (only for gamma above ~20, at directions
-          // near perpendicular to beta) X and X.beta are formed in FP64 from the FP64 records instead.
-          // (as the shift is at most u gamma, sources with gamma^2 < 100 never need it)
-          if (ig2 < 0.01f && __fmul_rn(kXbGuard, __fmul_rn(sqrtf(XX), fabsf(Xb))) > __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb))) {
-            const double* w0 = src64 + 6 * pA;  // FP64 record of slot k0: X = r - w_k0 - v_k0 (t_n - t_k0)
-            const double ct = kC * (a.state->t - __ldg(a.slot_t + pA));  // c (t_n - t_k0)
-            const double ic = 1.0 / kC;
-            const double* rr = a.rec64 + ((size_t)i * D + pn) * 6;
-            const double y0 = (__ldg(rr + 0) - __ldg(w0 + 0)) - __ldg(w0 + 3) * ic * ct;
-            const double y1 = (__ldg(rr + 1) - __ldg(w0 + 1)) - __ldg(w0 + 4) * ic * ct;
-            const double y2 = (__ldg(rr + 2) - __ldg(w0 + 2)) - __ldg(w0 + 5) * ic * ct;
-            X0 = (float)y0;
-            X1 = (float)y1;
-            X2 = (float)y2;
-            Xb = (float)((y0 * __ldg(w0 + 3) + y1 * __ldg(w0 + 4) + y2 * __ldg(w0 + 5)) * ic);
-            XX = dot3(X0, X1, X2, X0, X1, X2);
-            n_fb++;
-          }
-          const float Dh = __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb));
-          const float iD = rsqrtf(Dh);
-          if (!(Dh > 0.f) || !(ig2 > 0.f)) {
-            errbits |= (ig2 > 0.f) ? kErrCoincide : kErrDisc;
-            continue;
-          }
-          const float pref = __fmul_rn(__fmul_rn(s_kq[jj], ig2), __fmul_rn(__fmul_rn(iD, iD), iD));
-          if (ADAPT) {
-            // retarded distance c (t - t_r) = gamma^2 [X.beta + sqrt(Dh)], and v(t_r) = v1
-            const float sD = __fmul_rn(Dh, iD);
-            const float R = (Xb >= 0.f) ? __fmul_rn(__fadd_rn(Xb, sD), A.q2.w)
-                                        : __fdividef(dot3(X0, X1, X2, X0, X1, X2), __fsub_rn(sD, Xb));
-            if (R >= a.eta_allow) {
-              emin = fminf(emin, R);
-              const float dv0 = bi0 - A.q2.x, dv1 = bi1 - A.q2.y, dv2 = bi2 - A.q2.z;
-              vmax2 = fmaxf(vmax2, dv0 * dv0 + dv1 * dv1 + dv2 * dv2);
-            }
-          }
-          const float2 p01 = __ffma2_rn(make_float2(pref, pref), make_float2(X0, X1), make_float2(P[0], P[1]));
-          P[0] = p01.x;
-          P[1] = p01.y;
-          P[2] = __fmaf_rn(pref, X2, P[2]);
-          // c B = beta x E = pref (beta x X)
-          const float2 p34 = __ffma2_rn(make_float2(pref, pref),
-                                        make_float2(cross1(b11, b12, X1, X2), cross1(b12, b10, X2, X0)),
-                                        make_float2(P[3], P[4]));
-          P[3] = p34.x;
-          P[4] = p34.y;
-          P[5] = __fmaf_rn(pref, cross1(b10, b11, X0, X1), P[5]);
+          const float4 g0 = s_q0[jj], g1 = s_q1[jj];
+          heaviside(__fadd2_rn(sub2(r.h01, g0), sub2(r.l01, g1)), __fadd_rn(__fsub_rn(r.h2, g0.z), __fsub_rn(r.l2, g1.z)),
+                    make_float4(A.q2.x, A.q2.y, A.q2.z, A.q0.w), A.q2.w, pA);
           continue;
         }
         // ---- retarded state (light units) --------------------------------------------------------
@@ -632,7 +664,8 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           // of the segment (ext32) and tau = c (t_n - t_r) = R, the positive root of
           // (1 - beta1^2) tau^2 - 2 (p.beta1) tau - |p|^2 = 0, p = r - P (eq:dt about t_n). Formed this
           // way, eta keeps FP32 precision when R is far below c (t_n - t_{n-1}).
-          const float3 dp = separation(r, __ldg(a.ext32 + 3 * j), __ldg(a.ext32 + 3 * j + 1));
+          const float4* e = a.ext32 + (size_t)j * kExtCount;
+          const float3 dp = separation(r, __ldg(e + kExtSegHi), __ldg(e + kExtSegLo));
           const float pb = dot3(dp.x, dp.y, dp.z, b10, b11, b12);
           const float pp = dot3(dp.x, dp.y, dp.z, dp.x, dp.y, dp.z);
           qd = __fmaf_rn(pb, pb, __fmul_rn(ig2, pp));

@@ -89,6 +89,11 @@ __global__ void set_state_kernel(DeviceState s, long long n, double t, double dt
 // light-travel distance (c (t_n - t_k))^2 in exactly the operation order of the reference evaluation
 // (so that the FP64 node test decides identically), its guard-band thresholds in FP32, c (t_n - t_k) in
 // FP32, and 1 / (t_{k+1} - t_k).
+constexpr double kGuardHi = (1.0 + kGuardBand) / (1.0 - kGuardBand), kGuardLo = (1.0 - kGuardBand) / (1.0 + kGuardBand);
+
+// FP32 upper threshold of a slot's (c (t_n - t_k))^2 (the node test is true above it)
+__device__ __forceinline__ float upper_threshold(double lhs) { return __double2float_ru(lhs * kGuardHi); }
+
 __device__ __forceinline__ void slot_table(const DeviceState& s, int l, int p0, int nwin, double t_n) {
   int p = p0 + l;
   if (p >= s.D) p -= s.D;
@@ -105,8 +110,7 @@ __device__ __forceinline__ void slot_table(const DeviceState& s, int l, int p0, 
   } else {
     s.tab.inv_dtk[p] = 0.0;
   }
-  const double qhi = (1.0 + kGuardBand) / (1.0 - kGuardBand), qlo = (1.0 - kGuardBand) / (1.0 + kGuardBand);
-  s.tab.tab32[p] = make_float4(__double2float_ru(lhs * qhi), __double2float_rd(lhs * qlo), (float)ct, icdt);
+  s.tab.tab32[p] = make_float4(upper_threshold(lhs), __double2float_rd(lhs * kGuardLo), (float)ct, icdt);
 }
 
 // Per-step slot tables over the usable window k0..n alone (used before the delay sampler).
@@ -137,6 +141,10 @@ __global__ void prep_kernel(DeviceState s) {
 //     out-of-history case) is at t_n, relative to the source's present position. Along that line the
 //     source moves uniformly, so its field is Heaviside's field about the point w_{j,n} + X_j; the
 //     separation from a target is then (r - w_{j,n}) - X_j, formed without cancellation.
+//   c_j = w_{j,n} - w_{j,k0} and T (1 + 32u) - |c_j|^2 (1 - 32u), rounded up, with T the FP32 upper
+//     threshold of slot k0: the oldest-slot bound (kChordMargin), by which an out-of-history pair's
+//     node test of slot k0 needs no record of that slot; and the FP32 record's beta - beta_ref,
+//     1/gamma^2 and gamma^2 of slot k0, which Heaviside's field of that pair reads.
 __global__ void setup_kernel(DeviceState s, int extrap) {
   const long long n = s.state->n;
   const double t_n = s.state->t;
@@ -157,9 +165,20 @@ __global__ void setup_kernel(DeviceState s, int extrap) {
   const long long j = gid;
   const double* rn = s.rec64 + ((size_t)j * s.D + pn) * 6;
   const double* r0 = s.rec64 + ((size_t)j * s.D + p0) * 6;
+  const float* q0 = s.rec32 + ((size_t)j * s.D + p0) * 12;  // FP32 record of slot k0
+  float4* ext = s.ext32 + (size_t)j * kExtCount;
   const double dt0 = s.slot_t[pn] - s.slot_t[p0];
-  s.ext32[3 * j + 2] = make_float4((float)((r0[0] + r0[3] * dt0) - rn[0]), (float)((r0[1] + r0[4] * dt0) - rn[1]),
-                                   (float)((r0[2] + r0[5] * dt0) - rn[2]), 0.f);
+  ext[kExtLine] = make_float4((float)((r0[0] + r0[3] * dt0) - rn[0]), (float)((r0[1] + r0[4] * dt0) - rn[1]),
+                              (float)((r0[2] + r0[5] * dt0) - rn[2]), q0[11]);
+  ext[kExtOldest] = make_float4(q0[8], q0[9], q0[10], q0[3]);
+  {
+    const double c0 = rn[0] - r0[0], c1 = rn[1] - r0[1], c2 = rn[2] - r0[2];
+    const double ct = __dmul_rn(kC, __dsub_rn(t_n, s.slot_t[p0]));
+    const double cc = c0 * c0 + c1 * c1 + c2 * c2;
+    const double rhs = (double)upper_threshold(__dmul_rn(ct, ct)) * (1.0 + kChordMargin) - cc * (1.0 - kChordMargin);
+    const float inf = __int_as_float(0x7f800000);
+    ext[kExtChord] = make_float4((float)c0, (float)c1, (float)c2, n > k0 ? __double2float_ru(rhs) : inf);
+  }
   if (n <= k0) return;  // no segment [n-1, n] in the window
   const int p1 = pn == 0 ? s.D - 1 : pn - 1;
   const double dtl = s.slot_t[pn] - s.slot_t[p1];
@@ -169,8 +188,8 @@ __global__ void setup_kernel(DeviceState s, int extrap) {
   const double d1 = (r[1] + r[4] * dtl) - bd.origin[1];
   const double d2 = (r[2] + r[5] * dtl) - bd.origin[2];
   const float h0 = (float)d0, h1 = (float)d1, h2 = (float)d2;
-  s.ext32[3 * j] = make_float4(h0, h1, h2, 0.f);
-  s.ext32[3 * j + 1] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.f);
+  ext[kExtSegHi] = make_float4(h0, h1, h2, 0.f);
+  ext[kExtSegLo] = make_float4((float)(d0 - (double)h0), (float)(d1 - (double)h1), (float)(d2 - (double)h2), 0.f);
 }
 
 __global__ void reset_scale_kernel(DeviceState s) {

@@ -67,11 +67,13 @@ def record(name, values):
         f.write(json.dumps({"test": name, **values}) + "\n")
 
 
-def light_sphere_case(nb=64, n=40, seed=70):
+def light_sphere_case(nb=64, n=40, seed=70, oldest=False):
     """nb two-particle bunches (history n + 1 slots, step DT): in each, a resting target sits on the light
     sphere of one stored slot k of its source, c (t_n - t_k) from w_k to within 0 to 1e-12 relative, and
     the source moves with constant acceleration. Every node test at that slot falls inside the mixed path's
-    FP32 guard band. Returns (T, W, V, u)."""
+    FP32 guard band. With oldest, k is the oldest slot and the target lies ahead of the source along its
+    motion, so that the uniform-motion guess falls at the edge of the history and the mixed path's
+    oldest-slot bound is tried on pairs it must not decide. Returns (T, W, V, u)."""
     rng = np.random.default_rng(seed)
     C = inputs.C_LIGHT
     T = np.array([k * DT for k in range(n + 1)])
@@ -84,8 +86,10 @@ def light_sphere_case(nb=64, n=40, seed=70):
         v0 = beta * C * vdir / np.linalg.norm(vdir)
         acc = rng.normal(size=3) * 1e18
         w00 = rng.normal(size=3) * 1e-6
-        k = int(rng.integers(1, n - 1))
+        k = 0 if oldest else int(rng.integers(1, n - 1))
         nhat = rng.normal(size=3)
+        if oldest:
+            nhat = 0.3 * nhat + vdir / np.linalg.norm(vdir)
         nhat /= np.linalg.norm(nhat)
         wk = w00 + v0 * T[k] + 0.5 * acc * T[k] ** 2
         r = wk + C * (T[n] - T[k]) * (1.0 + eps[b % len(eps)]) * nhat

@@ -7,7 +7,8 @@ that table exactly -- zero mismatches -- which aggregate branch counts alone can
 flips, or a flip to an adjacent slot, leave every count unchanged). Cases: several target tiles with
 ragged tails, a ring window that has wrapped, a single-slot history, a learned proposal with an untrained
 network (starting slots all over the history), targets on the light sphere of a stored slot (every such
-test decided inside the FP32 guard band), and a bunch whose far cluster the FP32 split cannot hold.
+test decided inside the FP32 guard band; also of the oldest slot, ahead of the source, where the mixed
+path's oldest-slot bound is tried), and a bunch whose far cluster the FP32 split cannot hold.
 """
 import numpy as np
 import pytest
@@ -61,11 +62,12 @@ def test_bracket_dump_equals_oracle(N, n, D, sigma, seed, precision, proposal):
         assert set(np.unique(ref[ref >= 0] % 4)) >= {0, 2}
 
 
+@pytest.mark.parametrize("oldest", [False, True])
 @pytest.mark.parametrize("proposal", PROPOSALS)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_bracket_dump_at_the_light_sphere(precision, proposal):
+def test_bracket_dump_at_the_light_sphere(precision, proposal, oldest):
     n, D, nb = 40, 64, 64
-    T, W, V, u = light_sphere_case(nb, n)
+    T, W, V, u = light_sphere_case(nb, n, oldest=oldest)
     got, _ = _dump(T, W, V, u, n, D, precision, proposal, bunches=[2] * nb)
     ref = np.full((2 * nb, 2 * nb), -1, dtype=np.int32)
     for b in range(nb):

@@ -92,16 +92,18 @@ def test_mixed_path_far_from_the_split_origin():
     assert st["guard_fallbacks"] > 0  # the far cluster's tests ran in FP64
 
 
+@pytest.mark.parametrize("oldest", [False, True])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("proposal", ["bisect", "closed_form"])
-def test_node_tests_at_the_light_sphere(precision, proposal):
+def test_node_tests_at_the_light_sphere(precision, proposal, oldest):
     """Targets placed on the light sphere of one stored slot of their source, to within 1e-16 to 1e-12 of
     its radius (64 two-particle bunches in one batch): every such node test falls inside the FP32 guard
     band, the FP64 test decides it, and the brackets must be the oracle's (branch counts equal) with
-    fields within each path's bar."""
+    fields within each path's bar. With oldest the slot is the oldest one and the target lies ahead of
+    the source: the mixed path's oldest-slot bound must leave those tests to the guard band."""
     C = oracle.constants()["c"]
     n, D, nb = 40, 64, 64
-    T, W, V, u = light_sphere_case(nb, n)
+    T, W, V, u = light_sphere_case(nb, n, oldest=oldest)
     with emppp.Solver(0, D, DT, precision=precision, proposal=proposal, bunches=[2] * nb) as s:
         s.set_history(n, T, W, V, u)
         s.step(1)
