@@ -111,6 +111,18 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ src32, int p)
   return r;
 }
 
+// FP64 node tests (those between the guard-band thresholds) of the block, for the instances that count
+// in shared memory (SH); the others count per thread in n_fb
+__shared__ unsigned long long s_fallbacks;
+
+template <bool SH>
+__device__ __forceinline__ void count_fallback(unsigned& n_fb) {
+  if (SH)
+    atomicAdd(&s_fallbacks, 1ull);
+  else
+    n_fb++;
+}
+
 __device__ __forceinline__ bool exact_test(const double* __restrict__ rr, const double* __restrict__ w, double lhs) {
   const double d0 = __dsub_rn(__ldg(rr + 0), __ldg(w + 0));
   const double d1 = __dsub_rn(__ldg(rr + 1), __ldg(w + 1));
@@ -137,6 +149,7 @@ __device__ __forceinline__ float3 separation(const Target& r, float4 q0, float4 
 }
 
 // P(k) from a separation d already formed at physical slot p, with that slot's table entry tab
+template <bool SH>
 __device__ __forceinline__ bool node_test_d(const Target& r, float3 d, float4 tab, const double* __restrict__ src64,
                                             int p, const MixedArgs& a, unsigned& n_fb) {
   const float D2 = d.x * d.x + d.y * d.y + d.z * d.z;
@@ -144,15 +157,15 @@ __device__ __forceinline__ bool node_test_d(const Target& r, float3 d, float4 ta
     if (D2 > tab.x) return true;
     if (D2 < tab.y) return false;
   }
-  n_fb++;
+  count_fallback<SH>(n_fb);
   return exact_test(a.rec64 + ((size_t)r.idx * a.D + a.state->pn) * 6, src64 + 6 * p, __ldg(a.lhs64 + p));
 }
 
+template <bool SH>
 __device__ __forceinline__ bool node_test(const Target& r, const float4* __restrict__ src32,
-                                          const double* __restrict__ src64, int p, const MixedArgs& a,
-                                          unsigned& n_fb) {
-  return node_test_d(r, separation(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1)), __ldg(a.tab32 + p), src64, p,
-                     a, n_fb);
+                                          const double* __restrict__ src64, int p, const MixedArgs& a, unsigned& n_fb) {
+  return node_test_d<SH>(r, separation(r, __ldg(src32 + 3 * p), __ldg(src32 + 3 * p + 1)), __ldg(a.tab32 + p), src64,
+                         p, a, n_fb);
 }
 
 // uniform-motion guess of the retarded delay, from the staged present record of the source:
@@ -175,13 +188,14 @@ __device__ __forceinline__ int guessed_offset(float sc, int nw, float nw1) {
 }
 
 // bisection between offsets lo (P false) and hi (P true); returns lo
+template <bool SH>
 __device__ __forceinline__ int bisect(const Target& r, const float4* __restrict__ src32, const double* __restrict__ src64,
                                       const Window& w, int lo, int hi, const MixedArgs& a, unsigned& n_tests,
                                       unsigned& n_fb) {
   while (hi - lo > 1) {
     const int m = (lo + hi) >> 1;
     n_tests += 1;
-    if (node_test(r, src32, src64, w.phys(m), a, n_fb))
+    if (node_test<SH>(r, src32, src64, w.phys(m), a, n_fb))
       hi = m;
     else
       lo = m;
@@ -240,9 +254,27 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
   const float inv_cdt = (float)(1.0 / (kC * a.state->dt));
   const float nw1 = (float)(win.nw - 1);  // a guessed delay of at least nw - 1 steps is out of history
 
-  unsigned n_ooh = 0, n_sc = 0, n_bi = 0, n_tests = 0, n_fb = 0;
-  float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
+  // Counts and error bits. Node tests are counted per thread. The branch counts (added once per tile), the
+  // FP64 fallbacks and the error bits (both rare) are kept in shared memory by the guessed-search
+  // instances without the adaptive step (kShared), which frees their registers for the pair loop; the
+  // bisection and adaptive instances keep them per thread, where the register allocation comes out better.
+  constexpr bool kShared = PROP != kPropBisect && !ADAPT;
+  __shared__ unsigned long long s_cnt[3];  // out of history, shortcut, bisection
+  __shared__ int s_err;
+  if (threadIdx.x == 0) {
+    s_cnt[0] = s_cnt[1] = s_cnt[2] = 0;
+    s_fallbacks = 0;
+    s_err = 0;
+  }
+  unsigned n_tests = 0, n_ooh = 0, n_sc = 0, n_bi = 0, n_fb = 0;
   int errbits = 0;
+  auto set_err = [&](int bits) {
+    if (kShared)
+      atomicOr(&s_err, bits);
+    else
+      errbits |= bits;
+  };
+  float emin = __int_as_float(0x7f800000), vmax2 = 0.f;  // adaptive time step (Sec. 2.4), vmax2 in units of c^2
   // history windows: phase parity and pending copy of each of the warp's two buffers (warp-uniform), and
   // whether the warp still stages (a wait that gave up stops it; the pairs then gather from the ring)
   unsigned wph = 0, wpend = 0;
@@ -390,7 +422,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
               w_n = wd.y;
             } else {
               // the copy stays pending (drained before the block exits); no further windows
-              errbits |= kErrTimeout;
+              set_err(kErrTimeout);
               wok = false;
             }
           }
@@ -430,12 +462,12 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             X2 = (float)y2;
             Xb = (float)((y0 * __ldg(w0 + 3) + y1 * __ldg(w0 + 4) + y2 * __ldg(w0 + 5)) * ic);
             XX = dot3(X0, X1, X2, X0, X1, X2);
-            n_fb++;
+            count_fallback<kShared>(n_fb);
           }
           const float Dh = __fmaf_rn(XX, ig2, __fmul_rn(Xb, Xb));
           const float iD = rsqrtf(Dh);
           if (!(Dh > 0.f) || !(ig2 > 0.f)) {
-            errbits |= (ig2 > 0.f) ? kErrCoincide : kErrDisc;
+            set_err((ig2 > 0.f) ? kErrCoincide : kErrDisc);
             return;
           }
           const float pref = __fmul_rn(__fmul_rn(s_kq[jj], ig2), __fmul_rn(__fmul_rn(iD, iD), iD));
@@ -487,16 +519,16 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           A = load_rec(src32, pA);
           dA = separation(r, A.q0, A.q1);
           tabA = __ldg(a.tab32 + pA);
-          if (node_test_d(r, dA, tabA, src64, pA, a, n_fb)) {
+          if (node_test_d<kShared>(r, dA, tabA, src64, pA, a, n_fb)) {
             l1 = 0;
             br = 0;
           } else {
             n_tests += 1;
-            if (!node_test(r, src32, src64, win.phys(win.nw - 2), a, n_fb)) {
+            if (!node_test<kShared>(r, src32, src64, win.phys(win.nw - 2), a, n_fb)) {
               l1 = win.nw - 2;
               br = 1;
             } else {
-              l1 = bisect(r, src32, src64, win, 0, win.nw - 1, a, n_tests, n_fb);
+              l1 = bisect<kShared>(r, src32, src64, win, 0, win.nw - 1, a, n_tests, n_fb);
               br = 2;
             }
             fast = (l1 == 0);
@@ -538,7 +570,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
           if (lraw < 0) {
             // predicted out of history: the only record needed is the oldest slot's
             n_tests += 1;
-            if (node_test_d(r, dA, tabA, src64, pA, a, n_fb)) {
+            if (node_test_d<kShared>(r, dA, tabA, src64, pA, a, n_fb)) {
               l1 = 0;
               br = 0;
             } else {
@@ -551,11 +583,11 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
                   break;
                 }
                 n_tests += 1;
-                if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
+                if (node_test<kShared>(r, src32, src64, win.phys(hi), a, n_fb)) break;
                 lo = hi;
                 st <<= 1;
               }
-              l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
+              l1 = bisect<kShared>(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
               br = (l1 == win.nw - 2) ? 1 : 2;
               fast = (l1 == 0);
             }
@@ -572,12 +604,12 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
               Bn = load_rec(src32, pg1);
             }
             n_tests += 1;
-            const bool tA = node_test_d(r, dA, tabA, src64, pA, a, n_fb);
+            const bool tA = node_test_d<kShared>(r, dA, tabA, src64, pA, a, n_fb);
             if (!tA) {
               bool tB = true;  // P(n) is always true
               if (lg + 1 < win.nw - 1) {
                 n_tests += 1;
-                tB = node_test_d(r, separation(r, Bn.q0, Bn.q1), __ldg(a.tab32 + pg1), src64, pg1, a, n_fb);
+                tB = node_test_d<kShared>(r, separation(r, Bn.q0, Bn.q1), __ldg(a.tab32 + pg1), src64, pg1, a, n_fb);
               }
               if (tB) {
                 l1 = lg;
@@ -594,11 +626,11 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
                     break;
                   }
                   n_tests += 1;
-                  if (node_test(r, src32, src64, win.phys(hi), a, n_fb)) break;
+                  if (node_test<kShared>(r, src32, src64, win.phys(hi), a, n_fb)) break;
                   lo = hi;
                   st <<= 1;
                 }
-                l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
+                l1 = bisect<kShared>(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
                 br = (l1 == win.nw - 2) ? 1 : 2;
                 fast = false;
               }
@@ -616,7 +648,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
                 }
                 lo = max(hi - st, 0);
                 n_tests += 1;
-                if (!node_test(r, src32, src64, win.phys(lo), a, n_fb)) break;
+                if (!node_test<kShared>(r, src32, src64, win.phys(lo), a, n_fb)) break;
                 hi = lo;
                 st <<= 1;
               }
@@ -624,7 +656,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
                 l1 = 0;
                 br = 0;
               } else {
-                l1 = bisect(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
+                l1 = bisect<kShared>(r, src32, src64, win, lo, hi, a, n_tests, n_fb);
                 br = (l1 == win.nw - 2) ? 1 : 2;
               }
               fast = false;
@@ -698,7 +730,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
             qd = __fmaf_rn(hb, hb, -__fmul_rn(ig2, C0));
             sq = __fmul_rn(qd, rsqrtf(fmaxf(qd, 1e-37f)));
             s = (hb <= 0.f) ? __fdividef(C0, __fsub_rn(sq, hb)) : __fmul_rn(-__fadd_rn(hb, sq), g2);
-            n_fb++;
+            count_fallback<kShared>(n_fb);
           }
           const float2 e01 = __ffma2_rn(make_float2(-b10, -b11), make_float2(s, s), make_float2(d0, d1));
           e0 = e01.x;
@@ -747,7 +779,7 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         const float ieu = __fdividef(fw ? __fadd_rn(R, eb) : 1.f, fw ? rat : __fsub_rn(R, eb));
         const bool root_ok = (qd >= 0.f) && (ig2 > 0.f);
         if (!(root_ok && R2 > 0.f && ieu > 0.f && ieu < 3.0e38f)) {
-          errbits |= root_ok ? kErrCoincide : kErrDisc;
+          set_err(root_ok ? kErrCoincide : kErrDisc);
           continue;
         }
         const float pref = __fmul_rn(__fmul_rn(__fmul_rn(s_kq[jj], __fmul_rn(R, ieu)), ieu), ieu);
@@ -797,9 +829,20 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
         s_acc[6 + c][threadIdx.x] = tb;
       }
     }
-    n_ooh += brc & 1023u;
-    n_sc += (brc >> 10) & 1023u;
-    n_bi += brc >> 20;
+    if (!kShared) {
+      n_ooh += brc & 1023u;
+      n_sc += (brc >> 10) & 1023u;
+      n_bi += brc >> 20;
+    } else {
+      const unsigned c0 = __reduce_add_sync(0xffffffffu, brc & 1023u);
+      const unsigned c1 = __reduce_add_sync(0xffffffffu, (brc >> 10) & 1023u);
+      const unsigned c2 = __reduce_add_sync(0xffffffffu, brc >> 20);
+      if ((threadIdx.x & 31) == 0) {
+        if (c0) atomicAdd(&s_cnt[0], (unsigned long long)c0);
+        if (c1) atomicAdd(&s_cnt[1], (unsigned long long)c1);
+        if (c2) atomicAdd(&s_cnt[2], (unsigned long long)c2);
+      }
+    }
   }
   if (active) {
     double Et[3], Bt[3];
@@ -833,19 +876,29 @@ __global__ void __launch_bounds__(shape_block(SHAPE), EMPPP_MIXED_MIN_BLOCKS * 1
       if (wpend & (1u << sb))
         mbar_wait_bounded(smem_u32(&s_bar[(threadIdx.x >> 5) * 2 + sb]), (wph >> sb) & 1u, kDrainLimit);
   }
-  n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
-  n_sc = __reduce_add_sync(0xffffffffu, n_sc);
-  n_bi = __reduce_add_sync(0xffffffffu, n_bi);
   n_tests = __reduce_add_sync(0xffffffffu, n_tests);
-  n_fb = __reduce_add_sync(0xffffffffu, n_fb);
-  errbits = __reduce_or_sync(0xffffffffu, errbits);
-  if ((threadIdx.x & 31) == 0) {
-    if (n_ooh) atomicAdd(a.stats + kStatOOH, (unsigned long long)n_ooh);
-    if (n_sc) atomicAdd(a.stats + kStatShortcut, (unsigned long long)n_sc);
-    if (n_bi) atomicAdd(a.stats + kStatBisect, (unsigned long long)n_bi);
-    if (n_tests) atomicAdd(a.stats + kStatNodeTests, (unsigned long long)n_tests);
-    if (n_fb) atomicAdd(a.stats + kStatGuard, (unsigned long long)n_fb);
-    if (errbits) atomicOr(a.err, errbits);
+  if ((threadIdx.x & 31) == 0 && n_tests) atomicAdd(a.stats + kStatNodeTests, (unsigned long long)n_tests);
+  if (!kShared) {
+    n_ooh = __reduce_add_sync(0xffffffffu, n_ooh);
+    n_sc = __reduce_add_sync(0xffffffffu, n_sc);
+    n_bi = __reduce_add_sync(0xffffffffu, n_bi);
+    n_fb = __reduce_add_sync(0xffffffffu, n_fb);
+    errbits = __reduce_or_sync(0xffffffffu, errbits);
+    if ((threadIdx.x & 31) == 0) {
+      if (n_ooh) atomicAdd(&s_cnt[0], (unsigned long long)n_ooh);
+      if (n_sc) atomicAdd(&s_cnt[1], (unsigned long long)n_sc);
+      if (n_bi) atomicAdd(&s_cnt[2], (unsigned long long)n_bi);
+      if (n_fb) atomicAdd(&s_fallbacks, (unsigned long long)n_fb);
+      if (errbits) atomicOr(&s_err, errbits);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd(a.stats + kStatOOH, s_cnt[0]);
+    if (s_cnt[1]) atomicAdd(a.stats + kStatShortcut, s_cnt[1]);
+    if (s_cnt[2]) atomicAdd(a.stats + kStatBisect, s_cnt[2]);
+    if (s_fallbacks) atomicAdd(a.stats + kStatGuard, s_fallbacks);
+    if (s_err) atomicOr(a.err, s_err);
   }
 }
 
