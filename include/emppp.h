@@ -128,7 +128,7 @@ typedef struct {
  * tile) per resident block of 128 threads, which sets the sources per chunk; target_order 1 sorts the
  * targets spatially each step (both paths; the fields do not depend on it; a step of a system of at most
  * 2048 particles on the mixed path skips it). The tile shape: targets_per_block targets per work item and
- * thread block (64, 128 or 256; on the mixed path also the sources a block stages per tile) and, on the
+ * thread block (64, 128 or 256; a mixed-path block stages half that many sources per tile) and, on the
  * mixed path, sources_per_sum sources per FP32 partial sum before the compensated addition (8, 16 or 32;
  * 16 and 32 only at 128 targets per block). The FP64 path ignores sources_per_sum. The shape changes the order
  * of each target's sum, so fields of different shapes agree within rounding, not bit for bit; the

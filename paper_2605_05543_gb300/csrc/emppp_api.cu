@@ -200,7 +200,7 @@ emppp_status update_schedule(emppp_handle c) {
   // bracket dump run the default shape, and the FP64 path runs shape 3 as the default
   int shp = (ad || var64 != 0 || c->dumping) ? 0 : c->shape;
   if (!mixed && shp >= 3) shp = 0;
-  const long long TB = shape_block(shp);  // targets per work item (and sources per staged tile)
+  const long long TB = shape_block(shp);  // targets per work item (mixed path: twice the sources per staged tile)
   const long long key = (mixed ? 1 : 0) | ((long long)(c->opt.proposal & 3) << 1) |
                         ((long long)c->items_per_block << 3) | ((long long)c->opt.source_split << 13) |
                         ((long long)ad << 40) | ((long long)var64 << 41) | ((long long)shp << 44);

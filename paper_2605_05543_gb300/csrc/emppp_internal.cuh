@@ -236,7 +236,7 @@ struct BextParams {
   double center[3];
 };
 
-// Tile shapes of the pair kernels (emppp_tuning): targets per block, which is also the number of sources
+// Tile shapes of the pair kernels (emppp_tuning): targets per block, which is twice the number of sources
 // a mixed-path block stages per tile, the mixed path's sources per FP32 partial sum, and the slots of the
 // history window each warp of a mixed-path block stages per source by bulk copy (0: none). Shape 0 is the
 // default; the FP64 path runs shapes 3 to 5 as shape 0 (its sums are blocked by 64 sources).
