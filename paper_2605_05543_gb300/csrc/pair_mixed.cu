@@ -9,6 +9,9 @@
 //             the FP64 one. Search: the paper's bisection, or the guarded galloping
 //             search from the uniform-motion guess; with the guess, the records of the one or two slots
 //             the guess points at are loaded together, so a correct guess needs a single gather round.
+//             A pair the guess places beyond the history first tries the oldest-slot bound (kChordMargin,
+//             emppp_internal.cuh): from the staged present separation and the source's chord, it shows the
+//             oldest slot's FP32 test true at its first comparison without loading that slot's record.
 //   retarded  in light units (lengths in m, velocities as beta = v/c): with L1 = c (t - t1) and d = r - w1,
 //             (1 - beta1^2) s^2 + 2 (d.beta1 - L1) s + (L1^2 - |d|^2) = 0 for s = c (t_r - t1) (eq:dt),
 //             smaller root without cancellation; eta = d - beta1 s (eq:linear, retarded position w1 + v1 dt);
@@ -27,8 +30,8 @@
 //             the pair loop: 64 registers, 8 blocks of 128 threads per SM), converted to FP64 at the end.
 // Vector arithmetic takes x and y in one packed FP32x2 instruction where both operands come as pairs
 // (separations, velocity differences, the retarded point, u', F, the sums) and z as a scalar.
-// Sources are walked in tiles of kTile whose present records and FP32 charges are staged in shared
-// memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
+// Sources are walked in tiles of kTile (half a block's targets) whose present records, out-of-history
+// lines, oldest-slot chords and FP32 charges are staged in shared memory; targets are taken in the spatial order of order.cu so that a warp's retarded slots of a
 // source are close together in the source-major FP32 shadow ring. The window instance (shape_win)
 // also copies, per warp and one source ahead, the ring slots its lanes' guessed brackets fall in to
 // shared memory by bulk copy (bulk.cuh) and reads the predicted brackets' records there; the search,
